@@ -1,0 +1,355 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` function raises AssertionError on a violation. They are collected by
+``test_oracle_pins.py`` and re-run against deliberately broken copies of the oracle by
+``test_oracle_mutants.py``, to show that a plausible mistake anywhere in the oracle fails
+at least one of them. None of them re-types the oracle's formulas: they use closed forms,
+an independent great-circle formula, exact integer arithmetic, CPython's correctly rounded
+float parser, numpy library routines and brute force on tiny inputs.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+
+R = 6371000.0
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(a), abs(b), 1e-300)
+
+
+def vincenty_sphere_m(lat1, lon1, lat2, lon2, radius=R):
+    """Great-circle distance by the atan2 (Vincenty, sphere) formula: independent of the
+    haversine form and well conditioned for every separation."""
+    p1, p2 = np.radians(lat1), np.radians(lat2)
+    dl = np.radians(lon2 - lon1)
+    num = np.hypot(np.cos(p2) * np.sin(dl),
+                   np.cos(p1) * np.sin(p2) - np.sin(p1) * np.cos(p2) * np.cos(dl))
+    den = np.sin(p1) * np.sin(p2) + np.cos(p1) * np.cos(p2) * np.cos(dl)
+    return radius * np.arctan2(num, den)
+
+
+# ---------------------------------------------------------------- haversine
+def pin_haversine_closed_forms(o):
+    rng = np.random.default_rng(11)
+    # along a meridian: d = R |dphi|
+    for _ in range(200):
+        a, b = rng.uniform(-89.0, 89.0, 2)
+        lon = rng.uniform(-180, 180)
+        want = R * abs(math.radians(b) - math.radians(a))
+        got = o.haversine_m(a, lon, b, lon, R)
+        assert _rel(got, want) < 1e-11 or abs(got - want) < 1e-6, (a, b, got, want)
+    # along the equator: d = R |dlambda| for |dlambda| <= 180 deg
+    for _ in range(200):
+        a, b = rng.uniform(-90.0, 90.0, 2)
+        want = R * abs(math.radians(b) - math.radians(a))
+        got = o.haversine_m(0.0, a, 0.0, b, R)
+        assert _rel(got, want) < 1e-11 or abs(got - want) < 1e-6, (a, b, got, want)
+    # identity, symmetry, antipodes, one degree of latitude
+    for _ in range(100):
+        la, lo, lb, lob = rng.uniform(-80, 80), rng.uniform(-170, 170), rng.uniform(-80, 80), rng.uniform(-170, 170)
+        assert o.haversine_m(la, lo, la, lo, R) == 0.0
+        assert _rel(o.haversine_m(la, lo, lb, lob, R), o.haversine_m(lb, lob, la, lo, R)) < 1e-15
+    assert _rel(o.haversine_m(0.0, 0.0, 0.0, 180.0, R), math.pi * R) < 1e-15
+    assert _rel(o.haversine_m(30.0, 10.0, -30.0, -170.0, R), math.pi * R) < 1e-12
+    assert round(o.haversine_m(37.0, -92.0, 38.0, -92.0, R), 2) == 111194.93
+    # against the independent atan2 form, at mid latitudes, steps from 10 m to 200 km
+    lat1 = rng.uniform(36.0, 40.6, 2000)
+    lon1 = rng.uniform(-95.8, -89.1, 2000)
+    step = 10.0 ** rng.uniform(-4, 0.3, 2000)
+    ang = rng.uniform(0, 2 * math.pi, 2000)
+    lat2 = lat1 + step * np.cos(ang)
+    lon2 = lon1 + step * np.sin(ang)
+    want = vincenty_sphere_m(lat1, lon1, lat2, lon2)
+    for i in range(2000):
+        got = o.haversine_m(lat1[i], lon1[i], lat2[i], lon2[i], R)
+        assert _rel(got, want[i]) < 1e-8, (i, got, want[i])
+
+
+# ---------------------------------------------------------------- keys
+def pin_grid_index(o):
+    # exact rational floor for 6-decimal latitudes m / 1e6 away from cell edges
+    rng = np.random.default_rng(12)
+    m = rng.integers(35_500_000, 41_000_000, 20000)
+    for mi in m:
+        x = mi / 1e6
+        num = int(mi) - 36_000_000  # (x - 36) in micro-degrees
+        k, rem = divmod(num, 10_000)
+        got = o.grid_index(x, 36.0, 0.01, 460)
+        exp = k if 0 <= k < 460 else -1
+        if rem == 0:  # exactly on an edge: either side is a correct rounding
+            assert got in (exp, k - 1 if 0 <= k - 1 < 460 else -1), (x, got, exp)
+        else:
+            assert got == exp, (x, got, exp)
+    # longitudes likewise (negative coordinates)
+    m = rng.integers(-96_000_000, -89_000_000, 20000)
+    for mi in m:
+        x = mi / 1e6
+        num = int(mi) + 95_800_000
+        k, rem = divmod(num, 10_000)
+        got = o.grid_index(x, -95.8, 0.01, 670)
+        exp = k if 0 <= k < 670 else -1
+        if rem == 0:
+            assert got in (exp, k - 1 if 0 <= k - 1 < 670 else -1), (x, got, exp)
+        else:
+            assert got == exp, (x, got, exp)
+    # monotone across edges, at consecutive doubles
+    for k in (1, 57, 166, 459):
+        x = 36.0 + k * 0.01
+        xs = [x]
+        for _ in range(8):
+            xs.insert(0, np.nextafter(xs[0], -np.inf))
+            xs.append(np.nextafter(xs[-1], np.inf))
+        idx = [o.grid_index(v, 36.0, 0.01, 460) for v in xs]
+        assert idx == sorted(idx) and idx[0] == k - 1 and idx[-1] == k, (k, idx)
+    # out of range and non-finite
+    assert o.grid_index(35.999999, 36.0, 0.01, 460) == -1
+    assert o.grid_index(36.0, 36.0, 0.01, 460) == 0
+    assert o.grid_index(40.61, 36.0, 0.01, 460) == -1
+    assert o.grid_index(40.6 + 1e-9, 36.0, 0.01, 460) == -1
+    assert o.grid_index(40.599999, 36.0, 0.01, 460) == 459
+    for bad in (float("nan"), float("inf"), -float("inf")):
+        assert o.grid_index(bad, 36.0, 0.01, 460) == -1
+
+
+def pin_time_bin(o):
+    t0, w, nb = 1620518400000, 60000, 1440
+    rng = np.random.default_rng(13)
+    offs = list(rng.integers(-3 * 86400000, 3 * 86400000, 5000)) + [-1, 0, 59999, 60000, 86399999, 86400000, -60000, -60001]
+    for off in offs:
+        ts = t0 + int(off)
+        q = (ts - t0) // w  # Python integer floor division
+        exp = q if 0 <= q < nb else -1
+        assert o.time_bin(ts, t0, w, nb) == exp, (off, exp)
+    assert o.time_bin(-(2 ** 63), t0, w, nb) == -1
+    assert o.time_bin(2 ** 63 - 1, t0, w, nb) == -1
+
+
+# ---------------------------------------------------------------- extract
+def pin_parse_fields(o):
+    rng = np.random.default_rng(14)
+    for _ in range(3000):
+        nd = int(rng.integers(1, 16))
+        ni = int(rng.integers(1, nd + 1))
+        digits = "".join(str(d) for d in rng.integers(0, 10, nd))
+        s = digits[:ni] + ("." + digits[ni:] if ni < nd else "")
+        if rng.random() < 0.5:
+            s = "-" + s
+        got = o.parse_decimal(s)
+        assert got is not None and got == float(s), (s, got)  # CPython's correctly rounded parse
+    for good in ("0", "-0", "0.0", "007.5", "123456789012345", "1.23456789012345", "-90.000000"):
+        assert o.parse_decimal(good) == float(good), good
+    for bad in ("", "-", "1.", ".5", "+1", "1e5", "nan", "inf", " 1", "1 ", "1.2.3", "--1",
+                "1234567890123456", "1.234567890123456", "12a4", "0x10", "1,0"):
+        assert o.parse_decimal(bad) is None, bad
+    for good, v in (("0", 0), ("-12", -12), ("123456789012345678", 123456789012345678), ("0001", 1)):
+        assert o.parse_integer(good) == v, good
+    for bad in ("", "-", "1234567890123456789", "1.0", "+5", "1e3", " 7"):
+        assert o.parse_integer(bad) is None, bad
+
+
+def pin_table1(o):
+    with open(os.path.join(GOLDEN, "table1_expected.json")) as f:
+        exp = json.load(f)
+    with open(os.path.join(GOLDEN, "table1.csv"), "rb") as f:
+        buf = f.read()
+    cols, nl, nm = o.parse_csv(buf)
+    assert nl == exp["n_lines"] and nm == exp["n_malformed"]
+    r = o.run(cols)
+    assert list(r["points"]["perm"]) == exp["perm"]
+    assert list(r["points"]["flags"]) == exp["flags"]
+    for k, v in exp["journeys"].items():
+        assert list(r["journeys"][k]) == v, k
+    for k in ("key", "row", "col", "bin", "count"):
+        assert list(r["cells"][k]) == exp["cells"][k], k
+    spd = np.array([np.float32(float(s)) for s in exp["cells"]["speed_decimal"]], np.float32)
+    assert np.array_equal(r["cells"]["min"], spd) and np.array_equal(r["cells"]["max"], spd)
+    assert np.array_equal(r["cells"]["sum"], spd.astype(np.float64) * np.array(exp["cells"]["count"]))
+
+
+def pin_csv_roundtrip(o, cols):
+    import cvgen
+
+    buf, injected = cvgen.to_csv(cols, seed=5, malformed_frac=0.01)
+    got, nl, nm = o.parse_csv(buf)
+    n = cols["jid"].shape[0]
+    assert nl == n and nm == injected and got["jid"].shape[0] == n - injected
+    # kept rows are the generator's rows, in file order, rounded to their printed precision
+    cj, ct, gj, gt = cols["jid"].tolist(), cols["ts"].tolist(), got["jid"].tolist(), got["ts"].tolist()
+    src = np.empty(len(gj), np.int64)
+    i = 0
+    for k in range(len(gj)):
+        while not (cj[i] == gj[k] and ct[i] == gt[k]):
+            i += 1
+        src[k] = i
+        i += 1
+    assert np.all(np.abs(cols["lat"][src] - got["lat"]) <= 5.0000001e-7)
+    assert np.all(np.abs(cols["lon"][src] - got["lon"]) <= 5.0000001e-7)
+    assert np.all(np.abs(cols["speed"][src] - got["speed"]) <= 0.0051)
+
+
+# ---------------------------------------------------------------- whole path
+def pin_invariants(o, cols):
+    r = o.run(cols)
+    c, p, j, cl = r["counters"], r["points"], r["journeys"], r["cells"]
+    n = cols["jid"].shape[0]
+    nv = c["n_valid"]
+    assert c["n_in"] == n and nv + c["n_malformed"] == n
+    # conservation
+    assert int(cl["count"].sum()) + c["n_out_of_grid"] == nv
+    assert int(j["n"].sum()) == nv
+    assert int(np.count_nonzero(p["key"] == 0xFFFFFFFF)) == c["n_out_of_grid"]
+    # permutation is a bijection onto the valid records
+    perm = p["perm"].astype(np.int64)
+    assert np.unique(perm).shape[0] == nv
+    # sortedness and stability
+    sj, st = cols["jid"][perm], cols["ts"][perm]
+    assert np.all((sj[1:] > sj[:-1]) | ((sj[1:] == sj[:-1]) & (st[1:] > st[:-1])) |
+                  ((sj[1:] == sj[:-1]) & (st[1:] == st[:-1]) & (perm[1:] > perm[:-1])))
+    assert np.all(np.diff(j["jid"]) > 0)
+    # journey starts, durations, dwell
+    starts = np.flatnonzero(p["flags"] & 1)
+    assert np.array_equal(sj[starts], j["jid"])
+    bounds = np.append(starts, nv)
+    dt = np.diff(st)
+    for k in range(0, len(starts), max(1, len(starts) // 200)):
+        a, b = bounds[k], bounds[k + 1]
+        assert j["duration_ms"][k] == int(dt[a:b - 1].sum()) == j["end_ts"][k] - j["start_ts"][k]
+        assert 0 <= j["dwell_ms"][k] <= j["duration_ms"][k]
+    # flags agree with the data
+    dup = np.zeros(nv, bool)
+    dup[1:] = (sj[1:] == sj[:-1]) & (st[1:] == st[:-1])
+    assert np.array_equal((p["flags"] & 2) != 0, dup) and c["n_dup"] == int(dup.sum())
+    # cell aggregates
+    assert np.all(np.diff(cl["key"].astype(np.int64)) > 0)
+    assert np.all(cl["min"] <= cl["mean"] + 1e-9) and np.all(cl["mean"] <= cl["max"] + 1e-9)
+    assert np.all(cl["key"] == (cl["bin"].astype(np.int64) * 460 + cl["row"]) * 670 + cl["col"])
+
+
+def pin_library_cross_check(o, cols):
+    """numpy.lexsort for the order; numpy grouping for count / sum / min / max."""
+    r = o.run(cols)
+    p, cl = r["points"], r["cells"]
+    n = cols["jid"].shape[0]
+    idx = np.arange(n)
+    valid = np.isfinite(cols["lat"]) & np.isfinite(cols["lon"]) & np.isfinite(cols["speed"])
+    order = np.lexsort((idx[valid], cols["ts"][valid], cols["jid"][valid]))
+    assert np.array_equal(idx[valid][order], p["perm"].astype(np.int64))
+    keys = p["key"]
+    spd = cols["speed"][p["perm"]].astype(np.float32)
+    spd = np.where(spd == 0, np.float32(0), spd)
+    ok = keys != 0xFFFFFFFF
+    kk, ss = keys[ok], spd[ok]
+    o2 = np.argsort(kk, kind="stable")
+    kk, ss = kk[o2], ss[o2]
+    uk, first, cnt = np.unique(kk, return_index=True, return_counts=True)
+    assert np.array_equal(uk, cl["key"]) and np.array_equal(cnt, cl["count"])
+    assert np.array_equal(np.minimum.reduceat(ss, first), cl["min"])
+    assert np.array_equal(np.maximum.reduceat(ss, first), cl["max"])
+    sums = np.add.reduceat(ss.astype(np.float64), first)
+    assert np.all(np.abs(sums - cl["sum"]) <= 1e-12 * np.abs(sums) + 1e-9)
+
+
+def _independent_groups(cols):
+    """Grouping with plain Python containers: journeys as lists sorted by (ts, index)."""
+    groups = {}
+    for i in range(len(cols["jid"])):
+        groups.setdefault(int(cols["jid"][i]), []).append((int(cols["ts"][i]), i, float(cols["speed"][i])))
+    for v in groups.values():
+        v.sort()
+    return groups
+
+
+def pin_bruteforce_orders(o):
+    base = dict(
+        jid=np.array([7, 3, 7, 3, 7, 9, 7], np.int64),
+        ts=np.array([1620520000500, 1620520000000, 1620520000000, 1620520000900, 1620520000500, 1620519999000, 1620520061000], np.int64),
+        lat=np.array([37.00001, 38.5, 37.0, 38.5003, 37.00001, 40.61, 37.01], np.float64),
+        lon=np.array([-92.0, -91.0, -92.0, -91.0004, -92.0, -90.0, -92.0], np.float64),
+        speed=np.array([0.5, 40.0, 0.0, 41.0, 0.5, 10.0, 60.0], np.float32),
+    )
+    n = 7
+    ref = None
+    groups = _independent_groups(base)
+    for perm in itertools.permutations(range(n)):
+        perm = np.array(perm)
+        cols = {k: v[perm] for k, v in base.items()}
+        r = o.run(cols)
+        back = perm[r["points"]["perm"]]
+        sig = (tuple(back), tuple(r["points"]["flags"]), tuple(r["points"]["key"]),
+               tuple(np.round(r["points"]["d"], 9)), tuple(r["points"]["dwell"]),
+               tuple(r["journeys"]["n"]), tuple(r["journeys"]["duration_ms"]),
+               tuple(r["cells"]["key"]), tuple(r["cells"]["count"]),
+               tuple(np.round(r["cells"]["sum"], 9)))
+        if ref is None:
+            ref = sig
+            # independent grouping: journey sizes, durations and order
+            assert list(r["journeys"]["jid"]) == sorted(groups)
+            assert list(r["journeys"]["n"]) == [len(groups[k]) for k in sorted(groups)]
+            assert list(r["journeys"]["duration_ms"]) == [groups[k][-1][0] - groups[k][0][0] for k in sorted(groups)]
+        else:
+            # identical outputs for every input order (the two identical records of journey
+            # 7 keep their input order, so they map to different base indices; every value
+            # is equal)
+            assert sig[1:] == ref[1:]
+
+
+def pin_kinematics_hand(o):
+    t = 1620532122000
+    # one journey on a meridian: 0.001 deg steps every 500 ms, a stop, a duplicate, a 1 ms step
+    cols = dict(
+        jid=np.array([5, 5, 5, 5, 5, 5], np.int64),
+        ts=np.array([t, t + 500, t + 1000, t + 1000, t + 3000, t + 3001], np.int64),
+        lat=np.array([37.0, 37.001, 37.002, 37.002, 37.002, 37.002], np.float64),
+        lon=np.array([-92.5, -92.5, -92.5, -92.5, -92.5, -92.5], np.float64),
+        speed=np.array([30.0, 36.0, 0.5, 0.5, 0.25, 50.0], np.float32),
+    )
+    r = o.run(cols)
+    p, j = r["points"], r["journeys"]
+    step = R * math.radians(0.001)
+    assert abs(p["d"][1] - step) < 1e-6 and abs(p["d"][2] - step) < 1e-6
+    assert p["d"][0] == 0 and p["d"][3] == 0 and p["d"][4] == 0 and p["d"][5] == 0
+    assert abs(p["vhat"][1] - step / 0.5 * 3.6) < 1e-6
+    assert abs(p["accel"][1] - (6.0 / 3.6) / 0.5) < 1e-9
+    assert abs(p["accel"][2] - ((0.5 - 36.0) / 3.6) / 0.5) < 1e-9
+    assert p["accel"][3] == 0 and p["vhat"][3] == 0  # duplicate: dt = 0
+    assert abs(p["accel"][4] - ((0.25 - 0.5) / 3.6) / 2.0) < 1e-9
+    assert abs(p["accel"][5] - ((50.0 - 0.25) / 3.6) / 0.001) < 1e-6
+    assert list(p["flags"]) == [1, 0, 0, 2 | 8, 8, 0]
+    assert list(p["dwell"]) == [0, 0, 0, 0, 2000, 0]
+    assert j["n"][0] == 6 and j["duration_ms"][0] == 3001 and j["dwell_ms"][0] == 2000
+    assert abs(j["distance_m"][0] - 2 * step) < 1e-6
+    assert j["start_lat"][0] == 37.0 and j["end_lat"][0] == 37.002
+    # a -0.0 speed is +0.0 in the aggregates
+    cols2 = dict(jid=np.array([1], np.int64), ts=np.array([t], np.int64), lat=np.array([37.5]),
+                 lon=np.array([-92.5]), speed=np.array([-0.0], np.float32))
+    r2 = o.run(cols2)
+    assert r2["cells"]["min"][0] == 0 and not np.signbit(r2["cells"]["min"][0])
+
+
+def pin_invalid_records(o):
+    t = 1620532122000
+    cols = dict(
+        jid=np.array([1, 1, 1, 1, 1, 1], np.int64),
+        ts=np.array([t, t + 1, t + 2, t + 3, t + 4, t + 5], np.int64),
+        lat=np.array([37.0, np.nan, 91.0, 37.0, 37.0, 35.0], np.float64),
+        lon=np.array([-92.0, -92.0, -92.0, np.inf, -181.0, -92.0], np.float64),
+        speed=np.array([1, 2, 3, 4, 5, np.nan], np.float32),
+    )
+    r = o.run(cols)
+    assert r["counters"]["n_malformed"] == 5 and r["counters"]["n_valid"] == 1
+    assert list(r["points"]["perm"]) == [0]
+    cols["speed"][5] = 6.0
+    r = o.run(cols)
+    assert r["counters"]["n_valid"] == 2 and r["counters"]["n_out_of_grid"] == 1  # lat 35.0
+
+
+CPU_PINS = [pin_haversine_closed_forms, pin_grid_index, pin_time_bin, pin_parse_fields, pin_table1,
+            pin_bruteforce_orders, pin_kinematics_hand, pin_invalid_records]
+DATA_PINS = [pin_invariants, pin_library_cross_check, pin_csv_roundtrip]
