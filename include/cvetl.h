@@ -1,0 +1,221 @@
+/*
+ * cvetl.h — C ABI of the connected-vehicle ETL library (libcvetl.so, CUDA, sm_103a).
+ *
+ * The library runs the data-parallel hot path of the connected-vehicle extract-transform-
+ * load pipeline of arXiv 2305.07454 ("Accelerating Statewide Connected Vehicles Big
+ * (Sensor Fusion) Data ETL Pipelines on GPUs"), following the paper's extract / transform /
+ * load framing (Introduction, definition of ETL):
+ *
+ *   extract    records (journey id, timestamp, latitude, longitude, speed, heading) from
+ *              binary columns or CSV text (Methods, "Connected Vehicle Dataset"; Table 1),
+ *              keeping the columns of interest (Accelerated ETL section, step (2));
+ *   transform  order by (journey id, timestamp), per-point kinematics, and the floor-
+ *              division bins of Algorithm 2 unrolled into one global positional index
+ *              (Accelerated ETL section, steps (3)-(4));
+ *   load       per cell x time-bin count / sum / mean (Table 3 "Data Binning", "Reduction -
+ *              Sum") plus min / max, and per-journey summaries (steps (5)-(6)).
+ *
+ * Every step runs in the library's own CUDA kernels on one GPU. There is no CPU fallback: a
+ * call that cannot run on the device returns an error.
+ *
+ * Conventions
+ *  - Every call returns a cvetl_status and never aborts or throws across the ABI.
+ *    cvetl_last_error() returns the context's last error text.
+ *  - Calls are stream-ordered on config.stream (a cudaStream_t; NULL = the legacy default
+ *    stream). The caller owns input buffers. Host inputs are copied during cvetl_extract;
+ *    device inputs are read in place, so the caller keeps them alive and unchanged until the
+ *    work of cvetl_transform has completed on the stream.
+ *  - Result arrays are device memory owned by the context. They stay valid until the next
+ *    cvetl_extract or cvetl_destroy.
+ *  - Call order per batch: cvetl_extract -> cvetl_transform -> cvetl_load -> cvetl_results.
+ *    A call out of order returns CVETL_ESTATE and changes nothing.
+ *  - One context per host thread. Different contexts may run concurrently on different
+ *    streams.
+ *  - Sizes: at most CVETL_MAX_RECORDS records per batch.
+ */
+#ifndef CVETL_H
+#define CVETL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CVETL_VERSION 1
+#define CVETL_MAX_RECORDS 1073741823LL /* 2^30 - 1 */
+#define CVETL_KEY_INVALID 0xFFFFFFFFu
+
+typedef struct cvetl_ctx cvetl_ctx;
+
+typedef enum {
+  CVETL_OK = 0,
+  CVETL_EINVAL = 1,   /* bad argument (NULL pointer, bad size, bad configuration) */
+  CVETL_ENOMEM = 2,   /* device allocation failed */
+  CVETL_EFULL = 3,    /* the request would exceed config.mem_budget_bytes; state unchanged */
+  CVETL_ESTATE = 4,   /* call out of order */
+  CVETL_ECUDA = 5,    /* a CUDA runtime error; see cvetl_last_error */
+  CVETL_ETIMEOUT = 6, /* a bounded device-side wait gave up; results are not valid */
+  CVETL_EPARSE = 7    /* reserved for unrecoverable input errors */
+} cvetl_status;
+
+enum { CVETL_FP64 = 0, CVETL_FP32 = 1 };
+enum { CVETL_IN_COLUMNS = 0, CVETL_IN_CSV = 1 };
+
+/* per-point flags */
+#define CVETL_F_START 0x01u   /* first point of its journey */
+#define CVETL_F_DUP 0x02u     /* same timestamp as its predecessor in the journey */
+#define CVETL_F_OFFGRID 0x04u /* outside the grid or the day's time bins (key invalid) */
+#define CVETL_F_STOP 0x08u    /* this point and its predecessor both below v_stop_kmh */
+
+typedef struct {
+  /* Grid of Algorithm 2: row = floor((lat - lat_min) / cell_deg), col likewise for lon,
+   * valid when 0 <= row < n_rows and 0 <= col < n_cols. */
+  double lat_min, lon_min, cell_deg; /* 36.0, -95.8, 0.01 */
+  int32_t n_rows, n_cols;            /* 460, 670 */
+  /* Time bins: bin = floor((ts - t0_ms) / bin_ms), valid when 0 <= bin < n_bins. */
+  int32_t n_bins;                    /* 1440 */
+  int64_t t0_ms, bin_ms;             /* 2021-05-09 00:00:00 UTC in ms, 60000 */
+  float v_stop_kmh;                  /* 1.0: dwell threshold */
+  double earth_radius_m;             /* 6371000.0 */
+  int32_t precision;                 /* CVETL_FP64 (only FP64 is built) */
+  int32_t materialize_points;        /* 1: keep per-point columns in the results */
+  int32_t profile;                   /* 1: time every kernel with CUDA events */
+  int32_t device;                    /* CUDA device ordinal */
+  size_t mem_budget_bytes;           /* device memory the context may hold; 0 = unlimited */
+  void* stream;                      /* cudaStream_t */
+} cvetl_config;
+
+typedef struct {
+  int32_t kind;       /* CVETL_IN_COLUMNS or CVETL_IN_CSV */
+  int32_t on_device;  /* 1: the pointers below are device memory */
+  int64_t n;          /* rows (CVETL_IN_COLUMNS) */
+  /* CVETL_IN_COLUMNS: six columns of n rows. heading may be NULL (it is not used). */
+  const int64_t* jid;
+  const int64_t* ts;
+  const double* lat;
+  const double* lon;
+  const float* speed;
+  const float* heading;
+  /* CVETL_IN_CSV: csv_len bytes of text (see the grammar at cvetl_extract). */
+  const char* csv;
+  size_t csv_len;
+} cvetl_input;
+
+typedef struct {
+  /* cell x bin table, ascending key (device pointers, n_cells rows) */
+  int64_t n_cells;
+  const uint32_t* cell_key;
+  const int32_t* cell_row;
+  const int32_t* cell_col;
+  const int32_t* cell_bin;
+  const uint32_t* cell_count;
+  const double* cell_sum;
+  const double* cell_mean;
+  const float* cell_min;
+  const float* cell_max;
+  /* journey table, ascending journey id (device pointers, n_journeys rows) */
+  int64_t n_journeys;
+  const int64_t* j_id;
+  const int64_t* j_n;
+  const int64_t* j_offset;      /* sorted position of the journey's first point */
+  const int64_t* j_start_ts;
+  const int64_t* j_end_ts;
+  const int64_t* j_duration_ms;
+  const double* j_distance_m;
+  const int64_t* j_dwell_ms;
+  const double* j_start_lat;
+  const double* j_start_lon;
+  const double* j_end_lat;
+  const double* j_end_lon;
+  /* per-point columns in sorted order (NULL unless materialize_points; n_points rows) */
+  int64_t n_points;
+  const uint32_t* p_perm;  /* extracted-row index of the sorted point */
+  const double* p_d;       /* haversine step distance, m */
+  const float* p_vhat;     /* implied speed, km/h */
+  const float* p_accel;    /* acceleration, m/s^2 */
+  const int64_t* p_dwell;  /* dwell of the step, ms */
+  const uint32_t* p_key;   /* unrolled cell x bin key or CVETL_KEY_INVALID */
+  const uint8_t* p_flags;  /* CVETL_F_* */
+  /* extracted columns (device; the CSV path's parsed rows, or the caller's columns) */
+  int64_t n_extracted;
+  const int64_t* x_jid;
+  const int64_t* x_ts;
+  const double* x_lat;
+  const double* x_lon;
+  const float* x_speed;
+  /* counters */
+  int64_t n_in;          /* rows handed to cvetl_extract */
+  int64_t n_malformed;   /* rows dropped by validation */
+  int64_t n_valid;       /* rows kept */
+  int64_t n_out_of_grid; /* kept rows whose key is invalid */
+  int64_t n_dup;         /* kept rows flagged CVETL_F_DUP */
+  int64_t n_too_late;    /* always 0 in batch mode */
+} cvetl_tables;
+
+#define CVETL_MAX_STAGES 32
+typedef struct {
+  int32_t n_stages;
+  const char* name[CVETL_MAX_STAGES];   /* kernel / stage names (static strings) */
+  double ms[CVETL_MAX_STAGES];          /* summed CUDA-event time (profile = 1) */
+  int64_t launches[CVETL_MAX_STAGES];   /* kernel launches */
+  int64_t total_launches;               /* all of this context's kernel launches */
+} cvetl_stats;
+
+/* Fills *cfg with the statewide defaults listed beside each field. */
+void cvetl_config_default(cvetl_config* cfg);
+
+/* Creates a context. Validates the configuration: positive grid and bin sizes,
+ * n_rows * n_cols * n_bins <= 2^32 - 1 (so every key fits in 32 bits and differs from
+ * CVETL_KEY_INVALID), finite lat_min / lon_min, cell_deg > 0. Returns CVETL_EINVAL on a bad
+ * configuration, CVETL_ECUDA if the device cannot be used. *out is set only on success. */
+cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out);
+
+/* Extract (Methods, "Connected Vehicle Dataset"; Accelerated ETL step (2)).
+ * CVETL_IN_COLUMNS: takes n rows. A row is kept when lat, lon and speed are finite,
+ * |lat| <= 90 and |lon| <= 180; otherwise it is counted in n_malformed. Speed -0.0 is read
+ * as +0.0.
+ * CVETL_IN_CSV: reserved; returns CVETL_EINVAL in this version.
+ * Replaces the context's previous batch. Returns CVETL_EINVAL for NULL columns or
+ * n outside [0, CVETL_MAX_RECORDS], CVETL_EFULL if the budget is exceeded. */
+cvetl_status cvetl_extract(cvetl_ctx* ctx, const cvetl_input* in);
+
+/* Transform (Accelerated ETL steps (3)-(4); Algorithm 2). Orders the kept rows by
+ * (journey id, timestamp, extracted-row index), then for each point computes: the journey
+ * start flag; dt = ts - ts_prev; the haversine step distance on a sphere of radius
+ * earth_radius_m; implied speed d / dt * 3.6 km/h and acceleration (speed - speed_prev) /
+ * 3.6 / dt m/s^2 when dt > 0 (else 0); dwell = dt when both speeds are below v_stop_kmh;
+ * and the key (bin * n_rows + row) * n_cols + col with row, col, bin the floor-division
+ * bins of Algorithm 2 (row and col taken from the IEEE binary64 quotient of the binary64
+ * difference). Also builds the journey table. */
+cvetl_status cvetl_transform(cvetl_ctx* ctx);
+
+/* Load (Accelerated ETL steps (5)-(6); Table 3). Groups points with a valid key into the
+ * cell x bin table: count, sum of speed (binary64), min, max, mean = sum / count. */
+cvetl_status cvetl_load(cvetl_ctx* ctx);
+
+/* Results of the last batch: device pointers owned by the context, sizes and counters.
+ * Synchronises ctx->stream (it reads the sizes). */
+cvetl_status cvetl_results(cvetl_ctx* ctx, cvetl_tables* out);
+
+/* Streaming mode is not built in this version: returns CVETL_ESTATE. */
+cvetl_status cvetl_flush(cvetl_ctx* ctx);
+
+/* Per-kernel launch counts and (with profile = 1) CUDA-event times, summed since the
+ * context was created or since cvetl_stats_reset. Synchronises ctx->stream. */
+cvetl_status cvetl_stats_get(cvetl_ctx* ctx, cvetl_stats* out);
+cvetl_status cvetl_stats_reset(cvetl_ctx* ctx);
+
+/* Frees the context and all its device memory. NULL is accepted. */
+cvetl_status cvetl_destroy(cvetl_ctx* ctx);
+
+/* Last error text of the context (or of the last failed cvetl_create when ctx is NULL). */
+const char* cvetl_last_error(const cvetl_ctx* ctx);
+
+int32_t cvetl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

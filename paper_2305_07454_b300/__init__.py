@@ -1,0 +1,251 @@
+"""Python binding of libcvetl.so, the CUDA (sm_103a) connected-vehicle ETL library.
+
+Argument marshalling only: every step of extract / transform / load runs in the library's
+own CUDA kernels behind the C ABI declared in ``include/cvetl.h`` (arXiv 2305.07454,
+Accelerated ETL section and Algorithm 2). PyTorch supplies device memory and streams.
+There is no CPU fallback: importing this package without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcvetl.so")
+
+OK, EINVAL, ENOMEM, EFULL, ESTATE, ECUDA, ETIMEOUT, EPARSE = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EFULL", "ESTATE", "ECUDA", "ETIMEOUT", "EPARSE"]
+FP64, FP32 = 0, 1
+IN_COLUMNS, IN_CSV = 0, 1
+KEY_INVALID = 0xFFFFFFFF
+F_START, F_DUP, F_OFFGRID, F_STOP = 0x01, 0x02, 0x04, 0x08
+
+_P = ctypes.c_void_p
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("lat_min", ctypes.c_double), ("lon_min", ctypes.c_double), ("cell_deg", ctypes.c_double),
+        ("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+        ("t0_ms", ctypes.c_int64), ("bin_ms", ctypes.c_int64),
+        ("v_stop_kmh", ctypes.c_float), ("earth_radius_m", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("materialize_points", ctypes.c_int32),
+        ("profile", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("mem_budget_bytes", ctypes.c_size_t), ("stream", _P),
+    ]
+
+
+class Input(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("on_device", ctypes.c_int32), ("n", ctypes.c_int64),
+        ("jid", _P), ("ts", _P), ("lat", _P), ("lon", _P), ("speed", _P), ("heading", _P),
+        ("csv", _P), ("csv_len", ctypes.c_size_t),
+    ]
+
+
+_CELL = [("key", "<u4"), ("row", "<i4"), ("col", "<i4"), ("bin", "<i4"), ("count", "<u4"),
+         ("sum", "<f8"), ("mean", "<f8"), ("min", "<f4"), ("max", "<f4")]
+_JOURNEY = [("id", "<i8"), ("n", "<i8"), ("offset", "<i8"), ("start_ts", "<i8"), ("end_ts", "<i8"),
+            ("duration_ms", "<i8"), ("distance_m", "<f8"), ("dwell_ms", "<i8"),
+            ("start_lat", "<f8"), ("start_lon", "<f8"), ("end_lat", "<f8"), ("end_lon", "<f8")]
+_POINT = [("perm", "<u4"), ("d", "<f8"), ("vhat", "<f4"), ("accel", "<f4"), ("dwell", "<i8"),
+          ("key", "<u4"), ("flags", "|u1")]
+_EXTRACTED = [("jid", "<i8"), ("ts", "<i8"), ("lat", "<f8"), ("lon", "<f8"), ("speed", "<f4")]
+_COUNTERS = ["n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_too_late"]
+
+
+class Tables(ctypes.Structure):
+    _fields_ = (
+        [("n_cells", ctypes.c_int64)] + [("cell_" + k, _P) for k, _ in _CELL]
+        + [("n_journeys", ctypes.c_int64)] + [("j_" + k, _P) for k, _ in _JOURNEY]
+        + [("n_points", ctypes.c_int64)] + [("p_" + k, _P) for k, _ in _POINT]
+        + [("n_extracted", ctypes.c_int64)] + [("x_" + k, _P) for k, _ in _EXTRACTED]
+        + [(k, ctypes.c_int64) for k in _COUNTERS]
+    )
+
+
+MAX_STAGES = 32
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_stages", ctypes.c_int32), ("name", ctypes.c_char_p * MAX_STAGES),
+                ("ms", ctypes.c_double * MAX_STAGES), ("launches", ctypes.c_int64 * MAX_STAGES),
+                ("total_launches", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcvetl.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_2305_07454_b300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.cvetl_config_default.argtypes = [ctypes.POINTER(Config)]
+    lib.cvetl_config_default.restype = None
+    lib.cvetl_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(_P)]
+    lib.cvetl_extract.argtypes = [_P, ctypes.POINTER(Input)]
+    lib.cvetl_transform.argtypes = [_P]
+    lib.cvetl_load.argtypes = [_P]
+    lib.cvetl_results.argtypes = [_P, ctypes.POINTER(Tables)]
+    lib.cvetl_flush.argtypes = [_P]
+    lib.cvetl_stats_get.argtypes = [_P, ctypes.POINTER(Stats)]
+    lib.cvetl_stats_reset.argtypes = [_P]
+    lib.cvetl_destroy.argtypes = [_P]
+    lib.cvetl_last_error.argtypes = [_P]
+    lib.cvetl_last_error.restype = ctypes.c_char_p
+    lib.cvetl_version.restype = ctypes.c_int32
+    for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
+              "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+# The C-ABI entry points declared in include/cvetl.h (checked by the tests).
+EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load",
+           "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
+           "cvetl_last_error", "cvetl_version")
+
+
+class CvetlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class _DeviceArray:
+    """A device pointer exposed through the CUDA array interface (zero-copy for torch)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+def default_config(**kw) -> Config:
+    cfg = Config()
+    lib.cvetl_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Pipeline:
+    """One cvetl context: extract -> transform -> load -> results on one CUDA stream."""
+
+    def __init__(self, stream=None, **cfg):
+        import torch
+
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.config = default_config(**cfg)
+        self.config.stream = stream.cuda_stream
+        self.config.device = stream.device.index if stream.device.index is not None else 0
+        h = _P()
+        st = lib.cvetl_create(ctypes.byref(self.config), ctypes.byref(h))
+        if st != OK:
+            raise CvetlError(st, lib.cvetl_last_error(None).decode())
+        self._h = h
+        self._keep = None
+
+    def _check(self, st: int):
+        if st != OK:
+            raise CvetlError(st, lib.cvetl_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.cvetl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def extract(self, cols: dict):
+        """cols: jid, ts, lat, lon, speed (+ heading) as torch tensors, all on the device or
+        all on the host, or numpy arrays (host)."""
+        torch = self._torch
+        names = ("jid", "ts", "lat", "lon", "speed")
+        dtypes = (torch.int64, torch.int64, torch.float64, torch.float64, torch.float32)
+        ts = []
+        for k, dt in zip(names, dtypes):
+            v = cols[k]
+            if isinstance(v, np.ndarray):
+                v = torch.from_numpy(np.ascontiguousarray(v))
+            if v.dtype != dt or not v.is_contiguous() or v.dim() != 1:
+                raise ValueError(f"column {k} must be a contiguous 1-D {dt} tensor")
+            ts.append(v)
+        n = ts[0].shape[0]
+        if any(t.shape[0] != n for t in ts):
+            raise ValueError("columns differ in length")
+        dev = {t.is_cuda for t in ts}
+        if len(dev) != 1:
+            raise ValueError("columns must be all on the device or all on the host")
+        on_device = dev.pop()
+        inp = Input(kind=IN_COLUMNS, on_device=int(on_device), n=n,
+                    jid=ts[0].data_ptr(), ts=ts[1].data_ptr(), lat=ts[2].data_ptr(),
+                    lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None)
+        self._keep = ts
+        self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
+
+    def transform(self):
+        self._check(lib.cvetl_transform(self._h))
+
+    def load(self):
+        self._check(lib.cvetl_load(self._h))
+
+    def tables(self) -> Tables:
+        t = Tables()
+        self._check(lib.cvetl_results(self._h, ctypes.byref(t)))
+        return t
+
+    def results(self, to_host: bool = True) -> dict:
+        """Cells, journeys, per-point columns (if materialised) and counters. to_host=False
+        returns zero-copy device tensors valid until the next extract."""
+        torch = self._torch
+        t = self.tables()
+
+        def view(ptr, n, typestr):
+            if n == 0 or not ptr:
+                np_dt = np.dtype(typestr)
+                arr = torch.empty(0, dtype=torch.from_numpy(np.empty(0, np_dt)).dtype, device="cuda")
+            else:
+                arr = torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
+            return arr.cpu().numpy() if to_host else arr
+
+        out = {
+            "cells": {k: view(getattr(t, "cell_" + k), t.n_cells, ty) for k, ty in _CELL},
+            "journeys": {k: view(getattr(t, "j_" + k), t.n_journeys, ty) for k, ty in _JOURNEY},
+            "counters": {k: int(getattr(t, k)) for k in _COUNTERS},
+        }
+        if t.n_points and t.p_perm:
+            out["points"] = {k: view(getattr(t, "p_" + k), t.n_points, ty) for k, ty in _POINT}
+        out["counters"]["n_journeys"] = int(t.n_journeys)
+        out["counters"]["n_cells"] = int(t.n_cells)
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib.cvetl_stats_get(self._h, ctypes.byref(s)))
+        return {"stages": {s.name[i].decode(): {"ms": s.ms[i], "launches": int(s.launches[i])}
+                           for i in range(s.n_stages)},
+                "total_launches": int(s.total_launches)}
+
+    def stats_reset(self):
+        self._check(lib.cvetl_stats_reset(self._h))
+
+    def run(self, cols: dict, to_host: bool = True) -> dict:
+        self.extract(cols)
+        self.transform()
+        self.load()
+        return self.results(to_host=to_host)

@@ -1,0 +1,54 @@
+// cells.cuh — load stage: runs sorted by (key, first sorted position) are folded into the
+// cell x bin table (count, sum, min, max, mean), in a fixed order.
+#pragma once
+#include "common.cuh"
+
+namespace cvetl {
+
+__global__ void k_cell_heads(const unsigned long long* __restrict__ skey, uint32_t R,
+                             uint32_t* __restrict__ head) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < R) head[i] = (i == 0 || (skey[i] >> 32) != (skey[i - 1] >> 32)) ? 1u : 0u;
+}
+
+struct CellOut {
+  uint32_t* key;
+  int32_t *row, *col, *bin;
+  uint32_t* count;
+  double *sum, *mean;
+  float *min, *max;
+};
+
+__global__ void k_cell_write(const unsigned long long* __restrict__ skey,
+                             const uint32_t* __restrict__ sidx, uint32_t R,
+                             const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx,
+                             const uint32_t* __restrict__ run_cnt, const double* __restrict__ run_sum,
+                             const float* __restrict__ run_min, const float* __restrict__ run_max,
+                             int32_t n_rows, int32_t n_cols, CellOut o) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= R || !head[i]) return;
+  const uint32_t key = (uint32_t)(skey[i] >> 32);
+  uint32_t cnt = 0;
+  double sum = 0.0;
+  float mn = run_min[sidx[i]], mx = run_max[sidx[i]];
+  for (uint32_t m = i; m < R && (uint32_t)(skey[m] >> 32) == key; ++m) {
+    uint32_t r = sidx[m];
+    cnt += run_cnt[r];
+    sum += run_sum[r];
+    mn = fminf(mn, run_min[r]);
+    mx = fmaxf(mx, run_max[r]);
+  }
+  const uint32_t c = cidx[i];
+  const uint32_t cells = (uint32_t)n_rows * (uint32_t)n_cols;
+  o.key[c] = key;
+  o.bin[c] = (int32_t)(key / cells);
+  o.row[c] = (int32_t)((key % cells) / (uint32_t)n_cols);
+  o.col[c] = (int32_t)(key % (uint32_t)n_cols);
+  o.count[c] = cnt;
+  o.sum[c] = sum;
+  o.mean[c] = sum / (double)cnt;
+  o.min[c] = mn;
+  o.max[c] = mx;
+}
+
+}  // namespace cvetl

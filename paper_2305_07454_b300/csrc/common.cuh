@@ -1,0 +1,138 @@
+// common.cuh — device utilities shared by the cvetl kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+namespace cvetl {
+
+constexpr uint32_t kKeyInvalid = 0xFFFFFFFFu;
+constexpr uint64_t kSign64 = 0x8000000000000000ull;
+
+// per-point flags (same values as CVETL_F_* in cvetl.h)
+constexpr uint8_t kFStart = 0x01, kFDup = 0x02, kFOffgrid = 0x04, kFStop = 0x08;
+
+// Error bits written by kernels into DevState::err (never a trap).
+constexpr uint32_t kErrLookbackTimeout = 1u;
+constexpr uint32_t kErrHashOverflow = 2u;
+constexpr uint32_t kErrHashMissing = 4u;
+constexpr uint32_t kErrCapacity = 8u;
+
+// Device-side counters and status of one batch.
+struct DevState {
+  uint32_t err;
+  uint32_t n_distinct;  // distinct journey ids seen by the hash table
+  uint32_t n_runs;      // cell runs emitted by the journey kernel
+  uint32_t n_cells;
+  uint32_t n_big;       // journeys taking the chunked-sort path
+  uint32_t pad0;
+  unsigned long long n_malformed;
+  unsigned long long n_dup;
+  unsigned long long n_offgrid;
+};
+
+// One extracted record, bucketed by journey (32 bytes, one DRAM sector).
+struct __align__(32) Rec {
+  int64_t ts;
+  double lat;
+  double lon;
+  float spd;     // canonical speed (+0.0 for -0.0)
+  uint32_t idx;  // extracted-row index
+};
+static_assert(sizeof(Rec) == 32, "Rec must be one 32-byte sector");
+
+// Order-preserving map of a double onto uint64 (for finite values and +-inf).
+__host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
+#ifdef __CUDA_ARCH__
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+#endif
+  return (b & kSign64) ? ~b : (b | kSign64);
+}
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const unsigned long long* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Inclusive warp scan (Hillis-Steele with shuffles).
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan over a block of NT threads (one value each). scratch: NT/32 + 1 words.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratch, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) scratch[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < NT / 32) ? scratch[lane] : 0u;
+    uint32_t wi = warp_incl_scan(w);
+    if (lane < NT / 32) scratch[lane] = wi - w;
+    if (lane == NT / 32 - 1) scratch[NT / 32] = wi;
+  }
+  __syncthreads();
+  uint32_t r = scratch[warp] + inc - v;
+  if (total) *total = scratch[NT / 32];
+  __syncthreads();
+  return r;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warp partials in order).
+template <int NT, typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  T r = T(0);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) r += scratch[w];
+  }
+  __syncthreads();
+  return r;  // valid in thread 0
+}
+
+}  // namespace cvetl

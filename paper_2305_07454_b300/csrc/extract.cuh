@@ -1,0 +1,160 @@
+// extract.cuh — validation of binary columns, journey counting in an open-addressing hash
+// table, ranking of distinct journey ids, and the scatter of every kept record into its
+// journey's bucket as one 32-byte record.
+#pragma once
+#include "common.cuh"
+
+namespace cvetl {
+
+constexpr uint64_t kHashEmpty = ~0ull;  // bit pattern of id -1 (the table is filled with 0xFF); that id uses slot `cap`
+constexpr int kMaxProbe = 4096;
+
+struct Hash {
+  unsigned long long* keys;  // cap entries (+1 unused)
+  uint32_t* cnt;             // cap + 1 counts
+  uint32_t* aux;             // cap + 1 scatter cursors
+  uint32_t mask;             // cap - 1
+  uint32_t cap;
+};
+
+// A kept row has finite lat, lon and speed with |lat| <= 90 and |lon| <= 180. Tested on the bit
+// patterns: |x| <= c for c >= 0 is (bits(x) & ~sign) <= bits(c), which also rejects NaN/inf.
+__device__ __forceinline__ bool row_valid(double lat, double lon, float spd) {
+  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long b90 = 0x4056800000000000ull;   // 90.0
+  const unsigned long long b180 = 0x4066800000000000ull;  // 180.0
+  unsigned long long la = (unsigned long long)__double_as_longlong(lat) & kAbs;
+  unsigned long long lo = (unsigned long long)__double_as_longlong(lon) & kAbs;
+  uint32_t sp = (uint32_t)__float_as_int(spd) & 0x7FFFFFFFu;
+  return la <= b90 && lo <= b180 && sp < 0x7F800000u;
+}
+
+__device__ __forceinline__ float canon_speed(float s) {
+  return ((__float_as_int(s) & 0x7FFFFFFF) == 0) ? 0.0f : s;
+}
+
+__device__ __forceinline__ int64_t hash_insert(const Hash& h, uint64_t key, uint32_t* n_distinct) {
+  if (key == kHashEmpty) return (int64_t)h.cap;
+  uint32_t s = (uint32_t)fmix64(key) & h.mask;
+  for (int p = 0; p < kMaxProbe; ++p) {
+    uint64_t k = ld_relaxed_u64(&h.keys[s]);
+    if (k == key) return s;
+    if (k == kHashEmpty) {
+      unsigned long long prev = atomicCAS(&h.keys[s], (unsigned long long)kHashEmpty,
+                                          (unsigned long long)key);
+      if (prev == kHashEmpty) {
+        atomicAdd(n_distinct, 1u);
+        return s;
+      }
+      if (prev == key) return s;
+    }
+    s = (s + 1) & h.mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int64_t hash_find(const Hash& h, uint64_t key) {
+  if (key == kHashEmpty) return (int64_t)h.cap;
+  uint32_t s = (uint32_t)fmix64(key) & h.mask;
+  for (int p = 0; p < kMaxProbe; ++p) {
+    uint64_t k = h.keys[s];
+    if (k == key) return s;
+    if (k == kHashEmpty) return -1;
+    s = (s + 1) & h.mask;
+  }
+  return -1;
+}
+
+__global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ jid,
+                                                    const double* __restrict__ lat,
+                                                    const double* __restrict__ lon,
+                                                    const float* __restrict__ spd, uint32_t n,
+                                                    Hash h, DevState* st) {
+  __shared__ unsigned long long scratch[8];
+  unsigned long long bad = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!row_valid(lat[i], lon[i], spd[i])) {
+      ++bad;
+      continue;
+    }
+    int64_t s = hash_insert(h, (uint64_t)jid[i], &st->n_distinct);
+    if (s < 0) atomicOr(&st->err, kErrHashOverflow);
+    else atomicAdd(&h.cnt[s], 1u);
+  }
+  unsigned long long b = block_sum<256, unsigned long long>(bad, scratch);
+  if (threadIdx.x == 0 && b) atomicAdd(&st->n_malformed, b);
+}
+
+// Distinct ids (as order-preserving keys) and their slots, in arbitrary order.
+__global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
+                                uint32_t* __restrict__ uslot, uint32_t* counter) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= h.cap; s += gridDim.x * blockDim.x) {
+    bool occ;
+    uint64_t id;
+    if (s < h.cap) {
+      id = h.keys[s];
+      occ = id != kHashEmpty;
+    } else {
+      id = kHashEmpty;
+      occ = h.cnt[s] > 0;
+    }
+    if (occ) {
+      uint32_t i = atomicAdd(counter, 1u);
+      ukey[i] = id ^ kSign64;  // signed order as unsigned order
+      uslot[i] = s;
+    }
+  }
+}
+
+// Journey rank r (ascending id): size, id.
+__global__ void k_journey_sizes(const unsigned long long* __restrict__ skey,
+                                const uint32_t* __restrict__ sslot, uint32_t J, Hash h,
+                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out) {
+  uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < J) {
+    jn[r] = h.cnt[sslot[r]];
+    jid_out[r] = (int64_t)(skey[r] ^ kSign64);
+  }
+}
+
+__global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J,
+                                  const uint32_t* __restrict__ joff, Hash h) {
+  uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < J) h.aux[sslot[r]] = joff[r];
+}
+
+// Every kept row goes to its journey's bucket (the order inside a bucket is arbitrary; the
+// journey kernel sorts it by (timestamp, row index)).
+__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ jid,
+                                                 const int64_t* __restrict__ ts,
+                                                 const double* __restrict__ lat,
+                                                 const double* __restrict__ lon,
+                                                 const float* __restrict__ spd, uint32_t n, Hash h,
+                                                 Rec* __restrict__ rec, DevState* st) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double la = lat[i], lo = lon[i];
+    float sp = spd[i];
+    if (!row_valid(la, lo, sp)) continue;
+    int64_t s = hash_find(h, (uint64_t)jid[i]);
+    if (s < 0) {
+      atomicOr(&st->err, kErrHashMissing);
+      continue;
+    }
+    uint32_t pos = atomicAdd(&h.aux[s], 1u);
+    int64_t t = ts[i];
+    uint4 a, b;
+    a.x = (uint32_t)(uint64_t)t;
+    a.y = (uint32_t)((uint64_t)t >> 32);
+    a.z = (uint32_t)__double2loint(la);
+    a.w = (uint32_t)__double2hiint(la);
+    b.x = (uint32_t)__double2loint(lo);
+    b.y = (uint32_t)__double2hiint(lo);
+    b.z = (uint32_t)__float_as_int(canon_speed(sp));
+    b.w = i;
+    uint4* dst = reinterpret_cast<uint4*>(rec + pos);
+    dst[0] = a;
+    dst[1] = b;
+  }
+}
+
+}  // namespace cvetl

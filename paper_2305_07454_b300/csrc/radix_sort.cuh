@@ -1,0 +1,169 @@
+// radix_sort.cuh — stable LSD radix sort of (key, uint32 value) pairs, one scatter pass per
+// 8-bit digit with decoupled look-back (the single-pass "onesweep" scheme of Adinets and
+// Merrill, 2022): an up-front histogram pass computes every digit's global counts, then each
+// pass ranks a 4096-item tile in shared memory, publishes the tile's digit counts, looks back
+// over earlier tiles for its global offsets and scatters through shared memory so that
+// consecutive threads write consecutive addresses.
+#pragma once
+#include "common.cuh"
+
+namespace cvetl {
+namespace rs {
+
+constexpr int kBits = 8;
+constexpr int kRadix = 256;
+constexpr int kBlock = 256;
+constexpr int kIpt = 16;
+constexpr int kTile = kBlock * kIpt;  // 4096
+constexpr int kWarps = kBlock / 32;
+constexpr int kMaxPasses = 8;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;  // look-back polls before the tile gives up
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
+  return (uint32_t)(k >> shift) & (kRadix - 1);
+}
+
+// Histograms of n_passes digits starting at begin_bit. hist: [kMaxPasses][256], zeroed.
+template <typename K>
+__global__ void __launch_bounds__(kBlock) k_histogram(const K* __restrict__ keys, uint32_t n,
+                                                      int begin_bit, int n_passes,
+                                                      uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kMaxPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kBlock) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
+    K k = keys[i];
+    for (int p = 0; p < n_passes; ++p) atomicAdd(&sh[p][digit_of(k, begin_bit + kBits * p)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_passes * kRadix; i += kBlock) {
+    uint32_t v = (&sh[0][0])[i];
+    if (v) atomicAdd(&hist[i], v);
+  }
+}
+
+// In place: hist[p][d] -> exclusive prefix over d. One block of 256 threads per pass.
+__global__ void __launch_bounds__(kBlock) k_hist_scan(uint32_t* hist) {
+  __shared__ uint32_t scratch[kBlock / 32 + 1];
+  uint32_t* h = hist + blockIdx.x * kRadix;
+  uint32_t v = h[threadIdx.x];
+  uint32_t e = block_excl_scan<kBlock>(v, scratch, nullptr);
+  h[threadIdx.x] = e;
+}
+
+// One digit pass. status: [n_tiles][256] words, zeroed; tile_ctr zeroed.
+// vin == nullptr means value = input position (iota).
+template <typename K>
+__global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
+                                                     const uint32_t* __restrict__ vin,
+                                                     K* __restrict__ kout,
+                                                     uint32_t* __restrict__ vout, uint32_t n,
+                                                     int shift, const uint32_t* __restrict__ goff,
+                                                     uint32_t* status, uint32_t* tile_ctr,
+                                                     uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  K* s_keys = reinterpret_cast<K*>(smem_raw);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * kTile);
+  __shared__ uint16_t s_wcnt[kWarps][kRadix];
+  __shared__ uint32_t s_tstart[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ uint32_t s_scan[kBlock / 32 + 1];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  for (int i = tid; i < kWarps * kRadix; i += kBlock) (&s_wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint32_t base = tile * kTile;
+  const uint32_t n_valid = (base < n) ? min((uint32_t)kTile, n - base) : 0u;
+
+  K key[kIpt];
+  uint32_t val[kIpt], rank[kIpt];
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    uint32_t idx = base + warp * (32 * kIpt) + i * 32 + lane;
+    bool ok = idx < n;
+    key[i] = ok ? kin[idx] : ~K(0);
+    val[i] = ok ? (vin ? vin[idx] : idx) : 0u;
+  }
+  // Warp-level ranking in input order: items are visited warp by warp, i-major, lane-minor,
+  // which is their global order, so ranks are stable.
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    uint32_t d = digit_of(key[i], shift);
+    uint32_t peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = s_wcnt[warp][d];
+    __syncwarp();
+    if (lane == (__ffs(peers) - 1)) s_wcnt[warp][d] = (uint16_t)(before + __popc(peers));
+    __syncwarp();
+    rank[i] = before + __popc(peers & lanemask_lt());
+  }
+  __syncthreads();
+  // Thread t owns digit t: prefix over warps, tile count.
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    uint32_t c = s_wcnt[w][tid];
+    s_wcnt[w][tid] = (uint16_t)run;
+    run += c;
+  }
+  // Items past n carry key ~0 (digit 255) and rank after every valid digit-255 item.
+  uint32_t cnt_valid = run - ((tid == kRadix - 1) ? (kTile - n_valid) : 0u);
+  uint32_t* my_status = status + (size_t)tile * kRadix + tid;
+  uint32_t excl = 0;
+  if (tile == 0) {
+    st_relaxed_u32(my_status, kFlagPre | cnt_valid);
+  } else {
+    st_relaxed_u32(my_status, kFlagAgg | cnt_valid);
+    int64_t p = (int64_t)tile - 1;
+    while (p >= 0) {
+      const uint32_t* ps = status + (size_t)p * kRadix + tid;
+      uint32_t s = ld_relaxed_u32(ps);
+      int spins = 0;
+      while ((s & (kFlagAgg | kFlagPre)) == 0) {
+        if (++spins > kSpinLimit) break;
+        __nanosleep(32);
+        s = ld_relaxed_u32(ps);
+      }
+      if ((s & (kFlagAgg | kFlagPre)) == 0) {
+        atomicOr(err, kErrLookbackTimeout);
+        break;
+      }
+      excl += s & kValMask;
+      if (s & kFlagPre) break;
+      --p;
+    }
+    st_relaxed_u32(my_status, kFlagPre | (excl + cnt_valid));
+  }
+  s_gbase[tid] = goff[tid] + excl;
+  uint32_t ts = block_excl_scan<kBlock>(run, s_scan, nullptr);
+  s_tstart[tid] = ts;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) {
+    uint32_t d = digit_of(key[i], shift);
+    uint32_t pos = s_tstart[d] + s_wcnt[warp][d] + rank[i];
+    s_keys[pos] = key[i];
+    s_vals[pos] = val[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kIpt; ++j) {
+    uint32_t p = j * kBlock + tid;
+    if (p < n_valid) {
+      K k = s_keys[p];
+      uint32_t d = digit_of(k, shift);
+      uint32_t g = s_gbase[d] + (p - s_tstart[d]);
+      kout[g] = k;
+      vout[g] = s_vals[p];
+    }
+  }
+}
+
+}  // namespace rs
+}  // namespace cvetl

@@ -1,0 +1,179 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import cvgen
+from parity import close, compare, exact
+
+pytestmark = pytest.mark.gpu
+
+T0 = 1620518400000
+
+
+def run_gpu(cols, device=True, materialize=True, **cfg):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    t = {k: torch.from_numpy(np.ascontiguousarray(cols[k])) for k in ("jid", "ts", "lat", "lon", "speed")}
+    if device:
+        t = {k: v.cuda() for k, v in t.items()}
+    with P.Pipeline(materialize_points=int(materialize), **cfg) as p:
+        return p.run(t)
+
+
+def synth(sizes, seed, jids=None, dup_frac=0.0, t_start=T0 + 3_600_000):
+    """Shuffled journeys of exactly the given sizes (test-local inputs, no method arithmetic)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for j, m in enumerate(sizes):
+        jid = int(jids[j]) if jids is not None else int(rng.integers(0, 2 ** 40))
+        dt = rng.integers(300, 1000, m)
+        dt[0] = 0
+        if dup_frac:
+            dt[1:][rng.random(m - 1) < dup_frac] = 0
+        ts = t_start + int(rng.integers(0, 3_600_000)) + np.cumsum(dt)
+        lat = 38.0 + np.cumsum(rng.normal(0, 2e-5, m))
+        lon = -92.0 + np.cumsum(rng.normal(0, 2e-5, m))
+        spd = np.abs(rng.normal(40, 30, m)).astype(np.float32)
+        spd[rng.random(m) < 0.05] = 0.0
+        spd[rng.random(m) < 0.02] = -0.0
+        if dup_frac:  # exact duplicates: copy the predecessor's values
+            for i in np.flatnonzero(dt == 0)[1:] if m > 1 else []:
+                lat[i], lon[i], spd[i] = lat[i - 1], lon[i - 1], spd[i - 1]
+        parts.append(dict(jid=np.full(m, jid, np.int64), ts=ts.astype(np.int64), lat=lat, lon=lon, speed=spd))
+    cols = {k: np.concatenate([p[k] for p in parts]) if parts else np.empty(0, t)
+            for k, t in (("jid", np.int64), ("ts", np.int64), ("lat", np.float64), ("lon", np.float64),
+                         ("speed", np.float32))}
+    perm = rng.permutation(cols["jid"].shape[0])
+    return {k: np.ascontiguousarray(v[perm]) for k, v in cols.items()}
+
+
+def test_small_day(orc, small_day):
+    compare(run_gpu(small_day), orc.run(small_day))
+
+
+def test_small_day_host_input_matches(orc, small_day):
+    a = run_gpu(small_day, device=False)
+    compare(a, orc.run(small_day))
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_input_order_does_not_change_any_bit(small_day, seed):
+    base = run_gpu(small_day)
+    perm = np.random.default_rng(seed).permutation(small_day["jid"].shape[0])
+    shuffled = {k: np.ascontiguousarray(v[perm]) for k, v in small_day.items()}
+    got = run_gpu(shuffled)
+    for part in ("cells", "journeys"):
+        for k in base[part]:
+            exact(f"{part} {k}", got[part][k], base[part][k])
+    for k in ("d", "vhat", "accel", "dwell", "key", "flags"):
+        exact("point " + k, got["points"][k], base["points"][k])
+    # the sorted records are the same records in the same order; exact duplicates tie on
+    # (journey, time) and follow input order, so their indices may trade places
+    back = perm[got["points"]["perm"]]
+    for k in small_day:
+        exact("sorted " + k, small_day[k][back], small_day[k][base["points"]["perm"]])
+
+
+def test_empty_input(orc):
+    cols = synth([], 1)
+    g = run_gpu(cols)
+    assert g["counters"]["n_valid"] == 0 and g["counters"]["n_journeys"] == 0 and g["counters"]["n_cells"] == 0
+    compare(g, orc.run(cols), points=False)
+
+
+@pytest.mark.parametrize("sizes", [[1], [2], [255, 256, 257], [4095, 4096, 4097], [1, 8193, 3, 20000]])
+def test_journey_sizes_around_tile_edges(orc, sizes):
+    cols = synth(sizes, seed=sum(sizes), dup_frac=0.01)
+    compare(run_gpu(cols), orc.run(cols))
+
+
+def test_one_long_journey_many_chunks(orc):
+    cols = synth([70001], seed=9, dup_frac=0.003)
+    compare(run_gpu(cols), orc.run(cols))
+
+
+def test_duplicate_heavy_ties_follow_input_order(orc):
+    cols = synth([300, 5000], seed=5, dup_frac=0.5)
+    compare(run_gpu(cols), orc.run(cols))
+
+
+def test_sentinel_like_ids_and_full_int64_range(orc):
+    ids = [-1, -(2 ** 63), 2 ** 63 - 1, 0, 1, -2]
+    cols = synth([10, 20, 30, 40, 50, 60], seed=4, jids=ids)
+    compare(run_gpu(cols), orc.run(cols))
+    wide = cvgen.generate(cvgen.params("small_day", seed=4, n_journeys=300, jid_mode=1))
+    compare(run_gpu(wide), orc.run(wide))
+
+
+def test_malformed_offgrid_and_negative_zero(orc):
+    cols = synth([500, 700], seed=6)
+    n = cols["jid"].shape[0]
+    rng = np.random.default_rng(0)
+    i = rng.choice(n, 60, replace=False)
+    cols["lat"][i[:10]] = np.nan
+    cols["lon"][i[10:20]] = np.inf
+    cols["lat"][i[20:25]] = 90.0000001
+    cols["lon"][i[25:30]] = -180.5
+    cols["speed"][i[30:35]] = np.nan
+    cols["lat"][i[35:40]] = 35.5          # below the grid
+    cols["lon"][i[40:45]] = -89.0999999   # just east of the grid
+    cols["ts"][i[45:50]] = T0 - 5        # before the day
+    cols["ts"][i[50:55]] = T0 + 86_400_000  # after the last bin
+    cols["speed"][i[55:60]] = -0.0
+    o = orc.run(cols)
+    assert o["counters"]["n_malformed"] == 35 and o["counters"]["n_out_of_grid"] >= 20
+    compare(run_gpu(cols), o)
+
+
+def test_cell_edges_exactly(orc):
+    """Points placed exactly on 0.01 deg edges: the binary64 quotient decides the side."""
+    k = np.arange(0, 460)
+    lat = 36.0 + k * 0.01
+    lon = np.full_like(lat, -95.8 + 0.37)
+    n = lat.shape[0]
+    cols = dict(jid=np.arange(n, dtype=np.int64), ts=np.full(n, T0 + 1000, np.int64), lat=lat,
+                lon=lon, speed=np.ones(n, np.float32))
+    compare(run_gpu(cols), orc.run(cols))
+
+
+def test_aggregates_only_mode_matches(orc, small_day):
+    g = run_gpu(small_day, materialize=False)
+    assert "points" not in g
+    compare(g, orc.run(small_day), points=False)
+
+
+def test_call_order_and_budget_errors(small_day):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    with P.Pipeline() as p:
+        with pytest.raises(P.CvetlError) as e:
+            p.transform()
+        assert e.value.status == P.ESTATE
+        with pytest.raises(P.CvetlError) as e:
+            p.load()
+        assert e.value.status == P.ESTATE
+    with P.Pipeline(mem_budget_bytes=1 << 20) as p:
+        t = {k: torch.from_numpy(np.ascontiguousarray(small_day[k])).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+        p.extract(t)
+        with pytest.raises(P.CvetlError) as e:
+            p.transform()
+        assert e.value.status == P.EFULL
+
+
+def test_stats_count_launches(small_day):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    t = {k: torch.from_numpy(np.ascontiguousarray(small_day[k])).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+    with P.Pipeline(profile=1) as p:
+        p.run(t, to_host=False)
+        s = p.stats()
+    assert s["total_launches"] > 10
+    assert s["stages"]["journeys"]["launches"] == 1 and s["stages"]["journeys"]["ms"] > 0
