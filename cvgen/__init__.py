@@ -55,6 +55,9 @@ WORKLOADS = {
     # 60,000 journeys over one day, ~150M records: the median is raised to 1,875 points so
     # that the stated journey and record totals hold together (mean ~2,500 points).
     "full_day": dict(n_journeys=60000, median_len=1875.0),
+    # A tenth of the full day (6,000 journeys, ~15M records): still larger than L2, small
+    # enough for detailed profiler captures.
+    "tenth_day": dict(n_journeys=6000, median_len=1875.0),
 }
 
 DAY_START_MS = 1620518400000  # 2021-05-09 00:00:00 UTC

@@ -152,6 +152,7 @@ typedef struct {
   int64_t n_out_of_grid; /* kept rows whose key is invalid */
   int64_t n_dup;         /* kept rows flagged CVETL_F_DUP */
   int64_t n_too_late;    /* always 0 in batch mode */
+  int64_t n_runs;        /* runs of equal consecutive keys folded by the load stage */
 } cvetl_tables;
 
 #define CVETL_MAX_STAGES 32

@@ -690,6 +690,7 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
   r->n_out_of_grid = (int64_t)c->hstate->n_offgrid;
   r->n_dup = (int64_t)c->hstate->n_dup;
   r->n_too_late = 0;
+  r->n_runs = c->R;
   return CVETL_OK;
 }
 
