@@ -19,9 +19,9 @@ def declared():
 
 @pytest.fixture(scope="module")
 def so():
-    from paper_2305_07454_b300 import build
+    import __graft_entry__
 
-    return build.build()
+    return __graft_entry__._lib_build().build()
 
 
 def test_header_declares_the_five_etl_calls():
