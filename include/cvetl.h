@@ -216,6 +216,29 @@ const char* cvetl_last_error(const cvetl_ctx* ctx);
 
 int32_t cvetl_version(void);
 
+/* Allocation-free radix sort (the paper has no counterpart; it serves callers that may not
+ * allocate device memory: code inside a host framework that owns the device memory pool and
+ * forbids side allocations, and latency-critical loops where a cudaMalloc / cudaFree, which can
+ * synchronise the device, would stall the work).
+ * Stable sort of n 64-bit keys by bits [begin_bit, end_bit): keys_out receives the keys in
+ * ascending order and perm_out[i] the input position of the i-th key (equal keys keep input
+ * order). All three arrays are device memory owned by the caller; keys_out must not be
+ * keys_in. Work is queued on `stream` (a cudaStream_t) and the call synchronises it before
+ * returning (it reads a device error word).
+ * Scratch: a fixed device array of about 3 MB inside the library, one per device that loads
+ * it, held until the process exits; the call allocates nothing (no cudaMalloc, no cudaFree).
+ * The first call on each device looks up that array's device address and sets the kernel's
+ * shared-memory limit, so make the first call on a device before any stream capture.
+ * Calls share the array and clear what must start at zero; calls that overlap on the GPU
+ * (other streams, other threads) race on it, so serialise them.
+ * Errors (text via cvetl_last_error(NULL)): CVETL_EINVAL when n is outside
+ * [0, CVETL_NOALLOC_MAX_PAIRS], the bit range is not within [0, 64), an array is NULL or
+ * keys_out == keys_in; CVETL_ECUDA on a CUDA error; CVETL_ETIMEOUT if a bounded device-side
+ * wait gave up (the outputs are then not valid). */
+#define CVETL_NOALLOC_MAX_PAIRS 262144
+cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm_out,
+                                    int64_t n, int32_t begin_bit, int32_t end_bit, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

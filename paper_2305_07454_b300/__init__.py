@@ -94,6 +94,8 @@ def _load():
     lib.cvetl_last_error.argtypes = [_P]
     lib.cvetl_last_error.restype = ctypes.c_char_p
     lib.cvetl_version.restype = ctypes.c_int32
+    lib.cvetl_sort_u64_noalloc.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]
+    lib.cvetl_sort_u64_noalloc.restype = ctypes.c_int
     for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
               "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy"):
         getattr(lib, f).restype = ctypes.c_int
@@ -105,7 +107,8 @@ lib = _load()
 # The C-ABI entry points declared in include/cvetl.h (checked by the tests).
 EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load",
            "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
-           "cvetl_last_error", "cvetl_version")
+           "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc")
+NOALLOC_MAX_PAIRS = 262144
 
 
 class CvetlError(RuntimeError):

@@ -740,3 +740,6 @@ cvetl_status cvetl_stats_reset(cvetl_ctx* c) {
 }
 
 }  // extern "C"
+
+// The allocation-free sort entry point (its scratch array and set-up live in this file).
+#include "noalloc_sort.cuh"
