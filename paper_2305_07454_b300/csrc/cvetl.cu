@@ -365,6 +365,20 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   if ((s = ensure(c, "grid.rows", rt.size(), &c->row_thr)) != CVETL_OK) return bail(s);
   if ((s = ensure(c, "grid.cols", ct.size(), &c->col_thr)) != CVETL_OK) return bail(s);
   if ((s = ensure(c, "state", 1, &c->dstate)) != CVETL_OK) return bail(s);
+  // cosine table for the binary64 haversine: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180}
+  std::vector<double4> cos_tab(18001);
+  for (int k = -9000; k <= 9000; ++k) {
+    const double lat0 = (double)k * 0.01;
+    const double rad = M_PI / 180.0;
+    cos_tab[k + 9000] = make_double4(lat0, std::cos(lat0 * rad), std::sin(lat0 * rad) * rad, 0.0);
+  }
+  double4* d_cos = nullptr;
+  if ((s = ensure(c, "grid.cos", cos_tab.size(), &d_cos)) != CVETL_OK) return bail(s);
+  if (cudaMemcpy(d_cos, cos_tab.data(), cos_tab.size() * sizeof(double4), cudaMemcpyHostToDevice) != cudaSuccess) {
+    fail(c, CVETL_ECUDA, "cvetl_create: cosine table upload failed");
+    return bail(CVETL_ECUDA);
+  }
+  c->gp.cos_tab = d_cos;
   if (cudaMemcpy(c->row_thr, rt.data(), rt.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->col_thr, ct.data(), ct.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMallocHost(&c->hstate, sizeof(DevState)) != cudaSuccess) {

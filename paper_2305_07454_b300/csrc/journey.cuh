@@ -18,6 +18,7 @@ struct GridParams {
   unsigned long long t_span;  // n_bins * bin_ms, saturated
   float v_stop;
   double radius_m;
+  const double4* cos_tab;  // k = -9000..9000: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, 0}
 };
 
 struct JourneyOut {
@@ -96,6 +97,7 @@ __device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts,
 
 // ---------------------------------------------------------------- kinematics
 // Haversine distance on a sphere of radius R; coordinates differenced in degrees first.
+// General form with the CUDA math library (used for large steps).
 __device__ __forceinline__ double haversine_m(double la1, double lo1, double la2, double lo2, double R) {
   const double rad = 0.017453292519943295;  // pi / 180
   double dphi = (la2 - la1) * rad, dlam = (lo2 - lo1) * rad;
@@ -191,6 +193,170 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem*
   return src;
 }
 
+// ---------------------------------------------------------------- binary64 haversine, fast path
+// For the sub-second steps of a journey the half-angles a = dphi/2 and b = dlambda/2 are tiny.
+// With |a|, |b| < 2e-4 rad (steps under ~2.5 km):
+//   sin^2(x) = x^2 (1 - x^2/3) + O(x^6)           (Taylor; dropped term < 2x^4/45 < 1e-16 rel.)
+//   asin(s)  = s (1 + s^2/6 + 3 s^4/40) + O(s^7)   (Taylor of arcsine; s^2 = h)
+//   sqrt(h)  from a float reciprocal square root refined by two binary64 Newton steps
+//   cos(lat) = cos(lat0 + e) = c0 (1 - e^2/2) - s0 e (1 - e^2/6), lat0 the nearest 0.01 deg
+//              (angle addition; |e| <= 0.005 deg, dropped terms < 3e-18)
+// Larger steps take the general formula through the CUDA math library.
+constexpr double kHalfRad = 0.008726646259971648;   // pi / 360
+constexpr double kRad = 0.017453292519943295;       // pi / 180
+constexpr double kRad2Half = 1.5230870989335428e-4;  // (pi/180)^2 / 2
+constexpr double kRad2Sixth = 5.076956996445143e-5;  // (pi/180)^2 / 6
+
+__device__ __forceinline__ double cos_deg(double lat, const double4* __restrict__ tab) {
+  int k = __float2int_rn(leading_f32(lat) * 100.0f);
+  k = max(-9000, min(9000, k));
+  const double2* p = reinterpret_cast<const double2*>(tab + (k + 9000));
+  const double2 t0 = __ldg(p), t1 = __ldg(p + 1);  // {lat0, cos}, {sin * pi/180, -}
+  const double e = lat - t0.x;  // degrees
+  const double e2 = e * e;
+  const double c = t0.y * fma(e2, -kRad2Half, 1.0);
+  return fma(-(t1.x * e), fma(e2, -kRad2Sixth, 1.0), c);
+}
+
+__device__ __forceinline__ bool tiny_angle(double x) {
+  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long b2em4 = 0x3F2A36E2EB1C432Dull;  // 2e-4
+  return ((unsigned long long)__double_as_longlong(x) & kAbs) < b2em4;
+}
+
+__device__ __forceinline__ double haversine_fast(double la1, double lo1, double c1, double la2,
+                                                 double lo2, double c2, double R) {
+  const double a = (la2 - la1) * kHalfRad;
+  const double b = (lo2 - lo1) * kHalfRad;
+  if (tiny_angle(a) && tiny_angle(b)) {
+    const double a2 = a * a, b2 = b * b;
+    const double sa = a2 * fma(a2, -1.0 / 3.0, 1.0);
+    const double sb = b2 * fma(b2, -1.0 / 3.0, 1.0);
+    const double h = fma(c1 * c2, sb, sa);
+    if (h == 0.0) return 0.0;
+    const float hf = leading_f32(h);
+    if (hf > 0.0f) {
+      const float y = rsqrtf(hf);
+      const double yd = (double)y, yh = (double)(0.5f * y);
+      double s = h * yd;
+      s = fma(fma(-s, s, h), yh, s);
+      s = fma(fma(-s, s, h), yh, s);
+      const double R2 = 2.0 * R;
+      return s * fma(h, fma(h, R2 * 0.075, R2 / 6.0), R2);
+    }
+  }
+  return haversine_m(la1, lo1, la2, lo2, R);
+}
+
+// ---------------------------------------------------------------- CTA-wide radix sort
+// Stable LSD radix sort of n 64-bit keys (8-bit digits over bits [0, nbits)) by one CTA.
+// A and B are shared memory for n <= kJCap, else global scratch (a journey's scratch stays in
+// L2 while its CTA works on it). Ranking inside a 4096-key tile uses warp match + popc, as in
+// the device-wide sort; multi-tile passes add a digit histogram and carry running offsets
+// from tile to tile in order, which keeps the sort stable.
+struct SortSmem {
+  uint16_t wcnt[kJBlock / 32][256];
+  uint32_t run[256];
+  uint32_t scan[kJBlock / 32 + 1];
+};
+
+__device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned long long* B, int n,
+                                              int nbits, SortSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool one_tile = n <= kJCap;
+  for (int shift = 0; shift < nbits; shift += 8) {
+    if (!one_tile) {
+      sm.run[tid] = 0;
+      __syncthreads();
+      for (int i = tid; i < n; i += kJBlock) atomicAdd(&sm.run[(uint32_t)(A[i] >> shift) & 255u], 1u);
+      __syncthreads();
+      uint32_t v = sm.run[tid];
+      uint32_t e = block_excl_scan<kJBlock>(v, sm.scan, nullptr);
+      sm.run[tid] = e;
+      __syncthreads();
+    }
+    for (int t0 = 0; t0 < n; t0 += kJCap) {
+      const int m = min(kJCap, n - t0);
+      for (int i = tid; i < (kJBlock / 32) * 256; i += kJBlock) (&sm.wcnt[0][0])[i] = 0;
+      __syncthreads();
+      unsigned long long key[16];
+      uint32_t rank[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int idx = warp * 512 + i * 32 + lane;
+        key[i] = (idx < m) ? A[t0 + idx] : ~0ull;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = sm.wcnt[warp][d];
+        __syncwarp();
+        if (lane == (__ffs(peers) - 1)) sm.wcnt[warp][d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+        rank[i] = before + __popc(peers & lanemask_lt());
+      }
+      __syncthreads();
+      uint32_t cnt = 0;
+#pragma unroll
+      for (int w = 0; w < kJBlock / 32; ++w) {
+        const uint32_t c = sm.wcnt[w][tid];
+        sm.wcnt[w][tid] = (uint16_t)cnt;
+        cnt += c;
+      }
+      const uint32_t cnt_valid = cnt - ((tid == 255) ? (uint32_t)(kJCap - m) : 0u);
+      uint32_t base;
+      if (one_tile) base = block_excl_scan<kJBlock>(cnt, sm.scan, nullptr);
+      else base = sm.run[tid];
+      __syncthreads();
+      sm.run[tid] = base;  // this tile's first output position per digit
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int idx = warp * 512 + i * 32 + lane;
+        if (idx < m) {
+          const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
+          B[sm.run[d] + sm.wcnt[warp][d] + rank[i]] = key[i];
+        }
+      }
+      __syncthreads();
+      if (!one_tile) {
+        sm.run[tid] = base + cnt_valid;
+        __syncthreads();
+      }
+    }
+    unsigned long long* t = A;
+    A = B;
+    B = t;
+  }
+  return A;
+}
+
+// Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
+// slot (arbitrary) here; reorder each such group by extracted-row index.
+__device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
+  const unsigned long long mask = (1ull << pos_bits) - 1;
+  for (int k = threadIdx.x; k < n; k += kJBlock) {
+    const unsigned long long t = K[k] >> pos_bits;
+    const bool lead = (k == 0 || (K[k - 1] >> pos_bits) != t) && (k + 1 < n && (K[k + 1] >> pos_bits) == t);
+    if (lead) {
+      int e = k + 1;
+      while (e < n && (K[e] >> pos_bits) == t) ++e;
+      for (int i = k + 1; i < e; ++i) {  // insertion sort by row index
+        const unsigned long long v = K[i];
+        const uint32_t vi = R[v & mask].idx;
+        int q = i - 1;
+        while (q >= k && R[K[q] & mask].idx > vi) {
+          K[q + 1] = K[q];
+          --q;
+        }
+        K[q + 1] = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- the journey kernel
 __device__ __forceinline__ void emit_run(const JourneyOut& o, DevState* st, uint32_t key, uint32_t cnt,
                                          double sum, float mn, float mx, uint32_t start) {
@@ -206,23 +372,26 @@ __device__ __forceinline__ void emit_run(const JourneyOut& o, DevState* st, uint
   o.run_max[i] = mx;
 }
 
+__device__ __forceinline__ int bits_for(unsigned long long v) { return v ? 64 - __clzll(v) : 0; }
+
 __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ rec,
                                                       const uint32_t* __restrict__ jn,
                                                       const uint32_t* __restrict__ joff, uint32_t J,
                                                       Elem* scrA, Elem* scrB, GridParams g,
                                                       JourneyOut o, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Elem* E = reinterpret_cast<Elem*>(smem_raw);
+  __shared__ SortSmem ssort;
   __shared__ int64_t e_ts[kJBlock / 32 + 1];
-  __shared__ double e_lat[kJBlock / 32 + 1], e_lon[kJBlock / 32 + 1];
+  __shared__ double e_lat[kJBlock / 32 + 1], e_lon[kJBlock / 32 + 1], e_cos[kJBlock / 32 + 1];
   __shared__ float e_spd[kJBlock / 32 + 1];
   __shared__ uint32_t s_key[kJBlock];
   __shared__ float s_spd[kJBlock];
-  __shared__ uint32_t c_key, c_cnt, c_start, o_key, o_cnt, o_start;
+  __shared__ uint32_t c_key, c_cnt, c_start, o_key, o_cnt, o_start, s_prevc;
   __shared__ double c_sum, o_sum;
   __shared__ float c_min, c_max, o_min, o_max;
   __shared__ double red_d[kJBlock / 32];
   __shared__ long long red_i[kJBlock / 32];
+  __shared__ unsigned long long s_tmin, s_tmax;
   __shared__ int64_t s_first_ts, s_last_ts;
   __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
 
@@ -232,19 +401,65 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
+  const bool small = n <= kJCap;
+  unsigned long long* KA = small ? reinterpret_cast<unsigned long long*>(smem_raw)
+                                 : reinterpret_cast<unsigned long long*>(scrA + off);
+  unsigned long long* KB = small ? reinterpret_cast<unsigned long long*>(smem_raw) + kJCap
+                                 : reinterpret_cast<unsigned long long*>(scrB + off);
 
   // 1. order the bucket by (timestamp, row index)
-  const Elem* sorted;
-  if (n <= kJCap) {
-    int P = 1;
-    while (P < n) P <<= 1;
-    load_elems(E, R, 0, n, P);
-    bitonic_smem(E, P);
-    sorted = E;
-  } else {
-    if (tid == 0) atomicAdd(&st->n_big, 1u);
-    sorted = sort_big(E, R, n, scrA + off, scrB + off);
+  // 1a. timestamps as order-preserving keys, and their range
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int i = tid; i < n; i += kJBlock) {
+    const unsigned long long t = (unsigned long long)R[i].ts ^ kSign64;
+    KA[i] = t;
+    lo = min(lo, t);
+    hi = max(hi, t);
   }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o2));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o2));
+  }
+  if (tid == 0) {
+    s_tmin = ~0ull;
+    s_tmax = 0ull;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(&s_tmin, lo);
+    atomicMax(&s_tmax, hi);
+  }
+  __syncthreads();
+  const unsigned long long tmin = s_tmin;
+  const int pos_bits = max(1, bits_for((unsigned long long)(n > 1 ? n - 1 : 1)));
+  const int nbits = pos_bits + bits_for(s_tmax - tmin);
+  const bool radix = nbits <= 64;
+  const unsigned long long* sortedK = nullptr;
+  const Elem* sortedE = nullptr;
+  if (radix) {
+    // 1b. packed keys ((ts - tmin) << pos_bits) | slot, radix-sorted, ties by row index
+    for (int i = tid; i < n; i += kJBlock) KA[i] = ((KA[i] - tmin) << pos_bits) | (unsigned long long)i;
+    __syncthreads();
+    unsigned long long* K = cta_radix_sort(KA, KB, n, nbits, ssort);
+    fix_ties(K, n, pos_bits, R);
+    sortedK = K;
+  } else {
+    // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
+    __syncthreads();
+    if (tid == 0) atomicAdd(&st->n_big, 1u);
+    Elem* E = reinterpret_cast<Elem*>(smem_raw);
+    if (small) {
+      int P = 1;
+      while (P < n) P <<= 1;
+      load_elems(E, R, 0, n, P);
+      bitonic_smem(E, P);
+      sortedE = E;
+    } else {
+      sortedE = sort_big(E, R, n, scrA + off, scrB + off);
+    }
+  }
+  const unsigned long long pmask = (1ull << pos_bits) - 1;
 
   if (tid == 0) {
     c_key = kKeyInvalid;
@@ -255,61 +470,82 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   long long dwell_sum = 0, n_dup = 0, n_off = 0;
   __syncthreads();
 
-  // 2. walk the sorted journey, 256 points at a time
+  // 2. walk the sorted journey, 256 points at a time (two barriers per slice)
   for (int s0 = 0; s0 < n; s0 += kJBlock) {
     const int k = s0 + tid;
     const bool active = k < n;
+    // hand the run left open by the previous slice to the carry; publish its key
+    if (tid == 0) {
+      if (o_key != kKeyInvalid) {
+        c_key = o_key;
+        c_cnt = o_cnt;
+        c_sum = o_sum;
+        c_min = o_min;
+        c_max = o_max;
+        c_start = o_start;
+        o_key = kKeyInvalid;
+      }
+      s_prevc = c_key;
+    }
     Rec cur;
-    if (active) cur = R[sorted[k].pos];
-    else {
+    if (active) {
+      const uint32_t p = radix ? (uint32_t)(sortedK[k] & pmask) : sortedE[k].pos;
+      cur = R[p];
+    } else {
       cur.ts = 0; cur.lat = 0.0; cur.lon = 0.0; cur.spd = 0.0f; cur.idx = 0;
     }
-    // predecessor: the previous lane, or the previous warp's last lane, or the last point of
-    // the previous slice (e_*[0])
+    const double ccur = active ? cos_deg(cur.lat, g.cos_tab) : 0.0;
+    const uint32_t key = active ? cell_key(cur.lat, cur.lon, cur.ts, g) : kKeyInvalid;
+    // predecessor: previous lane; lane 0 takes the previous warp's last lane, or the last
+    // point of the previous slice (slot 0)
     int64_t p_ts = __shfl_up_sync(0xffffffffu, cur.ts, 1);
     double p_lat = __shfl_up_sync(0xffffffffu, cur.lat, 1);
     double p_lon = __shfl_up_sync(0xffffffffu, cur.lon, 1);
+    double p_cos = __shfl_up_sync(0xffffffffu, ccur, 1);
     float p_spd = __shfl_up_sync(0xffffffffu, cur.spd, 1);
     if (lane == 31) {
       e_ts[warp + 1] = cur.ts;
       e_lat[warp + 1] = cur.lat;
       e_lon[warp + 1] = cur.lon;
+      e_cos[warp + 1] = ccur;
       e_spd[warp + 1] = cur.spd;
     }
-    __syncthreads();
+    s_key[tid] = key;
+    s_spd[tid] = cur.spd;
+    __syncthreads();  // ---- S1
     if (lane == 0) {
       p_ts = e_ts[warp];
       p_lat = e_lat[warp];
       p_lon = e_lon[warp];
+      p_cos = e_cos[warp];
       p_spd = e_spd[warp];
     }
-    const uint32_t prevc = c_key;
-    uint8_t fl = 0;
-    double d = 0.0;
-    float vh = 0.0f, ac = 0.0f;
-    int64_t dw = 0;
-    uint32_t key = kKeyInvalid;
+    const uint32_t prevc = s_prevc;
     if (active) {
+      uint8_t fl = 0;
+      double d = 0.0;
+      float vh = 0.0f, ac = 0.0f;
+      int64_t dw = 0;
       if (k == 0) {
         fl |= kFStart;
         s_first_ts = cur.ts;
         s_first_lat = cur.lat;
         s_first_lon = cur.lon;
       } else {
-        int64_t dt = (int64_t)((unsigned long long)cur.ts - (unsigned long long)p_ts);
+        const int64_t dt = (int64_t)((unsigned long long)cur.ts - (unsigned long long)p_ts);
         if (dt == 0) fl |= kFDup;
-        d = haversine_m(p_lat, p_lon, cur.lat, cur.lon, g.radius_m);
+        d = haversine_fast(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g.radius_m);
         if (dt > 0) {
-          double dts = (double)dt / 1000.0;
-          vh = (float)(d / dts * 3.6);
-          ac = (float)((((double)cur.spd - (double)p_spd) / 3.6) / dts);
+          // stored as float32: computed in float32 from the binary64 distance
+          const float fdt = (float)dt;
+          vh = (float)d * (3600.0f / fdt);
+          ac = (cur.spd - p_spd) / (0.0036f * fdt);
         }
         if (p_spd < g.v_stop && cur.spd < g.v_stop) {
           fl |= kFStop;
           dw = dt;
         }
       }
-      key = cell_key(cur.lat, cur.lon, cur.ts, g);
       if (key == kKeyInvalid) fl |= kFOffgrid;
       if (k == n - 1) {
         s_last_ts = cur.ts;
@@ -326,27 +562,17 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         o.key[gp] = key;
         o.flags[gp] = fl;
       }
+      dist += d;
+      dwell_sum += dw;
+      n_dup += (fl & kFDup) ? 1 : 0;
+      n_off += (key == kKeyInvalid) ? 1 : 0;
     }
-    s_key[tid] = key;
-    s_spd[tid] = cur.spd;
-    // journey partial sums, in a fixed order
-    double sd = block_sum<kJBlock, double>(d, red_d);
-    long long sw = block_sum<kJBlock, long long>((long long)dw, red_i);
-    long long sdup = block_sum<kJBlock, long long>((fl & kFDup) ? 1 : 0, red_i);
-    long long soff = block_sum<kJBlock, long long>((active && key == kKeyInvalid) ? 1 : 0, red_i);
-    if (tid == 0) {
-      dist += sd;
-      dwell_sum += sw;
-      n_dup += sdup;
-      n_off += soff;
-    }
-    // (block_sum ends with __syncthreads, so s_key / s_spd are visible here)
     // runs of equal valid keys: the carried run first (thread 0), then runs starting here
     if (tid == 0 && prevc != kKeyInvalid) {
       if (s_key[0] == prevc) {
         int e = 0;
         while (e < kJBlock && s_key[e] == prevc) {
-          float v = s_spd[e];
+          const float v = s_spd[e];
           c_cnt += 1;
           c_sum += (double)v;
           c_min = fminf(c_min, v);
@@ -362,15 +588,14 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         c_key = kKeyInvalid;
       }
     }
-    const uint32_t mk = s_key[tid];
-    const bool head = mk != kKeyInvalid && (tid == 0 ? mk != prevc : mk != s_key[tid - 1]);
+    const bool head = key != kKeyInvalid && (tid == 0 ? key != prevc : key != s_key[tid - 1]);
     if (head) {
       int e = tid;
       uint32_t cnt = 0;
       double sum = 0.0;
       float mn = s_spd[tid], mx = s_spd[tid];
-      while (e < kJBlock && s_key[e] == mk) {
-        float v = s_spd[e];
+      while (e < kJBlock && s_key[e] == key) {
+        const float v = s_spd[e];
         cnt += 1;
         sum += (double)v;
         mn = fminf(mn, v);
@@ -379,9 +604,9 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
       }
       const uint32_t start = off + (uint32_t)(s0 + tid);
       if (e < kJBlock) {
-        emit_run(o, st, mk, cnt, sum, mn, mx, start);
-      } else {  // open at the slice end: becomes the carried run
-        o_key = mk;
+        emit_run(o, st, key, cnt, sum, mn, mx, start);
+      } else {  // open at the slice end: carried into the next slice
+        o_key = key;
         o_cnt = cnt;
         o_sum = sum;
         o_min = mn;
@@ -389,39 +614,44 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         o_start = start;
       }
     }
-    __syncthreads();
-    if (tid == 0 && o_key != kKeyInvalid) {
+    __syncthreads();  // ---- S2
+    if (tid == kJBlock - 1) {  // last point of this slice, for the next slice's first lane
+      e_ts[0] = cur.ts;
+      e_lat[0] = cur.lat;
+      e_lon[0] = cur.lon;
+      e_cos[0] = ccur;
+      e_spd[0] = cur.spd;
+    }
+  }
+  // journey sums: per-thread partials (fixed assignment of points to threads), fixed tree
+  const double sd = block_sum<kJBlock, double>(dist, red_d);
+  const long long sw = block_sum<kJBlock, long long>(dwell_sum, red_i);
+  const long long sdup = block_sum<kJBlock, long long>(n_dup, red_i);
+  const long long soff = block_sum<kJBlock, long long>(n_off, red_i);
+  if (tid == 0) {
+    if (o_key != kKeyInvalid) {  // a run open at the end of the last full slice
+      if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
       c_key = o_key;
       c_cnt = o_cnt;
       c_sum = o_sum;
       c_min = o_min;
       c_max = o_max;
       c_start = o_start;
-      o_key = kKeyInvalid;
     }
-    if (tid == kJBlock - 1) {  // last point of this slice, for the next slice's first lane
-      e_ts[0] = cur.ts;
-      e_lat[0] = cur.lat;
-      e_lon[0] = cur.lon;
-      e_spd[0] = cur.spd;
-    }
-    __syncthreads();
-  }
-  if (tid == 0) {
     if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
     o.n[j] = n;
     o.off[j] = off;
     o.start_ts[j] = s_first_ts;
     o.end_ts[j] = s_last_ts;
     o.duration[j] = (int64_t)((unsigned long long)s_last_ts - (unsigned long long)s_first_ts);
-    o.dist[j] = dist;
-    o.dwell[j] = dwell_sum;
+    o.dist[j] = sd;
+    o.dwell[j] = sw;
     o.slat[j] = s_first_lat;
     o.slon[j] = s_first_lon;
     o.elat[j] = s_last_lat;
     o.elon[j] = s_last_lon;
-    if (n_dup) atomicAdd(&st->n_dup, (unsigned long long)n_dup);
-    if (n_off) atomicAdd(&st->n_offgrid, (unsigned long long)n_off);
+    if (sdup) atomicAdd(&st->n_dup, (unsigned long long)sdup);
+    if (soff) atomicAdd(&st->n_offgrid, (unsigned long long)soff);
   }
 }
 
