@@ -400,6 +400,9 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.t_span = span > (unsigned __int128)~0ull ? ~0ull : (unsigned long long)span;
   g.v_stop = cfg->v_stop_kmh;
   g.radius_m = cfg->earth_radius_m;
+  g.asin_c1 = 2.0 * cfg->earth_radius_m;
+  g.asin_c2 = g.asin_c1 / 6.0;
+  g.asin_c3 = g.asin_c1 * 0.075;
   if (cudaFuncSetAttribute(k_journeys, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kJCap * (int)sizeof(Elem)) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,

@@ -19,6 +19,7 @@ struct GridParams {
   float v_stop;
   double radius_m;
   const double4* cos_tab;  // k = -9000..9000: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, 0}
+  double asin_c1, asin_c2, asin_c3;  // 2R, 2R/6, 2R*3/40: d = sqrt(h) (c1 + h (c2 + h c3))
 };
 
 struct JourneyOut {
@@ -225,27 +226,26 @@ __device__ __forceinline__ bool tiny_angle(double x) {
 }
 
 __device__ __forceinline__ double haversine_fast(double la1, double lo1, double c1, double la2,
-                                                 double lo2, double c2, double R) {
+                                                 double lo2, double c2, const GridParams& g) {
   const double a = (la2 - la1) * kHalfRad;
   const double b = (lo2 - lo1) * kHalfRad;
   if (tiny_angle(a) && tiny_angle(b)) {
     const double a2 = a * a, b2 = b * b;
     const double sa = a2 * fma(a2, -1.0 / 3.0, 1.0);
     const double sb = b2 * fma(b2, -1.0 / 3.0, 1.0);
-    const double h = fma(c1 * c2, sb, sa);
-    if (h == 0.0) return 0.0;
+    const double h = fma(c1 * c2, sb, sa);  // h >= 0
+    if (__double_as_longlong(h) == 0) return 0.0;
     const float hf = leading_f32(h);
     if (hf > 0.0f) {
       const float y = rsqrtf(hf);
-      const double yd = (double)y, yh = (double)(0.5f * y);
+      const double yd = (double)y, yh = 0.5 * yd;
       double s = h * yd;
       s = fma(fma(-s, s, h), yh, s);
       s = fma(fma(-s, s, h), yh, s);
-      const double R2 = 2.0 * R;
-      return s * fma(h, fma(h, R2 * 0.075, R2 / 6.0), R2);
+      return s * fma(h, fma(h, g.asin_c3, g.asin_c2), g.asin_c1);
     }
   }
-  return haversine_m(la1, lo1, la2, lo2, R);
+  return haversine_m(la1, lo1, la2, lo2, g.radius_m);
 }
 
 // ---------------------------------------------------------------- CTA-wide radix sort
@@ -358,6 +358,15 @@ __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* 
 }
 
 // ---------------------------------------------------------------- the journey kernel
+// Speed sums of a run: compensated float32 pairs (Neumaier's variant of Kahan summation; the
+// error stays below ~2^-45 relative for runs of any practical length), folded into binary64
+// once per run.
+__device__ __forceinline__ void fsum_add(float& s, float& c, float v) {
+  const float t = s + v;
+  c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+  s = t;
+}
+
 __device__ __forceinline__ void emit_run(const JourneyOut& o, DevState* st, uint32_t key, uint32_t cnt,
                                          double sum, float mn, float mx, uint32_t start) {
   uint32_t i = atomicAdd(&st->n_runs, 1u);
@@ -387,7 +396,7 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   __shared__ uint32_t s_key[kJBlock];
   __shared__ float s_spd[kJBlock];
   __shared__ uint32_t c_key, c_cnt, c_start, o_key, o_cnt, o_start, s_prevc;
-  __shared__ double c_sum, o_sum;
+  __shared__ float c_sum, c_cmp, o_sum, o_cmp;
   __shared__ float c_min, c_max, o_min, o_max;
   __shared__ double red_d[kJBlock / 32];
   __shared__ long long red_i[kJBlock / 32];
@@ -480,6 +489,7 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         c_key = o_key;
         c_cnt = o_cnt;
         c_sum = o_sum;
+        c_cmp = o_cmp;
         c_min = o_min;
         c_max = o_max;
         c_start = o_start;
@@ -534,10 +544,10 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
       } else {
         const int64_t dt = (int64_t)((unsigned long long)cur.ts - (unsigned long long)p_ts);
         if (dt == 0) fl |= kFDup;
-        d = haversine_fast(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g.radius_m);
+        d = haversine_fast(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g);
         if (dt > 0) {
           // stored as float32: computed in float32 from the binary64 distance
-          const float fdt = (float)dt;
+          const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : (float)dt;
           vh = (float)d * (3600.0f / fdt);
           ac = (cur.spd - p_spd) / (0.0036f * fdt);
         }
@@ -574,17 +584,17 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         while (e < kJBlock && s_key[e] == prevc) {
           const float v = s_spd[e];
           c_cnt += 1;
-          c_sum += (double)v;
+          fsum_add(c_sum, c_cmp, v);
           c_min = fminf(c_min, v);
           c_max = fmaxf(c_max, v);
           ++e;
         }
         if (e < kJBlock) {
-          emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
+          emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
           c_key = kKeyInvalid;
         }
       } else {
-        emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
+        emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
         c_key = kKeyInvalid;
       }
     }
@@ -592,23 +602,24 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
     if (head) {
       int e = tid;
       uint32_t cnt = 0;
-      double sum = 0.0;
+      float sum = 0.0f, cmp = 0.0f;
       float mn = s_spd[tid], mx = s_spd[tid];
       while (e < kJBlock && s_key[e] == key) {
         const float v = s_spd[e];
         cnt += 1;
-        sum += (double)v;
+        fsum_add(sum, cmp, v);
         mn = fminf(mn, v);
         mx = fmaxf(mx, v);
         ++e;
       }
       const uint32_t start = off + (uint32_t)(s0 + tid);
       if (e < kJBlock) {
-        emit_run(o, st, key, cnt, sum, mn, mx, start);
+        emit_run(o, st, key, cnt, (double)sum + (double)cmp, mn, mx, start);
       } else {  // open at the slice end: carried into the next slice
         o_key = key;
         o_cnt = cnt;
         o_sum = sum;
+        o_cmp = cmp;
         o_min = mn;
         o_max = mx;
         o_start = start;
@@ -630,15 +641,16 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   const long long soff = block_sum<kJBlock, long long>(n_off, red_i);
   if (tid == 0) {
     if (o_key != kKeyInvalid) {  // a run open at the end of the last full slice
-      if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
+      if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
       c_key = o_key;
       c_cnt = o_cnt;
       c_sum = o_sum;
+      c_cmp = o_cmp;
       c_min = o_min;
       c_max = o_max;
       c_start = o_start;
     }
-    if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, c_sum, c_min, c_max, c_start);
+    if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
     o.n[j] = n;
     o.off[j] = off;
     o.start_ts[j] = s_first_ts;
