@@ -403,8 +403,7 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c1 = 2.0 * cfg->earth_radius_m;
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
-  if (cudaFuncSetAttribute(k_journeys, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kJCap * (int)sizeof(Elem)) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_journeys, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -599,7 +598,7 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("run.max", nv, &o.run_max);
   o.run_cap = (uint32_t)nv;
   if (J) {
-    LAUNCH(ST_JOURNEYS, (k_journeys<<<J, kJBlock, kJCap * sizeof(Elem), c->st>>>(
+    LAUNCH(ST_JOURNEYS, (k_journeys<<<J, kJBlock, kJSmem, c->st>>>(
                             rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
     LAUNCH_CHECK();
   }

@@ -8,6 +8,11 @@ namespace cvetl {
 
 constexpr int kJBlock = 256;   // threads per journey CTA
 constexpr int kJCap = 4096;    // records sorted in shared memory in one piece
+constexpr int kBucketsBig = 16384;  // time buckets for journeys above kJCap (counters in shared memory)
+// dynamic shared memory of the journey kernel: two kJCap key buffers + kJCap bucket counters,
+// or (journeys above kJCap, keys in global scratch) kBucketsBig counters
+constexpr int kJSmem = 2 * kJCap * 8 + kJCap * 4;
+static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
 
 struct GridParams {
   const unsigned long long* row_thr;  // n_rows + 1 ordered thresholds (see keying below)
@@ -332,6 +337,68 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
   return A;
 }
 
+// Counting sort of a journey's keys by a monotone time bucket, then insertion sort inside each
+// bucket. Timestamps of a journey are spread almost evenly over its span (regular sampling),
+// so with about one bucket per point the buckets hold a few keys each and the sort is O(n).
+// bucket(t) = min(nb - 1, floor(float(t) * nb / (span + 1))) is non-decreasing in t, so the
+// buckets' concatenation is in key order once each bucket is sorted. Returns false, with the
+// keys untouched in A, when some bucket holds more than kMaxBucket keys (then the caller uses
+// the radix sort). cnt: nb counters in shared memory. The sorted keys end in B.
+constexpr int kMaxBucket = 48;
+
+__device__ bool cta_bucket_sort(const unsigned long long* A, unsigned long long* B, int n, int pos_bits,
+                                unsigned long long span, uint32_t* cnt, int nb, uint32_t* scan_scratch,
+                                int* flag) {
+  const int tid = threadIdx.x;
+  const float scale = (float)nb / ((float)span + 1.0f);
+  for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += kJBlock) {
+    const int b = min(nb - 1, (int)(__ull2float_rz(A[i] >> pos_bits) * scale));
+    atomicAdd(&cnt[b], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of the counters; each thread owns a contiguous chunk
+  const int chunk = (nb + kJBlock - 1) / kJBlock;
+  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
+  uint32_t sum = 0, mx = 0;
+  for (int i = c0; i < c1; ++i) {
+    sum += cnt[i];
+    mx = max(mx, cnt[i]);
+  }
+  if (tid == 0) *flag = 0;
+  uint32_t base = block_excl_scan<kJBlock>(sum, scan_scratch, nullptr);
+  if (mx > (uint32_t)kMaxBucket) *flag = 1;
+  for (int i = c0; i < c1; ++i) {
+    const uint32_t v = cnt[i];
+    cnt[i] = base;
+    base += v;
+  }
+  __syncthreads();
+  if (*flag) return false;
+  for (int i = tid; i < n; i += kJBlock) {
+    const unsigned long long k = A[i];
+    const int b = min(nb - 1, (int)(__ull2float_rz(k >> pos_bits) * scale));
+    B[atomicAdd(&cnt[b], 1u)] = k;
+  }
+  __syncthreads();
+  // cnt[b] is now the end of bucket b; sort each bucket by key value
+  for (int b = tid; b < nb; b += kJBlock) {
+    const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
+    for (int i = lo + 1; i < hi; ++i) {
+      const unsigned long long v = B[i];
+      int q = i - 1;
+      while (q >= lo && B[q] > v) {
+        B[q + 1] = B[q];
+        --q;
+      }
+      B[q + 1] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
 // slot (arbitrary) here; reorder each such group by extracted-row index.
 __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
@@ -401,6 +468,7 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   __shared__ double red_d[kJBlock / 32];
   __shared__ long long red_i[kJBlock / 32];
   __shared__ unsigned long long s_tmin, s_tmax;
+  __shared__ int s_flag;
   __shared__ int64_t s_first_ts, s_last_ts;
   __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
 
@@ -450,7 +518,15 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
     // 1b. packed keys ((ts - tmin) << pos_bits) | slot, radix-sorted, ties by row index
     for (int i = tid; i < n; i += kJBlock) KA[i] = ((KA[i] - tmin) << pos_bits) | (unsigned long long)i;
     __syncthreads();
-    unsigned long long* K = cta_radix_sort(KA, KB, n, nbits, ssort);
+    uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + 2 * kJCap * sizeof(unsigned long long))
+                          : reinterpret_cast<uint32_t*>(smem_raw);
+    const int nb = small ? max(1, n) : min(n, kBucketsBig);
+    unsigned long long* K;
+    if (n > kBucketsBig * 8 || !cta_bucket_sort(KA, KB, n, pos_bits, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
+      K = cta_radix_sort(KA, KB, n, nbits, ssort);
+    } else {
+      K = KB;
+    }
     fix_ties(K, n, pos_bits, R);
     sortedK = K;
   } else {
