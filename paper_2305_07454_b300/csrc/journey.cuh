@@ -7,8 +7,9 @@
 namespace cvetl {
 
 constexpr int kJBlock = 256;   // threads per journey CTA
-constexpr int kJCap = 4096;    // records sorted in shared memory in one piece
-constexpr int kBucketsBig = 16384;  // time buckets for journeys above kJCap (counters in shared memory)
+constexpr int kJCap = 3072;    // records sorted in shared memory in one piece
+constexpr int kBucketsBig = 15360;  // time buckets for journeys above kJCap (counters in shared memory)
+constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memory chunk (fallback)
 // dynamic shared memory of the journey kernel: two kJCap key buffers + kJCap bucket counters,
 // or (journeys above kJCap, keys in global scratch) kBucketsBig counters
 constexpr int kJSmem = 2 * kJCap * 8 + kJCap * 4;
@@ -162,12 +163,12 @@ __device__ __forceinline__ int merge_path(const Elem* A, int la, const Elem* B, 
   return lo;
 }
 
-// Sorts a journey larger than kJCap: shared-memory bitonic sort of kJCap chunks, then rounds
+// Sorts a journey by (timestamp, row) pairs: shared-memory bitonic sort of kEChunk chunks, then rounds
 // of CTA-wide merge-path merges between two global scratch buffers. Returns the buffer
 // holding the sorted elements.
 __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem* A, Elem* B) {
-  for (int c0 = 0; c0 < n; c0 += kJCap) {
-    int m = min(kJCap, n - c0);
+  for (int c0 = 0; c0 < n; c0 += kEChunk) {
+    int m = min(kEChunk, n - c0);
     int P = 1;
     while (P < m) P <<= 1;
     load_elems(E, R, c0, m, P);
@@ -176,7 +177,7 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem*
     __syncthreads();
   }
   Elem *src = A, *dst = B;
-  for (int L = kJCap; L < n; L <<= 1) {
+  for (int L = kEChunk; L < n; L <<= 1) {
     for (int a0 = 0; a0 < n; a0 += 2 * L) {
       int la = min(L, n - a0);
       int lb = max(0, min(L, n - a0 - la));
@@ -255,10 +256,12 @@ __device__ __forceinline__ double haversine_fast(double la1, double lo1, double 
 
 // ---------------------------------------------------------------- CTA-wide radix sort
 // Stable LSD radix sort of n 64-bit keys (8-bit digits over bits [0, nbits)) by one CTA.
-// A and B are shared memory for n <= kJCap, else global scratch (a journey's scratch stays in
+// A and B are shared memory for n <= kJCap (one tile), else global scratch (a journey's scratch stays in
 // L2 while its CTA works on it). Ranking inside a 4096-key tile uses warp match + popc, as in
 // the device-wide sort; multi-tile passes add a digit histogram and carry running offsets
 // from tile to tile in order, which keeps the sort stable.
+constexpr int kRTile = 16 * kJBlock;  // keys ranked per tile: 16 per thread
+
 struct SortSmem {
   uint16_t wcnt[kJBlock / 32][256];
   uint32_t run[256];
@@ -268,7 +271,7 @@ struct SortSmem {
 __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned long long* B, int n,
                                               int nbits, SortSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool one_tile = n <= kJCap;
+  const bool one_tile = n <= kRTile;
   for (int shift = 0; shift < nbits; shift += 8) {
     if (!one_tile) {
       sm.run[tid] = 0;
@@ -280,8 +283,8 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
       sm.run[tid] = e;
       __syncthreads();
     }
-    for (int t0 = 0; t0 < n; t0 += kJCap) {
-      const int m = min(kJCap, n - t0);
+    for (int t0 = 0; t0 < n; t0 += kRTile) {
+      const int m = min(kRTile, n - t0);
       for (int i = tid; i < (kJBlock / 32) * 256; i += kJBlock) (&sm.wcnt[0][0])[i] = 0;
       __syncthreads();
       unsigned long long key[16];
@@ -309,7 +312,7 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
         sm.wcnt[w][tid] = (uint16_t)cnt;
         cnt += c;
       }
-      const uint32_t cnt_valid = cnt - ((tid == 255) ? (uint32_t)(kJCap - m) : 0u);
+      const uint32_t cnt_valid = cnt - ((tid == 255) ? (uint32_t)(kRTile - m) : 0u);
       uint32_t base;
       if (one_tile) base = block_excl_scan<kJBlock>(cnt, sm.scan, nullptr);
       else base = sm.run[tid];
@@ -450,21 +453,43 @@ __device__ __forceinline__ void emit_run(const JourneyOut& o, DevState* st, uint
 
 __device__ __forceinline__ int bits_for(unsigned long long v) { return v ? 64 - __clzll(v) : 0; }
 
-__global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ rec,
-                                                      const uint32_t* __restrict__ jn,
-                                                      const uint32_t* __restrict__ joff, uint32_t J,
-                                                      Elem* scrA, Elem* scrB, GridParams g,
-                                                      JourneyOut o, DevState* st) {
+// Run fragments a thread hands to the stitch at the end of the walk.
+struct RunPart {
+  uint32_t key, cnt, start;
+  float s, c, mn, mx;
+};
+
+__device__ __forceinline__ void run_add(RunPart& r, float v) {
+  r.cnt += 1;
+  fsum_add(r.s, r.c, v);
+  r.mn = fminf(r.mn, v);
+  r.mx = fmaxf(r.mx, v);
+}
+__device__ __forceinline__ void run_merge(RunPart& r, const RunPart& q) {
+  r.cnt += q.cnt;
+  fsum_add(r.s, r.c, q.s);
+  r.c += q.c;
+  r.mn = fminf(r.mn, q.mn);
+  r.mx = fmaxf(r.mx, q.mx);
+}
+__device__ __forceinline__ void run_emit(const JourneyOut& o, DevState* st, const RunPart& r) {
+  if (r.key != kKeyInvalid && r.cnt) emit_run(o, st, r.key, r.cnt, (double)r.s + (double)r.c, r.mn, r.mx, r.start);
+}
+
+struct StitchSmem {
+  RunPart pre[kJBlock];  // run continuing from the previous thread's range (cnt 0: none)
+  RunPart suf[kJBlock];  // run open at the end of the range
+  uint8_t has[kJBlock];  // the thread had points
+  uint8_t cont[kJBlock]; // the whole range continued the previous thread's run
+};
+
+__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
+                                                         const uint32_t* __restrict__ jn,
+                                                         const uint32_t* __restrict__ joff, uint32_t J,
+                                                         Elem* scrA, Elem* scrB, GridParams g,
+                                                         JourneyOut o, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SortSmem ssort;
-  __shared__ int64_t e_ts[kJBlock / 32 + 1];
-  __shared__ double e_lat[kJBlock / 32 + 1], e_lon[kJBlock / 32 + 1], e_cos[kJBlock / 32 + 1];
-  __shared__ float e_spd[kJBlock / 32 + 1];
-  __shared__ uint32_t s_key[kJBlock];
-  __shared__ float s_spd[kJBlock];
-  __shared__ uint32_t c_key, c_cnt, c_start, o_key, o_cnt, o_start, s_prevc;
-  __shared__ float c_sum, c_cmp, o_sum, o_cmp;
-  __shared__ float c_min, c_max, o_min, o_max;
   __shared__ double red_d[kJBlock / 32];
   __shared__ long long red_i[kJBlock / 32];
   __shared__ unsigned long long s_tmin, s_tmax;
@@ -474,7 +499,7 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
 
   const uint32_t j = blockIdx.x;
   if (j >= J) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
@@ -515,7 +540,8 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
   const unsigned long long* sortedK = nullptr;
   const Elem* sortedE = nullptr;
   if (radix) {
-    // 1b. packed keys ((ts - tmin) << pos_bits) | slot, radix-sorted, ties by row index
+    // 1b. packed keys ((ts - tmin) << pos_bits) | slot; counting sort by time bucket (radix
+    // sort when the buckets are crowded); ties by row index
     for (int i = tid; i < n; i += kJBlock) KA[i] = ((KA[i] - tmin) << pos_bits) | (unsigned long long)i;
     __syncthreads();
     uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + 2 * kJCap * sizeof(unsigned long long))
@@ -533,81 +559,39 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
     // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
     __syncthreads();
     if (tid == 0) atomicAdd(&st->n_big, 1u);
-    Elem* E = reinterpret_cast<Elem*>(smem_raw);
-    if (small) {
-      int P = 1;
-      while (P < n) P <<= 1;
-      load_elems(E, R, 0, n, P);
-      bitonic_smem(E, P);
-      sortedE = E;
-    } else {
-      sortedE = sort_big(E, R, n, scrA + off, scrB + off);
-    }
+    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
   }
   const unsigned long long pmask = (1ull << pos_bits) - 1;
 
-  if (tid == 0) {
-    c_key = kKeyInvalid;
-    o_key = kKeyInvalid;
-    c_cnt = 0;
-  }
+  // 2. walk: thread t owns the sorted positions [k0, k1) and visits them in order; the
+  // predecessor stays in registers, runs of equal keys accumulate in the thread
+  const int k0 = (int)((long long)n * tid / kJBlock), k1 = (int)((long long)n * (tid + 1) / kJBlock);
   double dist = 0.0;
   long long dwell_sum = 0, n_dup = 0, n_off = 0;
-  __syncthreads();
-
-  // 2. walk the sorted journey, 256 points at a time (two barriers per slice)
-  for (int s0 = 0; s0 < n; s0 += kJBlock) {
-    const int k = s0 + tid;
-    const bool active = k < n;
-    // hand the run left open by the previous slice to the carry; publish its key
-    if (tid == 0) {
-      if (o_key != kKeyInvalid) {
-        c_key = o_key;
-        c_cnt = o_cnt;
-        c_sum = o_sum;
-        c_cmp = o_cmp;
-        c_min = o_min;
-        c_max = o_max;
-        c_start = o_start;
-        o_key = kKeyInvalid;
-      }
-      s_prevc = c_key;
+  RunPart pre{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
+  RunPart run{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
+  bool in_pre = false;  // the open run continues the previous thread's last run
+  bool cont_all = false;
+  if (k0 < k1) {
+    int64_t p_ts = 0;
+    double p_lat = 0.0, p_lon = 0.0, p_cos = 0.0;
+    float p_spd = 0.0f;
+    if (k0 > 0) {  // predecessor: the previous thread's last point
+      const Rec q = R[radix ? (uint32_t)(sortedK[k0 - 1] & pmask) : sortedE[k0 - 1].pos];
+      p_ts = q.ts;
+      p_lat = q.lat;
+      p_lon = q.lon;
+      p_spd = q.spd;
+      p_cos = cos_deg(q.lat, g.cos_tab);
+      run.key = cell_key(q.lat, q.lon, q.ts, g);
+      run.mn = __int_as_float(0x7F800000);   // +inf
+      run.mx = __int_as_float((int)0xFF800000u);  // -inf
+      in_pre = true;  // an empty fragment of the previous thread's run
     }
-    Rec cur;
-    if (active) {
-      const uint32_t p = radix ? (uint32_t)(sortedK[k] & pmask) : sortedE[k].pos;
-      cur = R[p];
-    } else {
-      cur.ts = 0; cur.lat = 0.0; cur.lon = 0.0; cur.spd = 0.0f; cur.idx = 0;
-    }
-    const double ccur = active ? cos_deg(cur.lat, g.cos_tab) : 0.0;
-    const uint32_t key = active ? cell_key(cur.lat, cur.lon, cur.ts, g) : kKeyInvalid;
-    // predecessor: previous lane; lane 0 takes the previous warp's last lane, or the last
-    // point of the previous slice (slot 0)
-    int64_t p_ts = __shfl_up_sync(0xffffffffu, cur.ts, 1);
-    double p_lat = __shfl_up_sync(0xffffffffu, cur.lat, 1);
-    double p_lon = __shfl_up_sync(0xffffffffu, cur.lon, 1);
-    double p_cos = __shfl_up_sync(0xffffffffu, ccur, 1);
-    float p_spd = __shfl_up_sync(0xffffffffu, cur.spd, 1);
-    if (lane == 31) {
-      e_ts[warp + 1] = cur.ts;
-      e_lat[warp + 1] = cur.lat;
-      e_lon[warp + 1] = cur.lon;
-      e_cos[warp + 1] = ccur;
-      e_spd[warp + 1] = cur.spd;
-    }
-    s_key[tid] = key;
-    s_spd[tid] = cur.spd;
-    __syncthreads();  // ---- S1
-    if (lane == 0) {
-      p_ts = e_ts[warp];
-      p_lat = e_lat[warp];
-      p_lon = e_lon[warp];
-      p_cos = e_cos[warp];
-      p_spd = e_spd[warp];
-    }
-    const uint32_t prevc = s_prevc;
-    if (active) {
+    for (int k = k0; k < k1; ++k) {
+      const Rec cur = R[radix ? (uint32_t)(sortedK[k] & pmask) : sortedE[k].pos];
+      const double ccur = cos_deg(cur.lat, g.cos_tab);
+      const uint32_t key = cell_key(cur.lat, cur.lon, cur.ts, g);
       uint8_t fl = 0;
       double d = 0.0;
       float vh = 0.0f, ac = 0.0f;
@@ -633,11 +617,6 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
         }
       }
       if (key == kKeyInvalid) fl |= kFOffgrid;
-      if (k == n - 1) {
-        s_last_ts = cur.ts;
-        s_last_lat = cur.lat;
-        s_last_lon = cur.lon;
-      }
       if (o.perm) {
         const uint32_t gp = off + (uint32_t)k;
         o.perm[gp] = cur.idx;
@@ -652,81 +631,55 @@ __global__ void __launch_bounds__(kJBlock) k_journeys(const Rec* __restrict__ re
       dwell_sum += dw;
       n_dup += (fl & kFDup) ? 1 : 0;
       n_off += (key == kKeyInvalid) ? 1 : 0;
-    }
-    // runs of equal valid keys: the carried run first (thread 0), then runs starting here
-    if (tid == 0 && prevc != kKeyInvalid) {
-      if (s_key[0] == prevc) {
-        int e = 0;
-        while (e < kJBlock && s_key[e] == prevc) {
-          const float v = s_spd[e];
-          c_cnt += 1;
-          fsum_add(c_sum, c_cmp, v);
-          c_min = fminf(c_min, v);
-          c_max = fmaxf(c_max, v);
-          ++e;
+      // runs of equal keys (the first fragment may continue the previous thread's run)
+      if (k > k0 || in_pre) {
+        if (key == run.key) {
+          run_add(run, cur.spd);
+          p_ts = cur.ts; p_lat = cur.lat; p_lon = cur.lon; p_cos = ccur; p_spd = cur.spd;
+          continue;
         }
-        if (e < kJBlock) {
-          emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
-          c_key = kKeyInvalid;
+        if (in_pre) {
+          pre = run;
+          in_pre = false;
+        } else {
+          run_emit(o, st, run);
         }
-      } else {
-        emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
-        c_key = kKeyInvalid;
       }
+      run = RunPart{key, 1u, off + (uint32_t)k, cur.spd, 0.f, cur.spd, cur.spd};
+      p_ts = cur.ts; p_lat = cur.lat; p_lon = cur.lon; p_cos = ccur; p_spd = cur.spd;
     }
-    const bool head = key != kKeyInvalid && (tid == 0 ? key != prevc : key != s_key[tid - 1]);
-    if (head) {
-      int e = tid;
-      uint32_t cnt = 0;
-      float sum = 0.0f, cmp = 0.0f;
-      float mn = s_spd[tid], mx = s_spd[tid];
-      while (e < kJBlock && s_key[e] == key) {
-        const float v = s_spd[e];
-        cnt += 1;
-        fsum_add(sum, cmp, v);
-        mn = fminf(mn, v);
-        mx = fmaxf(mx, v);
-        ++e;
-      }
-      const uint32_t start = off + (uint32_t)(s0 + tid);
-      if (e < kJBlock) {
-        emit_run(o, st, key, cnt, (double)sum + (double)cmp, mn, mx, start);
-      } else {  // open at the slice end: carried into the next slice
-        o_key = key;
-        o_cnt = cnt;
-        o_sum = sum;
-        o_cmp = cmp;
-        o_min = mn;
-        o_max = mx;
-        o_start = start;
-      }
+    if (k1 == n) {
+      s_last_ts = p_ts;
+      s_last_lat = p_lat;
+      s_last_lon = p_lon;
     }
-    __syncthreads();  // ---- S2
-    if (tid == kJBlock - 1) {  // last point of this slice, for the next slice's first lane
-      e_ts[0] = cur.ts;
-      e_lat[0] = cur.lat;
-      e_lon[0] = cur.lon;
-      e_cos[0] = ccur;
-      e_spd[0] = cur.spd;
+    if (in_pre) {  // no key change in the whole range
+      pre = run;
+      cont_all = true;
     }
   }
-  // journey sums: per-thread partials (fixed assignment of points to threads), fixed tree
+  // 3. journey sums in a fixed order; stitch run fragments across thread ranges in order
   const double sd = block_sum<kJBlock, double>(dist, red_d);
   const long long sw = block_sum<kJBlock, long long>(dwell_sum, red_i);
   const long long sdup = block_sum<kJBlock, long long>(n_dup, red_i);
   const long long soff = block_sum<kJBlock, long long>(n_off, red_i);
+  StitchSmem& ss = *reinterpret_cast<StitchSmem*>(smem_raw);  // the sort buffers are done
+  ss.pre[tid] = pre;
+  ss.suf[tid] = run;
+  ss.has[tid] = k0 < k1;
+  ss.cont[tid] = cont_all;
+  __syncthreads();
   if (tid == 0) {
-    if (o_key != kKeyInvalid) {  // a run open at the end of the last full slice
-      if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
-      c_key = o_key;
-      c_cnt = o_cnt;
-      c_sum = o_sum;
-      c_cmp = o_cmp;
-      c_min = o_min;
-      c_max = o_max;
-      c_start = o_start;
+    RunPart open{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < kJBlock; ++t) {
+      if (!ss.has[t]) continue;
+      const RunPart& p = ss.pre[t];
+      if (p.cnt) run_merge(open, p);
+      if (ss.cont[t]) continue;
+      run_emit(o, st, open);
+      open = ss.suf[t];
     }
-    if (c_key != kKeyInvalid) emit_run(o, st, c_key, c_cnt, (double)c_sum + (double)c_cmp, c_min, c_max, c_start);
+    run_emit(o, st, open);
     o.n[j] = n;
     o.off[j] = off;
     o.start_ts[j] = s_first_ts;
