@@ -485,9 +485,12 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
 
   // 1. count journeys (hash table of ids), growing the table if it overflows
+  // start small (2^18 slots stay hot in L2) and grow when the ids do not fit at load <= 1/2
   uint32_t cap = next_pow2(2ull * (n > 256 ? n : 256));
-  if (cap > (1u << 21)) cap = 1u << 21;
+  if (cap > (1u << 18)) cap = 1u << 18;
   Hash h{};
+  uint32_t* row_slot;
+  ENSURE("row.slot", (size_t)n, &row_slot);
   for (;;) {
     ENSURE("hash.keys", (size_t)cap + 1, &h.keys);
     ENSURE("hash.cnt", (size_t)cap + 1, &h.cnt);
@@ -498,8 +501,8 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     CK(cudaMemsetAsync(h.cnt, 0, ((size_t)cap + 1) * 4, c->st));
     CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
     if (n) {
-      LAUNCH(ST_HASH, (k_hash_count<<<grid_for(n, 256), 256, 0, c->st>>>(c->jid, c->lat, c->lon,
-                                                                          c->spd, n, h, c->dstate)));
+      LAUNCH(ST_HASH, (k_hash_count<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(c->jid, c->lat, c->lon,
+                                                                          c->spd, n, h, row_slot, c->dstate)));
       LAUNCH_CHECK();
     }
     cvetl_status s = read_state(c);
@@ -554,8 +557,8 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   Rec* rec;
   ENSURE("rec", nv, &rec);
   if (n) {
-    LAUNCH(ST_SCATTER, (k_scatter<<<grid_for(n, 256), 256, 0, c->st>>>(c->jid, c->ts, c->lat, c->lon,
-                                                                       c->spd, n, h, rec, c->dstate)));
+    LAUNCH(ST_SCATTER, (k_scatter<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
+                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)));
     LAUNCH_CHECK();
   }
 

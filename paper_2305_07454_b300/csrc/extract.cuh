@@ -65,21 +65,41 @@ __device__ __forceinline__ int64_t hash_find(const Hash& h, uint64_t key) {
   return -1;
 }
 
+constexpr int kUnroll = 4;  // records per thread per iteration: independent probe chains in flight
+
 __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ jid,
                                                     const double* __restrict__ lat,
                                                     const double* __restrict__ lon,
                                                     const float* __restrict__ spd, uint32_t n,
-                                                    Hash h, DevState* st) {
+                                                    Hash h, uint32_t* __restrict__ row_slot,
+                                                    DevState* st) {
   __shared__ unsigned long long scratch[8];
   unsigned long long bad = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (!row_valid(lat[i], lon[i], spd[i])) {
-      ++bad;
-      continue;
+  const uint32_t step = gridDim.x * blockDim.x * kUnroll;
+  for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll + threadIdx.x; i0 < n; i0 += step) {
+    uint64_t id[kUnroll];
+    bool ok[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t i = i0 + u * blockDim.x;
+      ok[u] = i < n && row_valid(lat[i], lon[i], spd[i]);
+      id[u] = (i < n) ? (uint64_t)jid[i] : 0;
+      if (i < n && !ok[u]) ++bad;
     }
-    int64_t s = hash_insert(h, (uint64_t)jid[i], &st->n_distinct);
-    if (s < 0) atomicOr(&st->err, kErrHashOverflow);
-    else atomicAdd(&h.cnt[s], 1u);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t i = i0 + u * blockDim.x;
+      uint32_t slot = kKeyInvalid;  // dropped row
+      if (ok[u]) {
+        int64_t s = hash_insert(h, id[u], &st->n_distinct);
+        if (s < 0) atomicOr(&st->err, kErrHashOverflow);
+        else {
+          atomicAdd(&h.cnt[s], 1u);
+          slot = (uint32_t)s;
+        }
+      }
+      if (i < n) row_slot[i] = slot;
+    }
   }
   unsigned long long b = block_sum<256, unsigned long long>(bad, scratch);
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_malformed, b);
@@ -124,36 +144,39 @@ __global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J
 }
 
 // Every kept row goes to its journey's bucket (the order inside a bucket is arbitrary; the
-// journey kernel sorts it by (timestamp, row index)).
-__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ jid,
-                                                 const int64_t* __restrict__ ts,
+// journey kernel sorts it by (timestamp, row index)). The counting pass left each row's hash
+// slot (or kKeyInvalid for a dropped row), so no probe is needed here. Four rows per thread per
+// iteration keep four atomic -> store chains in flight; each record is one 32-byte store.
+__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lat,
                                                  const double* __restrict__ lon,
-                                                 const float* __restrict__ spd, uint32_t n, Hash h,
-                                                 Rec* __restrict__ rec, DevState* st) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double la = lat[i], lo = lon[i];
-    float sp = spd[i];
-    if (!row_valid(la, lo, sp)) continue;
-    int64_t s = hash_find(h, (uint64_t)jid[i]);
-    if (s < 0) {
-      atomicOr(&st->err, kErrHashMissing);
-      continue;
+                                                 const float* __restrict__ spd,
+                                                 const uint32_t* __restrict__ row_slot, uint32_t n,
+                                                 Hash h, Rec* __restrict__ rec) {
+  const uint32_t step = gridDim.x * blockDim.x * kUnroll;
+  for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll + threadIdx.x; i0 < n; i0 += step) {
+    uint32_t slot[kUnroll], pos[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t i = i0 + u * blockDim.x;
+      slot[u] = (i < n) ? row_slot[i] : kKeyInvalid;
     }
-    uint32_t pos = atomicAdd(&h.aux[s], 1u);
-    int64_t t = ts[i];
-    uint4 a, b;
-    a.x = (uint32_t)(uint64_t)t;
-    a.y = (uint32_t)((uint64_t)t >> 32);
-    a.z = (uint32_t)__double2loint(la);
-    a.w = (uint32_t)__double2hiint(la);
-    b.x = (uint32_t)__double2loint(lo);
-    b.y = (uint32_t)__double2hiint(lo);
-    b.z = (uint32_t)__float_as_int(canon_speed(sp));
-    b.w = i;
-    uint4* dst = reinterpret_cast<uint4*>(rec + pos);
-    dst[0] = a;
-    dst[1] = b;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      pos[u] = (slot[u] != kKeyInvalid) ? atomicAdd(&h.aux[slot[u]], 1u) : 0u;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (slot[u] == kKeyInvalid) continue;
+      const uint32_t i = i0 + u * blockDim.x;
+      const unsigned long long a = (unsigned long long)ts[i];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(lat[i]);
+      const unsigned long long c = (unsigned long long)__double_as_longlong(lon[i]);
+      const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(spd[i])) |
+                                   ((unsigned long long)i << 32);
+      asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + pos[u]), "l"(a), "l"(b),
+                   "l"(c), "l"(d)
+                   : "memory");
+    }
   }
 }
 
