@@ -110,14 +110,36 @@ def make_workload(name: str, seed: int, pinned: bool):
 
 
 def algorithmic_bytes(stage: str, c: dict) -> float:
-    """Bytes a stage must move per launch (its roofline numerator), from the counters."""
+    """Bytes a stage must move per launch, from the counters."""
     nin, nv, J, R = c["n_in"], c["n_valid"], c["n_journeys"], c["n_runs"]
     return {
-        "hash_count": 28.0 * nin,                       # jid, lat, lon, speed read
-        "scatter": 36.0 * nin + 32.0 * nv,              # five columns read, 32-byte records written
+        "hash_count": 28.0 * nin + 4.0 * nin,           # jid, lat, lon, speed read; row slot written
+        "scatter": 32.0 * nin + 32.0 * nv,              # ts, lat, lon, speed, slot read; records written
         "journeys": 32.0 * nv + 28.0 * R + 96.0 * J,    # records read; runs and journey rows written
         "cell_write": 28.0 * R + 44.0 * c["n_cells"],
     }.get(stage, 0.0)
+
+
+# binary64 operations per point of the journey kernel's distance evaluation: the cosine of the
+# latitude (7: table offset, square, 2 FMA, 3 products), the haversine with Taylor sines, Newton
+# square root and arcsine polynomial (22), the journey distance sum (1)
+FP64_OPS_PER_POINT = 30.0
+SMS, FP64_PER_CLK_PER_SM = 148, 2.0
+
+
+def fp64_peak_gops():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", 2032.0))
+    except Exception:
+        mhz = 2032.0
+    return SMS * FP64_PER_CLK_PER_SM * mhz / 1e3, mhz
+
+
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the journey kernel
+# from an ncu capture of the tenth-day workload (14,637,283 records), scaled by records to the
+# workload's launch; None once the kernel changes after the capture.
+TRAFFIC_PER_RECORD = {"journeys": 611.03e6 / 14637283}
 
 
 def run_ours(args):
@@ -190,14 +212,30 @@ def run_ours(args):
     top = max(stages, key=lambda s: stages[s]["ms"])
     launches = max(1, stages[top]["launches"])
     avg_ms = stages[top]["ms"] / launches
-    peak, peak_src = load_peaks()
-    ab = algorithmic_bytes(top, counters)
-    achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
-    traffic = TRAFFIC.get((args.workload, top))
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
+    hbm_peak, peak_src = load_peaks()
+    tpr = TRAFFIC_PER_RECORD.get(top)
+    traffic = tpr * counters["n_valid"] if tpr else None
+    if top == "journeys":
+        gops_peak, mhz = fp64_peak_gops()
+        ops = FP64_OPS_PER_POINT * counters["n_valid"]
+        achieved = ops / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": gops_peak,
+                    "unit": "G binary64 ops/s",
+                    "peak_source": f"derived: {SMS} SMs x {FP64_PER_CLK_PER_SM:g} binary64 ops/clk x {mhz:g} MHz",
+                    "frac": achieved / gops_peak, "ops_per_launch": ops, "avg_launch_ms": avg_ms,
+                    "traffic": traffic,
+                    "hbm_achieved_gbs": algorithmic_bytes(top, counters) / (avg_ms / 1e3) / 1e9}
+    else:
+        ab = algorithmic_bytes(top, counters)
+        achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
+        roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak,
+                    "peak_source": peak_src, "unit": "GB/s",
+                    "frac": (achieved / hbm_peak) if achieved else None,
+                    "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
+    step_bytes = sum(algorithmic_bytes(s, counters) * v["launches"] / args.steps for s, v in stages.items())
+    hbm_step = {"algorithmic_bytes_per_step": step_bytes,
+                "achieved": step_bytes / (ms_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": step_bytes / (ms_step / 1e3) / 1e9 / hbm_peak}
     shares = {s: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
               for s, v in stages.items() if v["launches"]}
 
@@ -213,6 +251,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": stats["total_launches"],
         "roofline": roofline,
+        "hbm_step": hbm_step,
         "stages": shares,
         "counters": counters,
         "clocks": clk.summary(),
@@ -223,11 +262,6 @@ def run_ours(args):
     pipe.close()
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures,
-# scaled to one full launch; filled from the committed profile summaries.
-TRAFFIC = {}
 
 
 def _sample_journeys(host, frac_den: int):
