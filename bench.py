@@ -155,9 +155,28 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     host, n, J = make_workload(args.workload, seed=1 + rank, pinned=True)
+    csv_host = None
+    if args.input == "csv":
+        import cvgen
+
+        text, _ = cvgen.to_csv({k: host[k].numpy() for k in host}, seed=1 + rank, malformed_frac=0.005)
+        csv_host = torch.from_numpy(text).pin_memory()
+        d_csv = csv_host.to(dev, non_blocking=True)
     d_in = {k: host[k].to(dev, non_blocking=True) for k in COLS}
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+
+    def extract_dev(p):
+        if csv_host is None:
+            p.extract(d_in)
+        else:
+            p.extract_csv(d_csv)
+
+    def run_dev(p):
+        extract_dev(p)
+        p.transform()
+        p.load()
+        return p.results(to_host=False)
 
     def barrier():
         if world > 1:
@@ -167,14 +186,14 @@ def run_ours(args):
     # ---- device-resident steps ------------------------------------------------------------
     pipe = P.Pipeline(stream=stream, profile=1)
     for _ in range(args.warmup):
-        pipe.run(d_in, to_host=False)
+        run_dev(pipe)
     pipe.stats_reset()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            pipe.extract(d_in)
+            extract_dev(pipe)
             pipe.transform()
             pipe.load()
             pipe.tables()  # reads the sizes and counters back (synchronises the stream)
@@ -196,14 +215,24 @@ def run_ours(args):
     # ---- end to end through the C ABI with host inputs ------------------------------------
     e2e_steps = max(1, min(args.steps, 3))
     pipe_h = P.Pipeline(stream=stream)
-    pipe_h.run({k: host[k] for k in COLS}, to_host=True)
+
+    def run_host():
+        if csv_host is None:
+            pipe_h.extract({k: host[k] for k in COLS})
+        else:
+            pipe_h.extract_csv(csv_host)
+        pipe_h.transform()
+        pipe_h.load()
+        return pipe_h.results(to_host=True)
+
+    run_host()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        out = pipe_h.run({k: host[k] for k in COLS}, to_host=True)
+        out = run_host()
     barrier()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = sum(BYTES[k] for k in COLS) * n
+    h2d = sum(BYTES[k] for k in COLS) * n if csv_host is None else int(csv_host.numel())
     d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values()) + 8 * 6
     pipe_h.close()
 
@@ -243,8 +272,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {J} journeys, {n} records, one day, binary columns, "
-                               "fully shuffled", "records": n, "journeys": J,
+        "config": {"workload": f"{args.workload}: {J} journeys, {n} records, one day, "
+                               + ("binary columns" if csv_host is None else
+                                  f"CSV text ({int(csv_host.numel())} bytes, 0.5% malformed rows)")
+                               + ", fully shuffled", "records": n, "journeys": J, "input": args.input,
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -348,6 +379,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="full_day")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--input", default="columns", choices=["columns", "csv"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

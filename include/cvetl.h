@@ -138,13 +138,14 @@ typedef struct {
   const int64_t* p_dwell;  /* dwell of the step, ms */
   const uint32_t* p_key;   /* unrolled cell x bin key or CVETL_KEY_INVALID */
   const uint8_t* p_flags;  /* CVETL_F_* */
-  /* extracted columns (device; the CSV path's parsed rows, or the caller's columns) */
+  /* extracted columns (device; the CSV path's parsed rows, or the caller's columns), n_extracted rows */
   int64_t n_extracted;
   const int64_t* x_jid;
   const int64_t* x_ts;
   const double* x_lat;
   const double* x_lon;
   const float* x_speed;
+  const float* x_heading;  /* NULL when the caller's binary columns had no heading */
   /* counters */
   int64_t n_in;          /* rows handed to cvetl_extract */
   int64_t n_malformed;   /* rows dropped by validation */
@@ -177,7 +178,14 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out);
  * CVETL_IN_COLUMNS: takes n rows. A row is kept when lat, lon and speed are finite,
  * |lat| <= 90 and |lon| <= 180; otherwise it is counted in n_malformed. Speed -0.0 is read
  * as +0.0.
- * CVETL_IN_CSV: reserved; returns CVETL_EINVAL in this version.
+ * CVETL_IN_CSV: csv_len bytes of text (host or device; a device buffer that is not 16-byte
+ * aligned is copied). Grammar (the paper's CSV files, Table 1, have no stated grammar; this is
+ * the library's): lines end at '\n' (one trailing '\r' is stripped, the last line may lack
+ * '\n'); a row is exactly six ','-separated fields jid,ts,lat,lon,speed,heading; jid and ts
+ * match -?[0-9]{1,18}; the others match -?[0-9]+(\.[0-9]+)? with at most 15 digits and take the
+ * binary64 value nearest to the decimal (speed and heading then rounded to float32);
+ * |lat| <= 90 and |lon| <= 180. Any other line (empty lines included) is counted in
+ * n_malformed and dropped; n_in counts lines. Kept rows keep file order as their row index.
  * Replaces the context's previous batch. Returns CVETL_EINVAL for NULL columns or
  * n outside [0, CVETL_MAX_RECORDS], CVETL_EFULL if the budget is exceeded. */
 cvetl_status cvetl_extract(cvetl_ctx* ctx, const cvetl_input* in);
@@ -197,7 +205,8 @@ cvetl_status cvetl_transform(cvetl_ctx* ctx);
 cvetl_status cvetl_load(cvetl_ctx* ctx);
 
 /* Results of the last batch: device pointers owned by the context, sizes and counters.
- * Synchronises ctx->stream (it reads the sizes). */
+ * After cvetl_extract alone it reports the extracted columns and n_in (the cell, journey and
+ * point tables are empty until cvetl_load). Synchronises ctx->stream (it reads the sizes). */
 cvetl_status cvetl_results(cvetl_ctx* ctx, cvetl_tables* out);
 
 /* Streaming mode is not built in this version: returns CVETL_ESTATE. */

@@ -52,7 +52,8 @@ _JOURNEY = [("id", "<i8"), ("n", "<i8"), ("offset", "<i8"), ("start_ts", "<i8"),
             ("start_lat", "<f8"), ("start_lon", "<f8"), ("end_lat", "<f8"), ("end_lon", "<f8")]
 _POINT = [("perm", "<u4"), ("d", "<f8"), ("vhat", "<f4"), ("accel", "<f4"), ("dwell", "<i8"),
           ("key", "<u4"), ("flags", "|u1")]
-_EXTRACTED = [("jid", "<i8"), ("ts", "<i8"), ("lat", "<f8"), ("lon", "<f8"), ("speed", "<f4")]
+_EXTRACTED = [("jid", "<i8"), ("ts", "<i8"), ("lat", "<f8"), ("lon", "<f8"), ("speed", "<f4"),
+              ("heading", "<f4")]
 _COUNTERS = ["n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_too_late", "n_runs"]
 
 
@@ -200,6 +201,35 @@ class Pipeline:
                     lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None)
         self._keep = ts
         self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
+
+    def extract_csv(self, text):
+        """CSV text as bytes / numpy uint8 (host) or a uint8 torch tensor (host or device)."""
+        torch = self._torch
+        if isinstance(text, (bytes, bytearray)):
+            text = np.frombuffer(bytes(text), dtype=np.uint8).copy()
+        if isinstance(text, np.ndarray):
+            text = torch.from_numpy(np.ascontiguousarray(text, dtype=np.uint8))
+        if text.dtype != torch.uint8 or not text.is_contiguous() or text.dim() != 1:
+            raise ValueError("CSV text must be a contiguous 1-D uint8 tensor")
+        n = int(text.shape[0])
+        inp = Input(kind=IN_CSV, on_device=int(text.is_cuda), n=0,
+                    csv=text.data_ptr() if n else None, csv_len=n)
+        self._keep = [text]
+        self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
+
+    def extracted(self, to_host: bool = True) -> dict:
+        """The extracted columns (the parsed rows of CSV input), valid until the next extract."""
+        torch = self._torch
+        t = self.tables()
+        out = {}
+        for k, ty in _EXTRACTED:
+            ptr = getattr(t, "x_" + k)
+            if not ptr or t.n_extracted == 0:
+                out[k] = np.empty(0, np.dtype(ty)) if to_host else None
+                continue
+            a = torch.as_tensor(_DeviceArray(ptr, t.n_extracted, ty), device="cuda")
+            out[k] = a.cpu().numpy() if to_host else a
+        return out
 
     def transform(self):
         self._check(lib.cvetl_transform(self._h))

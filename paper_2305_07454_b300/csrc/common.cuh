@@ -29,6 +29,7 @@ struct DevState {
   unsigned long long n_malformed;
   unsigned long long n_dup;
   unsigned long long n_offgrid;
+  unsigned long long n_lines;  // CSV: lines in the text
 };
 
 // One extracted record, bucketed by journey (32 bytes, one DRAM sector).

@@ -1,0 +1,333 @@
+// csv.cuh — extract from CSV text: split lines, parse and validate each row, and write the
+// kept rows to columns in file order (Methods, "Connected Vehicle Dataset": per-vehicle CSV
+// text; Table 1 shows the columns). The paper gives no grammar; the one used here:
+//   row      = 6 fields separated by ','; one trailing '\r' is stripped; empty lines are rows
+//   integer  = -?[0-9]{1,18}                (journey id, timestamp in ms)
+//   decimal  = -?[0-9]+(\.[0-9]+)?  with at most 15 digits in total
+//   value    = the binary64 value nearest to M / 10^k (M the digits as an integer, k the number
+//              of fraction digits), i.e. one round-to-nearest division of two exact binary64s
+//   range    = |lat| <= 90 and |lon| <= 180; speed and heading are rounded to float32
+// A row breaking any rule is dropped and counted as malformed.
+//
+// Decimal conversion uses no floating-point division: M / 10^k = (M / 5^k) * 2^-k, and
+// M / 5^k is computed exactly as an integer quotient of M * 2^t (128-bit) by 5^k through a
+// 128-bit reciprocal ceil(2^128 / 5^k) with one correction step; the 55-57-bit quotient and its
+// remainder then give the round-to-nearest-even binary64 result directly.
+#pragma once
+#include "common.cuh"
+
+namespace cvetl {
+
+constexpr int kCsvTile = 12288;  // bytes per tile (multiple of 16)
+constexpr int kCsvHalo = 1024;   // bytes past the tile kept in shared memory (lines crossing its end)
+constexpr int kCsvBlock = 256;
+constexpr int kCsvRounds = 4;    // lines per thread kept in registers (tiles of <= 1024 lines)
+
+__constant__ unsigned long long kPow5[16] = {1ull, 5ull, 25ull, 125ull, 625ull, 3125ull, 15625ull,
+                                             78125ull, 390625ull, 1953125ull, 9765625ull,
+                                             48828125ull, 244140625ull, 1220703125ull,
+                                             6103515625ull, 30517578125ull};
+// ceil(2^128 / 5^k) as {high 64 bits, low 64 bits}
+__constant__ unsigned long long kRecip5[16][2] = {
+    {0ull, 0ull},  // k = 0: no division
+    {0x3333333333333333ull, 0x3333333333333334ull},
+    {0x0a3d70a3d70a3d70ull, 0xa3d70a3d70a3d70bull},
+    {0x020c49ba5e353f7cull, 0xed916872b020c49cull},
+    {0x0068db8bac710cb2ull, 0x95e9e1b089a02753ull},
+    {0x0014f8b588e368f0ull, 0x8461f9f01b866e44ull},
+    {0x000431bde82d7b63ull, 0x4dad31fcd24e160eull},
+    {0x0000d6bf94d5e57aull, 0x42bc3d329076046aull},
+    {0x00002af31dc46118ull, 0x73bf3f70834acdafull},
+    {0x0000089705f4136bull, 0x4a59731680a88f8aull},
+    {0x000001b7cdfd9d7bull, 0xdbab7d6ae6881cb6ull},
+    {0x00000057f5ff85e5ull, 0x92557f7bc7b4d28bull},
+    {0x000000119799812dull, 0xea11197f27f0f6e9ull},
+    {0x0000000384b84d09ull, 0x2ed0384ca19697c9ull},
+    {0x00000000b424dc35ull, 0x095cd80f538484c2ull},
+    {0x0000000024075f3dull, 0xceac2b3643e74dc1ull},
+};
+
+typedef unsigned __int128 u128;
+
+// floor(a * b / 2^128) from 64-bit limbs
+__device__ __forceinline__ u128 mulhi128(u128 a, u128 b) {
+  const unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
+  const unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
+  const u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+  const u128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
+  return p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+}
+
+// The binary64 value nearest to M / 10^k (ties to even), M < 10^15, 0 <= k <= 15.
+__device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
+  if (M == 0) return 0.0;
+  if (k == 0) return __ull2double_rn(M);  // exact: M < 2^53
+  const unsigned long long d = kPow5[k];
+  const int L = 64 - __clzll((long long)M), Ld = 64 - __clzll((long long)d);
+  const int t = 56 + Ld - L;  // x / d lies in [2^55, 2^57)
+  const u128 x = (u128)M << t;
+  const u128 R = ((u128)kRecip5[k][0] << 64) | kRecip5[k][1];
+  unsigned long long q = (unsigned long long)mulhi128(x, R);  // q or q + 1
+  __int128 r = (__int128)x - (__int128)((u128)q * d);
+  if (r < 0) {
+    q -= 1;
+    r += d;
+  }
+  const int b = 64 - __clzll((long long)q);
+  int s = b - 53;  // 3 or 4 bits below the binary64 significand
+  unsigned long long mant = q >> s;
+  const unsigned long long low = q & ((1ull << s) - 1), half = 1ull << (s - 1);
+  if (low > half || (low == half && (r != 0 || (mant & 1)))) mant += 1;
+  if (mant >> 53) {
+    mant >>= 1;
+    s += 1;
+  }
+  const int e = 52 + s - t - k;
+  return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ bool is_digit(unsigned c) { return c - '0' <= 9u; }
+
+// Parses one line (without its '\n'); p may point to shared or global memory.
+__device__ bool parse_row(const unsigned char* p, int len, int64_t& jid, int64_t& ts, double& lat,
+                          double& lon, float& spd, float& hd) {
+  if (len > 0 && p[len - 1] == '\r') --len;
+  if (len == 0) return false;
+  int i = 0;
+  long long iv[2];
+  for (int f = 0; f < 2; ++f) {
+    bool neg = false;
+    if (i < len && p[i] == '-') {
+      neg = true;
+      ++i;
+    }
+    int nd = 0;
+    unsigned long long v = 0;
+    while (i < len && p[i] != ',') {
+      const unsigned c = p[i];
+      if (!is_digit(c) || ++nd > 18) return false;
+      v = v * 10 + (c - '0');
+      ++i;
+    }
+    if (nd == 0 || i >= len) return false;
+    ++i;  // ','
+    iv[f] = neg ? -(long long)v : (long long)v;
+  }
+  double dv[4];
+  for (int f = 0; f < 4; ++f) {
+    bool neg = false;
+    if (i < len && p[i] == '-') {
+      neg = true;
+      ++i;
+    }
+    int ni = 0, nf = 0;
+    unsigned long long M = 0;
+    while (i < len && is_digit(p[i])) {
+      if (++ni > 15) return false;
+      M = M * 10 + (p[i] - '0');
+      ++i;
+    }
+    if (ni == 0) return false;
+    if (i < len && p[i] == '.') {
+      ++i;
+      while (i < len && is_digit(p[i])) {
+        if (ni + ++nf > 15) return false;
+        M = M * 10 + (p[i] - '0');
+        ++i;
+      }
+      if (nf == 0) return false;
+    }
+    if (f < 3) {
+      if (i >= len || p[i] != ',') return false;
+      ++i;
+    } else if (i != len) {
+      return false;
+    }
+    const double v = dec_to_f64(M, nf);
+    dv[f] = neg ? -v : v;
+  }
+  // |lat| <= 90, |lon| <= 180 (on the bit patterns)
+  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  if (((unsigned long long)__double_as_longlong(dv[0]) & kAbs) > 0x4056800000000000ull) return false;
+  if (((unsigned long long)__double_as_longlong(dv[1]) & kAbs) > 0x4066800000000000ull) return false;
+  jid = iv[0];
+  ts = iv[1];
+  lat = dv[0];
+  lon = dv[1];
+  spd = __double2float_rn(dv[2]);
+  hd = __double2float_rn(dv[3]);
+  return true;
+}
+
+struct CsvOut {
+  int64_t *jid, *ts;
+  double *lat, *lon;
+  float *speed, *heading;
+};
+
+// Pass 1: count '\n' bytes; the number of lines is at most that count + 1.
+__global__ void __launch_bounds__(kCsvBlock) k_csv_count(const unsigned char* __restrict__ buf,
+                                                         unsigned long long len,
+                                                         unsigned long long* __restrict__ n_lines) {
+  __shared__ unsigned long long scratch[kCsvBlock / 32];
+  unsigned long long c = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * kCsvBlock * 16;
+  for (unsigned long long b0 = ((unsigned long long)blockIdx.x * kCsvBlock + threadIdx.x) * 16; b0 < len;
+       b0 += stride) {
+    if (b0 + 16 <= len) {
+      const uint4 v = *reinterpret_cast<const uint4*>(buf + b0);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t x = w[q] ^ 0x0A0A0A0Au;  // bytes equal to '\n' become 0
+        c += __popc((x - 0x01010101u) & ~x & 0x80808080u);
+      }
+    } else {
+      for (unsigned long long p = b0; p < len; ++p) c += buf[p] == '\n';
+    }
+  }
+  // (line starts <= newlines + 1: the caller sizes its columns with that bound)
+  c = block_sum<kCsvBlock, unsigned long long>(c, scratch);
+  if (threadIdx.x == 0 && c) atomicAdd(n_lines, c);
+}
+
+// Pass 2: parse. Tiles are taken in order (ticket); each tile publishes its count of kept rows
+// and looks back over earlier tiles for its first output row, so rows keep file order.
+__global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __restrict__ buf,
+                                                         unsigned long long len, uint32_t n_tiles,
+                                                         CsvOut out, uint32_t cap,
+                                                         uint32_t* status, uint32_t* tile_ctr,
+                                                         DevState* st) {
+  __shared__ __align__(16) unsigned char s_buf[kCsvTile + kCsvHalo];
+  __shared__ uint16_t s_start[kCsvTile];
+  __shared__ uint32_t s_scan[kCsvBlock / 32 + 1];
+  __shared__ uint32_t s_tile, s_base;
+  __shared__ unsigned char s_prev;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  if (tile >= n_tiles) return;
+  const unsigned long long base = (unsigned long long)tile * kCsvTile;
+  const int tlen = (int)min((unsigned long long)kCsvTile, len - base);
+  const int wlen = (int)min((unsigned long long)(kCsvTile + kCsvHalo), len - base);
+  // stage the tile (+ halo) in shared memory: 16-byte loads (base is 16-byte aligned)
+  for (int o = tid * 16; o < wlen; o += kCsvBlock * 16) {
+    if (o + 16 <= wlen) *reinterpret_cast<uint4*>(s_buf + o) = *reinterpret_cast<const uint4*>(buf + base + o);
+    else
+      for (int q = o; q < wlen; ++q) s_buf[q] = buf[base + q];
+  }
+  if (tid == 0) s_prev = (base == 0) ? (unsigned char)'\n' : buf[base - 1];
+  __syncthreads();
+  // line starts inside the tile: each thread scans 64 bytes
+  constexpr int kPer = kCsvTile / kCsvBlock;
+  const int c0 = tid * kPer, c1 = min(tlen, c0 + kPer);
+  uint32_t cnt = 0;
+  for (int p = c0; p < c1; ++p) cnt += ((p == 0 ? s_prev : s_buf[p - 1]) == '\n');
+  uint32_t total;
+  uint32_t r = block_excl_scan<kCsvBlock>(cnt, s_scan, &total);
+  for (int p = c0; p < c1; ++p)
+    if ((p == 0 ? s_prev : s_buf[p - 1]) == '\n') s_start[r++] = (uint16_t)p;
+  __syncthreads();
+  const int nstart = (int)total;
+  // parse the lines starting here; keep up to kCsvRounds per thread in registers
+  const bool in_regs = nstart <= kCsvRounds * kCsvBlock;
+  int64_t vj[kCsvRounds], vt[kCsvRounds];
+  double vla[kCsvRounds], vlo[kCsvRounds];
+  float vs[kCsvRounds], vh[kCsvRounds];
+  bool ok[kCsvRounds];
+  uint32_t mine = 0;
+  auto parse_at = [&](int i, int64_t& a, int64_t& b, double& c, double& d, float& e, float& f) -> bool {
+    const int s = s_start[i];
+    int q = s;
+    while (q < wlen && s_buf[q] != '\n') ++q;
+    if (q < wlen || base + wlen == len) return parse_row(s_buf + s, q - s, a, b, c, d, e, f);
+    // the line runs past the staged window: read it from global memory
+    unsigned long long g = base + q;
+    while (g < len && buf[g] != '\n') ++g;
+    return parse_row(buf + base + s, (int)(g - (base + s)), a, b, c, d, e, f);
+  };
+  if (in_regs) {
+#pragma unroll
+    for (int u = 0; u < kCsvRounds; ++u) {
+      const int i = tid + u * kCsvBlock;
+      ok[u] = (i < nstart) && parse_at(i, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
+      mine += ok[u];
+    }
+  } else {
+    for (int i = tid; i < nstart; i += kCsvBlock) {
+      int64_t a, b;
+      double c, d;
+      float e, f;
+      mine += parse_at(i, a, b, c, d, e, f);
+    }
+  }
+  uint32_t tile_valid;
+  block_excl_scan<kCsvBlock>(mine, s_scan, &tile_valid);
+  // look back for the first output row of this tile
+  if (tid == 0) {
+    uint32_t excl = 0;
+    if (tile == 0) {
+      st_relaxed_u32(status, (2u << 30) | tile_valid);
+    } else {
+      st_relaxed_u32(status + tile, (1u << 30) | tile_valid);
+      for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
+        uint32_t s = ld_relaxed_u32(status + p);
+        int spins = 0;
+        while ((s >> 30) == 0) {
+          if (++spins > (1 << 22)) break;
+          __nanosleep(32);
+          s = ld_relaxed_u32(status + p);
+        }
+        if ((s >> 30) == 0) {
+          atomicOr(&st->err, kErrLookbackTimeout);
+          break;
+        }
+        excl += s & ((1u << 30) - 1);
+        if ((s >> 30) == 2u) break;
+      }
+      st_relaxed_u32(status + tile, (2u << 30) | (excl + tile_valid));
+    }
+    s_base = excl;
+    atomicAdd(&st->n_lines, (unsigned long long)nstart);
+    if ((uint32_t)nstart > tile_valid) atomicAdd(&st->n_malformed, (unsigned long long)(nstart - tile_valid));
+  }
+  __syncthreads();
+  // write the kept rows in file order (line i of the tile before line i + 1)
+  uint32_t pos = s_base;
+  auto put = [&](uint32_t o, int64_t a, int64_t b, double c, double d, float e, float f) {
+    if (o < cap) {
+      out.jid[o] = a;
+      out.ts[o] = b;
+      out.lat[o] = c;
+      out.lon[o] = d;
+      out.speed[o] = e;
+      out.heading[o] = f;
+    } else {
+      atomicOr(&st->err, kErrCapacity);
+    }
+  };
+  if (in_regs) {
+#pragma unroll
+    for (int u = 0; u < kCsvRounds; ++u) {
+      uint32_t round_total;
+      const uint32_t rk = block_excl_scan<kCsvBlock>(ok[u] ? 1u : 0u, s_scan, &round_total);
+      if (ok[u]) put(pos + rk, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
+      pos += round_total;
+    }
+  } else {  // a tile of very short lines: parse again
+    for (int i0 = 0; i0 < nstart; i0 += kCsvBlock) {
+      const int i = i0 + tid;
+      int64_t a = 0, b = 0;
+      double c = 0.0, d = 0.0;
+      float e = 0.f, f = 0.f;
+      const bool v = (i < nstart) && parse_at(i, a, b, c, d, e, f);
+      uint32_t round_total;
+      const uint32_t rk = block_excl_scan<kCsvBlock>(v ? 1u : 0u, s_scan, &round_total);
+      if (v) put(pos + rk, a, b, c, d, e, f);
+      pos += round_total;
+    }
+  }
+}
+
+}  // namespace cvetl

@@ -20,6 +20,7 @@
 #include "extract.cuh"
 #include "journey.cuh"
 #include "cells.cuh"
+#include "csv.cuh"
 
 using namespace cvetl;
 
@@ -27,11 +28,12 @@ namespace {
 
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
-  ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_COUNT
+  ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
-                                     "scatter", "journeys", "cell_heads", "cell_write"};
+                                     "scatter", "journeys", "cell_heads", "cell_write",
+                                     "csv_count", "csv_parse"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -49,8 +51,9 @@ struct cvetl_ctx {
   int state = 0;  // 0 empty, 1 extracted, 2 transformed, 3 loaded
   size_t held = 0;
   std::map<std::string, DevBuf> bufs;
-  // extracted columns
-  int64_t n_in = 0;
+  // extracted columns (n_rows of them) from n_in input rows or lines
+  int64_t n_in = 0, n_rows = 0, csv_malformed = 0;
+  const float* heading = nullptr;
   const int64_t* jid = nullptr;
   const int64_t* ts = nullptr;
   const double* lat = nullptr;
@@ -305,6 +308,71 @@ uint32_t next_pow2(uint64_t v) {
 
 }  // namespace
 
+// CSV text -> parsed columns on the device (count pass sizes the columns; parse pass keeps
+// file order through a decoupled look-back over tiles).
+cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
+  const size_t len = in->csv_len;
+  if (len && !in->csv) return fail(c, CVETL_EINVAL, "cvetl_extract: NULL csv");
+  if (len > (size_t)CVETL_MAX_RECORDS * 128) return fail(c, CVETL_EINVAL, "csv_len %zu is too large", len);
+  cudaSetDevice(c->cfg.device);
+  c->state = 0;
+  const unsigned char* buf = (const unsigned char*)in->csv;
+  if (len && (!in->on_device || ((uintptr_t)buf & 15))) {
+    unsigned char* d;
+    ENSURE("in.csv", len, &d);
+    CK(cudaMemcpyAsync(d, in->csv, len, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    buf = d;
+  }
+  unsigned long long* nl;
+  ENSURE("csv.newlines", 1, &nl);
+  CK(cudaMemsetAsync(nl, 0, 8, c->st));
+  if (len) {
+    LAUNCH(ST_CSV_COUNT, (k_csv_count<<<grid_for((len + 15) / 16, kCsvBlock), kCsvBlock, 0, c->st>>>(buf, len, nl)));
+    LAUNCH_CHECK();
+  }
+  unsigned long long newlines = 0;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&newlines, nl, 8, cudaMemcpyDeviceToHost));
+  const size_t cap = len ? (size_t)newlines + 1 : 0;
+  if (cap > (size_t)CVETL_MAX_RECORDS) return fail(c, CVETL_EINVAL, "the text holds more than %lld lines", (long long)CVETL_MAX_RECORDS);
+  int64_t *jid, *ts;
+  double *lat, *lon;
+  float *spd, *hd;
+  ENSURE("csv.jid", cap, &jid);
+  ENSURE("csv.ts", cap, &ts);
+  ENSURE("csv.lat", cap, &lat);
+  ENSURE("csv.lon", cap, &lon);
+  ENSURE("csv.spd", cap, &spd);
+  ENSURE("csv.hd", cap, &hd);
+  const uint32_t n_tiles = (uint32_t)((len + kCsvTile - 1) / kCsvTile);
+  uint32_t *status, *tiles;
+  ENSURE("csv.status", (size_t)n_tiles + 1, &status);
+  ENSURE("csv.tiles", 1, &tiles);
+  CK(cudaMemsetAsync(status, 0, ((size_t)n_tiles + 1) * 4, c->st));
+  CK(cudaMemsetAsync(tiles, 0, 4, c->st));
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (n_tiles) {
+    CsvOut o{jid, ts, lat, lon, spd, hd};
+    LAUNCH(ST_CSV_PARSE, (k_csv_parse<<<n_tiles, kCsvBlock, 0, c->st>>>(buf, len, n_tiles, o, (uint32_t)cap,
+                                                                         status, tiles, c->dstate)));
+    LAUNCH_CHECK();
+  }
+  cvetl_status s = read_state(c);
+  if (s != CVETL_OK) return s;
+  c->n_in = (int64_t)c->hstate->n_lines;
+  c->csv_malformed = (int64_t)c->hstate->n_malformed;
+  c->n_rows = c->n_in - c->csv_malformed;
+  c->jid = jid;
+  c->ts = ts;
+  c->lat = lat;
+  c->lon = lon;
+  c->spd = spd;
+  c->heading = hd;
+  c->J = c->R = c->K = c->n_valid = 0;
+  c->state = 1;
+  return CVETL_OK;
+}
+
 // ======================================================================================
 extern "C" {
 
@@ -366,15 +434,15 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   if ((s = ensure(c, "grid.cols", ct.size(), &c->col_thr)) != CVETL_OK) return bail(s);
   if ((s = ensure(c, "state", 1, &c->dstate)) != CVETL_OK) return bail(s);
   // cosine table for the binary64 haversine: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180}
-  std::vector<double4> cos_tab(18001);
+  std::vector<CosEntry> cos_tab(18001);
   for (int k = -9000; k <= 9000; ++k) {
     const double lat0 = (double)k * 0.01;
     const double rad = M_PI / 180.0;
-    cos_tab[k + 9000] = make_double4(lat0, std::cos(lat0 * rad), std::sin(lat0 * rad) * rad, 0.0);
+    cos_tab[k + 9000] = CosEntry{lat0, std::cos(lat0 * rad), std::sin(lat0 * rad) * rad, 0.0};
   }
-  double4* d_cos = nullptr;
+  CosEntry* d_cos = nullptr;
   if ((s = ensure(c, "grid.cos", cos_tab.size(), &d_cos)) != CVETL_OK) return bail(s);
-  if (cudaMemcpy(d_cos, cos_tab.data(), cos_tab.size() * sizeof(double4), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaMemcpy(d_cos, cos_tab.data(), cos_tab.size() * sizeof(CosEntry), cudaMemcpyHostToDevice) != cudaSuccess) {
     fail(c, CVETL_ECUDA, "cvetl_create: cosine table upload failed");
     return bail(CVETL_ECUDA);
   }
@@ -434,7 +502,7 @@ cvetl_status cvetl_destroy(cvetl_ctx* c) {
 cvetl_status cvetl_extract(cvetl_ctx* c, const cvetl_input* in) {
   if (!c) return CVETL_EINVAL;
   if (!in) return fail(c, CVETL_EINVAL, "cvetl_extract: NULL input");
-  if (in->kind == CVETL_IN_CSV) return fail(c, CVETL_EINVAL, "CSV input is not built in this version");
+  if (in->kind == CVETL_IN_CSV) return extract_csv(c, in);
   if (in->kind != CVETL_IN_COLUMNS) return fail(c, CVETL_EINVAL, "unknown input kind %d", in->kind);
   if (in->n < 0 || in->n > CVETL_MAX_RECORDS)
     return fail(c, CVETL_EINVAL, "n = %lld outside [0, %lld]", (long long)in->n, (long long)CVETL_MAX_RECORDS);
@@ -472,6 +540,9 @@ cvetl_status cvetl_extract(cvetl_ctx* c, const cvetl_input* in) {
     c->spd = spd;
   }
   c->n_in = in->n;
+  c->n_rows = in->n;
+  c->csv_malformed = 0;
+  c->heading = in->heading;
   c->J = c->R = c->K = c->n_valid = 0;
   c->state = 1;
   return CVETL_OK;
@@ -481,7 +552,7 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   if (!c) return CVETL_EINVAL;
   if (c->state != 1) return fail(c, CVETL_ESTATE, "cvetl_transform needs a preceding cvetl_extract");
   cudaSetDevice(c->cfg.device);
-  const uint32_t n = (uint32_t)c->n_in;
+  const uint32_t n = (uint32_t)c->n_rows;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
 
   // 1. count journeys (hash table of ids), growing the table if it overflows
@@ -657,11 +728,23 @@ cvetl_status cvetl_load(cvetl_ctx* c) {
 cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
   if (!c) return CVETL_EINVAL;
   if (!r) return fail(c, CVETL_EINVAL, "cvetl_results: NULL output");
-  if (c->state != 3) return fail(c, CVETL_ESTATE, "cvetl_results needs a preceding cvetl_load");
+  if (c->state < 1) return fail(c, CVETL_ESTATE, "cvetl_results needs a preceding cvetl_extract");
   cudaSetDevice(c->cfg.device);
+  memset(r, 0, sizeof(*r));
+  r->n_extracted = c->n_rows;
+  r->x_jid = c->jid;
+  r->x_ts = c->ts;
+  r->x_lat = c->lat;
+  r->x_lon = c->lon;
+  r->x_speed = c->spd;
+  r->x_heading = c->heading;
+  r->n_in = c->n_in;
+  if (c->state < 3) {  // extracted only: tables come with cvetl_load
+    r->n_malformed = c->csv_malformed;
+    return CVETL_OK;
+  }
   cvetl_status s = read_state(c);
   if (s != CVETL_OK) return s;
-  memset(r, 0, sizeof(*r));
   const CellOut& co = c->co;
   r->n_cells = c->K;
   r->cell_key = co.key;
@@ -697,14 +780,7 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
     r->p_key = o.key;
     r->p_flags = o.flags;
   }
-  r->n_extracted = c->n_in;
-  r->x_jid = c->jid;
-  r->x_ts = c->ts;
-  r->x_lat = c->lat;
-  r->x_lon = c->lon;
-  r->x_speed = c->spd;
-  r->n_in = c->n_in;
-  r->n_malformed = (int64_t)c->hstate->n_malformed;
+  r->n_malformed = c->csv_malformed + (int64_t)c->hstate->n_malformed;
   r->n_valid = c->n_valid;
   r->n_out_of_grid = (int64_t)c->hstate->n_offgrid;
   r->n_dup = (int64_t)c->hstate->n_dup;

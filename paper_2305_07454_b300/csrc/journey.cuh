@@ -15,6 +15,11 @@ constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memor
 constexpr int kJSmem = 2 * kJCap * 8 + kJCap * 4;
 static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
 
+// cosine table entry: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, unused}
+struct __align__(32) CosEntry {
+  double lat0, c0, s0r, pad;
+};
+
 struct GridParams {
   const unsigned long long* row_thr;  // n_rows + 1 ordered thresholds (see keying below)
   const unsigned long long* col_thr;  // n_cols + 1
@@ -24,7 +29,7 @@ struct GridParams {
   unsigned long long t_span;  // n_bins * bin_ms, saturated
   float v_stop;
   double radius_m;
-  const double4* cos_tab;  // k = -9000..9000: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, 0}
+  const CosEntry* cos_tab;  // k = -9000..9000
   double asin_c1, asin_c2, asin_c3;  // 2R, 2R/6, 2R*3/40: d = sqrt(h) (c1 + h (c2 + h c3))
 };
 
@@ -214,7 +219,7 @@ constexpr double kRad = 0.017453292519943295;       // pi / 180
 constexpr double kRad2Half = 1.5230870989335428e-4;  // (pi/180)^2 / 2
 constexpr double kRad2Sixth = 5.076956996445143e-5;  // (pi/180)^2 / 6
 
-__device__ __forceinline__ double cos_deg(double lat, const double4* __restrict__ tab) {
+__device__ __forceinline__ double cos_deg(double lat, const CosEntry* __restrict__ tab) {
   int k = __float2int_rn(leading_f32(lat) * 100.0f);
   k = max(-9000, min(9000, k));
   const double2* p = reinterpret_cast<const double2*>(tab + (k + 9000));
