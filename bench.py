@@ -184,7 +184,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     # ---- device-resident steps ------------------------------------------------------------
-    pipe = P.Pipeline(stream=stream, profile=1)
+    prec = P.FP32 if args.precision == "fp32" else P.FP64
+    pipe = P.Pipeline(stream=stream, profile=1, precision=prec)
     for _ in range(args.warmup):
         run_dev(pipe)
     pipe.stats_reset()
@@ -214,7 +215,7 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host inputs ------------------------------------
     e2e_steps = max(1, min(args.steps, 3))
-    pipe_h = P.Pipeline(stream=stream)
+    pipe_h = P.Pipeline(stream=stream, precision=prec)
 
     def run_host():
         if csv_host is None:
@@ -244,7 +245,7 @@ def run_ours(args):
     hbm_peak, peak_src = load_peaks()
     tpr = TRAFFIC_PER_RECORD.get(top)
     traffic = tpr * counters["n_valid"] if tpr else None
-    if top == "journeys":
+    if top == "journeys" and args.precision == "fp64":
         gops_peak, mhz = fp64_peak_gops()
         ops = FP64_OPS_PER_POINT * counters["n_valid"]
         achieved = ops / (avg_ms / 1e3) / 1e9
@@ -271,11 +272,13 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32 (binary64 coordinate differences)",
+        "data": "synthetic",
         "config": {"workload": f"{args.workload}: {J} journeys, {n} records, one day, "
                                + ("binary columns" if csv_host is None else
                                   f"CSV text ({int(csv_host.numel())} bytes, 0.5% malformed rows)")
-                               + ", fully shuffled", "records": n, "journeys": J, "input": args.input,
+                               + ", fully shuffled", "records": n, "journeys": J, "input": args.input, "precision": args.precision,
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -380,6 +383,7 @@ def main():
     ap.add_argument("--workload", default="full_day")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--input", default="columns", choices=["columns", "csv"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -79,7 +79,10 @@ typedef struct {
   int64_t t0_ms, bin_ms;             /* 2021-05-09 00:00:00 UTC in ms, 60000 */
   float v_stop_kmh;                  /* 1.0: dwell threshold */
   double earth_radius_m;             /* 6371000.0 */
-  int32_t precision;                 /* CVETL_FP64 (only FP64 is built) */
+  int32_t precision;                 /* CVETL_FP64: distances in binary64. CVETL_FP32: coordinates
+                                        differenced in binary64, the haversine and per-point
+                                        arithmetic in float32, distance and speed sums in
+                                        compensated float32 (keys, counts, order unchanged) */
   int32_t materialize_points;        /* 1: keep per-point columns in the results */
   int32_t profile;                   /* 1: time every kernel with CUDA events */
   int32_t device;                    /* CUDA device ordinal */

@@ -413,8 +413,8 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   if (!std::isfinite(cfg->lat_min) || !std::isfinite(cfg->lon_min) || !(cfg->cell_deg > 0.0) ||
       !std::isfinite(cfg->cell_deg) || !std::isfinite(cfg->earth_radius_m))
     return fail(nullptr, CVETL_EINVAL, "lat_min, lon_min, cell_deg and earth_radius_m must be finite, cell_deg > 0");
-  if (cfg->precision != CVETL_FP64)
-    return fail(nullptr, CVETL_EINVAL, "only the FP64 form (CVETL_FP64) is built");
+  if (cfg->precision != CVETL_FP64 && cfg->precision != CVETL_FP32)
+    return fail(nullptr, CVETL_EINVAL, "precision must be CVETL_FP64 or CVETL_FP32");
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) return fail(nullptr, CVETL_ECUDA, "cudaSetDevice(%d): %s", cfg->device, cudaGetErrorString(e));
   c = new cvetl_ctx();
@@ -471,7 +471,8 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c1 = 2.0 * cfg->earth_radius_m;
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
-  if (cudaFuncSetAttribute(k_journeys, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_journeys<Fp64Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp32Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -672,8 +673,11 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("run.max", nv, &o.run_max);
   o.run_cap = (uint32_t)nv;
   if (J) {
-    LAUNCH(ST_JOURNEYS, (k_journeys<<<J, kJBlock, kJSmem, c->st>>>(
-                            rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
+    if (c->cfg.precision == CVETL_FP32) {
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
+    } else {
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
+    }
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);

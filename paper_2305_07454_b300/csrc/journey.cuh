@@ -458,6 +458,65 @@ __device__ __forceinline__ void emit_run(const JourneyOut& o, DevState* st, uint
 
 __device__ __forceinline__ int bits_for(unsigned long long v) { return v ? 64 - __clzll(v) : 0; }
 
+// ---------------------------------------------------------------- the two arithmetic forms
+// Binary64 form: the distance is evaluated in binary64 throughout (haversine_fast above).
+// Float32 form: the coordinates are differenced in binary64 (exact for nearby points) and
+// rounded to float32; the bulk of the haversine, the cosines and the per-point arithmetic run
+// in float32; the journey distance is summed in compensated float32 pairs. Keys, counts and
+// the order are the same integer computation in both forms.
+constexpr float kHalfRadF = 0.0087266462599716f;  // pi / 360
+constexpr float kRadF = 0.017453292519943295f;     // pi / 180
+
+__device__ __forceinline__ float haversine_f32(double la1, double lo1, float c1, double la2, double lo2,
+                                               float c2, const GridParams& g) {
+  const float a = leading_f32(la2 - la1) * kHalfRadF;
+  const float b = leading_f32(lo2 - lo1) * kHalfRadF;
+  const float R2 = (float)g.asin_c1;
+  if (fabsf(a) < 1e-2f && fabsf(b) < 1e-2f) {
+    // sin^2 x = x^2 (1 - x^2/3) + O(x^6); asin s = s (1 + h/6 + 3 h^2/40) + O(s^7), h = s^2
+    const float a2 = a * a, b2 = b * b;
+    const float h = fmaf(c1 * c2, b2 * fmaf(b2, -1.0f / 3.0f, 1.0f), a2 * fmaf(a2, -1.0f / 3.0f, 1.0f));
+    const float s = sqrtf(h);
+    return R2 * s * fmaf(h, fmaf(h, 0.075f, 1.0f / 6.0f), 1.0f);
+  }
+  const float sa = sinf(a), sb = sinf(b);
+  return R2 * asinf(fminf(1.0f, sqrtf(fmaf(c1 * c2, sb * sb, sa * sa))));
+}
+
+struct Fp64Form {
+  typedef double Cos;
+  typedef double Dist;
+  static __device__ __forceinline__ double cosine(double lat, const GridParams& g) {
+    return cos_deg(lat, g.cos_tab);
+  }
+  static __device__ __forceinline__ double distance(double la1, double lo1, double c1, double la2,
+                                                    double lo2, double c2, const GridParams& g) {
+    return haversine_fast(la1, lo1, c1, la2, lo2, c2, g);
+  }
+  struct Acc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double d) { s += d; }
+    __device__ __forceinline__ double value() const { return s; }
+  };
+};
+
+struct Fp32Form {
+  typedef float Cos;
+  typedef float Dist;
+  static __device__ __forceinline__ float cosine(double lat, const GridParams&) {
+    return cosf(leading_f32(lat) * kRadF);
+  }
+  static __device__ __forceinline__ float distance(double la1, double lo1, float c1, double la2,
+                                                   double lo2, float c2, const GridParams& g) {
+    return haversine_f32(la1, lo1, c1, la2, lo2, c2, g);
+  }
+  struct Acc {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float d) { fsum_add(s, c, d); }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  };
+};
+
 // Run fragments a thread hands to the stitch at the end of the walk.
 struct RunPart {
   uint32_t key, cnt, start;
@@ -488,6 +547,7 @@ struct StitchSmem {
   uint8_t cont[kJBlock]; // the whole range continued the previous thread's run
 };
 
+template <class Form>
 __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
                                                          const uint32_t* __restrict__ jn,
                                                          const uint32_t* __restrict__ joff, uint32_t J,
@@ -571,7 +631,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   // 2. walk: thread t owns the sorted positions [k0, k1) and visits them in order; the
   // predecessor stays in registers, runs of equal keys accumulate in the thread
   const int k0 = (int)((long long)n * tid / kJBlock), k1 = (int)((long long)n * (tid + 1) / kJBlock);
-  double dist = 0.0;
+  typename Form::Acc dist;
   long long dwell_sum = 0, n_dup = 0, n_off = 0;
   RunPart pre{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
   RunPart run{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
@@ -579,7 +639,8 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   bool cont_all = false;
   if (k0 < k1) {
     int64_t p_ts = 0;
-    double p_lat = 0.0, p_lon = 0.0, p_cos = 0.0;
+    double p_lat = 0.0, p_lon = 0.0;
+    typename Form::Cos p_cos = 0;
     float p_spd = 0.0f;
     if (k0 > 0) {  // predecessor: the previous thread's last point
       const Rec q = R[radix ? (uint32_t)(sortedK[k0 - 1] & pmask) : sortedE[k0 - 1].pos];
@@ -587,7 +648,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       p_lat = q.lat;
       p_lon = q.lon;
       p_spd = q.spd;
-      p_cos = cos_deg(q.lat, g.cos_tab);
+      p_cos = Form::cosine(q.lat, g);
       run.key = cell_key(q.lat, q.lon, q.ts, g);
       run.mn = __int_as_float(0x7F800000);   // +inf
       run.mx = __int_as_float((int)0xFF800000u);  // -inf
@@ -595,10 +656,10 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
     }
     for (int k = k0; k < k1; ++k) {
       const Rec cur = R[radix ? (uint32_t)(sortedK[k] & pmask) : sortedE[k].pos];
-      const double ccur = cos_deg(cur.lat, g.cos_tab);
+      const typename Form::Cos ccur = Form::cosine(cur.lat, g);
       const uint32_t key = cell_key(cur.lat, cur.lon, cur.ts, g);
       uint8_t fl = 0;
-      double d = 0.0;
+      typename Form::Dist d = 0;
       float vh = 0.0f, ac = 0.0f;
       int64_t dw = 0;
       if (k == 0) {
@@ -609,7 +670,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       } else {
         const int64_t dt = (int64_t)((unsigned long long)cur.ts - (unsigned long long)p_ts);
         if (dt == 0) fl |= kFDup;
-        d = haversine_fast(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g);
+        d = Form::distance(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g);
         if (dt > 0) {
           // stored as float32: computed in float32 from the binary64 distance
           const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : (float)dt;
@@ -625,14 +686,14 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       if (o.perm) {
         const uint32_t gp = off + (uint32_t)k;
         o.perm[gp] = cur.idx;
-        o.d[gp] = d;
+        o.d[gp] = (double)d;
         o.vhat[gp] = vh;
         o.accel[gp] = ac;
         o.dwell_pt[gp] = dw;
         o.key[gp] = key;
         o.flags[gp] = fl;
       }
-      dist += d;
+      dist.add(d);
       dwell_sum += dw;
       n_dup += (fl & kFDup) ? 1 : 0;
       n_off += (key == kKeyInvalid) ? 1 : 0;
@@ -664,7 +725,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
     }
   }
   // 3. journey sums in a fixed order; stitch run fragments across thread ranges in order
-  const double sd = block_sum<kJBlock, double>(dist, red_d);
+  const double sd = block_sum<kJBlock, double>(dist.value(), red_d);
   const long long sw = block_sum<kJBlock, long long>(dwell_sum, red_i);
   const long long sdup = block_sum<kJBlock, long long>(n_dup, red_i);
   const long long soff = block_sum<kJBlock, long long>(n_off, red_i);

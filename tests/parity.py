@@ -42,7 +42,7 @@ def exact(name, got, want):
                       f"{int(np.flatnonzero(~ok)[0])}: got {got[~ok][0]!r} want {want[~ok][0]!r}")
 
 
-def compare(gpu: dict, orc: dict, points: bool = True):
+def compare(gpu: dict, orc: dict, points: bool = True, rel: float = REL):
     gc, oc = gpu["counters"], orc["counters"]
     for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_journeys", "n_cells"):
         assert gc[k] == oc[k], (k, gc[k], oc[k])
@@ -53,16 +53,16 @@ def compare(gpu: dict, orc: dict, points: bool = True):
     exact("journey offset", gj["offset"], offs)
     for k in ("start_ts", "end_ts", "duration_ms", "dwell_ms", "start_lat", "start_lon", "end_lat", "end_lon"):
         exact("journey " + k, gj[k], oj[k])
-    close("journey distance", gj["distance_m"], oj["distance_m"])
+    close("journey distance", gj["distance_m"], oj["distance_m"], rel)
     g, o = gpu["cells"], orc["cells"]
     for k in ("key", "row", "col", "bin", "count", "min", "max"):
         exact("cell " + k, g[k], o[k])
-    close("cell sum", g["sum"], o["sum"])
-    close("cell mean", g["mean"], o["mean"])
+    close("cell sum", g["sum"], o["sum"], rel)
+    close("cell mean", g["mean"], o["mean"], rel)
     if points:
         gp, op = gpu["points"], orc["points"]
         for k in ("perm", "key", "flags", "dwell"):
             exact("point " + k, gp[k], op[k])
-        close("point d", gp["d"], op["d"])
-        close("point vhat", gp["vhat"], op["vhat"])
-        close("point accel", gp["accel"], op["accel"])
+        close("point d", gp["d"], op["d"], rel)
+        close("point vhat", gp["vhat"], op["vhat"], rel)
+        close("point accel", gp["accel"], op["accel"], rel)

@@ -55,7 +55,7 @@ def test_create_rejects_bad_config_without_touching_the_gpu(so):
     assert b"positive" in P.lib.cvetl_last_error(None)
     cfg = P.default_config(n_rows=100000, n_cols=100000)
     assert P.lib.cvetl_create(ctypes.byref(cfg), ctypes.byref(h)) == P.EINVAL
-    cfg = P.default_config(precision=P.FP32)
+    cfg = P.default_config(precision=7)
     assert P.lib.cvetl_create(ctypes.byref(cfg), ctypes.byref(h)) == P.EINVAL
     assert P.lib.cvetl_transform(None) == P.EINVAL
     assert P.lib.cvetl_destroy(None) == P.OK
