@@ -243,7 +243,7 @@ def run_ours(args):
     launches = max(1, stages[top]["launches"])
     avg_ms = stages[top]["ms"] / launches
     hbm_peak, peak_src = load_peaks()
-    tpr = TRAFFIC_PER_RECORD.get(top)
+    tpr = TRAFFIC_PER_RECORD.get(top) if args.precision == "fp64" else None
     traffic = tpr * counters["n_valid"] if tpr else None
     if top == "journeys" and args.precision == "fp64":
         gops_peak, mhz = fp64_peak_gops()

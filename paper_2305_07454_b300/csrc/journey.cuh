@@ -7,13 +7,14 @@
 namespace cvetl {
 
 constexpr int kJBlock = 256;   // threads per journey CTA
-constexpr int kJCap = 3072;    // records sorted in shared memory in one piece
-constexpr int kBucketsBig = 15360;  // time buckets for journeys above kJCap (counters in shared memory)
+constexpr int kJCap = 4096;    // records sorted in shared memory in one piece
+constexpr int kBucketsBig = 12288;  // time buckets for journeys above kJCap (counters in shared memory)
 constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memory chunk (fallback)
-// dynamic shared memory of the journey kernel: two kJCap key buffers + kJCap bucket counters,
-// or (journeys above kJCap, keys in global scratch) kBucketsBig counters
-constexpr int kJSmem = 2 * kJCap * 8 + kJCap * 4;
+// dynamic shared memory of the journey kernel: a kJCap key buffer + kJCap bucket counters, or
+// (journeys above kJCap, keys in global scratch) kBucketsBig counters
+constexpr int kJSmem = kJCap * 8 + kJCap * 4;
 static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
+static_assert(kEChunk * 16 <= kJSmem, "fallback pair chunks must fit the dynamic shared memory");
 
 // cosine table entry: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, unused}
 struct __align__(32) CosEntry {
@@ -407,6 +408,64 @@ __device__ bool cta_bucket_sort(const unsigned long long* A, unsigned long long*
   return true;
 }
 
+// The same counting sort, with the keys rebuilt from the journey's records on each pass
+// (the records stay in L2), so that only the output buffer B takes shared memory.
+__device__ __forceinline__ unsigned long long rec_key(const Rec* __restrict__ R, int i,
+                                                      unsigned long long tmin, int pos_bits) {
+  return ((((unsigned long long)R[i].ts ^ kSign64) - tmin) << pos_bits) | (unsigned long long)i;
+}
+
+__device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long long tmin, int pos_bits,
+                                    unsigned long long* B, int n, unsigned long long span,
+                                    uint32_t* cnt, int nb, uint32_t* scan_scratch, int* flag) {
+  const int tid = threadIdx.x;
+  const float scale = (float)nb / ((float)span + 1.0f);
+  for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
+  __syncthreads();
+  for (int i = tid; i < n; i += kJBlock) {
+    const int b = min(nb - 1, (int)(__ull2float_rz(rec_key(R, i, tmin, pos_bits) >> pos_bits) * scale));
+    atomicAdd(&cnt[b], 1u);
+  }
+  __syncthreads();
+  const int chunk = (nb + kJBlock - 1) / kJBlock;
+  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
+  uint32_t sum = 0, mx = 0;
+  for (int i = c0; i < c1; ++i) {
+    sum += cnt[i];
+    mx = max(mx, cnt[i]);
+  }
+  if (tid == 0) *flag = 0;
+  uint32_t base = block_excl_scan<kJBlock>(sum, scan_scratch, nullptr);
+  if (mx > (uint32_t)kMaxBucket) *flag = 1;
+  for (int i = c0; i < c1; ++i) {
+    const uint32_t v = cnt[i];
+    cnt[i] = base;
+    base += v;
+  }
+  __syncthreads();
+  if (*flag) return false;
+  for (int i = tid; i < n; i += kJBlock) {
+    const unsigned long long k = rec_key(R, i, tmin, pos_bits);
+    const int b = min(nb - 1, (int)(__ull2float_rz(k >> pos_bits) * scale));
+    B[atomicAdd(&cnt[b], 1u)] = k;
+  }
+  __syncthreads();
+  for (int b = tid; b < nb; b += kJBlock) {
+    const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
+    for (int i = lo + 1; i < hi; ++i) {
+      const unsigned long long v = B[i];
+      int q = i - 1;
+      while (q >= lo && B[q] > v) {
+        B[q + 1] = B[q];
+        --q;
+      }
+      B[q + 1] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
 // slot (arbitrary) here; reorder each such group by extracted-row index.
 __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
@@ -548,7 +607,7 @@ struct StitchSmem {
 };
 
 template <class Form>
-__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
+__global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__ rec,
                                                          const uint32_t* __restrict__ jn,
                                                          const uint32_t* __restrict__ joff, uint32_t J,
                                                          Elem* scrA, Elem* scrB, GridParams g,
@@ -569,17 +628,12 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
   const bool small = n <= kJCap;
-  unsigned long long* KA = small ? reinterpret_cast<unsigned long long*>(smem_raw)
-                                 : reinterpret_cast<unsigned long long*>(scrA + off);
-  unsigned long long* KB = small ? reinterpret_cast<unsigned long long*>(smem_raw) + kJCap
-                                 : reinterpret_cast<unsigned long long*>(scrB + off);
 
   // 1. order the bucket by (timestamp, row index)
-  // 1a. timestamps as order-preserving keys, and their range
+  // 1a. range of the timestamps (as order-preserving keys)
   unsigned long long lo = ~0ull, hi = 0ull;
   for (int i = tid; i < n; i += kJBlock) {
     const unsigned long long t = (unsigned long long)R[i].ts ^ kSign64;
-    KA[i] = t;
     lo = min(lo, t);
     hi = max(hi, t);
   }
@@ -605,24 +659,29 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   const unsigned long long* sortedK = nullptr;
   const Elem* sortedE = nullptr;
   if (radix) {
-    // 1b. packed keys ((ts - tmin) << pos_bits) | slot; counting sort by time bucket (radix
-    // sort when the buckets are crowded); ties by row index
-    for (int i = tid; i < n; i += kJBlock) KA[i] = ((KA[i] - tmin) << pos_bits) | (unsigned long long)i;
-    __syncthreads();
-    uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + 2 * kJCap * sizeof(unsigned long long))
+    // 1b. keys ((ts - tmin) << pos_bits) | slot: counting sort by time bucket into shared memory
+    // (global scratch above kJCap); radix sort through global scratch when buckets are crowded;
+    // ties by row index
+    unsigned long long* KB = small ? reinterpret_cast<unsigned long long*>(smem_raw)
+                                   : reinterpret_cast<unsigned long long*>(scrB + off);
+    uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + kJCap * sizeof(unsigned long long))
                           : reinterpret_cast<uint32_t*>(smem_raw);
     const int nb = small ? max(1, n) : min(n, kBucketsBig);
     unsigned long long* K;
-    if (n > kBucketsBig * 8 || !cta_bucket_sort(KA, KB, n, pos_bits, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
-      K = cta_radix_sort(KA, KB, n, nbits, ssort);
-    } else {
+    if (n <= kBucketsBig * 8 &&
+        cta_bucket_sort_rec(R, tmin, pos_bits, KB, n, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
       K = KB;
+    } else {
+      unsigned long long* GA = reinterpret_cast<unsigned long long*>(scrA + off);
+      unsigned long long* GB = reinterpret_cast<unsigned long long*>(scrB + off);
+      for (int i = tid; i < n; i += kJBlock) GA[i] = rec_key(R, i, tmin, pos_bits);
+      __syncthreads();
+      K = cta_radix_sort(GA, GB, n, nbits, ssort);
     }
     fix_ties(K, n, pos_bits, R);
     sortedK = K;
   } else {
     // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
-    __syncthreads();
     if (tid == 0) atomicAdd(&st->n_big, 1u);
     sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
   }
@@ -654,8 +713,11 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       run.mx = __int_as_float((int)0xFF800000u);  // -inf
       in_pre = true;  // an empty fragment of the previous thread's run
     }
+    // the next record is loaded one point ahead, so its latency overlaps this point's work
+    Rec nxt = R[radix ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos];
     for (int k = k0; k < k1; ++k) {
-      const Rec cur = R[radix ? (uint32_t)(sortedK[k] & pmask) : sortedE[k].pos];
+      const Rec cur = nxt;
+      if (k + 1 < k1) nxt = R[radix ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos];
       const typename Form::Cos ccur = Form::cosine(cur.lat, g);
       const uint32_t key = cell_key(cur.lat, cur.lon, cur.ts, g);
       uint8_t fl = 0;
