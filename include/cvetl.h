@@ -62,6 +62,7 @@ typedef enum {
 
 enum { CVETL_FP64 = 0, CVETL_FP32 = 1 };
 enum { CVETL_IN_COLUMNS = 0, CVETL_IN_CSV = 1 };
+enum { CVETL_BATCH = 0, CVETL_STREAM = 1 };
 
 /* per-point flags */
 #define CVETL_F_START 0x01u   /* first point of its journey */
@@ -88,6 +89,8 @@ typedef struct {
   int32_t device;                    /* CUDA device ordinal */
   size_t mem_budget_bytes;           /* device memory the context may hold; 0 = unlimited */
   void* stream;                      /* cudaStream_t */
+  int32_t mode;                      /* CVETL_BATCH (one batch per extract) or CVETL_STREAM */
+  int64_t lateness_ms;               /* stream mode: how late a record may arrive (30000) */
 } cvetl_config;
 
 typedef struct {
@@ -104,6 +107,9 @@ typedef struct {
   /* CVETL_IN_CSV: csv_len bytes of text (see the grammar at cvetl_extract). */
   const char* csv;
   size_t csv_len;
+  /* stream mode: the end of the window's arrival interval (ms, same clock as ts); after the
+   * window the watermark is window_end_ms - lateness_ms */
+  int64_t window_end_ms;
 } cvetl_input;
 
 typedef struct {
@@ -212,7 +218,18 @@ cvetl_status cvetl_load(cvetl_ctx* ctx);
  * point tables are empty until cvetl_load). Synchronises ctx->stream (it reads the sizes). */
 cvetl_status cvetl_results(cvetl_ctx* ctx, cvetl_tables* out);
 
-/* Streaming mode is not built in this version: returns CVETL_ESTATE. */
+/* Stream mode (config.mode = CVETL_STREAM; the paper runs batches only, this serves windows of
+ * records as they arrive). Per window: cvetl_extract appends the window's rows (binary columns)
+ * to a pending store on the device; cvetl_transform finalises every pending point whose
+ * timestamp is at or below the watermark W = window_end_ms - lateness_ms, in (journey,
+ * timestamp, arrival) order, each journey continuing from its device-resident last point, open
+ * run and running sums; cvetl_load folds the window's closed runs into the device-resident
+ * cell table. A row whose timestamp is below the previous window's watermark when it arrives
+ * is dropped and counted in n_too_late. cvetl_results reports the tables of everything
+ * finalised so far. cvetl_flush finalises every pending point and closes every open run (end of
+ * the stream); afterwards the tables equal those of one batch over the same rows (integers,
+ * min and max exactly, sums within rounding) and the stream accepts no more windows.
+ * Windows must come in order of window_end_ms. In batch mode cvetl_flush returns CVETL_ESTATE. */
 cvetl_status cvetl_flush(cvetl_ctx* ctx);
 
 /* Per-kernel launch counts and (with profile = 1) CUDA-event times, summed since the

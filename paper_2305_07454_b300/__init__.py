@@ -19,6 +19,7 @@ OK, EINVAL, ENOMEM, EFULL, ESTATE, ECUDA, ETIMEOUT, EPARSE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "EFULL", "ESTATE", "ECUDA", "ETIMEOUT", "EPARSE"]
 FP64, FP32 = 0, 1
 IN_COLUMNS, IN_CSV = 0, 1
+BATCH, STREAM = 0, 1
 KEY_INVALID = 0xFFFFFFFF
 F_START, F_DUP, F_OFFGRID, F_STOP = 0x01, 0x02, 0x04, 0x08
 
@@ -34,6 +35,7 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("materialize_points", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("device", ctypes.c_int32),
         ("mem_budget_bytes", ctypes.c_size_t), ("stream", _P),
+        ("mode", ctypes.c_int32), ("lateness_ms", ctypes.c_int64),
     ]
 
 
@@ -41,7 +43,7 @@ class Input(ctypes.Structure):
     _fields_ = [
         ("kind", ctypes.c_int32), ("on_device", ctypes.c_int32), ("n", ctypes.c_int64),
         ("jid", _P), ("ts", _P), ("lat", _P), ("lon", _P), ("speed", _P), ("heading", _P),
-        ("csv", _P), ("csv_len", ctypes.c_size_t),
+        ("csv", _P), ("csv_len", ctypes.c_size_t), ("window_end_ms", ctypes.c_int64),
     ]
 
 
@@ -175,9 +177,9 @@ class Pipeline:
     def __exit__(self, *a):
         self.close()
 
-    def extract(self, cols: dict):
+    def extract(self, cols: dict, window_end_ms: int = 0):
         """cols: jid, ts, lat, lon, speed (+ heading) as torch tensors, all on the device or
-        all on the host, or numpy arrays (host)."""
+        all on the host, or numpy arrays (host). window_end_ms: stream mode only."""
         torch = self._torch
         names = ("jid", "ts", "lat", "lon", "speed")
         dtypes = (torch.int64, torch.int64, torch.float64, torch.float64, torch.float32)
@@ -198,7 +200,8 @@ class Pipeline:
         on_device = dev.pop()
         inp = Input(kind=IN_COLUMNS, on_device=int(on_device), n=n,
                     jid=ts[0].data_ptr(), ts=ts[1].data_ptr(), lat=ts[2].data_ptr(),
-                    lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None)
+                    lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None,
+                    window_end_ms=int(window_end_ms))
         self._keep = ts
         self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
 
@@ -230,6 +233,16 @@ class Pipeline:
             a = torch.as_tensor(_DeviceArray(ptr, t.n_extracted, ty), device="cuda")
             out[k] = a.cpu().numpy() if to_host else a
         return out
+
+    def flush(self):
+        """Stream mode: finalise every pending point and close every open run."""
+        self._check(lib.cvetl_flush(self._h))
+
+    def push_window(self, cols: dict, window_end_ms: int):
+        """Stream mode: one window (extract + transform + load)."""
+        self.extract(cols, window_end_ms)
+        self.transform()
+        self.load()
 
     def transform(self):
         self._check(lib.cvetl_transform(self._h))

@@ -21,6 +21,7 @@
 #include "journey.cuh"
 #include "cells.cuh"
 #include "csv.cuh"
+#include "stream.cuh"
 
 using namespace cvetl;
 
@@ -28,12 +29,14 @@ namespace {
 
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
-  ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_COUNT
+  ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
+  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
-                                     "csv_count", "csv_parse"};
+                                     "csv_count", "csv_parse", "stream_append", "stream_split",
+                                     "stream_tables"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -71,6 +74,18 @@ struct cvetl_ctx {
   JourneyOut jo{};
   CellOut co{};
   int64_t* jid_sorted = nullptr;
+  // stream mode
+  struct {
+    bool flushed = false, has_w_prev = false;
+    int64_t w_prev = 0, window_end = 0;
+    uint32_t arrival = 0, n_pending = 0, n_window = 0;
+    int side = 0, jgen = 0, cgen = 0;
+    Hash jh{};
+    JState js{};
+    CellHash ch{};
+    uint32_t n_journeys = 0, n_cells = 0;
+    int64_t tot_malformed = 0, tot_late = 0, tot_dup = 0, tot_off = 0, tot_final = 0, tot_runs = 0;
+  } ss;
   // statistics
   int64_t launches[ST_COUNT] = {};
   double ms[ST_COUNT] = {};
@@ -373,6 +388,456 @@ cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
   return CVETL_OK;
 }
 
+// ---- stream mode ------------------------------------------------------------------------
+// A persistent buffer that grows by copying its first `keep` elements (the per-batch scratch of
+// ensure() is reallocated without copying).
+template <typename T>
+cvetl_status grow_keep(cvetl_ctx* c, const char* name, size_t count, size_t keep, T** out) {
+  size_t bytes = count * sizeof(T);
+  if (bytes < 256) bytes = 256;
+  DevBuf& b = c->bufs[name];
+  if (b.bytes >= bytes) {
+    *out = reinterpret_cast<T*>(b.p);
+    return CVETL_OK;
+  }
+  const size_t grow = bytes + bytes / 4;
+  if (c->cfg.mem_budget_bytes && c->held + grow > c->cfg.mem_budget_bytes)
+    return fail(c, CVETL_EFULL, "buffer %s needs %zu more bytes; the context holds %zu of a %zu budget",
+                name, grow, c->held, c->cfg.mem_budget_bytes);
+  void* p = nullptr;
+  if (cudaMalloc(&p, grow) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, CVETL_ENOMEM, "cudaMalloc(%zu) for %s failed", grow, name);
+  }
+  if (b.p) {
+    if (keep) CK(cudaMemcpyAsync(p, b.p, keep * sizeof(T), cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(b.p);
+    c->held -= b.bytes;
+  }
+  b.p = p;
+  b.bytes = grow;
+  c->held += grow;
+  *out = reinterpret_cast<T*>(p);
+  return CVETL_OK;
+}
+
+#define GROW(name, count, keep, ptr)                           \
+  do {                                                         \
+    cvetl_status s_ = grow_keep(c, name, (count), (keep), (ptr)); \
+    if (s_ != CVETL_OK) return s_;                             \
+  } while (0)
+
+// A journey table of `cap` slots (+ the spare slot) and its state arrays, zeroed.
+cvetl_status alloc_journey_table(cvetl_ctx* c, uint32_t cap, int gen, Hash* h, JState* js) {
+  const size_t m = (size_t)cap + 1;
+  char nm[64];
+#define JBUF(field, type, ptr)                                        \
+  snprintf(nm, sizeof nm, "sj%d." field, gen);                       \
+  ENSURE(nm, m, ptr);                                                 \
+  CK(cudaMemsetAsync(*(ptr), 0, m * sizeof(type), c->st));
+  JBUF("keys", unsigned long long, &h->keys);
+  CK(cudaMemsetAsync(h->keys, 0xFF, m * 8, c->st));
+  JBUF("cnt", uint32_t, &h->cnt);
+  JBUF("aux", uint32_t, &h->aux);
+  JBUF("n", int64_t, &js->n);
+  JBUF("start", int64_t, &js->start_ts);
+  JBUF("end", int64_t, &js->end_ts);
+  JBUF("dwell", int64_t, &js->dwell);
+  JBUF("dist", double, &js->dist);
+  JBUF("slat", double, &js->slat);
+  JBUF("slon", double, &js->slon);
+  JBUF("lts", int64_t, &js->l_ts);
+  JBUF("llat", double, &js->l_lat);
+  JBUF("llon", double, &js->l_lon);
+  JBUF("lspd", float, &js->l_spd);
+  JBUF("lkey", uint32_t, &js->l_key);
+  JBUF("rcnt", uint32_t, &js->r_cnt);
+  JBUF("rs", float, &js->r_s);
+  JBUF("rc", float, &js->r_c);
+  JBUF("rmn", float, &js->r_mn);
+  JBUF("rmx", float, &js->r_mx);
+#undef JBUF
+  h->cap = cap;
+  h->mask = cap - 1;
+  return CVETL_OK;
+}
+
+cvetl_status alloc_cell_table(cvetl_ctx* c, uint32_t cap, int gen, CellHash* ch) {
+  char nm[64];
+  const size_t m = cap;
+#define CBUF(field, type, ptr)                                        \
+  snprintf(nm, sizeof nm, "sc%d." field, gen);                       \
+  ENSURE(nm, m, ptr);                                                 \
+  CK(cudaMemsetAsync(*(ptr), 0, m * sizeof(type), c->st));
+  CBUF("keys", uint32_t, &ch->keys);
+  CK(cudaMemsetAsync(ch->keys, 0xFF, m * 4, c->st));
+  CBUF("count", uint32_t, &ch->count);
+  CBUF("sum", double, &ch->sum);
+  CBUF("mn", float, &ch->mn);
+  CBUF("mx", float, &ch->mx);
+#undef CBUF
+  ch->cap = cap;
+  ch->mask = cap - 1;
+  return CVETL_OK;
+}
+
+void free_gen(cvetl_ctx* c, const char* prefix) {
+  cudaStreamSynchronize(c->st);
+  for (auto it = c->bufs.begin(); it != c->bufs.end();) {
+    if (it->first.rfind(prefix, 0) == 0) {
+      if (it->second.p) cudaFree(it->second.p);
+      c->held -= it->second.bytes;
+      it = c->bufs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+uint32_t* stream_counter(cvetl_ctx* c, const char* name) {
+  uint32_t* p = nullptr;
+  ensure(c, name, 1, &p);
+  return p;
+}
+
+cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
+  auto& ss = c->ss;
+  if (ss.flushed) return fail(c, CVETL_ESTATE, "the stream was flushed; create a new context for a new stream");
+  if (in->kind != CVETL_IN_COLUMNS) return fail(c, CVETL_EINVAL, "stream mode takes binary columns");
+  if (c->state == 1 || c->state == 2)
+    return fail(c, CVETL_ESTATE, "the previous window has not been transformed and loaded");
+  if (ss.has_w_prev && in->window_end_ms < ss.window_end)
+    return fail(c, CVETL_EINVAL, "windows must come in order of window_end_ms");
+  const size_t n = (size_t)in->n;
+  if ((uint64_t)ss.arrival + n > 0xFFFFFFFFull) return fail(c, CVETL_EINVAL, "the stream exceeds 2^32 rows");
+  // admission: the pending store must hold what is pending plus this window
+  const size_t need = (size_t)ss.n_pending + n;
+  int64_t* pj;
+  Rec* pr;
+  char nj[32], nr[32];
+  snprintf(nj, sizeof nj, "sp.jid%d", ss.side);
+  snprintf(nr, sizeof nr, "sp.rec%d", ss.side);
+  GROW(nj, need, ss.n_pending, &pj);
+  GROW(nr, need, ss.n_pending, &pr);
+  const int64_t* jid = in->jid;
+  const int64_t* ts = in->ts;
+  const double* lat = in->lat;
+  const double* lon = in->lon;
+  const float* spd = in->speed;
+  if (!in->on_device && n) {
+    int64_t *a, *b;
+    double *x, *y;
+    float* z;
+    ENSURE("in.jid", n, &a);
+    ENSURE("in.ts", n, &b);
+    ENSURE("in.lat", n, &x);
+    ENSURE("in.lon", n, &y);
+    ENSURE("in.spd", n, &z);
+    CK(cudaMemcpyAsync(a, in->jid, n * 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(b, in->ts, n * 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(x, in->lat, n * 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(y, in->lon, n * 8, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(z, in->speed, n * 4, cudaMemcpyHostToDevice, c->st));
+    jid = a; ts = b; lat = x; lon = y; spd = z;
+  }
+  uint32_t* pc = stream_counter(c, "sp.count");
+  CK(cudaMemcpyAsync(pc, &ss.n_pending, 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (n) {
+    LAUNCH(ST_STREAM_APPEND, (k_stream_append<<<grid_for(n, 256), 256, 0, c->st>>>(
+                                 jid, ts, lat, lon, spd, (uint32_t)n, ss.arrival, ss.w_prev,
+                                 ss.has_w_prev ? 1 : 0, pj, pr, pc, (uint32_t)need, c->dstate)));
+    LAUNCH_CHECK();
+  }
+  cvetl_status s = read_state(c);
+  if (s != CVETL_OK) return s;
+  uint32_t np = 0;
+  CK(cudaMemcpy(&np, pc, 4, cudaMemcpyDeviceToHost));
+  ss.n_pending = np;
+  ss.tot_malformed += (int64_t)c->hstate->n_malformed;
+  ss.tot_late += (int64_t)c->hstate->n_too_late;
+  ss.arrival += (uint32_t)n;
+  ss.n_window = (uint32_t)n;
+  ss.window_end = in->window_end_ms;
+  c->n_in += (int64_t)n;
+  c->state = 1;
+  return CVETL_OK;
+}
+
+// Finalises the pending points at or below the watermark (all of them when `all`), continuing
+// each journey from its state; the window's closed runs are left for stream_fold.
+cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
+  auto& ss = c->ss;
+  const int64_t wm = ss.window_end - c->cfg.lateness_ms;
+  // the journey table must keep a load <= 1/2 after this window's new journeys
+  if (ss.jh.cap == 0 || (uint64_t)(ss.n_journeys + ss.n_pending) * 2 > ss.jh.cap) {
+    uint32_t cap = next_pow2(2ull * ((uint64_t)ss.n_journeys + ss.n_pending + 1024));
+    Hash nh{};
+    JState nj{};
+    const int gen = ss.jgen ^ 1;
+    cvetl_status s = alloc_journey_table(c, cap, gen, &nh, &nj);
+    if (s != CVETL_OK) return s;
+    uint32_t* nd = stream_counter(c, "sj.distinct");
+    CK(cudaMemsetAsync(nd, 0, 4, c->st));
+    if (ss.jh.cap) {
+      CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+      LAUNCH(ST_STREAM_TABLES, (k_journey_rehash<<<grid_for((size_t)ss.jh.cap + 1, 256), 256, 0, c->st>>>(
+                                   ss.jh, ss.js, nh, nj, nd, c->dstate)));
+      LAUNCH_CHECK();
+      if ((s = read_state(c)) != CVETL_OK) return s;
+      char pre[16];
+      snprintf(pre, sizeof pre, "sj%d.", ss.jgen);
+      free_gen(c, pre);
+    }
+    ss.jh = nh;
+    ss.js = nj;
+    ss.jgen = gen;
+  }
+  Hash& h = ss.jh;
+  CK(cudaMemsetAsync(h.cnt, 0, ((size_t)h.cap + 1) * 4, c->st));
+  // split the pending store
+  const uint32_t np = ss.n_pending;
+  int64_t *pj, *qj;
+  Rec *pr, *qr, *fr;
+  uint32_t* fs;
+  char n1[32], n2[32];
+  snprintf(n1, sizeof n1, "sp.jid%d", ss.side);
+  snprintf(n2, sizeof n2, "sp.rec%d", ss.side);
+  GROW(n1, np, np, &pj);
+  GROW(n2, np, np, &pr);
+  snprintf(n1, sizeof n1, "sp.jid%d", ss.side ^ 1);
+  snprintf(n2, sizeof n2, "sp.rec%d", ss.side ^ 1);
+  GROW(n1, np, 0, &qj);
+  GROW(n2, np, 0, &qr);
+  ENSURE("sf.rec", np, &fr);
+  ENSURE("sf.slot", np, &fs);
+  uint32_t* qc = stream_counter(c, "sp.qcount");
+  uint32_t* fc = stream_counter(c, "sf.count");
+  CK(cudaMemsetAsync(qc, 0, 4, c->st));
+  CK(cudaMemsetAsync(fc, 0, 4, c->st));
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (np) {
+    LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
+                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, qc, fr, fs, fc, c->dstate)));
+    LAUNCH_CHECK();
+  }
+  cvetl_status s = read_state(c);
+  if (s != CVETL_OK) return s;
+  if (c->hstate->err & kErrHashOverflow) return fail(c, CVETL_ECUDA, "internal: journey table overflow");
+  uint32_t nf = 0, nq = 0;
+  CK(cudaMemcpy(&nf, fc, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&nq, qc, 4, cudaMemcpyDeviceToHost));
+  ss.n_journeys += c->hstate->n_distinct;
+  ss.side ^= 1;
+  ss.n_pending = nq;
+  // journeys touched by the window, ascending id: bucket offsets
+  unsigned long long* ukey;
+  uint32_t *uslot, *counter;
+  ENSURE("j.ukey", (size_t)nf + 1, &ukey);
+  ENSURE("j.uslot", (size_t)nf + 1, &uslot);
+  ENSURE("j.counter", 1, &counter);
+  CK(cudaMemsetAsync(counter, 0, 4, c->st));
+  if (nf) {
+    LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, counter)));
+    LAUNCH_CHECK();
+  }
+  uint32_t J = 0;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&J, counter, 4, cudaMemcpyDeviceToHost));
+  unsigned long long* skey;
+  uint32_t* sslot;
+  if ((s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot)) != CVETL_OK) return s;
+  uint32_t *jn, *joff, *total;
+  int64_t* jid_tmp;
+  ENSURE("j.n32", (size_t)J, &jn);
+  ENSURE("j.off32", (size_t)J, &joff);
+  ENSURE("j.total", 1, &total);
+  ENSURE("j.idtmp", (size_t)J, &jid_tmp);
+  if (J) {
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp)));
+    LAUNCH_CHECK();
+  }
+  if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
+  if (J) {
+    LAUNCH(ST_CURSORS, (k_journey_cursors<<<(J + 255) / 256, 256, 0, c->st>>>(sslot, J, joff, h)));
+    LAUNCH_CHECK();
+  }
+  Rec* rec;
+  ENSURE("rec", nf, &rec);
+  if (nf) {
+    LAUNCH(ST_SCATTER, (k_stream_scatter<<<grid_for(nf, 256), 256, 0, c->st>>>(fr, fs, nf, h, rec)));
+    LAUNCH_CHECK();
+  }
+  Elem *scrA, *scrB;
+  ENSURE("scr.a", nf, &scrA);
+  ENSURE("scr.b", nf, &scrB);
+  JourneyOut o{};
+  ENSURE("run.sortkey", (size_t)nf + ss.n_journeys, &o.run_sortkey);
+  ENSURE("run.cnt", (size_t)nf + ss.n_journeys, &o.run_cnt);
+  ENSURE("run.sum", (size_t)nf + ss.n_journeys, &o.run_sum);
+  ENSURE("run.min", (size_t)nf + ss.n_journeys, &o.run_min);
+  ENSURE("run.max", (size_t)nf + ss.n_journeys, &o.run_max);
+  o.run_cap = (uint32_t)(nf + ss.n_journeys);
+  c->jo = o;
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (J) {
+    if (c->cfg.precision == CVETL_FP32) {
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+    } else {
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+    }
+    LAUNCH_CHECK();
+  }
+  if (all) {  // end of the stream: close every open run
+    LAUNCH(ST_STREAM_TABLES, (k_stream_close_runs<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(
+                                 h, ss.js, o.run_sortkey, o.run_cnt, o.run_sum, o.run_min, o.run_max,
+                                 o.run_cap, c->dstate)));
+    LAUNCH_CHECK();
+  }
+  if ((s = read_state(c)) != CVETL_OK) return s;
+  c->R = c->hstate->n_runs;
+  ss.tot_dup += (int64_t)c->hstate->n_dup;
+  ss.tot_off += (int64_t)c->hstate->n_offgrid;
+  ss.tot_final += nf;
+  ss.tot_runs += c->R;
+  ss.w_prev = wm;
+  ss.has_w_prev = true;
+  return CVETL_OK;
+}
+
+// Folds the window's closed runs into the device-resident cell table.
+cvetl_status stream_fold(cvetl_ctx* c) {
+  auto& ss = c->ss;
+  const uint32_t R = c->R;
+  if ((uint64_t)(ss.n_cells + R) * 2 > ss.ch.cap) {
+    const uint32_t cap = next_pow2(2ull * ((uint64_t)ss.n_cells + R + 4096));
+    CellHash nc{};
+    const int gen = ss.cgen ^ 1;
+    cvetl_status s = alloc_cell_table(c, cap, gen, &nc);
+    if (s != CVETL_OK) return s;
+    uint32_t* ncount = stream_counter(c, "sc.count");
+    CK(cudaMemsetAsync(ncount, 0, 4, c->st));
+    if (ss.ch.cap) {
+      CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+      LAUNCH(ST_STREAM_TABLES, (k_cell_rehash<<<grid_for(ss.ch.cap, 256), 256, 0, c->st>>>(ss.ch, nc, ncount, c->dstate)));
+      LAUNCH_CHECK();
+      if ((s = read_state(c)) != CVETL_OK) return s;
+      char pre[16];
+      snprintf(pre, sizeof pre, "sc%d.", ss.cgen);
+      free_gen(c, pre);
+    }
+    ss.ch = nc;
+    ss.cgen = gen;
+  }
+  unsigned long long* skey;
+  uint32_t* sidx;
+  cvetl_status s = sort_pairs<unsigned long long>(c, "rsort", c->jo.run_sortkey, nullptr, R, 0, 64, &skey, &sidx);
+  if (s != CVETL_OK) return s;
+  uint32_t* head;
+  ENSURE("cell.head", (size_t)R, &head);
+  uint32_t* ncount = stream_counter(c, "sc.count");
+  CK(cudaMemcpyAsync(ncount, &ss.n_cells, 4, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (R) {
+    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head)));
+    LAUNCH_CHECK();
+    LAUNCH(ST_CELL_WRITE, (k_cell_fold<<<(R + 255) / 256, 256, 0, c->st>>>(
+                              skey, sidx, R, head, c->jo.run_cnt, c->jo.run_sum, c->jo.run_min,
+                              c->jo.run_max, ss.ch, ncount, c->dstate)));
+    LAUNCH_CHECK();
+  }
+  if ((s = read_state(c)) != CVETL_OK) return s;
+  if (c->hstate->err & kErrHashOverflow) return fail(c, CVETL_ECUDA, "internal: cell table overflow");
+  CK(cudaMemcpy(&ss.n_cells, ncount, 4, cudaMemcpyDeviceToHost));
+  return CVETL_OK;
+}
+
+// Builds the result tables from the device-resident journey and cell tables.
+cvetl_status stream_tables(cvetl_ctx* c) {
+  auto& ss = c->ss;
+  // cells, ascending key
+  const uint32_t K = ss.n_cells;
+  unsigned long long* ck;
+  uint32_t *cs, *counter;
+  ENSURE("t.ckey", (size_t)K + 1, &ck);
+  ENSURE("t.cslot", (size_t)K + 1, &cs);
+  ENSURE("j.counter", 1, &counter);
+  CK(cudaMemsetAsync(counter, 0, 4, c->st));
+  if (ss.ch.cap) {
+    LAUNCH(ST_STREAM_TABLES, (k_cell_collect<<<grid_for(ss.ch.cap, 256), 256, 0, c->st>>>(ss.ch, ck, cs, counter)));
+    LAUNCH_CHECK();
+  }
+  unsigned long long* sk;
+  uint32_t* sslot;
+  cvetl_status s = sort_pairs<unsigned long long>(c, "csort", ck, cs, K, 0, 32, &sk, &sslot);
+  if (s != CVETL_OK) return s;
+  CellOut& co = c->co;
+  ENSURE("out.c_key", (size_t)K, &co.key);
+  ENSURE("out.c_row", (size_t)K, &co.row);
+  ENSURE("out.c_col", (size_t)K, &co.col);
+  ENSURE("out.c_bin", (size_t)K, &co.bin);
+  ENSURE("out.c_count", (size_t)K, &co.count);
+  ENSURE("out.c_sum", (size_t)K, &co.sum);
+  ENSURE("out.c_mean", (size_t)K, &co.mean);
+  ENSURE("out.c_min", (size_t)K, &co.min);
+  ENSURE("out.c_max", (size_t)K, &co.max);
+  if (K) {
+    LAUNCH(ST_STREAM_TABLES, (k_cell_table_from_hash<<<(K + 255) / 256, 256, 0, c->st>>>(
+                                 sk, sslot, K, ss.ch, c->cfg.n_rows, c->cfg.n_cols, co)));
+    LAUNCH_CHECK();
+  }
+  c->K = K;
+  // journeys, ascending id
+  const uint32_t J = ss.n_journeys;
+  unsigned long long* jk;
+  uint32_t* jsl;
+  ENSURE("t.jkey", (size_t)J + 1, &jk);
+  ENSURE("t.jslot", (size_t)J + 1, &jsl);
+  CK(cudaMemsetAsync(counter, 0, 4, c->st));
+  if (ss.jh.cap) {
+    LAUNCH(ST_STREAM_TABLES, (k_journey_collect<<<grid_for((size_t)ss.jh.cap + 1, 256), 256, 0, c->st>>>(
+                                 ss.jh, ss.js, jk, jsl, counter)));
+    LAUNCH_CHECK();
+  }
+  uint32_t Jn = 0;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&Jn, counter, 4, cudaMemcpyDeviceToHost));
+  unsigned long long* jsk;
+  uint32_t* jss;
+  if ((s = sort_pairs<unsigned long long>(c, "jtsort", jk, jsl, Jn, 0, 64, &jsk, &jss)) != CVETL_OK) return s;
+  JourneyOut& o = c->jo;
+  uint32_t *n32, *off32, *total;
+  ENSURE("t.n32", (size_t)Jn, &n32);
+  ENSURE("t.off32", (size_t)Jn, &off32);
+  ENSURE("j.total", 1, &total);
+  ENSURE("out.j_id", (size_t)Jn, &c->jid_sorted);
+  ENSURE("out.j_n", (size_t)Jn, &o.n);
+  ENSURE("out.j_off", (size_t)Jn, &o.off);
+  ENSURE("out.j_start_ts", (size_t)Jn, &o.start_ts);
+  ENSURE("out.j_end_ts", (size_t)Jn, &o.end_ts);
+  ENSURE("out.j_duration", (size_t)Jn, &o.duration);
+  ENSURE("out.j_dwell", (size_t)Jn, &o.dwell);
+  ENSURE("out.j_dist", (size_t)Jn, &o.dist);
+  ENSURE("out.j_slat", (size_t)Jn, &o.slat);
+  ENSURE("out.j_slon", (size_t)Jn, &o.slon);
+  ENSURE("out.j_elat", (size_t)Jn, &o.elat);
+  ENSURE("out.j_elon", (size_t)Jn, &o.elon);
+  if (Jn) {
+    LAUNCH(ST_STREAM_TABLES, (k_journey_n32<<<(Jn + 255) / 256, 256, 0, c->st>>>(jss, Jn, ss.js, n32)));
+    LAUNCH_CHECK();
+  }
+  if ((s = scan_u32(c, n32, Jn, off32, total)) != CVETL_OK) return s;
+  if (Jn) {
+    LAUNCH(ST_STREAM_TABLES, (k_journey_table_from_state<<<(Jn + 255) / 256, 256, 0, c->st>>>(
+                                 jsk, jss, Jn, ss.js, off32, c->jid_sorted, o)));
+    LAUNCH_CHECK();
+  }
+  c->J = Jn;
+  CK(cudaStreamSynchronize(c->st));
+  return CVETL_OK;
+}
+
 // ======================================================================================
 extern "C" {
 
@@ -395,6 +860,8 @@ void cvetl_config_default(cvetl_config* cfg) {
   cfg->device = 0;
   cfg->mem_budget_bytes = 0;
   cfg->stream = nullptr;
+  cfg->mode = CVETL_BATCH;
+  cfg->lateness_ms = 30000;
 }
 
 int32_t cvetl_version(void) { return CVETL_VERSION; }
@@ -413,6 +880,10 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   if (!std::isfinite(cfg->lat_min) || !std::isfinite(cfg->lon_min) || !(cfg->cell_deg > 0.0) ||
       !std::isfinite(cfg->cell_deg) || !std::isfinite(cfg->earth_radius_m))
     return fail(nullptr, CVETL_EINVAL, "lat_min, lon_min, cell_deg and earth_radius_m must be finite, cell_deg > 0");
+  if (cfg->mode != CVETL_BATCH && cfg->mode != CVETL_STREAM)
+    return fail(nullptr, CVETL_EINVAL, "mode must be CVETL_BATCH or CVETL_STREAM");
+  if (cfg->mode == CVETL_STREAM && cfg->lateness_ms < 0)
+    return fail(nullptr, CVETL_EINVAL, "lateness_ms must be >= 0");
   if (cfg->precision != CVETL_FP64 && cfg->precision != CVETL_FP32)
     return fail(nullptr, CVETL_EINVAL, "precision must be CVETL_FP64 or CVETL_FP32");
   cudaError_t e = cudaSetDevice(cfg->device);
@@ -503,6 +974,14 @@ cvetl_status cvetl_destroy(cvetl_ctx* c) {
 cvetl_status cvetl_extract(cvetl_ctx* c, const cvetl_input* in) {
   if (!c) return CVETL_EINVAL;
   if (!in) return fail(c, CVETL_EINVAL, "cvetl_extract: NULL input");
+  if (c->cfg.mode == CVETL_STREAM) {
+    if (in->n < 0 || in->n > CVETL_MAX_RECORDS)
+      return fail(c, CVETL_EINVAL, "n = %lld outside [0, %lld]", (long long)in->n, (long long)CVETL_MAX_RECORDS);
+    if (in->n > 0 && (!in->jid || !in->ts || !in->lat || !in->lon || !in->speed))
+      return fail(c, CVETL_EINVAL, "cvetl_extract: NULL column");
+    cudaSetDevice(c->cfg.device);
+    return stream_extract(c, in);
+  }
   if (in->kind == CVETL_IN_CSV) return extract_csv(c, in);
   if (in->kind != CVETL_IN_COLUMNS) return fail(c, CVETL_EINVAL, "unknown input kind %d", in->kind);
   if (in->n < 0 || in->n > CVETL_MAX_RECORDS)
@@ -553,6 +1032,12 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   if (!c) return CVETL_EINVAL;
   if (c->state != 1) return fail(c, CVETL_ESTATE, "cvetl_transform needs a preceding cvetl_extract");
   cudaSetDevice(c->cfg.device);
+  if (c->cfg.mode == CVETL_STREAM) {
+    cvetl_status s = stream_finalize(c, false);
+    if (s != CVETL_OK) return s;
+    c->state = 2;
+    return CVETL_OK;
+  }
   const uint32_t n = (uint32_t)c->n_rows;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
 
@@ -674,9 +1159,9 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   o.run_cap = (uint32_t)nv;
   if (J) {
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
     }
     LAUNCH_CHECK();
   }
@@ -691,6 +1176,12 @@ cvetl_status cvetl_load(cvetl_ctx* c) {
   if (!c) return CVETL_EINVAL;
   if (c->state != 2) return fail(c, CVETL_ESTATE, "cvetl_load needs a preceding cvetl_transform");
   cudaSetDevice(c->cfg.device);
+  if (c->cfg.mode == CVETL_STREAM) {
+    cvetl_status s = stream_fold(c);
+    if (s != CVETL_OK) return s;
+    c->state = 3;
+    return CVETL_OK;
+  }
   const uint32_t R = c->R;
   unsigned long long* skey;
   uint32_t* sidx;
@@ -743,6 +1234,36 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
   r->x_speed = c->spd;
   r->x_heading = c->heading;
   r->n_in = c->n_in;
+  if (c->cfg.mode == CVETL_STREAM) {  // tables of everything finalised so far
+    auto& ss = c->ss;
+    r->n_extracted = 0;
+    r->x_jid = nullptr;
+    r->x_ts = nullptr;
+    r->x_lat = r->x_lon = nullptr;
+    r->x_speed = r->x_heading = nullptr;
+    if (c->state == 1 || c->state == 2)
+      return fail(c, CVETL_ESTATE, "finish the window (transform, load) before reading results");
+    cvetl_status s = stream_tables(c);
+    if (s != CVETL_OK) return s;
+    const CellOut& co = c->co;
+    r->n_cells = c->K;
+    r->cell_key = co.key; r->cell_row = co.row; r->cell_col = co.col; r->cell_bin = co.bin;
+    r->cell_count = co.count; r->cell_sum = co.sum; r->cell_mean = co.mean;
+    r->cell_min = co.min; r->cell_max = co.max;
+    const JourneyOut& o = c->jo;
+    r->n_journeys = c->J;
+    r->j_id = c->jid_sorted; r->j_n = o.n; r->j_offset = o.off; r->j_start_ts = o.start_ts;
+    r->j_end_ts = o.end_ts; r->j_duration_ms = o.duration; r->j_distance_m = o.dist;
+    r->j_dwell_ms = o.dwell; r->j_start_lat = o.slat; r->j_start_lon = o.slon;
+    r->j_end_lat = o.elat; r->j_end_lon = o.elon;
+    r->n_malformed = ss.tot_malformed;
+    r->n_valid = ss.tot_final;
+    r->n_out_of_grid = ss.tot_off;
+    r->n_dup = ss.tot_dup;
+    r->n_too_late = ss.tot_late;
+    r->n_runs = ss.tot_runs;
+    return CVETL_OK;
+  }
   if (c->state < 3) {  // extracted only: tables come with cvetl_load
     r->n_malformed = c->csv_malformed;
     return CVETL_OK;
@@ -795,7 +1316,17 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
 
 cvetl_status cvetl_flush(cvetl_ctx* c) {
   if (!c) return CVETL_EINVAL;
-  return fail(c, CVETL_ESTATE, "streaming mode is not built in this version");
+  if (c->cfg.mode != CVETL_STREAM) return fail(c, CVETL_ESTATE, "cvetl_flush is for stream mode");
+  if (c->ss.flushed) return fail(c, CVETL_ESTATE, "the stream was already flushed");
+  if (c->state == 1 || c->state == 2)
+    return fail(c, CVETL_ESTATE, "finish the window (transform, load) before flushing");
+  cudaSetDevice(c->cfg.device);
+  cvetl_status s = stream_finalize(c, true);
+  if (s != CVETL_OK) return s;
+  if ((s = stream_fold(c)) != CVETL_OK) return s;
+  c->ss.flushed = true;
+  c->state = 3;
+  return CVETL_OK;
 }
 
 cvetl_status cvetl_stats_get(cvetl_ctx* c, cvetl_stats* out) {

@@ -576,6 +576,20 @@ struct Fp32Form {
   };
 };
 
+// device-resident state of every journey seen so far, indexed by its slot in the journey hash
+struct JState {
+  int64_t *n, *start_ts, *end_ts, *dwell;
+  double *dist, *slat, *slon;
+  // last finalised point: the predecessor of the journey's next point
+  int64_t* l_ts;
+  double *l_lat, *l_lon;
+  float* l_spd;
+  uint32_t* l_key;
+  // run of equal keys still open at the last finalised point
+  uint32_t *r_cnt;
+  float *r_s, *r_c, *r_mn, *r_mx;
+};
+
 // Run fragments a thread hands to the stitch at the end of the walk.
 struct RunPart {
   uint32_t key, cnt, start;
@@ -611,7 +625,8 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
                                                          const uint32_t* __restrict__ jn,
                                                          const uint32_t* __restrict__ joff, uint32_t J,
                                                          Elem* scrA, Elem* scrB, GridParams g,
-                                                         JourneyOut o, DevState* st) {
+                                                         JourneyOut o, DevState* st,
+                                                         const uint32_t* __restrict__ jslot, JState js) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SortSmem ssort;
   __shared__ double red_d[kJBlock / 32];
@@ -620,6 +635,8 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   __shared__ int s_flag;
   __shared__ int64_t s_first_ts, s_last_ts;
   __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
+  __shared__ float s_last_spd;
+  __shared__ uint32_t s_last_key;
 
   const uint32_t j = blockIdx.x;
   if (j >= J) return;
@@ -628,6 +645,10 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
   const bool small = n <= kJCap;
+  // stream mode: the journey continues from its state (last point, open run, running sums)
+  const bool stream = js.n != nullptr;
+  const uint32_t slot = stream ? jslot[j] : 0u;
+  const bool has_prev = stream && js.n[slot] > 0;
 
   // 1. order the bucket by (timestamp, row index)
   // 1a. range of the timestamps (as order-preserving keys)
@@ -712,6 +733,16 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       run.mn = __int_as_float(0x7F800000);   // +inf
       run.mx = __int_as_float((int)0xFF800000u);  // -inf
       in_pre = true;  // an empty fragment of the previous thread's run
+    } else if (has_prev) {  // predecessor: the journey's last point of an earlier window
+      p_ts = js.l_ts[slot];
+      p_lat = js.l_lat[slot];
+      p_lon = js.l_lon[slot];
+      p_spd = js.l_spd[slot];
+      p_cos = Form::cosine(p_lat, g);
+      run.key = js.l_key[slot];
+      run.mn = __int_as_float(0x7F800000);
+      run.mx = __int_as_float((int)0xFF800000u);
+      in_pre = true;
     }
     // the next record is loaded one point ahead, so its latency overlaps this point's work
     Rec nxt = R[radix ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos];
@@ -725,10 +756,12 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       float vh = 0.0f, ac = 0.0f;
       int64_t dw = 0;
       if (k == 0) {
-        fl |= kFStart;
         s_first_ts = cur.ts;
         s_first_lat = cur.lat;
         s_first_lon = cur.lon;
+      }
+      if (k == 0 && !has_prev) {
+        fl |= kFStart;
       } else {
         const int64_t dt = (int64_t)((unsigned long long)cur.ts - (unsigned long long)p_ts);
         if (dt == 0) fl |= kFDup;
@@ -780,6 +813,8 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       s_last_ts = p_ts;
       s_last_lat = p_lat;
       s_last_lon = p_lon;
+      s_last_spd = p_spd;
+      s_last_key = run.key;
     }
     if (in_pre) {  // no key change in the whole range
       pre = run;
@@ -799,6 +834,8 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   __syncthreads();
   if (tid == 0) {
     RunPart open{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
+    if (has_prev)  // the run left open by the last window; emitted under this window's offset
+      open = RunPart{js.l_key[slot], js.r_cnt[slot], off, js.r_s[slot], js.r_c[slot], js.r_mn[slot], js.r_mx[slot]};
     for (int t = 0; t < kJBlock; ++t) {
       if (!ss.has[t]) continue;
       const RunPart& p = ss.pre[t];
@@ -806,6 +843,31 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       if (ss.cont[t]) continue;
       run_emit(o, st, open);
       open = ss.suf[t];
+    }
+    if (stream) {  // the open run and the journey's sums stay on the device
+      if (!has_prev) {
+        js.start_ts[slot] = s_first_ts;
+        js.slat[slot] = s_first_lat;
+        js.slon[slot] = s_first_lon;
+      }
+      js.n[slot] += n;
+      js.end_ts[slot] = s_last_ts;
+      js.dist[slot] += sd;
+      js.dwell[slot] += sw;
+      js.l_ts[slot] = s_last_ts;
+      js.l_lat[slot] = s_last_lat;
+      js.l_lon[slot] = s_last_lon;
+      js.l_spd[slot] = s_last_spd;
+      js.l_key[slot] = s_last_key;
+      const bool keep = open.key != kKeyInvalid;
+      js.r_cnt[slot] = keep ? open.cnt : 0u;
+      js.r_s[slot] = open.s;
+      js.r_c[slot] = open.c;
+      js.r_mn[slot] = open.mn;
+      js.r_mx[slot] = open.mx;
+      if (sdup) atomicAdd(&st->n_dup, (unsigned long long)sdup);
+      if (soff) atomicAdd(&st->n_offgrid, (unsigned long long)soff);
+      return;
     }
     run_emit(o, st, open);
     o.n[j] = n;

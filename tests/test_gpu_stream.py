@@ -1,0 +1,162 @@
+"""Stream mode: windows of records by arrival time. After the last window and cvetl_flush the
+tables equal the batch tables of the oracle over the same records (integers, min and max
+exactly, sums within the tolerance); records older than the previous watermark when they arrive
+are dropped and counted; a stream gives the same bits alone and interleaved with others."""
+import numpy as np
+import pytest
+
+import cvgen
+from parity import compare, exact
+
+pytestmark = pytest.mark.gpu
+
+T0 = 1620518400000
+LATE = 30000
+
+
+def arrivals(cols, seed, late_frac=0.02, max_delay=30000):
+    rng = np.random.default_rng(seed)
+    n = cols["jid"].shape[0]
+    delay = np.zeros(n, np.int64)
+    k = rng.random(n) < late_frac
+    delay[k] = rng.integers(1, max_delay + 1, int(k.sum()))
+    return cols["ts"] + delay
+
+
+def windows(cols, arrival, width=60000):
+    """Records grouped by arrival window (input order inside a window), with window ends."""
+    w = (arrival - T0) // width
+    order = np.argsort(w, kind="stable")
+    ws = w[order]
+    bounds = np.flatnonzero(np.diff(ws)) + 1
+    out = []
+    for idx in np.split(order, bounds):
+        if idx.size == 0:
+            continue
+        wid = int(w[idx[0]])
+        out.append(({k: np.ascontiguousarray(v[idx]) for k, v in cols.items()}, T0 + (wid + 1) * width))
+    return out
+
+
+def stream_run(wins, precision=0, stream=None, lateness=LATE):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    with P.Pipeline(stream=stream, mode=P.STREAM, lateness_ms=lateness, precision=precision) as p:
+        for cols, end in wins:
+            t = {k: torch.from_numpy(cols[k]).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+            p.push_window(t, end)
+        p.flush()
+        return p.results()
+
+
+def expected_drops(wins, lateness=LATE):
+    """The watermark rule applied on the host: a record is too late when its timestamp is below
+    the watermark left by the previous window."""
+    keep = []
+    wprev = None
+    for cols, end in wins:
+        ok = np.ones(cols["ts"].shape[0], bool) if wprev is None else cols["ts"] >= wprev
+        keep.append({k: v[ok] for k, v in cols.items()})
+        wprev = end - lateness
+    return {k: np.concatenate([c[k] for c in keep]) for k in keep[0]}
+
+
+def test_stream_equals_batch(orc, small_day):
+    wins = windows(small_day, arrivals(small_day, 1))
+    assert len(wins) > 100
+    g = stream_run(wins)
+    o = orc.run({k: np.concatenate([c[k] for c, _ in wins]) for k in small_day})
+    assert g["counters"]["n_too_late"] == 0
+    compare(g, o, points=False)
+
+
+def test_stream_drops_records_beyond_the_lateness(orc, small_day):
+    wins = windows(small_day, arrivals(small_day, 2, late_frac=0.05, max_delay=120000))
+    kept = expected_drops(wins)
+    g = stream_run(wins)
+    n_late = sum(c["ts"].shape[0] for c, _ in wins) - kept["ts"].shape[0]
+    assert n_late > 0 and g["counters"]["n_too_late"] == n_late
+    o = orc.run(kept)
+    g["counters"]["n_in"] -= n_late
+    compare(g, o, points=False)
+
+
+def test_stream_float32_form(orc, small_day):
+    import paper_2305_07454_b300 as P
+
+    wins = windows(small_day, arrivals(small_day, 3))
+    g = stream_run(wins, precision=P.FP32)
+    o = orc.run({k: np.concatenate([c[k] for c, _ in wins]) for k in small_day})
+    compare(g, o, points=False, rel=1e-4)
+
+
+def test_each_stream_is_the_same_alone_and_in_the_mix():
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    days = [cvgen.generate(cvgen.params("small_day", seed=s, n_journeys=300)) for s in (11, 12, 13)]
+    wins = [windows(d, arrivals(d, s)) for s, d in zip((11, 12, 13), days)]
+    alone = [stream_run(w) for w in wins]
+    # interleaved: three contexts on three CUDA streams, windows pushed round-robin
+    streams = [torch.cuda.Stream() for _ in wins]
+    pipes = [P.Pipeline(stream=s, mode=P.STREAM, lateness_ms=LATE) for s in streams]
+    pos = [0, 0, 0]
+    while any(pos[i] < len(wins[i]) for i in range(3)):
+        for i in range(3):
+            if pos[i] < len(wins[i]):
+                cols, end = wins[i][pos[i]]
+                with torch.cuda.stream(streams[i]):
+                    t = {k: torch.from_numpy(cols[k]).cuda(non_blocking=False) for k in ("jid", "ts", "lat", "lon", "speed")}
+                streams[i].synchronize()
+                pipes[i].push_window(t, end)
+                pos[i] += 1
+    mixed = []
+    for p in pipes:
+        p.flush()
+        mixed.append(p.results())
+        p.close()
+    for a, m in zip(alone, mixed):
+        assert a["counters"] == m["counters"]
+        for part in ("cells", "journeys"):
+            for k in a[part]:
+                exact(f"{part} {k}", m[part][k], a[part][k])
+
+
+def test_stream_call_order_and_errors(small_day):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    wins = windows(small_day, arrivals(small_day, 4))[:3]
+    with P.Pipeline(mode=P.STREAM) as p:
+        t = {k: torch.from_numpy(wins[1][0][k]).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+        p.push_window(t, wins[1][1])
+        t0 = {k: torch.from_numpy(wins[0][0][k]).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+        with pytest.raises(P.CvetlError) as e:
+            p.extract(t0, wins[0][1])  # out of order
+        assert e.value.status == P.EINVAL
+        p.flush()
+        with pytest.raises(P.CvetlError) as e:
+            p.extract(t, wins[2][1])
+        assert e.value.status == P.ESTATE
+    with P.Pipeline() as p:
+        with pytest.raises(P.CvetlError) as e:
+            p.flush()
+        assert e.value.status == P.ESTATE
+
+
+def test_stream_memory_admission(small_day):
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    wins = windows(small_day, arrivals(small_day, 5))
+    big = {k: np.concatenate([c[k] for c, _ in wins]) for k in small_day}
+    with P.Pipeline(mode=P.STREAM, mem_budget_bytes=4 << 20) as p:
+        t = {k: torch.from_numpy(big[k]).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+        with pytest.raises(P.CvetlError) as e:
+            p.extract(t, wins[-1][1])
+        assert e.value.status == P.EFULL
