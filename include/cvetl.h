@@ -172,6 +172,7 @@ typedef struct {
   double ms[CVETL_MAX_STAGES];          /* summed CUDA-event time (profile = 1) */
   int64_t launches[CVETL_MAX_STAGES];   /* kernel launches */
   int64_t total_launches;               /* all of this context's kernel launches */
+  int64_t device_bytes;                 /* device memory the context holds now */
 } cvetl_stats;
 
 /* Fills *cfg with the statewide defaults listed beside each field. */
@@ -244,6 +245,79 @@ cvetl_status cvetl_destroy(cvetl_ctx* ctx);
 const char* cvetl_last_error(const cvetl_ctx* ctx);
 
 int32_t cvetl_version(void);
+
+/* ---- Serving runtime ---------------------------------------------------------------------
+ * The paper processes whole days as batches; the server serves windows of records as they
+ * arrive, with continuous batching across feeds. A feed is one stream-mode context (its own
+ * non-blocking CUDA stream, open-journey state and running cell table on the device). Each
+ * submitted window or flush is a request with a ticket. n_slots worker threads take requests
+ * from one FIFO queue: the requests of one feed run one at a time in submission order, the
+ * requests of different feeds run at the same time on their own streams, so windows that
+ * arrive while others are on the GPU start as soon as a slot and the memory budget allow.
+ * Admission by memory: a request reserves kServeBytesPerRow (CVETL_SERVE_BYTES_PER_ROW) per
+ * row while it runs; it is admitted when the memory the feeds hold plus the reservations of
+ * the running requests plus its own fits in mem_budget_bytes, or when nothing else runs.
+ * Admission is first come, first served: when the oldest request that its feed's order allows
+ * does not fit, no later request starts before it. */
+#define CVETL_SERVE_BYTES_PER_ROW 320
+#define CVETL_SERVE_MAX_SLOTS 64
+
+typedef struct cvetl_server cvetl_server;
+
+typedef struct {
+  int32_t n_slots;          /* requests on the GPU at once (worker threads), 1..CVETL_SERVE_MAX_SLOTS */
+  int32_t device;           /* CUDA device ordinal */
+  size_t mem_budget_bytes;  /* device memory of all feeds plus running reservations; 0 = unlimited */
+} cvetl_server_config;
+
+typedef struct {
+  int32_t status;     /* cvetl_status of the request */
+  int32_t feed;
+  int32_t kind;       /* 0 window, 1 flush */
+  int32_t slot;       /* the worker that ran it */
+  int64_t n;          /* rows of the window */
+  int64_t submit_ns;  /* steady clock (CLOCK_MONOTONIC) at submission */
+  int64_t start_ns;   /* at admission */
+  int64_t done_ns;    /* when its work had completed on the GPU */
+  int32_t peak_in_flight; /* most requests running at once at any time so far (server-wide) */
+  char message[164];  /* error text when status != CVETL_OK */
+} cvetl_ticket_info;
+
+/* Creates the server and its n_slots worker threads. CVETL_EINVAL for n_slots outside
+ * [1, CVETL_SERVE_MAX_SLOTS]. */
+cvetl_status cvetl_server_create(const cvetl_server_config* cfg, cvetl_server** out);
+
+/* Adds a feed: a stream-mode context created from *cfg (mode, stream, device and
+ * mem_budget_bytes are set by the server) on a new non-blocking stream. *feed gets its index. */
+cvetl_status cvetl_server_add_feed(cvetl_server* s, const cvetl_config* cfg, int32_t* feed);
+
+/* Queues one window of binary columns (in->kind = CVETL_IN_COLUMNS, host or device pointers,
+ * in->window_end_ms set) for a feed; returns at once with *ticket. The caller keeps the
+ * columns alive and unchanged until cvetl_server_wait on the ticket returns (host columns in
+ * pinned memory are copied asynchronously). CVETL_EINVAL for a bad feed or input,
+ * CVETL_EFULL when the window alone exceeds the budget, CVETL_ESTATE after the feed's flush. */
+cvetl_status cvetl_server_submit(cvetl_server* s, int32_t feed, const cvetl_input* in, uint64_t* ticket);
+
+/* Queues the end of a feed's stream (cvetl_flush): after it the feed takes no more windows. */
+cvetl_status cvetl_server_submit_flush(cvetl_server* s, int32_t feed, uint64_t* ticket);
+
+/* Waits for a ticket and releases it; *info (may be NULL) receives its record. Returns the
+ * request's own status, or CVETL_EINVAL for an unknown ticket. */
+cvetl_status cvetl_server_wait(cvetl_server* s, uint64_t ticket, cvetl_ticket_info* info);
+
+/* Waits until no request is queued or running. */
+cvetl_status cvetl_server_drain(cvetl_server* s);
+
+/* The feed's context, for cvetl_results / cvetl_stats_get while the feed has no request queued
+ * or running (CVETL_ESTATE otherwise); do not submit to the feed while using it. */
+cvetl_status cvetl_server_feed(cvetl_server* s, int32_t feed, cvetl_ctx** ctx);
+
+/* Runs what is running to completion, fails what is still queued with CVETL_ESTATE (their
+ * tickets are dropped), joins the workers and destroys the feeds. NULL is accepted. */
+cvetl_status cvetl_server_destroy(cvetl_server* s);
+
+/* Last error text of a server call (not of a request: see cvetl_ticket_info.message). */
+const char* cvetl_server_last_error(const cvetl_server* s);
 
 /* Allocation-free radix sort (the paper has no counterpart; it serves callers that may not
  * allocate device memory: code inside a host framework that owns the device memory pool and

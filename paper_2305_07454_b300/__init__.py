@@ -75,7 +75,19 @@ MAX_STAGES = 32
 class Stats(ctypes.Structure):
     _fields_ = [("n_stages", ctypes.c_int32), ("name", ctypes.c_char_p * MAX_STAGES),
                 ("ms", ctypes.c_double * MAX_STAGES), ("launches", ctypes.c_int64 * MAX_STAGES),
-                ("total_launches", ctypes.c_int64)]
+                ("total_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_size_t)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("feed", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("slot", ctypes.c_int32), ("n", ctypes.c_int64), ("submit_ns", ctypes.c_int64),
+                ("start_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("peak_in_flight", ctypes.c_int32), ("message", ctypes.c_char * 164)]
 
 
 def _load():
@@ -99,8 +111,21 @@ def _load():
     lib.cvetl_version.restype = ctypes.c_int32
     lib.cvetl_sort_u64_noalloc.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]
     lib.cvetl_sort_u64_noalloc.restype = ctypes.c_int
+    lib.cvetl_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
+    lib.cvetl_server_add_feed.argtypes = [_P, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int32)]
+    lib.cvetl_server_submit.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Input), ctypes.POINTER(ctypes.c_uint64)]
+    lib.cvetl_server_submit_flush.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.cvetl_server_wait.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(TicketInfo)]
+    lib.cvetl_server_drain.argtypes = [_P]
+    lib.cvetl_server_feed.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(_P)]
+    lib.cvetl_server_destroy.argtypes = [_P]
+    lib.cvetl_server_last_error.argtypes = [_P]
+    lib.cvetl_server_last_error.restype = ctypes.c_char_p
     for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
-              "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy"):
+              "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
+              "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
+              "cvetl_server_submit_flush", "cvetl_server_wait", "cvetl_server_drain",
+              "cvetl_server_feed", "cvetl_server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -110,8 +135,13 @@ lib = _load()
 # The C-ABI entry points declared in include/cvetl.h (checked by the tests).
 EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load",
            "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
-           "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc")
+           "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc", "cvetl_server_create",
+           "cvetl_server_add_feed", "cvetl_server_submit", "cvetl_server_submit_flush",
+           "cvetl_server_wait", "cvetl_server_drain", "cvetl_server_feed", "cvetl_server_destroy",
+           "cvetl_server_last_error")
 NOALLOC_MAX_PAIRS = 262144
+SERVE_BYTES_PER_ROW = 320
+SERVE_MAX_SLOTS = 64
 
 
 class CvetlError(RuntimeError):
@@ -136,6 +166,35 @@ def default_config(**kw) -> Config:
     return cfg
 
 
+def _columns_input(cols: dict, window_end_ms: int = 0):
+    """An Input over the five columns (torch tensors or numpy arrays) and the tensors to keep
+    alive while the library may read them."""
+    import torch
+
+    names = ("jid", "ts", "lat", "lon", "speed")
+    dtypes = (torch.int64, torch.int64, torch.float64, torch.float64, torch.float32)
+    ts = []
+    for k, dt in zip(names, dtypes):
+        v = cols[k]
+        if isinstance(v, np.ndarray):
+            v = torch.from_numpy(np.ascontiguousarray(v))
+        if v.dtype != dt or not v.is_contiguous() or v.dim() != 1:
+            raise ValueError(f"column {k} must be a contiguous 1-D {dt} tensor")
+        ts.append(v)
+    n = ts[0].shape[0]
+    if any(t.shape[0] != n for t in ts):
+        raise ValueError("columns differ in length")
+    dev = {t.is_cuda for t in ts}
+    if len(dev) != 1:
+        raise ValueError("columns must be all on the device or all on the host")
+    on_device = dev.pop()
+    inp = Input(kind=IN_COLUMNS, on_device=int(on_device), n=n,
+                jid=ts[0].data_ptr(), ts=ts[1].data_ptr(), lat=ts[2].data_ptr(),
+                lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None,
+                window_end_ms=int(window_end_ms))
+    return inp, ts
+
+
 class Pipeline:
     """One cvetl context: extract -> transform -> load -> results on one CUDA stream."""
 
@@ -155,6 +214,19 @@ class Pipeline:
             raise CvetlError(st, lib.cvetl_last_error(None).decode())
         self._h = h
         self._keep = None
+        self._owned = True
+
+    @classmethod
+    def _view(cls, handle):
+        """A Pipeline over a context the library owns (a server feed): results and stats only."""
+        import torch
+
+        p = cls.__new__(cls)
+        p._torch = torch
+        p._h = handle
+        p._keep = None
+        p._owned = False
+        return p
 
     def _check(self, st: int):
         if st != OK:
@@ -162,7 +234,8 @@ class Pipeline:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib.cvetl_destroy(self._h)
+            if self._owned:
+                lib.cvetl_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -180,29 +253,7 @@ class Pipeline:
     def extract(self, cols: dict, window_end_ms: int = 0):
         """cols: jid, ts, lat, lon, speed (+ heading) as torch tensors, all on the device or
         all on the host, or numpy arrays (host). window_end_ms: stream mode only."""
-        torch = self._torch
-        names = ("jid", "ts", "lat", "lon", "speed")
-        dtypes = (torch.int64, torch.int64, torch.float64, torch.float64, torch.float32)
-        ts = []
-        for k, dt in zip(names, dtypes):
-            v = cols[k]
-            if isinstance(v, np.ndarray):
-                v = torch.from_numpy(np.ascontiguousarray(v))
-            if v.dtype != dt or not v.is_contiguous() or v.dim() != 1:
-                raise ValueError(f"column {k} must be a contiguous 1-D {dt} tensor")
-            ts.append(v)
-        n = ts[0].shape[0]
-        if any(t.shape[0] != n for t in ts):
-            raise ValueError("columns differ in length")
-        dev = {t.is_cuda for t in ts}
-        if len(dev) != 1:
-            raise ValueError("columns must be all on the device or all on the host")
-        on_device = dev.pop()
-        inp = Input(kind=IN_COLUMNS, on_device=int(on_device), n=n,
-                    jid=ts[0].data_ptr(), ts=ts[1].data_ptr(), lat=ts[2].data_ptr(),
-                    lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None,
-                    window_end_ms=int(window_end_ms))
-        self._keep = ts
+        inp, self._keep = _columns_input(cols, window_end_ms)
         self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
 
     def extract_csv(self, text):
@@ -295,3 +346,83 @@ class Pipeline:
         self.transform()
         self.load()
         return self.results(to_host=to_host)
+
+
+class Server:
+    """The serving runtime (cvetl_server_*): stream-mode feeds, one FIFO request queue,
+    n_slots windows on the GPU at once (different feeds on their own CUDA streams), admission
+    by a device-memory budget. submit() returns a ticket at once; wait() returns its record
+    as a dict (status, feed, kind, slot, n, submit_ns, start_ns, done_ns, peak_in_flight,
+    message) and raises CvetlError when the request failed and check is true."""
+
+    def __init__(self, n_slots: int = 4, mem_budget_bytes: int = 0, device: int = 0):
+        cfg = ServerConfig(n_slots=n_slots, device=device, mem_budget_bytes=mem_budget_bytes)
+        h = _P()
+        st = lib.cvetl_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise CvetlError(st, lib.cvetl_server_last_error(None).decode())
+        self._h = h
+        self._keep = {}
+
+    def _check(self, st: int):
+        if st != OK:
+            raise CvetlError(st, lib.cvetl_server_last_error(self._h).decode())
+
+    def add_feed(self, **cfg) -> int:
+        c = default_config(**cfg)
+        f = ctypes.c_int32()
+        self._check(lib.cvetl_server_add_feed(self._h, ctypes.byref(c), ctypes.byref(f)))
+        return int(f.value)
+
+    def submit(self, feed: int, cols: dict, window_end_ms: int) -> int:
+        """Queues a window (host columns should be in pinned memory); the columns are kept
+        alive until wait() on the ticket."""
+        inp, keep = _columns_input(cols, window_end_ms)
+        t = ctypes.c_uint64()
+        self._check(lib.cvetl_server_submit(self._h, int(feed), ctypes.byref(inp), ctypes.byref(t)))
+        self._keep[int(t.value)] = keep
+        return int(t.value)
+
+    def submit_flush(self, feed: int) -> int:
+        t = ctypes.c_uint64()
+        self._check(lib.cvetl_server_submit_flush(self._h, int(feed), ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int, check: bool = True) -> dict:
+        info = TicketInfo()
+        st = lib.cvetl_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(info))
+        if st == EINVAL and info.submit_ns == 0:
+            self._check(st)
+        self._keep.pop(int(ticket), None)
+        out = {k: getattr(info, k) for k, _ in TicketInfo._fields_ if k != "message"}
+        out["message"] = info.message.decode(errors="replace")
+        if check and st != OK:
+            raise CvetlError(st, out["message"])
+        return out
+
+    def drain(self):
+        self._check(lib.cvetl_server_drain(self._h))
+
+    def feed(self, feed: int) -> Pipeline:
+        """A view of the feed's context (results, stats) while it has no request queued."""
+        h = _P()
+        self._check(lib.cvetl_server_feed(self._h, int(feed), ctypes.byref(h)))
+        return Pipeline._view(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.cvetl_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

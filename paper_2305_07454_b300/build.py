@@ -8,7 +8,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "libcvetl.so")
-SRC = os.path.join(HERE, "csrc", "cvetl.cu")
+SRC = [os.path.join(HERE, "csrc", "cvetl.cu"), os.path.join(HERE, "csrc", "server.cpp")]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -26,7 +26,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in _sources())
     if not force and os.path.exists(SO) and os.path.getmtime(SO) >= newest:
         return SO
-    cmd = ["nvcc", *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", SO, SRC]
+    cmd = ["nvcc", *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", SO, *SRC, "-lpthread"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

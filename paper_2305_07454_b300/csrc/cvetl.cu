@@ -1349,6 +1349,7 @@ cvetl_status cvetl_stats_get(cvetl_ctx* c, cvetl_stats* out) {
     out->launches[i] = c->launches[i];
   }
   out->total_launches = c->total_launches;
+  out->device_bytes = (int64_t)c->held;
   return CVETL_OK;
 }
 

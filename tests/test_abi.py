@@ -59,3 +59,16 @@ def test_create_rejects_bad_config_without_touching_the_gpu(so):
     assert P.lib.cvetl_create(ctypes.byref(cfg), ctypes.byref(h)) == P.EINVAL
     assert P.lib.cvetl_transform(None) == P.EINVAL
     assert P.lib.cvetl_destroy(None) == P.OK
+
+
+def test_server_rejects_bad_slot_counts_without_touching_the_gpu(so):
+    import ctypes
+
+    import paper_2305_07454_b300 as P
+
+    for n in (0, -1, P.SERVE_MAX_SLOTS + 1):
+        cfg = P.ServerConfig(n_slots=n, device=0, mem_budget_bytes=0)
+        h = ctypes.c_void_p()
+        assert P.lib.cvetl_server_create(ctypes.byref(cfg), ctypes.byref(h)) == P.EINVAL
+        assert b"n_slots" in P.lib.cvetl_server_last_error(None)
+        assert not h.value

@@ -7,36 +7,9 @@ import pytest
 
 import cvgen
 from parity import compare, exact
+from streams import LATE, arrivals, windows
 
 pytestmark = pytest.mark.gpu
-
-T0 = 1620518400000
-LATE = 30000
-
-
-def arrivals(cols, seed, late_frac=0.02, max_delay=30000):
-    rng = np.random.default_rng(seed)
-    n = cols["jid"].shape[0]
-    delay = np.zeros(n, np.int64)
-    k = rng.random(n) < late_frac
-    delay[k] = rng.integers(1, max_delay + 1, int(k.sum()))
-    return cols["ts"] + delay
-
-
-def windows(cols, arrival, width=60000):
-    """Records grouped by arrival window (input order inside a window), with window ends."""
-    w = (arrival - T0) // width
-    order = np.argsort(w, kind="stable")
-    ws = w[order]
-    bounds = np.flatnonzero(np.diff(ws)) + 1
-    out = []
-    for idx in np.split(order, bounds):
-        if idx.size == 0:
-            continue
-        wid = int(w[idx[0]])
-        out.append(({k: np.ascontiguousarray(v[idx]) for k, v in cols.items()}, T0 + (wid + 1) * width))
-    return out
-
 
 def stream_run(wins, precision=0, stream=None, lateness=LATE):
     import torch
