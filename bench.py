@@ -9,6 +9,15 @@ steps whose inputs are already in HBM; `e2e` times the same calls with pinned ho
 the host->device copy and the read-back of the result tables inside the timed region.
 Prints one JSON line (rank 0).
 
+The serving leg (`serving` in the line; --serve-feeds 0 skips it) replays the same day as
+one-minute arrival windows (2% of records up to 30 s late, so none is too late for the 30 s
+lateness) through the library's server: the day is split into journey-hash feeds, each window
+into one request per feed, FP32 form. "paced" submits a minute's requests only after the
+previous minute has completed (the GPU is idle when a window arrives, as under real-time
+60 s pacing; every latency is far below 60 s); "max_rate" submits the whole day at once.
+Window latency = the last request's completion - the first request's submission. The served
+tables are compared with the batch tables of the same day.
+
 --impl reference times the plain CPU oracle (the reference of this build) on the host, on a
 bounded sample of the same workload.
 """
@@ -290,12 +299,119 @@ def run_ours(args):
         "counters": counters,
         "clocks": clk.summary(),
     }
+    if args.serve_feeds > 0:
+        batch_cells = pipe.results(to_host=True)["cells"]
+        line["serving"] = serving(host, n, args, batch_cells, ms_step)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(host, n, budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
     pipe.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _window_order(host, n, feeds, t0, seed=7):
+    """Row order of the replay: by arrival minute, then feed (journey hash), input order inside."""
+    ts = host["ts"].numpy()
+    rng = np.random.default_rng(seed)
+    late = rng.random(n) < 0.02
+    arrival = ts.copy()
+    arrival[late] += rng.integers(1, 30001, int(late.sum()))
+    w = (arrival - t0) // 60000
+    del arrival, late
+    h = (host["jid"].numpy().astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(40)
+    key = w * feeds + (h % np.uint64(feeds)).astype(np.int64)
+    # 16-bit keys take numpy's radix sort
+    key = key.astype(np.int16 if int(key.max()) < 32767 else np.int32)
+    order = np.argsort(key, kind="stable")
+    n_win = int(w.max()) + 1
+    bounds = np.searchsorted(key[order], np.arange(n_win * feeds + 1))
+    return order, bounds, n_win
+
+
+def _replay(P, cols, bounds, n_win, feeds, t0, slots, budget, paced, upto=None):
+    """One replay through a fresh server; returns (per-window latency ms, per-window service ms,
+    seconds from the first submission to the last completion, feed results)."""
+    upto = n_win if upto is None else upto
+    with P.Server(n_slots=slots, mem_budget_bytes=budget) as srv:
+        ids = [srv.add_feed(precision=P.FP32, lateness_ms=30000) for _ in range(feeds)]
+
+        def submit(m):
+            out = []
+            for f in range(feeds):
+                a, b = int(bounds[m * feeds + f]), int(bounds[m * feeds + f + 1])
+                out.append(srv.submit(ids[f], {k: cols[k][a:b] for k in COLS}, t0 + (m + 1) * 60000))
+            return out
+
+        win = []
+        if paced:
+            for m in range(upto):
+                win.append([srv.wait(t) for t in submit(m)])
+        else:
+            tickets = [submit(m) for m in range(upto)]
+            win = [[srv.wait(t) for t in ts] for ts in tickets]
+        fl = [srv.wait(srv.submit_flush(f)) for f in ids]
+        first = min(i["submit_ns"] for w in win for i in w)
+        last = max(i["done_ns"] for i in fl)
+        lat = [(max(i["done_ns"] for i in w) - min(i["submit_ns"] for i in w)) / 1e6 for w in win]
+        svc = [(max(i["done_ns"] for i in w) - min(i["start_ns"] for i in w)) / 1e6 for w in win]
+        res = [srv.feed(f).results(to_host=True) for f in ids]
+        peak = max(i["peak_in_flight"] for i in fl)
+    return lat, svc, (last - first) / 1e9, res, peak
+
+
+def _merged_cells(res):
+    parts = [r["cells"] for r in res]
+    key = np.concatenate([p["key"] for p in parts])
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    head = np.flatnonzero(np.concatenate([[True], key[1:] != key[:-1]])) if key.size else np.zeros(0, np.int64)
+    cat = lambda k: np.concatenate([p[k] for p in parts])[order]
+    return {"key": key[head],
+            "count": np.add.reduceat(cat("count").astype(np.int64), head) if key.size else np.zeros(0, np.int64),
+            "sum": np.add.reduceat(cat("sum"), head) if key.size else np.zeros(0),
+            "min": np.minimum.reduceat(cat("min"), head) if key.size else np.zeros(0, np.float32),
+            "max": np.maximum.reduceat(cat("max"), head) if key.size else np.zeros(0, np.float32)}
+
+
+def serving(host, n, args, batch_cells, batch_ms):
+    """The serving leg: the day replayed through the server, paced and at maximum rate."""
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    t0 = int(P.default_config().t0_ms)
+    feeds, slots = args.serve_feeds, args.serve_slots or args.serve_feeds
+    budget = int(args.serve_budget_gb * (1 << 30))
+    order, bounds, n_win = _window_order(host, n, feeds, t0)
+    cols = {k: torch.empty(n, dtype=host[k].dtype, pin_memory=True) for k in COLS}
+    for k in COLS:
+        np.take(host[k].numpy(), order, out=cols[k].numpy())
+    del order
+    _replay(P, cols, bounds, n_win, feeds, t0, slots, budget, paced=True, upto=90)  # loads the kernels
+    pct = lambda v, q: float(np.percentile(np.asarray(v), q))
+    out = {"workload": f"the batch day replayed as {n_win} one-minute arrival windows, 2% of records "
+                       f"up to 30 s late, {feeds} journey-hash feeds, FP32 form",
+           "windows": n_win, "feeds": feeds, "slots": slots, "mem_budget_bytes": budget,
+           "records": n, "batch_fp64_ms_per_day": batch_ms}
+    sizes = np.diff(bounds[::feeds][: n_win + 1]) if feeds else []
+    out["window_records"] = {"min": int(np.min(sizes)), "p50": int(np.median(sizes)), "max": int(np.max(sizes))}
+    for mode, paced in (("paced", True), ("max_rate", False)):
+        lat, svc, secs, res, peak = _replay(P, cols, bounds, n_win, feeds, t0, slots, budget, paced)
+        out[mode] = {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "max_ms": max(lat),
+                     "service_p50_ms": pct(svc, 50), "service_p99_ms": pct(svc, 99),
+                     "records_per_s": n / secs, "seconds": secs, "peak_in_flight": peak}
+        if paced:
+            c = {k: sum(r["counters"][k] for r in res) for k in ("n_in", "n_too_late", "n_valid")}
+            m = _merged_cells(res)
+            b = batch_cells
+            same = (m["key"].shape == b["key"].shape and np.array_equal(m["key"], b["key"])
+                    and np.array_equal(m["count"], b["count"].astype(np.int64))
+                    and np.array_equal(m["min"], b["min"]) and np.array_equal(m["max"], b["max"]))
+            rel = float(np.max(np.abs(m["sum"] - b["sum"]) / np.maximum(np.abs(b["sum"]), 1e-300))) if same and b["sum"].size else None
+            out["vs_batch"] = {"counters": c, "keys_counts_min_max_equal": bool(same),
+                               "cell_sum_max_rel_err": rel}
+    return out
 
 
 def _sample_journeys(host, frac_den: int):
@@ -385,6 +501,9 @@ def main():
     ap.add_argument("--input", default="columns", choices=["columns", "csv"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve-feeds", type=int, default=4, help="0 skips the serving leg")
+    ap.add_argument("--serve-slots", type=int, default=0, help="server slots (default: one per feed)")
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

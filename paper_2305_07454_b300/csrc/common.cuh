@@ -25,13 +25,13 @@ struct DevState {
   uint32_t n_runs;      // cell runs emitted by the journey kernel
   uint32_t n_cells;
   uint32_t n_big;       // journeys taking the chunked-sort path
-  uint32_t pad0;
+  uint32_t n_touched;   // stream mode: journeys with points finalised by this window
   unsigned long long n_malformed;
   unsigned long long n_dup;
   unsigned long long n_offgrid;
   unsigned long long n_lines;  // CSV: lines in the text
   unsigned long long n_too_late;  // stream mode: records older than the previous watermark
-  uint32_t n_final, n_pending;    // stream mode: finalised / still pending in this window
+  uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
 };
 
 // One extracted record, bucketed by journey (32 bytes, one DRAM sector).

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "radix_sort.cuh"
+#include "cta_sort.cuh"
 #include "scan.cuh"
 #include "extract.cuh"
 #include "journey.cuh"
@@ -30,13 +31,13 @@ namespace {
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
   ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
-  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_COUNT
+  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
                                      "csv_count", "csv_parse", "stream_append", "stream_split",
-                                     "stream_tables"};
+                                     "stream_tables", "cta_sort"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -249,6 +250,14 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   uint32_t *va, *vb, *hist, *status, *tiles;
   ENSURE((t + ".k2").c_str(), n, &k2);
   ENSURE((t + ".vb").c_str(), n, &vb);
+  if (n <= kCtaSortMax) {  // small: one block, shared memory
+    LAUNCH(ST_CTA_SORT, (k_cta_sort<K><<<1, kCtaSortBlock, cta_sort_smem<K>(), c->st>>>(
+                            keys, vals, n, begin_bit, end_bit, k2, vb)));
+    LAUNCH_CHECK();
+    *ko = k2;
+    *vo = vb;
+    return CVETL_OK;
+  }
   if (vals) va = vals;
   else ENSURE((t + ".va").c_str(), n, &va);
   const uint32_t ntiles = (n + rs::kTile - 1) / rs::kTile;
@@ -292,6 +301,11 @@ cvetl_status scan_u32(cvetl_ctx* c, const uint32_t* in, uint32_t n, uint32_t* ou
   ENSURE("scan.sums", nb + 1, &sums);
   if (n == 0) {
     CK(cudaMemsetAsync(total_dev, 0, 4, c->st));
+    return CVETL_OK;
+  }
+  if (nb == 1) {
+    LAUNCH(ST_SCAN, (scan::k_scan_small<<<1, scan::kBlock, 0, c->st>>>(in, n, out, total_dev)));
+    LAUNCH_CHECK();
     return CVETL_OK;
   }
   LAUNCH(ST_SCAN, (scan::k_tile_sums<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums)));
@@ -541,20 +555,16 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
     CK(cudaMemcpyAsync(z, in->speed, n * 4, cudaMemcpyHostToDevice, c->st));
     jid = a; ts = b; lat = x; lon = y; spd = z;
   }
-  uint32_t* pc = stream_counter(c, "sp.count");
-  CK(cudaMemcpyAsync(pc, &ss.n_pending, 4, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (n) {
     LAUNCH(ST_STREAM_APPEND, (k_stream_append<<<grid_for(n, 256), 256, 0, c->st>>>(
                                  jid, ts, lat, lon, spd, (uint32_t)n, ss.arrival, ss.w_prev,
-                                 ss.has_w_prev ? 1 : 0, pj, pr, pc, (uint32_t)need, c->dstate)));
+                                 ss.has_w_prev ? 1 : 0, pj, pr, ss.n_pending, (uint32_t)need, c->dstate)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
   if (s != CVETL_OK) return s;
-  uint32_t np = 0;
-  CK(cudaMemcpy(&np, pc, 4, cudaMemcpyDeviceToHost));
-  ss.n_pending = np;
+  ss.n_pending += c->hstate->n_pending;
   ss.tot_malformed += (int64_t)c->hstate->n_malformed;
   ss.tot_late += (int64_t)c->hstate->n_too_late;
   ss.arrival += (uint32_t)n;
@@ -612,39 +622,27 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   GROW(n2, np, 0, &qr);
   ENSURE("sf.rec", np, &fr);
   ENSURE("sf.slot", np, &fs);
-  uint32_t* qc = stream_counter(c, "sp.qcount");
-  uint32_t* fc = stream_counter(c, "sf.count");
-  CK(cudaMemsetAsync(qc, 0, 4, c->st));
-  CK(cudaMemsetAsync(fc, 0, 4, c->st));
+  // journeys touched by the window, ascending id: bucket offsets
+  unsigned long long* ukey;
+  uint32_t* uslot;
+  ENSURE("j.ukey", (size_t)np + 1, &ukey);
+  ENSURE("j.uslot", (size_t)np + 1, &uslot);
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (np) {
     LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
-                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, qc, fr, fs, fc, c->dstate)));
+                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
+    LAUNCH_CHECK();
+    LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
   if (s != CVETL_OK) return s;
   if (c->hstate->err & kErrHashOverflow) return fail(c, CVETL_ECUDA, "internal: journey table overflow");
-  uint32_t nf = 0, nq = 0;
-  CK(cudaMemcpy(&nf, fc, 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&nq, qc, 4, cudaMemcpyDeviceToHost));
+  const uint32_t nf = c->hstate->n_final, nq = c->hstate->n_pending;
   ss.n_journeys += c->hstate->n_distinct;
   ss.side ^= 1;
   ss.n_pending = nq;
-  // journeys touched by the window, ascending id: bucket offsets
-  unsigned long long* ukey;
-  uint32_t *uslot, *counter;
-  ENSURE("j.ukey", (size_t)nf + 1, &ukey);
-  ENSURE("j.uslot", (size_t)nf + 1, &uslot);
-  ENSURE("j.counter", 1, &counter);
-  CK(cudaMemsetAsync(counter, 0, 4, c->st));
-  if (nf) {
-    LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, counter)));
-    LAUNCH_CHECK();
-  }
-  uint32_t J = 0;
-  CK(cudaStreamSynchronize(c->st));
-  CK(cudaMemcpy(&J, counter, 4, cudaMemcpyDeviceToHost));
+  const uint32_t J = c->hstate->n_touched;
   unsigned long long* skey;
   uint32_t* sslot;
   if ((s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot)) != CVETL_OK) return s;
@@ -736,20 +734,18 @@ cvetl_status stream_fold(cvetl_ctx* c) {
   if (s != CVETL_OK) return s;
   uint32_t* head;
   ENSURE("cell.head", (size_t)R, &head);
-  uint32_t* ncount = stream_counter(c, "sc.count");
-  CK(cudaMemcpyAsync(ncount, &ss.n_cells, 4, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (R) {
     LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head)));
     LAUNCH_CHECK();
     LAUNCH(ST_CELL_WRITE, (k_cell_fold<<<(R + 255) / 256, 256, 0, c->st>>>(
                               skey, sidx, R, head, c->jo.run_cnt, c->jo.run_sum, c->jo.run_min,
-                              c->jo.run_max, ss.ch, ncount, c->dstate)));
+                              c->jo.run_max, ss.ch, &c->dstate->n_cells, c->dstate)));
     LAUNCH_CHECK();
   }
   if ((s = read_state(c)) != CVETL_OK) return s;
   if (c->hstate->err & kErrHashOverflow) return fail(c, CVETL_ECUDA, "internal: cell table overflow");
-  CK(cudaMemcpy(&ss.n_cells, ncount, 4, cudaMemcpyDeviceToHost));
+  ss.n_cells += c->hstate->n_cells;
   return CVETL_OK;
 }
 
@@ -947,7 +943,11 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           rs::kTile * 8) != cudaSuccess) {
+                           rs::kTile * 8) != cudaSuccess ||
+      cudaFuncSetAttribute(k_cta_sort<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cta_sort_smem<unsigned long long>()) != cudaSuccess ||
+      cudaFuncSetAttribute(k_cta_sort<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)cta_sort_smem<uint32_t>()) != cudaSuccess) {
     fail(c, CVETL_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
     return bail(CVETL_ECUDA);
   }

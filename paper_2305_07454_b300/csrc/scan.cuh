@@ -49,5 +49,20 @@ __global__ void __launch_bounds__(kBlock) k_apply(const uint32_t* __restrict__ i
   }
 }
 
+// Single block for n <= kTile: out = exclusive prefix of in, *total = the sum (one launch).
+__global__ void __launch_bounds__(kBlock) k_scan_small(const uint32_t* __restrict__ in, uint32_t n,
+                                                       uint32_t* __restrict__ out, uint32_t* total) {
+  __shared__ uint32_t scratch[kBlock / 32 + 1];
+  uint32_t carry = 0;
+  for (uint32_t b = 0; b < n; b += kBlock) {
+    const uint32_t i = b + threadIdx.x;
+    uint32_t v = (i < n) ? in[i] : 0u, tot;
+    const uint32_t e = block_excl_scan<kBlock>(v, scratch, &tot);
+    if (i < n) out[i] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
 }  // namespace scan
 }  // namespace cvetl

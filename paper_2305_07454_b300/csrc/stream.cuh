@@ -14,8 +14,9 @@
 
 namespace cvetl {
 
-// Appends the window's kept rows to the pending store (arrival index = base + row); rows whose
-// timestamp is below the previous watermark are dropped as too late.
+// Appends the window's kept rows to the pending store after its first p_base entries (arrival
+// index = arrival_base + row; st->n_pending counts the appended rows); rows whose timestamp is
+// below the previous watermark are dropped as too late.
 __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict__ jid,
                                                        const int64_t* __restrict__ ts,
                                                        const double* __restrict__ lat,
@@ -23,7 +24,7 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
                                                        const float* __restrict__ spd, uint32_t n,
                                                        uint32_t arrival_base, int64_t w_prev,
                                                        int has_w_prev, int64_t* __restrict__ p_jid,
-                                                       Rec* __restrict__ p_rec, uint32_t* p_count,
+                                                       Rec* __restrict__ p_rec, uint32_t p_base,
                                                        uint32_t p_cap, DevState* st) {
   __shared__ unsigned long long scratch[8];
   unsigned long long bad = 0, late = 0;
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
       ++late;
       continue;
     }
-    const uint32_t o = atomicAdd(p_count, 1u);
+    const uint32_t o = p_base + atomicAdd(&st->n_pending, 1u);
     if (o >= p_cap) {
       atomicOr(&st->err, kErrCapacity);
       continue;
@@ -62,14 +63,14 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
 }
 
 // Splits the pending store: timestamps <= watermark go to the finalised list (with their hash
-// slot and the count per journey), the rest to the next pending store.
+// slot and the count per journey; st->n_final), the rest to the next pending store
+// (st->n_pending).
 __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict__ p_jid,
                                                       const Rec* __restrict__ p_rec, uint32_t n,
                                                       int64_t wm, int finalize_all, Hash h,
                                                       int64_t* __restrict__ q_jid, Rec* __restrict__ q_rec,
-                                                      uint32_t* q_count, Rec* __restrict__ f_rec,
-                                                      uint32_t* __restrict__ f_slot, uint32_t* f_count,
-                                                      DevState* st) {
+                                                      Rec* __restrict__ f_rec,
+                                                      uint32_t* __restrict__ f_slot, DevState* st) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Rec r = p_rec[i];
     const int64_t id = p_jid[i];
@@ -80,24 +81,25 @@ __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict_
         continue;
       }
       atomicAdd(&h.cnt[s], 1u);
-      const uint32_t o = atomicAdd(f_count, 1u);
+      const uint32_t o = atomicAdd(&st->n_final, 1u);
       f_rec[o] = r;
       f_slot[o] = (uint32_t)s;
     } else {
-      const uint32_t o = atomicAdd(q_count, 1u);
+      const uint32_t o = atomicAdd(&st->n_pending, 1u);
       q_jid[o] = id;
       q_rec[o] = r;
     }
   }
 }
 
-// Journeys touched by this window (count > 0), with their ids as order-preserving keys.
+// Journeys touched by this window (count > 0; st->n_touched), with their ids as order-preserving
+// keys.
 __global__ void k_stream_touched(Hash h, unsigned long long* __restrict__ ukey,
-                                 uint32_t* __restrict__ uslot, uint32_t* counter) {
+                                 uint32_t* __restrict__ uslot, DevState* st) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= h.cap; s += gridDim.x * blockDim.x) {
     if (h.cnt[s] == 0) continue;
     const uint64_t id = (s < h.cap) ? h.keys[s] : kHashEmpty;
-    const uint32_t i = atomicAdd(counter, 1u);
+    const uint32_t i = atomicAdd(&st->n_touched, 1u);
     ukey[i] = id ^ kSign64;
     uslot[i] = s;
   }
