@@ -34,13 +34,15 @@ struct DevState {
   uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
 };
 
-// One extracted record, bucketed by journey (32 bytes, one DRAM sector).
+// One extracted record, bucketed by journey (32 bytes, one DRAM sector). The record's row index
+// (the tie-break of equal timestamps, and the materialised permutation) travels in a parallel
+// uint32 array at the same bucket position.
 struct __align__(32) Rec {
   int64_t ts;
   double lat;
   double lon;
   float spd;     // canonical speed (+0.0 for -0.0)
-  uint32_t idx;  // extracted-row index
+  uint32_t key;  // the point's cell x bin key (Algorithm 2), kKeyInvalid off the grid
 };
 static_assert(sizeof(Rec) == 32, "Rec must be one 32-byte sector");
 

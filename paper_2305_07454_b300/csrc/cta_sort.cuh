@@ -5,12 +5,14 @@
 // thousand pairs). Here one block loads the pairs into shared memory, pads to a power of two
 // and runs a bitonic network on (key bits [begin_bit, end_bit), input position): positions are
 // distinct, so the network yields exactly the stable order, then writes keys and values out.
+// The network does O(n log^2 n) work on one SM: above a few thousand pairs the device-wide sort
+// is faster, hence the limit.
 #pragma once
 #include "common.cuh"
 
 namespace cvetl {
 
-constexpr uint32_t kCtaSortMax = 8192;
+constexpr uint32_t kCtaSortMax = 2048;
 constexpr int kCtaSortBlock = 1024;
 
 template <typename K>

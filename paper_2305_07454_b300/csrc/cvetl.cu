@@ -529,11 +529,14 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
   const size_t need = (size_t)ss.n_pending + n;
   int64_t* pj;
   Rec* pr;
-  char nj[32], nr[32];
+  uint32_t* pi;
+  char nj[32], nr[32], ni[32];
   snprintf(nj, sizeof nj, "sp.jid%d", ss.side);
   snprintf(nr, sizeof nr, "sp.rec%d", ss.side);
+  snprintf(ni, sizeof ni, "sp.idx%d", ss.side);
   GROW(nj, need, ss.n_pending, &pj);
   GROW(nr, need, ss.n_pending, &pr);
+  GROW(ni, need, ss.n_pending, &pi);
   const int64_t* jid = in->jid;
   const int64_t* ts = in->ts;
   const double* lat = in->lat;
@@ -559,7 +562,8 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
   if (n) {
     LAUNCH(ST_STREAM_APPEND, (k_stream_append<<<grid_for(n, 256), 256, 0, c->st>>>(
                                  jid, ts, lat, lon, spd, (uint32_t)n, ss.arrival, ss.w_prev,
-                                 ss.has_w_prev ? 1 : 0, pj, pr, ss.n_pending, (uint32_t)need, c->dstate)));
+                                 ss.has_w_prev ? 1 : 0, pj, pr, pi, ss.n_pending, (uint32_t)need, c->gp,
+                                 c->dstate)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
@@ -610,17 +614,22 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   const uint32_t np = ss.n_pending;
   int64_t *pj, *qj;
   Rec *pr, *qr, *fr;
-  uint32_t* fs;
-  char n1[32], n2[32];
+  uint32_t *pi, *qi, *fi, *fs;
+  char n1[32], n2[32], n3[32];
   snprintf(n1, sizeof n1, "sp.jid%d", ss.side);
   snprintf(n2, sizeof n2, "sp.rec%d", ss.side);
+  snprintf(n3, sizeof n3, "sp.idx%d", ss.side);
   GROW(n1, np, np, &pj);
   GROW(n2, np, np, &pr);
+  GROW(n3, np, np, &pi);
   snprintf(n1, sizeof n1, "sp.jid%d", ss.side ^ 1);
   snprintf(n2, sizeof n2, "sp.rec%d", ss.side ^ 1);
+  snprintf(n3, sizeof n3, "sp.idx%d", ss.side ^ 1);
   GROW(n1, np, 0, &qj);
   GROW(n2, np, 0, &qr);
+  GROW(n3, np, 0, &qi);
   ENSURE("sf.rec", np, &fr);
+  ENSURE("sf.idx", np, &fi);
   ENSURE("sf.slot", np, &fs);
   // journeys touched by the window, ascending id: bucket offsets
   unsigned long long* ukey;
@@ -630,7 +639,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (np) {
     LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
-                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
+                                pj, pr, pi, np, wm, all ? 1 : 0, h, qj, qr, qi, fr, fi, fs, c->dstate)));
     LAUNCH_CHECK();
     LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate)));
     LAUNCH_CHECK();
@@ -662,9 +671,11 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
     LAUNCH_CHECK();
   }
   Rec* rec;
+  uint32_t* ridx;
   ENSURE("rec", nf, &rec);
+  ENSURE("ridx", nf, &ridx);
   if (nf) {
-    LAUNCH(ST_SCATTER, (k_stream_scatter<<<grid_for(nf, 256), 256, 0, c->st>>>(fr, fs, nf, h, rec)));
+    LAUNCH(ST_SCATTER, (k_stream_scatter<<<grid_for(nf, 256), 256, 0, c->st>>>(fr, fi, fs, nf, h, rec, ridx)));
     LAUNCH_CHECK();
   }
   Elem *scrA, *scrB;
@@ -681,9 +692,9 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (J) {
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
     }
     LAUNCH_CHECK();
   }
@@ -1112,10 +1123,12 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   // 3. scatter kept rows into journey buckets
   const size_t nv = c->n_valid;
   Rec* rec;
+  uint32_t* ridx;
   ENSURE("rec", nv, &rec);
+  ENSURE("ridx", nv, &ridx);
   if (n) {
     LAUNCH(ST_SCATTER, (k_scatter<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
-                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)));
+                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, rec, ridx)));
     LAUNCH_CHECK();
   }
 
@@ -1159,9 +1172,9 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   o.run_cap = (uint32_t)nv;
   if (J) {
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
     }
     LAUNCH_CHECK();
   }

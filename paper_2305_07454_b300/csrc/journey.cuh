@@ -3,6 +3,7 @@
 // journey summary, and the runs of equal cell x bin keys that feed the load stage.
 #pragma once
 #include "common.cuh"
+#include "keying.cuh"
 
 namespace cvetl {
 
@@ -15,24 +16,6 @@ constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memor
 constexpr int kJSmem = kJCap * 8 + kJCap * 4;
 static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
 static_assert(kEChunk * 16 <= kJSmem, "fallback pair chunks must fit the dynamic shared memory");
-
-// cosine table entry: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, unused}
-struct __align__(32) CosEntry {
-  double lat0, c0, s0r, pad;
-};
-
-struct GridParams {
-  const unsigned long long* row_thr;  // n_rows + 1 ordered thresholds (see keying below)
-  const unsigned long long* col_thr;  // n_cols + 1
-  float lat_min_f, lon_min_f, inv_cell_f;
-  int32_t n_rows, n_cols, n_bins;
-  int64_t t0_ms, bin_ms;
-  unsigned long long t_span;  // n_bins * bin_ms, saturated
-  float v_stop;
-  double radius_m;
-  const CosEntry* cos_tab;  // k = -9000..9000
-  double asin_c1, asin_c2, asin_c3;  // 2R, 2R/6, 2R*3/40: d = sqrt(h) (c1 + h (c2 + h c3))
-};
 
 struct JourneyOut {
   // journey table, indexed by rank
@@ -61,51 +44,6 @@ struct __align__(16) Elem {
 
 __device__ __forceinline__ bool elem_less(const Elem& a, const Elem& b) {
   return a.t < b.t || (a.t == b.t && a.idx < b.idx);
-}
-
-// ---------------------------------------------------------------- keying (Algorithm 2)
-// row = floor(RN(RN(lat - lat_min) / cell)) is a non-decreasing function of lat, so it is
-// fixed by the smallest binary64 value at which it reaches each k (computed once on the host
-// with the binary64 formula itself). The device compares order-preserving bit patterns with
-// that table: no floating-point division, bit-exact with the binary64 definition. A float
-// estimate from the double's leading bits picks the table entry; one or two compares fix it.
-__device__ __forceinline__ float leading_f32(double x) {
-  uint64_t b = (uint64_t)__double_as_longlong(x);
-  uint32_t hi = (uint32_t)(b >> 32);
-  uint32_t sign = hi & 0x80000000u;
-  int e = (int)((hi >> 20) & 0x7FF);
-  if (e < 1023 - 126) return __int_as_float((int)sign);
-  if (e > 1023 + 127) return __int_as_float((int)(sign | 0x7F800000u));
-  uint32_t mant = ((hi & 0xFFFFFu) << 3) | (uint32_t)((b >> 29) & 7u);
-  return __int_as_float((int)(sign | ((uint32_t)(e - 1023 + 127) << 23) | mant));
-}
-
-__device__ __forceinline__ int grid_index(double x, const unsigned long long* __restrict__ thr,
-                                          int n, float xmin_f, float inv_f) {
-  unsigned long long u = ord_f64(x);
-  if (u < __ldg(&thr[0]) || u >= __ldg(&thr[n])) return -1;
-  int r = __float2int_rd((leading_f32(x) - xmin_f) * inv_f);
-  r = max(0, min(n - 1, r));
-  while (r > 0 && u < __ldg(&thr[r])) --r;
-  while (r < n - 1 && u >= __ldg(&thr[r + 1])) ++r;
-  return r;
-}
-
-// bin = floor((ts - t0) / bin_ms) when 0 <= bin < n_bins, else -1 (exact integer arithmetic).
-__device__ __forceinline__ int time_bin(int64_t ts, const GridParams& g) {
-  if (ts < g.t0_ms) return -1;
-  unsigned long long off = (unsigned long long)ts - (unsigned long long)g.t0_ms;
-  if (off >= g.t_span) return -1;
-  if (g.t_span <= 0xFFFFFFFFull) return (int)((uint32_t)off / (uint32_t)g.bin_ms);
-  return (int)(off / (unsigned long long)g.bin_ms);
-}
-
-__device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts, const GridParams& g) {
-  int r = grid_index(lat, g.row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
-  int c = grid_index(lon, g.col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
-  int b = time_bin(ts, g);
-  if (r < 0 || c < 0 || b < 0) return kKeyInvalid;
-  return ((uint32_t)b * (uint32_t)g.n_rows + (uint32_t)r) * (uint32_t)g.n_cols + (uint32_t)c;
 }
 
 // ---------------------------------------------------------------- kinematics
@@ -140,13 +78,14 @@ __device__ __forceinline__ void bitonic_smem(Elem* E, int P) {
   }
 }
 
-__device__ __forceinline__ void load_elems(Elem* E, const Rec* __restrict__ R, int base, int m, int P) {
+__device__ __forceinline__ void load_elems(Elem* E, const Rec* __restrict__ R, const uint32_t* __restrict__ RI,
+                                           int base, int m, int P) {
   for (int i = threadIdx.x; i < P; i += kJBlock) {
     Elem e;
     if (i < m) {
       const Rec* r = R + base + i;
       e.t = (unsigned long long)r->ts ^ kSign64;
-      e.idx = r->idx;
+      e.idx = RI[base + i];
       e.pos = (uint32_t)(base + i);
     } else {
       e.t = ~0ull;
@@ -172,12 +111,13 @@ __device__ __forceinline__ int merge_path(const Elem* A, int la, const Elem* B, 
 // Sorts a journey by (timestamp, row) pairs: shared-memory bitonic sort of kEChunk chunks, then rounds
 // of CTA-wide merge-path merges between two global scratch buffers. Returns the buffer
 // holding the sorted elements.
-__device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem* A, Elem* B) {
+__device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, const uint32_t* __restrict__ RI, int n,
+                                Elem* A, Elem* B) {
   for (int c0 = 0; c0 < n; c0 += kEChunk) {
     int m = min(kEChunk, n - c0);
     int P = 1;
     while (P < m) P <<= 1;
-    load_elems(E, R, c0, m, P);
+    load_elems(E, R, RI, c0, m, P);
     bitonic_smem(E, P);
     for (int i = threadIdx.x; i < m; i += kJBlock) A[c0 + i] = E[i];
     __syncthreads();
@@ -355,15 +295,23 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
 // the radix sort). cnt: nb counters in shared memory. The sorted keys end in B.
 constexpr int kMaxBucket = 48;
 
+// Bucket of a time offset t in [0, span]: a journey spanning under 2^32 ms (any real one)
+// converts through 32 bits, which gives the same float as the 64-bit conversion.
+__device__ __forceinline__ int time_bucket(unsigned long long t, bool narrow, float scale, int nb) {
+  const float f = narrow ? __uint2float_rz((uint32_t)t) : __ull2float_rz(t);
+  return min(nb - 1, (int)(f * scale));
+}
+
 __device__ bool cta_bucket_sort(const unsigned long long* A, unsigned long long* B, int n, int pos_bits,
                                 unsigned long long span, uint32_t* cnt, int nb, uint32_t* scan_scratch,
                                 int* flag) {
   const int tid = threadIdx.x;
   const float scale = (float)nb / ((float)span + 1.0f);
+  const bool narrow = span <= 0xFFFFFFFFull;
   for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
   __syncthreads();
   for (int i = tid; i < n; i += kJBlock) {
-    const int b = min(nb - 1, (int)(__ull2float_rz(A[i] >> pos_bits) * scale));
+    const int b = time_bucket(A[i] >> pos_bits, narrow, scale, nb);
     atomicAdd(&cnt[b], 1u);
   }
   __syncthreads();
@@ -387,7 +335,7 @@ __device__ bool cta_bucket_sort(const unsigned long long* A, unsigned long long*
   if (*flag) return false;
   for (int i = tid; i < n; i += kJBlock) {
     const unsigned long long k = A[i];
-    const int b = min(nb - 1, (int)(__ull2float_rz(k >> pos_bits) * scale));
+    const int b = time_bucket(k >> pos_bits, narrow, scale, nb);
     B[atomicAdd(&cnt[b], 1u)] = k;
   }
   __syncthreads();
@@ -420,10 +368,11 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
                                     uint32_t* cnt, int nb, uint32_t* scan_scratch, int* flag) {
   const int tid = threadIdx.x;
   const float scale = (float)nb / ((float)span + 1.0f);
+  const bool narrow = span <= 0xFFFFFFFFull;
   for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
   __syncthreads();
   for (int i = tid; i < n; i += kJBlock) {
-    const int b = min(nb - 1, (int)(__ull2float_rz(rec_key(R, i, tmin, pos_bits) >> pos_bits) * scale));
+    const int b = time_bucket(rec_key(R, i, tmin, pos_bits) >> pos_bits, narrow, scale, nb);
     atomicAdd(&cnt[b], 1u);
   }
   __syncthreads();
@@ -446,7 +395,7 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
   if (*flag) return false;
   for (int i = tid; i < n; i += kJBlock) {
     const unsigned long long k = rec_key(R, i, tmin, pos_bits);
-    const int b = min(nb - 1, (int)(__ull2float_rz(k >> pos_bits) * scale));
+    const int b = time_bucket(k >> pos_bits, narrow, scale, nb);
     B[atomicAdd(&cnt[b], 1u)] = k;
   }
   __syncthreads();
@@ -468,7 +417,7 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
 
 // Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
 // slot (arbitrary) here; reorder each such group by extracted-row index.
-__device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
+__device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const uint32_t* __restrict__ RI) {
   const unsigned long long mask = (1ull << pos_bits) - 1;
   for (int k = threadIdx.x; k < n; k += kJBlock) {
     const unsigned long long t = K[k] >> pos_bits;
@@ -478,9 +427,9 @@ __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* 
       while (e < n && (K[e] >> pos_bits) == t) ++e;
       for (int i = k + 1; i < e; ++i) {  // insertion sort by row index
         const unsigned long long v = K[i];
-        const uint32_t vi = R[v & mask].idx;
+        const uint32_t vi = RI[v & mask];
         int q = i - 1;
-        while (q >= k && R[K[q] & mask].idx > vi) {
+        while (q >= k && RI[K[q] & mask] > vi) {
           K[q + 1] = K[q];
           --q;
         }
@@ -609,9 +558,6 @@ __device__ __forceinline__ void run_merge(RunPart& r, const RunPart& q) {
   r.mn = fminf(r.mn, q.mn);
   r.mx = fmaxf(r.mx, q.mx);
 }
-__device__ __forceinline__ void run_emit(const JourneyOut& o, DevState* st, const RunPart& r) {
-  if (r.key != kKeyInvalid && r.cnt) emit_run(o, st, r.key, r.cnt, (double)r.s + (double)r.c, r.mn, r.mx, r.start);
-}
 
 struct StitchSmem {
   RunPart pre[kJBlock];  // run continuing from the previous thread's range (cnt 0: none)
@@ -620,8 +566,133 @@ struct StitchSmem {
   uint8_t cont[kJBlock]; // the whole range continued the previous thread's run
 };
 
+// Closed runs are staged in shared memory (the bucket counters' space, free once the journey
+// is sorted) and written out with one global allocation per journey; a journey with more runs
+// than the buffer holds emits the rest directly.
+struct __align__(8) RunSlot {
+  double sum;
+  uint32_t key, cnt, start;
+  float mn, mx;
+  uint32_t pad;
+};
+constexpr int kRunBuf = 512;
+constexpr int kRunBufOff = kJCap * 8;  // after the sort keys of a journey of up to kJCap points
+static_assert(kRunBufOff + kRunBuf * (int)sizeof(RunSlot) <= kJSmem, "run buffer must fit");
+static_assert((int)sizeof(StitchSmem) <= kRunBufOff, "stitch arrays must not overlap the run buffer");
+static_assert(kEChunk * 16 <= kRunBufOff, "fallback pair chunks must not overlap the run buffer");
+
+__device__ __forceinline__ void run_put(RunSlot* buf, uint32_t* nbuf, const JourneyOut& o, DevState* st,
+                                        const RunPart& r) {
+  if (r.key == kKeyInvalid || r.cnt == 0) return;
+  const double sum = (double)r.s + (double)r.c;
+  const uint32_t i = atomicAdd(nbuf, 1u);
+  if (i < (uint32_t)kRunBuf) {
+    RunSlot& q = buf[i];
+    q.sum = sum;
+    q.key = r.key;
+    q.cnt = r.cnt;
+    q.start = r.start;
+    q.mn = r.mn;
+    q.mx = r.mx;
+  } else {
+    emit_run(o, st, r.key, r.cnt, sum, r.mn, r.mx, r.start);
+  }
+}
+
+// ---- stitching the threads' run fragments in parallel
+// Thread t of the walk acts on the run left open before its range as one of two maps:
+// continue (its whole range has the open run's key: open <- open + X) or reset (emit
+// open + X, then open <- S, the run open at the end of its range). Maps compose
+// associatively (continue.continue = continue with X1 + X2; continue.reset = reset with
+// X1 + X2; reset.continue = reset with S1 + X2; reset.reset = reset keeping X1, S2, the run
+// S1 + X2 in between being emitted by its owner), so one warp scans them: each lane folds
+// kJBlock / 32 consecutive threads, an exclusive warp scan gives each lane its incoming open
+// run, and each lane then replays its threads, emitting as the serial order would.
+__device__ __forceinline__ RunPart run_empty() {
+  return RunPart{kKeyInvalid, 0u, 0u, 0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
+}
+
+__device__ __forceinline__ RunPart rp_merge(RunPart a, const RunPart& b) {
+  if (b.cnt == 0) return a;
+  if (a.cnt == 0) return b;
+  run_merge(a, b);
+  return a;
+}
+
+struct RunMap {
+  uint32_t reset;
+  RunPart X, S;
+};
+
+__device__ __forceinline__ RunMap map_then(RunMap f, const RunMap& g) {
+  if (!g.reset) {
+    if (!f.reset) f.X = rp_merge(f.X, g.X);
+    else f.S = rp_merge(f.S, g.X);
+    return f;
+  }
+  RunMap r;
+  r.reset = 1u;
+  r.X = f.reset ? f.X : rp_merge(f.X, g.X);
+  r.S = g.S;
+  return r;
+}
+
+__device__ __forceinline__ RunPart shfl_up_rp(const RunPart& r, int d) {
+  RunPart o;
+  o.key = __shfl_up_sync(0xffffffffu, r.key, d);
+  o.cnt = __shfl_up_sync(0xffffffffu, r.cnt, d);
+  o.start = __shfl_up_sync(0xffffffffu, r.start, d);
+  o.s = __shfl_up_sync(0xffffffffu, r.s, d);
+  o.c = __shfl_up_sync(0xffffffffu, r.c, d);
+  o.mn = __shfl_up_sync(0xffffffffu, r.mn, d);
+  o.mx = __shfl_up_sync(0xffffffffu, r.mx, d);
+  return o;
+}
+
+__device__ __forceinline__ RunMap shfl_up_map(const RunMap& f, int d) {
+  RunMap o;
+  o.reset = __shfl_up_sync(0xffffffffu, f.reset, d);
+  o.X = shfl_up_rp(f.X, d);
+  o.S = shfl_up_rp(f.S, d);
+  return o;
+}
+
+// Called by warp 0 only. Returns, in lane 31, the run open after the journey's last point.
+__device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlot* buf, uint32_t* nbuf,
+                               const JourneyOut& o, DevState* st) {
+  constexpr int kPer = kJBlock / 32;
+  const int lane = threadIdx.x & 31, t0 = lane * kPer;
+  RunMap f{0u, run_empty(), run_empty()};
+#pragma unroll 1
+  for (int t = t0; t < t0 + kPer; ++t) {
+    if (!ss.has[t]) continue;
+    const RunMap g{ss.cont[t] ? 0u : 1u, ss.pre[t], ss.suf[t]};
+    f = map_then(f, g);
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const RunMap q = shfl_up_map(f, d);
+    if (lane >= d) f = map_then(q, f);
+  }
+  RunMap ex = shfl_up_map(f, 1);
+  if (lane == 0) ex = RunMap{0u, run_empty(), run_empty()};
+  RunPart open = ex.reset ? ex.S : rp_merge(init, ex.X);
+#pragma unroll 1
+  for (int t = t0; t < t0 + kPer; ++t) {
+    if (!ss.has[t]) continue;
+    if (ss.cont[t]) {
+      open = rp_merge(open, ss.pre[t]);
+    } else {
+      run_put(buf, nbuf, o, st, rp_merge(open, ss.pre[t]));
+      open = ss.suf[t];
+    }
+  }
+  return open;
+}
+
 template <class Form>
-__global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__ rec,
+__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
+                                                         const uint32_t* __restrict__ ridx,
                                                          const uint32_t* __restrict__ jn,
                                                          const uint32_t* __restrict__ joff, uint32_t J,
                                                          Elem* scrA, Elem* scrB, GridParams g,
@@ -637,6 +708,9 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
   __shared__ float s_last_spd;
   __shared__ uint32_t s_last_key;
+  __shared__ uint32_t s_nbuf, s_base;
+  __shared__ RunPart s_open;
+  RunSlot* rbuf = reinterpret_cast<RunSlot*>(smem_raw + kRunBufOff);
 
   const uint32_t j = blockIdx.x;
   if (j >= J) return;
@@ -644,6 +718,7 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
+  const uint32_t* RI = ridx + off;  // row index of each bucket position
   const bool small = n <= kJCap;
   // stream mode: the journey continues from its state (last point, open run, running sums)
   const bool stream = js.n != nullptr;
@@ -666,6 +741,7 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   if (tid == 0) {
     s_tmin = ~0ull;
     s_tmax = 0ull;
+    s_nbuf = 0u;
   }
   __syncthreads();
   if (lane == 0) {
@@ -699,12 +775,12 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       __syncthreads();
       K = cta_radix_sort(GA, GB, n, nbits, ssort);
     }
-    fix_ties(K, n, pos_bits, R);
+    fix_ties(K, n, pos_bits, RI);
     sortedK = K;
   } else {
     // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
     if (tid == 0) atomicAdd(&st->n_big, 1u);
-    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
+    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, RI, n, scrA + off, scrB + off);
   }
   const unsigned long long pmask = (1ull << pos_bits) - 1;
 
@@ -729,7 +805,7 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       p_lon = q.lon;
       p_spd = q.spd;
       p_cos = Form::cosine(q.lat, g);
-      run.key = cell_key(q.lat, q.lon, q.ts, g);
+      run.key = q.key;
       run.mn = __int_as_float(0x7F800000);   // +inf
       run.mx = __int_as_float((int)0xFF800000u);  // -inf
       in_pre = true;  // an empty fragment of the previous thread's run
@@ -745,12 +821,17 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       in_pre = true;
     }
     // the next record is loaded one point ahead, so its latency overlaps this point's work
-    Rec nxt = R[radix ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos];
+    uint32_t nxt_p = radix ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos;
+    Rec nxt = R[nxt_p];
     for (int k = k0; k < k1; ++k) {
       const Rec cur = nxt;
-      if (k + 1 < k1) nxt = R[radix ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos];
+      const uint32_t cur_p = nxt_p;
+      if (k + 1 < k1) {
+        nxt_p = radix ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos;
+        nxt = R[nxt_p];
+      }
       const typename Form::Cos ccur = Form::cosine(cur.lat, g);
-      const uint32_t key = cell_key(cur.lat, cur.lon, cur.ts, g);
+      const uint32_t key = cur.key;
       uint8_t fl = 0;
       typename Form::Dist d = 0;
       float vh = 0.0f, ac = 0.0f;
@@ -780,7 +861,7 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       if (key == kKeyInvalid) fl |= kFOffgrid;
       if (o.perm) {
         const uint32_t gp = off + (uint32_t)k;
-        o.perm[gp] = cur.idx;
+        o.perm[gp] = RI[cur_p];
         o.d[gp] = (double)d;
         o.vhat[gp] = vh;
         o.accel[gp] = ac;
@@ -803,7 +884,7 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
           pre = run;
           in_pre = false;
         } else {
-          run_emit(o, st, run);
+          run_put(rbuf, &s_nbuf, o, st, run);
         }
       }
       run = RunPart{key, 1u, off + (uint32_t)k, cur.spd, 0.f, cur.spd, cur.spd};
@@ -832,18 +913,17 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
   ss.has[tid] = k0 < k1;
   ss.cont[tid] = cont_all;
   __syncthreads();
+  if (tid < 32) {
+    // the run left open by the last window continues here, under this window's offset
+    const RunPart init = has_prev ? RunPart{js.l_key[slot], js.r_cnt[slot], off, js.r_s[slot], js.r_c[slot],
+                                            js.r_mn[slot], js.r_mx[slot]}
+                                  : run_empty();
+    const RunPart open = stitch_runs(ss, init, rbuf, &s_nbuf, o, st);
+    if (tid == 31) s_open = open;
+  }
+  __syncthreads();
   if (tid == 0) {
-    RunPart open{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
-    if (has_prev)  // the run left open by the last window; emitted under this window's offset
-      open = RunPart{js.l_key[slot], js.r_cnt[slot], off, js.r_s[slot], js.r_c[slot], js.r_mn[slot], js.r_mx[slot]};
-    for (int t = 0; t < kJBlock; ++t) {
-      if (!ss.has[t]) continue;
-      const RunPart& p = ss.pre[t];
-      if (p.cnt) run_merge(open, p);
-      if (ss.cont[t]) continue;
-      run_emit(o, st, open);
-      open = ss.suf[t];
-    }
+    const RunPart open = s_open;
     if (stream) {  // the open run and the journey's sums stay on the device
       if (!has_prev) {
         js.start_ts[slot] = s_first_ts;
@@ -865,24 +945,40 @@ __global__ void __launch_bounds__(kJBlock, 4) k_journeys(const Rec* __restrict__
       js.r_c[slot] = open.c;
       js.r_mn[slot] = open.mn;
       js.r_mx[slot] = open.mx;
-      if (sdup) atomicAdd(&st->n_dup, (unsigned long long)sdup);
-      if (soff) atomicAdd(&st->n_offgrid, (unsigned long long)soff);
-      return;
+    } else {
+      run_put(rbuf, &s_nbuf, o, st, open);
+      o.n[j] = n;
+      o.off[j] = off;
+      o.start_ts[j] = s_first_ts;
+      o.end_ts[j] = s_last_ts;
+      o.duration[j] = (int64_t)((unsigned long long)s_last_ts - (unsigned long long)s_first_ts);
+      o.dist[j] = sd;
+      o.dwell[j] = sw;
+      o.slat[j] = s_first_lat;
+      o.slon[j] = s_first_lon;
+      o.elat[j] = s_last_lat;
+      o.elon[j] = s_last_lon;
     }
-    run_emit(o, st, open);
-    o.n[j] = n;
-    o.off[j] = off;
-    o.start_ts[j] = s_first_ts;
-    o.end_ts[j] = s_last_ts;
-    o.duration[j] = (int64_t)((unsigned long long)s_last_ts - (unsigned long long)s_first_ts);
-    o.dist[j] = sd;
-    o.dwell[j] = sw;
-    o.slat[j] = s_first_lat;
-    o.slon[j] = s_first_lon;
-    o.elat[j] = s_last_lat;
-    o.elon[j] = s_last_lon;
     if (sdup) atomicAdd(&st->n_dup, (unsigned long long)sdup);
     if (soff) atomicAdd(&st->n_offgrid, (unsigned long long)soff);
+    const uint32_t nb = min(s_nbuf, (uint32_t)kRunBuf);
+    s_base = nb ? atomicAdd(&st->n_runs, nb) : 0u;
+  }
+  __syncthreads();
+  // the staged runs, written out together
+  const uint32_t nb = min(s_nbuf, (uint32_t)kRunBuf), base = s_base;
+  for (uint32_t i = tid; i < nb; i += kJBlock) {
+    const uint32_t g = base + i;
+    if (g >= o.run_cap) {
+      atomicOr(&st->err, kErrCapacity);
+      break;
+    }
+    const RunSlot q = rbuf[i];
+    o.run_sortkey[g] = ((unsigned long long)q.key << 32) | q.start;
+    o.run_cnt[g] = q.cnt;
+    o.run_sum[g] = q.sum;
+    o.run_min[g] = q.mn;
+    o.run_max[g] = q.mx;
   }
 }
 
