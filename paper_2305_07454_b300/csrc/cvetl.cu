@@ -949,6 +949,7 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c1 = 2.0 * cfg->earth_radius_m;
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
+  g.dist_k = cfg->earth_radius_m * (3.141592653589793 / 180.0);
   if (cudaFuncSetAttribute(k_journeys<Fp64Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp32Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,

@@ -147,54 +147,88 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, const uint32
 }
 
 // ---------------------------------------------------------------- binary64 haversine, fast path
-// For the sub-second steps of a journey the half-angles a = dphi/2 and b = dlambda/2 are tiny.
-// With |a|, |b| < 2e-4 rad (steps under ~2.5 km):
-//   sin^2(x) = x^2 (1 - x^2/3) + O(x^6)           (Taylor; dropped term < 2x^4/45 < 1e-16 rel.)
-//   asin(s)  = s (1 + s^2/6 + 3 s^4/40) + O(s^7)   (Taylor of arcsine; s^2 = h)
-//   sqrt(h)  from a float reciprocal square root refined by two binary64 Newton steps
-//   cos(lat) = cos(lat0 + e) = c0 (1 - e^2/2) - s0 e (1 - e^2/6), lat0 the nearest 0.01 deg
-//              (angle addition; |e| <= 0.005 deg, dropped terms < 3e-18)
-// Larger steps take the general formula through the CUDA math library.
-constexpr double kHalfRad = 0.008726646259971648;   // pi / 360
-constexpr double kRad = 0.017453292519943295;       // pi / 180
-constexpr double kRad2Half = 1.5230870989335428e-4;  // (pi/180)^2 / 2
-constexpr double kRad2Sixth = 5.076956996445143e-5;  // (pi/180)^2 / 6
+// For the sub-second steps of a journey the half-angles x = dphi/2 and y = dlambda/2 (radians)
+// are tiny. With K = pi/360, u = dphi^2, v = dlambda^2 (degrees) and C = cos(lat1) cos(lat2),
+// and |dphi|, |dlambda| < 0.0229 deg (|x|, |y| < 2e-4 rad, steps under ~2.5 km):
+//   sin^2(x) = x^2 (1 - x^2/3) + O(x^6)            (dropped term < 2x^4/45 < 1e-16 relative)
+//   h = sin^2 x + C sin^2 y = K^2 m (1 + eC - q),  m = u + C v,  q = K^2 (u^2 + C v^2) / (3m)
+//   asin(s) = s (1 + h/6 + 3h^2/40) + O(s^7)
+//   cos(lat0 + e) = c0 - s0 E - c0 E^2/2 + s0 E^3/6 + O(E^4), E = e pi/180, lat0 the nearest
+//                   0.01 deg (|E| < 8.8e-5, dropped terms < 3e-18); eC collects the E^2, E^3
+//                   terms of both cosines relative to C v / m
+//   sqrt(m) = s0 sqrt(1 + r / s0^2) = s0 (1 + p/2 + 3p^2/8) + O(p^3),  p = r / m,
+//             s0 = m * rsqrt_f32(m),  r = m - s0^2 (|p| ~ 2^-21)
+// so d = 2R asin(sqrt h) = 2R K s0 (1 + ds)(1 + dr) with
+//   ds = p/2 + 3p^2/8,  dr = (eC - q)/2 + h/6 + 3h^2/40   (|ds| < 3e-7, |dr| < 2e-8).
+// Every term above 2^-22 relative (differences, squares, the cosine product, m, s0, the
+// residual r, the scaling and the final fma) is binary64; delta, a sum of small corrections, is
+// float32, which puts at most ~1e-14 relative error on d. That is 14 binary64 operations per
+// point (cosine 2, distance 10, journey sum 1, implied speed 1) where the direct evaluation
+// takes about 30 on a part that runs 2 per clock per SM. Larger steps take the general formula
+// through the CUDA math library.
+constexpr double kRad = 0.017453292519943295;  // pi / 180
+constexpr float kRadF = 0.017453292519943295f;
+constexpr float kK2F = 7.615435494667714e-5f;  // (pi/360)^2
+constexpr double kTinyDeg = 0.0229;           // |dphi|, |dlambda| below this take the series
 
-__device__ __forceinline__ double cos_deg(double lat, const CosEntry* __restrict__ tab) {
+// float -> double by the bit layout, exact for normal floats and zero (denormals read as zero),
+// without a conversion instruction on the binary64 pipe.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xFFu;
+  if (ex == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+  const uint32_t hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// cosine of a latitude: binary64 value c0 - s0 E, its float32 copy, and the float32 relative
+// correction of the E^2 and E^3 terms
+struct Cos64 {
+  double t;
+  float tf, eps;
+};
+
+__device__ __forceinline__ Cos64 cos64(double lat, const CosEntry* __restrict__ tab) {
   int k = __float2int_rn(leading_f32(lat) * 100.0f);
   k = max(-9000, min(9000, k));
   const double2* p = reinterpret_cast<const double2*>(tab + (k + 9000));
   const double2 t0 = __ldg(p), t1 = __ldg(p + 1);  // {lat0, cos}, {sin * pi/180, -}
-  const double e = lat - t0.x;  // degrees
-  const double e2 = e * e;
-  const double c = t0.y * fma(e2, -kRad2Half, 1.0);
-  return fma(-(t1.x * e), fma(e2, -kRad2Sixth, 1.0), c);
+  const double e = lat - t0.x;                      // degrees
+  Cos64 c;
+  c.t = fma(-t1.x, e, t0.y);
+  c.tf = leading_f32(c.t);
+  const float ef = leading_f32(e), E = ef * kRadF;
+  // -c0 E^2/2 + s0 E^3/6 = E^2 (s0r e / 6 - c0 / 2), relative to the value
+  c.eps = E * E * fmaf(leading_f32(t1.x) * ef, 1.0f / 6.0f, -0.5f * leading_f32(t0.y)) / c.tf;
+  return c;
 }
 
-__device__ __forceinline__ bool tiny_angle(double x) {
-  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long b2em4 = 0x3F2A36E2EB1C432Dull;  // 2e-4
-  return ((unsigned long long)__double_as_longlong(x) & kAbs) < b2em4;
-}
+__device__ __forceinline__ bool tiny_deg(double x) { return fabs(x) < kTinyDeg; }
 
-__device__ __forceinline__ double haversine_fast(double la1, double lo1, double c1, double la2,
-                                                 double lo2, double c2, const GridParams& g) {
-  const double a = (la2 - la1) * kHalfRad;
-  const double b = (lo2 - lo1) * kHalfRad;
-  if (tiny_angle(a) && tiny_angle(b)) {
-    const double a2 = a * a, b2 = b * b;
-    const double sa = a2 * fma(a2, -1.0 / 3.0, 1.0);
-    const double sb = b2 * fma(b2, -1.0 / 3.0, 1.0);
-    const double h = fma(c1 * c2, sb, sa);  // h >= 0
-    if (__double_as_longlong(h) == 0) return 0.0;
-    const float hf = leading_f32(h);
-    if (hf > 0.0f) {
-      const float y = rsqrtf(hf);
-      const double yd = (double)y, yh = 0.5 * yd;
-      double s = h * yd;
-      s = fma(fma(-s, s, h), yh, s);
-      s = fma(fma(-s, s, h), yh, s);
-      return s * fma(h, fma(h, g.asin_c3, g.asin_c2), g.asin_c1);
+__device__ __forceinline__ double haversine64(double la1, double lo1, const Cos64& c1, double la2,
+                                              double lo2, const Cos64& c2, const GridParams& g) {
+  const double dp = la2 - la1, dl = lo2 - lo1;  // exact for nearby points
+  if (tiny_deg(dp) && tiny_deg(dl)) {
+    const double u = dp * dp, v = dl * dl;
+    const double C = c1.t * c2.t;
+    const double m = fma(C, v, u);
+    if (__double_as_longlong(m) == 0) return 0.0;
+    const float mf = leading_f32(m);
+    if (mf > 0.0f) {
+      const double s0 = m * f32_to_f64(rsqrtf(mf));
+      const double r = fma(-s0, s0, m);
+      const float dpf = leading_f32(dp), dlf = leading_f32(dl);
+      const float uf = dpf * dpf, vf = dlf * dlf, Cvf = c1.tf * c2.tf * vf;
+      const float inv_m = 1.0f / mf;
+      const float q = (kK2F / 3.0f) * fmaf(Cvf, vf, uf * uf) * inv_m;
+      const float eC = Cvf * (c1.eps + c2.eps) * inv_m;
+      const float hf = kK2F * mf;
+      const float p = leading_f32(r) * inv_m;
+      const float ds = p * fmaf(0.375f, p, 0.5f);
+      const float dr = fmaf(0.5f, eC - q, hf * fmaf(hf, 0.075f, 1.0f / 6.0f));
+      const float delta = fmaf(ds, dr, ds + dr);
+      const double Ks = g.dist_k * s0;
+      return fma(Ks, f32_to_f64(delta), Ks);
     }
   }
   return haversine_m(la1, lo1, la2, lo2, g.radius_m);
@@ -473,7 +507,6 @@ __device__ __forceinline__ int bits_for(unsigned long long v) { return v ? 64 - 
 // in float32; the journey distance is summed in compensated float32 pairs. Keys, counts and
 // the order are the same integer computation in both forms.
 constexpr float kHalfRadF = 0.0087266462599716f;  // pi / 360
-constexpr float kRadF = 0.017453292519943295f;     // pi / 180
 
 __device__ __forceinline__ float haversine_f32(double la1, double lo1, float c1, double la2, double lo2,
                                                float c2, const GridParams& g) {
@@ -492,14 +525,14 @@ __device__ __forceinline__ float haversine_f32(double la1, double lo1, float c1,
 }
 
 struct Fp64Form {
-  typedef double Cos;
+  typedef Cos64 Cos;
   typedef double Dist;
-  static __device__ __forceinline__ double cosine(double lat, const GridParams& g) {
-    return cos_deg(lat, g.cos_tab);
+  static __device__ __forceinline__ Cos64 cosine(double lat, const GridParams& g) {
+    return cos64(lat, g.cos_tab);
   }
-  static __device__ __forceinline__ double distance(double la1, double lo1, double c1, double la2,
-                                                    double lo2, double c2, const GridParams& g) {
-    return haversine_fast(la1, lo1, c1, la2, lo2, c2, g);
+  static __device__ __forceinline__ double distance(double la1, double lo1, const Cos64& c1, double la2,
+                                                    double lo2, const Cos64& c2, const GridParams& g) {
+    return haversine64(la1, lo1, c1, la2, lo2, c2, g);
   }
   struct Acc {
     double s = 0.0;
@@ -796,7 +829,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   if (k0 < k1) {
     int64_t p_ts = 0;
     double p_lat = 0.0, p_lon = 0.0;
-    typename Form::Cos p_cos = 0;
+    typename Form::Cos p_cos{};
     float p_spd = 0.0f;
     if (k0 > 0) {  // predecessor: the previous thread's last point
       const Rec q = R[radix ? (uint32_t)(sortedK[k0 - 1] & pmask) : sortedE[k0 - 1].pos];

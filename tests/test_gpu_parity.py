@@ -55,6 +55,18 @@ def test_small_day(orc, small_day):
     compare(run_gpu(small_day), orc.run(small_day))
 
 
+def test_fp64_form_distances_are_binary64_close(orc, small_day):
+    """The FP64 form evaluates every term above 2^-22 relative in binary64 and only a sum of
+    small corrections in float32 (a bound of about 1e-14 relative): per-point distances within
+    1e-13 relative of the oracle's libm haversine, journey sums within 1e-12."""
+    g, o = run_gpu(small_day), orc.run(small_day)
+    close("point d", g["points"]["d"], o["points"]["d"], rel=1e-13, abs_=1e-12)
+    close("journey distance", g["journeys"]["distance_m"], o["journeys"]["distance_m"], rel=1e-12)
+    d_g, d_o = g["points"]["d"], o["points"]["d"]
+    nz = d_o > 0
+    print("max relative error of d:", float(np.max(np.abs(d_g[nz] - d_o[nz]) / d_o[nz])))
+
+
 def test_small_day_host_input_matches(orc, small_day):
     a = run_gpu(small_day, device=False)
     compare(a, orc.run(small_day))
