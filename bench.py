@@ -129,10 +129,11 @@ def algorithmic_bytes(stage: str, c: dict) -> float:
     }.get(stage, 0.0)
 
 
-# binary64 operations per point of the journey kernel's distance evaluation: the cosine of the
-# latitude (7: table offset, square, 2 FMA, 3 products), the haversine with Taylor sines, Newton
-# square root and arcsine polynomial (22), the journey distance sum (1)
-FP64_OPS_PER_POINT = 30.0
+# binary64 operations per point of the journey kernel: the cosine of the latitude (2: offset from
+# the table point, one fma), the distance (10: two differences, two squares, the cosine product,
+# one fma, the scaled square root and its residual, the scaling, the final fma), the journey
+# distance sum (1) and the implied speed's rounding to float32 (1)
+FP64_OPS_PER_POINT = 14.0
 SMS, FP64_PER_CLK_PER_SM = 148, 2.0
 
 
@@ -330,7 +331,7 @@ def _window_order(host, n, feeds, t0, seed=7):
 
 
 def _replay(P, cols, bounds, n_win, feeds, t0, slots, budget, paced, upto=None):
-    """One replay through a fresh server; returns (per-window latency ms, per-window service ms,
+    """One replay through a fresh server; returns (per-window latency ms, per-request service ms,
     seconds from the first submission to the last completion, feed results)."""
     upto = n_win if upto is None else upto
     with P.Server(n_slots=slots, mem_budget_bytes=budget) as srv:
@@ -354,7 +355,7 @@ def _replay(P, cols, bounds, n_win, feeds, t0, slots, budget, paced, upto=None):
         first = min(i["submit_ns"] for w in win for i in w)
         last = max(i["done_ns"] for i in fl)
         lat = [(max(i["done_ns"] for i in w) - min(i["submit_ns"] for i in w)) / 1e6 for w in win]
-        svc = [(max(i["done_ns"] for i in w) - min(i["start_ns"] for i in w)) / 1e6 for w in win]
+        svc = [(i["done_ns"] - i["start_ns"]) / 1e6 for w in win for i in w]  # per request
         res = [srv.feed(f).results(to_host=True) for f in ids]
         peak = max(i["peak_in_flight"] for i in fl)
     return lat, svc, (last - first) / 1e9, res, peak
