@@ -150,3 +150,39 @@ def to_csv(cols: dict, seed: int = 1, malformed_frac: float = 0.005, threads: in
     if got != size:
         raise RuntimeError("cvgen_csv write failed")
     return buf[: int(size)], int(bad.value)
+
+
+# The batched workload: 7 days x the 4 quadrant boxes of the statewide box, each instance a
+# day of one region with its own grid (230 x 335 cells of 0.01 deg) and its own day start.
+# Instance sizes are log-uniform in [2M, 150M] records (times `scale`), journey lengths Zipf
+# with s = 1.5 on [10, 200,000].
+WEEK_BOX = (36.0, 40.6, -95.8, -89.1)
+ZIPF_S, ZIPF_MIN, ZIPF_MAX = 1.5, 10, 200_000
+
+
+def _zipf_mean(s: float, lo: int, hi: int) -> float:
+    k = np.arange(lo, hi + 1, dtype=np.float64)
+    w = k ** -s
+    return float((w * k).sum() / w.sum())
+
+
+def week_regions(seed: int = 1, scale: float = 1.0, days: int = 7, min_records: float = 2e6,
+                 max_records: float = 150e6, zipf_max: int = ZIPF_MAX) -> list:
+    """Instance recipes: dicts with the generator parameters (``params``) and the grid
+    (lat_min, lon_min, n_rows, n_cols, t0_ms) of each (day, quadrant) instance."""
+    rng = np.random.default_rng(seed)
+    lat0, lat1, lon0, lon1 = WEEK_BOX
+    latm, lonm = (lat0 + lat1) / 2, (lon0 + lon1) / 2
+    quads = [(lat0, latm, lon0, lonm), (lat0, latm, lonm, lon1), (latm, lat1, lon0, lonm), (latm, lat1, lonm, lon1)]
+    mean_len = _zipf_mean(ZIPF_S, ZIPF_MIN, zipf_max)
+    out = []
+    for d in range(days):
+        for q, (a, b, c, e) in enumerate(quads):
+            target = float(np.exp(rng.uniform(np.log(min_records), np.log(max_records)))) * scale
+            t0 = DAY_START_MS + d * 86_400_000
+            p = params(None, seed=seed * 1000 + d * 4 + q + 1, n_journeys=max(1, int(round(target / mean_len))),
+                       len_dist=1, zipf_s=ZIPF_S, min_len=ZIPF_MIN, max_len=zipf_max, day_start_ms=t0,
+                       n_days=1, lat_lo=a, lat_hi=b, lon_lo=c, lon_hi=e)
+            out.append({"params": p, "lat_min": a, "lon_min": c, "n_rows": int(round((b - a) / 0.01)),
+                        "n_cols": int(round((e - c) / 0.01)), "t0_ms": t0})
+    return out

@@ -219,6 +219,44 @@ cvetl_status cvetl_load(cvetl_ctx* ctx);
  * point tables are empty until cvetl_load). Synchronises ctx->stream (it reads the sizes). */
 cvetl_status cvetl_results(cvetl_ctx* ctx, cvetl_tables* out);
 
+/* Batch of instances (the paper runs one statewide day at a time; this takes many days and
+ * regions of very uneven size in one pass of every kernel). An instance has its own grid
+ * origin and size and its own day; cell_deg, n_bins, bin_ms, the thresholds and the precision
+ * are the context's. */
+typedef struct {
+  double lat_min, lon_min;  /* grid origin of the instance */
+  int32_t n_rows, n_cols;   /* its grid size */
+  int64_t t0_ms;            /* start of its first time bin */
+  int64_t n;                /* rows */
+  const int64_t* jid;
+  const int64_t* ts;
+  const double* lat;
+  const double* lon;
+  const float* speed;
+} cvetl_instance;
+
+#define CVETL_MAX_INSTANCES 32
+
+/* Extract for a batch (batch-mode context): the instances' rows are concatenated in instance
+ * order (all host or all device columns, per on_device), and cvetl_transform / cvetl_load then
+ * treat every instance as its own batch in one pass: a journey is (instance, journey id), a
+ * point is keyed on its instance's grid and day. The result tables hold the instances one after
+ * another: journeys by (instance, id), cells by (instance, key) with each instance's own keys,
+ * rows and columns (cvetl_batch_ranges gives each instance's slice). Materialised per-point keys
+ * are offset by the instance's first key. Counters are totals.
+ * CVETL_EINVAL for n_inst outside [1, CVETL_MAX_INSTANCES], a NULL column, a bad grid, more than
+ * CVETL_MAX_RECORDS rows, or keys (sum of n_rows * n_cols * n_bins) reaching 2^32 - 1; the
+ * journey ids of a batch must lie within [-2^57, 2^57) (cvetl_transform returns CVETL_EINVAL
+ * otherwise). Host columns are copied before the call returns. */
+cvetl_status cvetl_extract_batch(cvetl_ctx* ctx, const cvetl_instance* inst, int32_t n_inst, int32_t on_device);
+
+/* Slices of a loaded batch, n = n_inst + 1 entries per array (any array may be NULL): the first
+ * extracted row, first key, first cell row and first journey row of each instance, the last
+ * entry being the total. CVETL_ESTATE unless the last batch was a cvetl_extract_batch taken
+ * through cvetl_load. */
+cvetl_status cvetl_batch_ranges(cvetl_ctx* ctx, int64_t* row_begin, int64_t* key_begin, int64_t* cell_begin,
+                                int64_t* journey_begin, int32_t n);
+
 /* Stream mode (config.mode = CVETL_STREAM; the paper runs batches only, this serves windows of
  * records as they arrive). Per window: cvetl_extract appends the window's rows (binary columns)
  * to a pending store on the device; cvetl_transform finalises every pending point whose

@@ -78,6 +78,16 @@ class Stats(ctypes.Structure):
                 ("total_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("lat_min", ctypes.c_double), ("lon_min", ctypes.c_double),
+                ("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("t0_ms", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("jid", _P), ("ts", _P), ("lat", _P), ("lon", _P), ("speed", _P)]
+
+
+MAX_INSTANCES = 32
+GRID_KEYS = ("lat_min", "lon_min", "n_rows", "n_cols", "t0_ms")
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_size_t)]
@@ -111,6 +121,9 @@ def _load():
     lib.cvetl_version.restype = ctypes.c_int32
     lib.cvetl_sort_u64_noalloc.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]
     lib.cvetl_sort_u64_noalloc.restype = ctypes.c_int
+    lib.cvetl_extract_batch.argtypes = [_P, ctypes.POINTER(Instance), ctypes.c_int32, ctypes.c_int32]
+    _I64P = ctypes.POINTER(ctypes.c_int64)
+    lib.cvetl_batch_ranges.argtypes = [_P, _I64P, _I64P, _I64P, _I64P, ctypes.c_int32]
     lib.cvetl_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
     lib.cvetl_server_add_feed.argtypes = [_P, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int32)]
     lib.cvetl_server_submit.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Input), ctypes.POINTER(ctypes.c_uint64)]
@@ -123,7 +136,7 @@ def _load():
     lib.cvetl_server_last_error.restype = ctypes.c_char_p
     for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
               "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
-              "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
+              "cvetl_extract_batch", "cvetl_batch_ranges", "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
               "cvetl_server_submit_flush", "cvetl_server_wait", "cvetl_server_drain",
               "cvetl_server_feed", "cvetl_server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
@@ -135,7 +148,8 @@ lib = _load()
 # The C-ABI entry points declared in include/cvetl.h (checked by the tests).
 EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load",
            "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
-           "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc", "cvetl_server_create",
+           "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc", "cvetl_extract_batch",
+           "cvetl_batch_ranges", "cvetl_server_create",
            "cvetl_server_add_feed", "cvetl_server_submit", "cvetl_server_submit_flush",
            "cvetl_server_wait", "cvetl_server_drain", "cvetl_server_feed", "cvetl_server_destroy",
            "cvetl_server_last_error")
@@ -255,6 +269,55 @@ class Pipeline:
         all on the host, or numpy arrays (host). window_end_ms: stream mode only."""
         inp, self._keep = _columns_input(cols, window_end_ms)
         self._check(lib.cvetl_extract(self._h, ctypes.byref(inp)))
+
+    def extract_batch(self, instances: list):
+        """A batch of instances: each a dict with its grid (lat_min, lon_min, n_rows, n_cols,
+        t0_ms) and its columns jid, ts, lat, lon, speed (all instances' columns on the device,
+        or all on the host)."""
+        arr = (Instance * len(instances))()
+        keep, dev = [], set()
+        for q, inst in zip(arr, instances):
+            inp, ts = _columns_input(inst)
+            keep.append(ts)
+            dev.add(bool(inp.on_device))
+            for k in GRID_KEYS:
+                setattr(q, k, inst[k])
+            q.n = inp.n
+            q.jid, q.ts, q.lat, q.lon, q.speed = inp.jid, inp.ts, inp.lat, inp.lon, inp.speed
+        if len(dev) > 1:
+            raise ValueError("instances must be all on the device or all on the host")
+        self._keep = keep
+        self._check(lib.cvetl_extract_batch(self._h, arr, len(instances), int(dev.pop()) if dev else 0))
+
+    def batch_ranges(self) -> dict:
+        """First row, key, cell row and journey row of each instance (+ the totals)."""
+        m = len(self._keep) + 1
+        out = {k: (ctypes.c_int64 * m)() for k in ("row_begin", "key_begin", "cell_begin", "journey_begin")}
+        self._check(lib.cvetl_batch_ranges(self._h, out["row_begin"], out["key_begin"], out["cell_begin"],
+                                           out["journey_begin"], m))
+        return {k: np.array(v[:], dtype=np.int64) for k, v in out.items()}
+
+    def run_batch(self, instances: list, to_host: bool = True) -> list:
+        """extract_batch -> transform -> load; each instance's cells and journeys (and points,
+        when materialised) as its own result dict, plus the batch's total counters."""
+        self.extract_batch(instances)
+        self.transform()
+        self.load()
+        r = self.results(to_host=to_host)
+        rg = self.batch_ranges()
+        out = []
+        for i in range(len(instances)):
+            c0, c1 = rg["cell_begin"][i], rg["cell_begin"][i + 1]
+            j0, j1 = rg["journey_begin"][i], rg["journey_begin"][i + 1]
+            one = {"cells": {k: v[c0:c1] for k, v in r["cells"].items()},
+                   "journeys": {k: v[j0:j1] for k, v in r["journeys"].items()},
+                   "batch_counters": r["counters"], "ranges": {k: v[i] for k, v in rg.items()}}
+            if "points" in r:
+                p0 = int(r["journeys"]["offset"][j0]) if j1 > j0 else 0
+                p1 = int(r["journeys"]["offset"][j1 - 1] + r["journeys"]["n"][j1 - 1]) if j1 > j0 else 0
+                one["points"] = {k: v[p0:p1] for k, v in r["points"].items()}
+            out.append(one)
+        return out
 
     def extract_csv(self, text):
         """CSV text as bytes / numpy uint8 (host) or a uint8 torch tensor (host or device)."""

@@ -2,6 +2,7 @@
 // cell x bin table (count, sum, min, max, mean), in a fixed order.
 #pragma once
 #include "common.cuh"
+#include "keying.cuh"
 
 namespace cvetl {
 
@@ -24,7 +25,8 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
                              const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx,
                              const uint32_t* __restrict__ run_cnt, const double* __restrict__ run_sum,
                              const float* __restrict__ run_min, const float* __restrict__ run_max,
-                             int32_t n_rows, int32_t n_cols, CellOut o) {
+                             int32_t n_rows, int32_t n_cols, Batch bt,
+                             uint32_t* __restrict__ inst_cells, CellOut o) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= R || !head[i]) return;
   const uint32_t key = (uint32_t)(skey[i] >> 32);
@@ -39,11 +41,19 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
     mx = fmaxf(mx, run_max[r]);
   }
   const uint32_t c = cidx[i];
+  uint32_t lkey = key;  // a batch reports each instance's own keys
+  if (bt.n_inst) {
+    const int q = inst_of_key(bt, key);
+    lkey = key - bt.inst[q].key_off;
+    n_rows = bt.inst[q].n_rows;
+    n_cols = bt.inst[q].n_cols;
+    atomicAdd(&inst_cells[q], 1u);
+  }
   const uint32_t cells = (uint32_t)n_rows * (uint32_t)n_cols;
-  o.key[c] = key;
-  o.bin[c] = (int32_t)(key / cells);
-  o.row[c] = (int32_t)((key % cells) / (uint32_t)n_cols);
-  o.col[c] = (int32_t)(key % (uint32_t)n_cols);
+  o.key[c] = lkey;
+  o.bin[c] = (int32_t)(lkey / cells);
+  o.row[c] = (int32_t)((lkey % cells) / (uint32_t)n_cols);
+  o.col[c] = (int32_t)(lkey % (uint32_t)n_cols);
   o.count[c] = cnt;
   o.sum[c] = sum;
   o.mean[c] = sum / (double)cnt;

@@ -17,6 +17,7 @@ constexpr uint32_t kErrLookbackTimeout = 1u;
 constexpr uint32_t kErrHashOverflow = 2u;
 constexpr uint32_t kErrHashMissing = 4u;
 constexpr uint32_t kErrCapacity = 8u;
+constexpr uint32_t kErrIdRange = 16u;  // a batch row's journey id is outside [-2^57, 2^57)
 
 // Device-side counters and status of one batch.
 struct DevState {

@@ -75,6 +75,11 @@ struct cvetl_ctx {
   JourneyOut jo{};
   CellOut co{};
   int64_t* jid_sorted = nullptr;
+  // batch of instances (cvetl_extract_batch); bt.n_inst = 0 for one instance
+  Batch bt{};
+  std::vector<int64_t> inst_rows, inst_keys;  // first row / key of each instance, + the totals
+  std::vector<int64_t> inst_cells, inst_journeys;  // first cell / journey row (after cvetl_load)
+  uint32_t* inst_counts = nullptr;  // device: journeys [kMaxInst], then cells [kMaxInst]
   // stream mode
   struct {
     bool flushed = false, has_w_prev = false;
@@ -398,6 +403,7 @@ cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
   c->spd = spd;
   c->heading = hd;
   c->J = c->R = c->K = c->n_valid = 0;
+  c->bt = Batch{};
   c->state = 1;
   return CVETL_OK;
 }
@@ -662,7 +668,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   ENSURE("j.total", 1, &total);
   ENSURE("j.idtmp", (size_t)J, &jid_tmp);
   if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp)));
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0, nullptr)));
     LAUNCH_CHECK();
   }
   if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
@@ -1035,8 +1041,115 @@ cvetl_status cvetl_extract(cvetl_ctx* c, const cvetl_input* in) {
   c->n_rows = in->n;
   c->csv_malformed = 0;
   c->heading = in->heading;
+  c->bt = Batch{};
   c->J = c->R = c->K = c->n_valid = 0;
   c->state = 1;
+  return CVETL_OK;
+}
+
+cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32_t n_inst, int32_t on_device) {
+  if (!c) return CVETL_EINVAL;
+  if (c->cfg.mode != CVETL_BATCH) return fail(c, CVETL_EINVAL, "cvetl_extract_batch needs a batch-mode context");
+  if (!inst || n_inst < 1 || n_inst > kMaxInst)
+    return fail(c, CVETL_EINVAL, "a batch holds 1 to %d instances", kMaxInst);
+  int64_t rows = 0;
+  uint64_t keys = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    const cvetl_instance& q = inst[i];
+    if (q.n < 0) return fail(c, CVETL_EINVAL, "instance %d: negative row count", i);
+    if (q.n > 0 && (!q.jid || !q.ts || !q.lat || !q.lon || !q.speed))
+      return fail(c, CVETL_EINVAL, "instance %d: NULL column", i);
+    if (q.n_rows <= 0 || q.n_cols <= 0 || !std::isfinite(q.lat_min) || !std::isfinite(q.lon_min))
+      return fail(c, CVETL_EINVAL, "instance %d: the grid needs finite origin and positive size", i);
+    rows += q.n;
+    keys += (uint64_t)q.n_rows * (uint64_t)q.n_cols * (uint64_t)c->cfg.n_bins;
+  }
+  if (rows > CVETL_MAX_RECORDS) return fail(c, CVETL_EINVAL, "the batch holds more than %lld rows", (long long)CVETL_MAX_RECORDS);
+  if (keys > 0xFFFFFFFEull) return fail(c, CVETL_EINVAL, "the instances' keys (rows x cols x bins, summed) must stay below 2^32 - 1");
+  cudaSetDevice(c->cfg.device);
+  c->state = 0;
+  const size_t n = (size_t)rows;
+  int64_t *jid, *ts;
+  double *lat, *lon;
+  float* spd;
+  ENSURE("in.jid", n, &jid);
+  ENSURE("in.ts", n, &ts);
+  ENSURE("in.lat", n, &lat);
+  ENSURE("in.lon", n, &lon);
+  ENSURE("in.spd", n, &spd);
+  // instance table: threshold tables and offsets
+  std::vector<BatchInst> bi(n_inst);
+  std::vector<unsigned long long> thr;
+  std::vector<size_t> thr_at(n_inst);
+  c->inst_rows.assign(n_inst + 1, 0);
+  c->inst_keys.assign(n_inst + 1, 0);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int i = 0; i < n_inst; ++i) {
+    const cvetl_instance& q = inst[i];
+    const size_t r0 = (size_t)c->inst_rows[i], m = (size_t)q.n;
+    if (m) {
+      CK(cudaMemcpyAsync(jid + r0, q.jid, m * 8, kind, c->st));
+      CK(cudaMemcpyAsync(ts + r0, q.ts, m * 8, kind, c->st));
+      CK(cudaMemcpyAsync(lat + r0, q.lat, m * 8, kind, c->st));
+      CK(cudaMemcpyAsync(lon + r0, q.lon, m * 8, kind, c->st));
+      CK(cudaMemcpyAsync(spd + r0, q.speed, m * 4, kind, c->st));
+    }
+    c->inst_rows[i + 1] = (int64_t)(r0 + m);
+    c->inst_keys[i + 1] = c->inst_keys[i] + (int64_t)q.n_rows * q.n_cols * c->cfg.n_bins;
+    thr_at[i] = thr.size();
+    for (int k = 0; k <= q.n_rows; ++k) thr.push_back(threshold(q.lat_min, c->cfg.cell_deg, k));
+    for (int k = 0; k <= q.n_cols; ++k) thr.push_back(threshold(q.lon_min, c->cfg.cell_deg, k));
+    bi[i].lat_min_f = (float)q.lat_min;
+    bi[i].lon_min_f = (float)q.lon_min;
+    bi[i].n_rows = q.n_rows;
+    bi[i].n_cols = q.n_cols;
+    bi[i].t0_ms = q.t0_ms;
+    bi[i].row_begin = (uint32_t)r0;
+    bi[i].key_off = (uint32_t)c->inst_keys[i];
+  }
+  unsigned long long* dthr;
+  BatchInst* dbi;
+  ENSURE("batch.thr", thr.size(), &dthr);
+  ENSURE("batch.inst", (size_t)n_inst, &dbi);
+  ENSURE("batch.counts", 2 * kMaxInst, &c->inst_counts);
+  for (int i = 0; i < n_inst; ++i) {
+    bi[i].row_thr = dthr + thr_at[i];
+    bi[i].col_thr = dthr + thr_at[i] + inst[i].n_rows + 1;
+  }
+  // the tables are pageable host memory: copy synchronously so they may go out of scope
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(dthr, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dbi, bi.data(), bi.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
+  c->bt.n_inst = n_inst;
+  c->bt.inst = dbi;
+  c->jid = jid;
+  c->ts = ts;
+  c->lat = lat;
+  c->lon = lon;
+  c->spd = spd;
+  c->heading = nullptr;
+  c->n_in = rows;
+  c->n_rows = rows;
+  c->csv_malformed = 0;
+  c->J = c->R = c->K = c->n_valid = 0;
+  c->inst_cells.clear();
+  c->inst_journeys.clear();
+  c->state = 1;
+  return CVETL_OK;
+}
+
+cvetl_status cvetl_batch_ranges(cvetl_ctx* c, int64_t* row_begin, int64_t* key_begin, int64_t* cell_begin,
+                                int64_t* journey_begin, int32_t n) {
+  if (!c) return CVETL_EINVAL;
+  if (!c->bt.n_inst || c->state < 3 || c->inst_cells.empty())
+    return fail(c, CVETL_ESTATE, "cvetl_batch_ranges needs a batch that went through cvetl_load");
+  if (n != c->bt.n_inst + 1) return fail(c, CVETL_EINVAL, "the ranges have n_inst + 1 = %d entries", c->bt.n_inst + 1);
+  for (int i = 0; i < n; ++i) {
+    if (row_begin) row_begin[i] = c->inst_rows[i];
+    if (key_begin) key_begin[i] = c->inst_keys[i];
+    if (cell_begin) cell_begin[i] = c->inst_cells[i];
+    if (journey_begin) journey_begin[i] = c->inst_journeys[i];
+  }
   return CVETL_OK;
 }
 
@@ -1052,6 +1165,7 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   }
   const uint32_t n = (uint32_t)c->n_rows;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (c->bt.n_inst) CK(cudaMemsetAsync(c->inst_counts, 0, 2 * kMaxInst * 4, c->st));
 
   // 1. count journeys (hash table of ids), growing the table if it overflows
   // start small (2^18 slots stay hot in L2) and grow when the ids do not fit at load <= 1/2
@@ -1070,12 +1184,14 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     CK(cudaMemsetAsync(h.cnt, 0, ((size_t)cap + 1) * 4, c->st));
     CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
     if (n) {
-      LAUNCH(ST_HASH, (k_hash_count<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(c->jid, c->lat, c->lon,
-                                                                          c->spd, n, h, row_slot, c->dstate)));
+      LAUNCH(ST_HASH, (k_hash_count<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
+                          c->jid, c->lat, c->lon, c->spd, n, h, c->bt, row_slot, c->dstate)));
       LAUNCH_CHECK();
     }
     cvetl_status s = read_state(c);
     if (s != CVETL_OK) return s;
+    if (c->hstate->err & kErrIdRange)
+      return fail(c, CVETL_EINVAL, "a batch's journey ids must lie within [-2^57, 2^57)");
     bool overflow = (c->hstate->err & kErrHashOverflow) || (uint64_t)c->hstate->n_distinct * 2 > cap;
     if (!overflow) break;
     uint32_t limit = next_pow2(2ull * (n > 256 ? n : 256));
@@ -1109,7 +1225,8 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("j.total", 1, &total);
   ENSURE("out.j_id", (size_t)J, &c->jid_sorted);
   if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted)));
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted,
+                                                                       c->bt.n_inst ? 1 : 0, c->inst_counts)));
     LAUNCH_CHECK();
   }
   {
@@ -1129,7 +1246,7 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("ridx", nv, &ridx);
   if (n) {
     LAUNCH(ST_SCATTER, (k_scatter<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
-                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, rec, ridx)));
+                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)));
     LAUNCH_CHECK();
   }
 
@@ -1223,13 +1340,25 @@ cvetl_status cvetl_load(cvetl_ctx* c) {
   if (R) {
     LAUNCH(ST_CELL_WRITE, (k_cell_write<<<(R + 255) / 256, 256, 0, c->st>>>(
                               skey, sidx, R, head, cidx, c->jo.run_cnt, c->jo.run_sum,
-                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, co)));
+                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt,
+                              c->inst_counts + kMaxInst, co)));
     LAUNCH_CHECK();
   }
   if ((s = read_state(c)) != CVETL_OK) return s;
   uint32_t K = 0;
   CK(cudaMemcpy(&K, total, 4, cudaMemcpyDeviceToHost));
   c->K = R ? K : 0;
+  if (c->bt.n_inst) {  // first journey and cell row of each instance
+    uint32_t cnt[2 * kMaxInst];
+    CK(cudaMemcpy(cnt, c->inst_counts, sizeof cnt, cudaMemcpyDeviceToHost));
+    const int m = c->bt.n_inst;
+    c->inst_journeys.assign(m + 1, 0);
+    c->inst_cells.assign(m + 1, 0);
+    for (int i = 0; i < m; ++i) {
+      c->inst_journeys[i + 1] = c->inst_journeys[i] + cnt[i];
+      c->inst_cells[i + 1] = c->inst_cells[i] + cnt[kMaxInst + i];
+    }
+  }
   c->state = 3;
   return CVETL_OK;
 }

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ 
                                                     const double* __restrict__ lat,
                                                     const double* __restrict__ lon,
                                                     const float* __restrict__ spd, uint32_t n,
-                                                    Hash h, uint32_t* __restrict__ row_slot,
+                                                    Hash h, Batch bt, uint32_t* __restrict__ row_slot,
                                                     DevState* st) {
   __shared__ unsigned long long scratch[8];
   unsigned long long bad = 0;
@@ -86,6 +86,10 @@ __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ 
       ok[u] = i < n && row_valid(lat[i], lon[i], spd[i]);
       id[u] = (i < n) ? (uint64_t)jid[i] : 0;
       if (i < n && !ok[u]) ++bad;
+      if (ok[u] && bt.n_inst && !composite_id(inst_of_row(bt, i), (int64_t)id[u], &id[u])) {
+        atomicOr(&st->err, kErrIdRange);
+        ok[u] = false;
+      }
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -127,14 +131,22 @@ __global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
   }
 }
 
-// Journey rank r (ascending id): size, id.
+// Journey rank r (ascending id): size, id (a batch's (instance, id) is unpacked, and the
+// instance's journeys counted in inst_journeys).
 __global__ void k_journey_sizes(const unsigned long long* __restrict__ skey,
                                 const uint32_t* __restrict__ sslot, uint32_t J, Hash h,
-                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out) {
+                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out,
+                                int batched, uint32_t* __restrict__ inst_journeys) {
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < J) {
     jn[r] = h.cnt[sslot[r]];
-    jid_out[r] = (int64_t)(skey[r] ^ kSign64);
+    const uint64_t id = skey[r] ^ kSign64;
+    if (batched) {
+      jid_out[r] = composite_jid(id);
+      atomicAdd(&inst_journeys[id >> kInstShift], 1u);
+    } else {
+      jid_out[r] = (int64_t)id;
+    }
   }
 }
 
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lon,
                                                  const float* __restrict__ spd,
                                                  const uint32_t* __restrict__ row_slot, uint32_t n,
-                                                 Hash h, GridParams g, Rec* __restrict__ rec,
+                                                 Hash h, GridParams g, Batch bt, Rec* __restrict__ rec,
                                                  uint32_t* __restrict__ ridx) {
   const uint32_t step = gridDim.x * blockDim.x * kUnroll;
   for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll + threadIdx.x; i0 < n; i0 += step) {
@@ -174,7 +186,8 @@ __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
       const uint32_t i = i0 + u * blockDim.x;
       const int64_t t = ts[i];
       const double la = lat[i], lo = lon[i];
-      const uint32_t key = cell_key(la, lo, t, g);
+      const uint32_t key = bt.n_inst ? batch_cell_key(la, lo, t, g, bt.inst[inst_of_row(bt, i)])
+                                     : cell_key(la, lo, t, g);
       const unsigned long long a = (unsigned long long)t;
       const unsigned long long b = (unsigned long long)__double_as_longlong(la);
       const unsigned long long c = (unsigned long long)__double_as_longlong(lo);

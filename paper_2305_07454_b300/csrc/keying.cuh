@@ -70,4 +70,71 @@ __device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts,
   return ((uint32_t)b * (uint32_t)g.n_rows + (uint32_t)r) * (uint32_t)g.n_cols + (uint32_t)c;
 }
 
+// ---------------------------------------------------------------- batches of instances
+// A batch holds up to kMaxInst instances (days x regions), each with its own grid origin and
+// size and its own day, processed together: rows are concatenated, a journey is identified by
+// (instance, id) packed as (instance << 58) + (id + 2^57) (ids within [-2^57, 2^57)), and each
+// instance's keys are offset into one 32-bit key space, so every kernel makes one pass over all
+// instances and the results come out instance by instance.
+constexpr int kMaxInst = 32;  // CVETL_MAX_INSTANCES
+constexpr int kInstShift = 58;
+constexpr long long kIdBias = 1ll << 57;
+
+struct BatchInst {
+  const unsigned long long* row_thr;  // the instance's n_rows + 1 thresholds
+  const unsigned long long* col_thr;  // n_cols + 1
+  float lat_min_f, lon_min_f;
+  int32_t n_rows, n_cols;
+  int64_t t0_ms;
+  uint32_t row_begin;  // first row of the instance in the concatenated columns
+  uint32_t key_off;    // first key of the instance in the concatenated key space
+};
+
+struct Batch {
+  int n_inst;              // 0: one instance described by GridParams
+  const BatchInst* inst;   // n_inst entries, ascending row_begin and key_off
+};
+
+// last instance whose row_begin (or key_off) is <= v
+__device__ __forceinline__ int inst_of_row(const Batch& b, uint32_t row) {
+  int lo = 0, hi = b.n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&b.inst[mid].row_begin) <= row) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int inst_of_key(const Batch& b, uint32_t key) {
+  int lo = 0, hi = b.n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&b.inst[mid].key_off) <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool composite_id(int inst, int64_t jid, uint64_t* out) {
+  if (jid < -kIdBias || jid >= kIdBias) return false;
+  *out = ((uint64_t)inst << kInstShift) + (uint64_t)(jid + kIdBias);
+  return true;
+}
+__device__ __forceinline__ int64_t composite_jid(uint64_t cid) {
+  return (int64_t)(cid & ((1ull << kInstShift) - 1)) - kIdBias;
+}
+
+// The key of a row of instance bi, offset into the batch's key space.
+__device__ __forceinline__ uint32_t batch_cell_key(double lat, double lon, int64_t ts, const GridParams& g,
+                                                   const BatchInst& bi) {
+  const int r = grid_index(lat, bi.row_thr, bi.n_rows, bi.lat_min_f, g.inv_cell_f);
+  const int c = grid_index(lon, bi.col_thr, bi.n_cols, bi.lon_min_f, g.inv_cell_f);
+  if (r < 0 || c < 0 || ts < bi.t0_ms) return kKeyInvalid;
+  const unsigned long long off = (unsigned long long)ts - (unsigned long long)bi.t0_ms;
+  if (off >= g.t_span) return kKeyInvalid;
+  const int b = (g.t_span <= 0xFFFFFFFFull) ? (int)((uint32_t)off / (uint32_t)g.bin_ms)
+                                            : (int)(off / (unsigned long long)g.bin_ms);
+  return bi.key_off + ((uint32_t)b * (uint32_t)bi.n_rows + (uint32_t)r) * (uint32_t)bi.n_cols + (uint32_t)c;
+}
+
 }  // namespace cvetl

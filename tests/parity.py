@@ -42,10 +42,11 @@ def exact(name, got, want):
                       f"{int(np.flatnonzero(~ok)[0])}: got {got[~ok][0]!r} want {want[~ok][0]!r}")
 
 
-def compare(gpu: dict, orc: dict, points: bool = True, rel: float = REL):
-    gc, oc = gpu["counters"], orc["counters"]
-    for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_journeys", "n_cells"):
-        assert gc[k] == oc[k], (k, gc[k], oc[k])
+def compare(gpu: dict, orc: dict, points: bool = True, rel: float = REL, counters: bool = True):
+    if counters:
+        gc, oc = gpu["counters"], orc["counters"]
+        for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_journeys", "n_cells"):
+            assert gc[k] == oc[k], (k, gc[k], oc[k])
     gj, oj = gpu["journeys"], orc["journeys"]
     exact("journey id", gj["id"], oj["jid"])
     exact("journey n", gj["n"], oj["n"])
