@@ -257,6 +257,32 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* ctx, const cvetl_instance* inst, int
 cvetl_status cvetl_batch_ranges(cvetl_ctx* ctx, int64_t* row_begin, int64_t* key_begin, int64_t* cell_begin,
                                 int64_t* journey_begin, int32_t n);
 
+/* Launch shapes. They change how the work is spread over the GPU, never a result bit. */
+typedef struct {
+  int32_t journey_ctas;    /* 0: one CTA per journey, longest journey first (default); 1..3: that
+                              many persistent CTAs per SM taking journeys from the longest-first
+                              work list */
+  int32_t row_unroll;      /* rows per thread per iteration of the counting pass and the scatter:
+                              2, 4 (default) or 8 */
+  int32_t small_sort_max;  /* sorts of up to this many pairs run in one thread block (0..2048,
+                              default 2048), larger ones device-wide */
+} cvetl_tuning;
+
+cvetl_status cvetl_tuning_get(cvetl_ctx* ctx, cvetl_tuning* out);
+/* CVETL_EINVAL for a value outside the ranges above (the context keeps its shapes). */
+cvetl_status cvetl_tuning_set(cvetl_ctx* ctx, const cvetl_tuning* t);
+
+/* Autotuner (batch-mode contexts). Times cvetl_transform + cvetl_load on the extracted rows
+ * with CUDA events for candidate shapes: each field in turn over its candidates (journey_ctas
+ * 0..3, row_unroll 2/4/8, small_sort_max 0/512/1024/2048) with the others fixed, the median of
+ * `reps` timed runs (1..10) after one untimed run per candidate, a candidate kept only when at
+ * least 2% faster. The context keeps the fastest shapes; *out (may be NULL) receives them and
+ * *ms_best (may be NULL) their median time. Needs a preceding cvetl_extract or
+ * cvetl_extract_batch (CVETL_ESTATE otherwise) whose inputs stay valid during the call, and
+ * leaves the context extracted: call cvetl_transform and cvetl_load next. Launch statistics are
+ * left as they were. */
+cvetl_status cvetl_autotune(cvetl_ctx* ctx, int32_t reps, cvetl_tuning* out, double* ms_best);
+
 /* Stream mode (config.mode = CVETL_STREAM; the paper runs batches only, this serves windows of
  * records as they arrive). Per window: cvetl_extract appends the window's rows (binary columns)
  * to a pending store on the device; cvetl_transform finalises every pending point whose

@@ -88,6 +88,11 @@ MAX_INSTANCES = 32
 GRID_KEYS = ("lat_min", "lon_min", "n_rows", "n_cols", "t0_ms")
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("journey_ctas", ctypes.c_int32), ("row_unroll", ctypes.c_int32),
+                ("small_sort_max", ctypes.c_int32)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_size_t)]
@@ -124,6 +129,9 @@ def _load():
     lib.cvetl_extract_batch.argtypes = [_P, ctypes.POINTER(Instance), ctypes.c_int32, ctypes.c_int32]
     _I64P = ctypes.POINTER(ctypes.c_int64)
     lib.cvetl_batch_ranges.argtypes = [_P, _I64P, _I64P, _I64P, _I64P, ctypes.c_int32]
+    lib.cvetl_tuning_get.argtypes = [_P, ctypes.POINTER(Tuning)]
+    lib.cvetl_tuning_set.argtypes = [_P, ctypes.POINTER(Tuning)]
+    lib.cvetl_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double)]
     lib.cvetl_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]
     lib.cvetl_server_add_feed.argtypes = [_P, ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_int32)]
     lib.cvetl_server_submit.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Input), ctypes.POINTER(ctypes.c_uint64)]
@@ -136,7 +144,8 @@ def _load():
     lib.cvetl_server_last_error.restype = ctypes.c_char_p
     for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
               "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
-              "cvetl_extract_batch", "cvetl_batch_ranges", "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
+              "cvetl_extract_batch", "cvetl_batch_ranges", "cvetl_tuning_get", "cvetl_tuning_set",
+              "cvetl_autotune", "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
               "cvetl_server_submit_flush", "cvetl_server_wait", "cvetl_server_drain",
               "cvetl_server_feed", "cvetl_server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
@@ -149,7 +158,8 @@ lib = _load()
 EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load",
            "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
            "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc", "cvetl_extract_batch",
-           "cvetl_batch_ranges", "cvetl_server_create",
+           "cvetl_batch_ranges", "cvetl_tuning_get", "cvetl_tuning_set", "cvetl_autotune",
+           "cvetl_server_create",
            "cvetl_server_add_feed", "cvetl_server_submit", "cvetl_server_submit_flush",
            "cvetl_server_wait", "cvetl_server_drain", "cvetl_server_feed", "cvetl_server_destroy",
            "cvetl_server_last_error")
@@ -318,6 +328,23 @@ class Pipeline:
                 one["points"] = {k: v[p0:p1] for k, v in r["points"].items()}
             out.append(one)
         return out
+
+    @property
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(lib.cvetl_tuning_get(self._h, ctypes.byref(t)))
+        return {k: int(getattr(t, k)) for k, _ in Tuning._fields_}
+
+    @tuning.setter
+    def tuning(self, value: dict):
+        t = Tuning(**{**self.tuning, **value})
+        self._check(lib.cvetl_tuning_set(self._h, ctypes.byref(t)))
+
+    def autotune(self, reps: int = 2) -> dict:
+        """Tunes the launch shapes on the extracted rows (leaves the context extracted)."""
+        t, ms = Tuning(), ctypes.c_double()
+        self._check(lib.cvetl_autotune(self._h, int(reps), ctypes.byref(t), ctypes.byref(ms)))
+        return {**{k: int(getattr(t, k)) for k, _ in Tuning._fields_}, "ms": float(ms.value)}
 
     def extract_csv(self, text):
         """CSV text as bytes / numpy uint8 (host) or a uint8 torch tensor (host or device)."""

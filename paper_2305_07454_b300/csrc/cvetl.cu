@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <utility>
@@ -92,6 +93,12 @@ struct cvetl_ctx {
     uint32_t n_journeys = 0, n_cells = 0;
     int64_t tot_malformed = 0, tot_late = 0, tot_dup = 0, tot_off = 0, tot_final = 0, tot_runs = 0;
   } ss;
+  // launch shapes (cvetl_tuning); results do not depend on them
+  struct {
+    int journey_ctas = 0;      // persistent journey CTAs per SM (1..3); 0: one CTA per journey
+    int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
+    int small_sort_max = 2048;  // pairs up to which one block sorts (0..kCtaSortMax)
+  } tune;
   // statistics
   int64_t launches[ST_COUNT] = {};
   double ms[ST_COUNT] = {};
@@ -255,7 +262,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   uint32_t *va, *vb, *hist, *status, *tiles;
   ENSURE((t + ".k2").c_str(), n, &k2);
   ENSURE((t + ".vb").c_str(), n, &vb);
-  if (n <= kCtaSortMax) {  // small: one block, shared memory
+  if (n <= (uint32_t)c->tune.small_sort_max) {  // small: one block, shared memory
     LAUNCH(ST_CTA_SORT, (k_cta_sort<K><<<1, kCtaSortBlock, cta_sort_smem<K>(), c->st>>>(
                             keys, vals, n, begin_bit, end_bit, k2, vb)));
     LAUNCH_CHECK();
@@ -698,9 +705,9 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (J) {
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
     }
     LAUNCH_CHECK();
   }
@@ -956,8 +963,10 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
   g.dist_k = cfg->earth_radius_m * (3.141592653589793 / 180.0);
-  if (cudaFuncSetAttribute(k_journeys<Fp64Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journeys<Fp32Form>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_journeys<Fp64Form, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp32Form, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp64Form, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp32Form, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1153,6 +1162,110 @@ cvetl_status cvetl_batch_ranges(cvetl_ctx* c, int64_t* row_begin, int64_t* key_b
   return CVETL_OK;
 }
 
+cvetl_status cvetl_tuning_get(cvetl_ctx* c, cvetl_tuning* out) {
+  if (!c) return CVETL_EINVAL;
+  if (!out) return fail(c, CVETL_EINVAL, "cvetl_tuning_get: NULL output");
+  out->journey_ctas = c->tune.journey_ctas;
+  out->row_unroll = c->tune.row_unroll;
+  out->small_sort_max = c->tune.small_sort_max;
+  return CVETL_OK;
+}
+
+cvetl_status cvetl_tuning_set(cvetl_ctx* c, const cvetl_tuning* t) {
+  if (!c) return CVETL_EINVAL;
+  if (!t) return fail(c, CVETL_EINVAL, "cvetl_tuning_set: NULL tuning");
+  if (t->journey_ctas < 0 || t->journey_ctas > 3) return fail(c, CVETL_EINVAL, "journey_ctas must be in [0, 3]");
+  if (t->row_unroll != 2 && t->row_unroll != 4 && t->row_unroll != 8)
+    return fail(c, CVETL_EINVAL, "row_unroll must be 2, 4 or 8");
+  if (t->small_sort_max < 0 || t->small_sort_max > (int32_t)kCtaSortMax)
+    return fail(c, CVETL_EINVAL, "small_sort_max must be in [0, %u]", kCtaSortMax);
+  c->tune.journey_ctas = t->journey_ctas;
+  c->tune.row_unroll = t->row_unroll;
+  c->tune.small_sort_max = t->small_sort_max;
+  return CVETL_OK;
+}
+
+cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, double* ms_best) {
+  if (!c) return CVETL_EINVAL;
+  if (c->cfg.mode != CVETL_BATCH) return fail(c, CVETL_EINVAL, "cvetl_autotune tunes batch-mode contexts");
+  if (c->state < 1) return fail(c, CVETL_ESTATE, "cvetl_autotune needs a preceding cvetl_extract");
+  cudaSetDevice(c->cfg.device);
+  reps = std::max(1, std::min(10, (int)reps));
+  // launch statistics are restored afterwards
+  CK(cudaStreamSynchronize(c->st));
+  int64_t launches[ST_COUNT], total = c->total_launches;
+  double ms_saved[ST_COUNT];
+  memcpy(launches, c->launches, sizeof launches);
+  memcpy(ms_saved, c->ms, sizeof ms_saved);
+  const int profile = c->cfg.profile;
+  c->cfg.profile = 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cvetl_status st = CVETL_OK;
+  auto run_once = [&](double* ms) -> cvetl_status {
+    c->state = 1;
+    CK(cudaEventRecord(a, c->st));
+    cvetl_status s = cvetl_transform(c);
+    if (s == CVETL_OK) s = cvetl_load(c);
+    if (s != CVETL_OK) return s;
+    CK(cudaEventRecord(b, c->st));
+    CK(cudaEventSynchronize(b));
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, a, b));
+    *ms = f;
+    return CVETL_OK;
+  };
+  auto measure = [&](double* med) -> cvetl_status {
+    double t;
+    cvetl_status s = run_once(&t);  // untimed: first use of this shape
+    if (s != CVETL_OK) return s;
+    std::vector<double> v;
+    for (int r = 0; r < reps; ++r) {
+      if ((s = run_once(&t)) != CVETL_OK) return s;
+      v.push_back(t);
+    }
+    std::sort(v.begin(), v.end());
+    *med = v[v.size() / 2];
+    return CVETL_OK;
+  };
+  auto best = c->tune;
+  double best_ms = 0.0;
+  if ((st = measure(&best_ms)) == CVETL_OK) {
+    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048};
+    for (int field = 0; field < 3 && st == CVETL_OK; ++field) {
+      const int* cand = field == 0 ? ctas : field == 1 ? unroll : smax;
+      const int nc = field == 1 ? 3 : 4;
+      for (int k = 0; k < nc && st == CVETL_OK; ++k) {
+        auto t = best;
+        int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : t.small_sort_max;
+        if (f == cand[k]) continue;
+        f = cand[k];
+        c->tune = t;
+        double ms = 0.0;
+        if ((st = measure(&ms)) != CVETL_OK) break;
+        if (ms < 0.98 * best_ms) {
+          best = t;
+          best_ms = ms;
+        }
+      }
+    }
+  }
+  c->tune = best;
+  c->state = 1;
+  cudaStreamSynchronize(c->st);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->cfg.profile = profile;
+  memcpy(c->launches, launches, sizeof launches);
+  memcpy(c->ms, ms_saved, sizeof ms_saved);
+  c->total_launches = total;
+  if (st != CVETL_OK) return st;
+  if (out) cvetl_tuning_get(c, out);
+  if (ms_best) *ms_best = best_ms;
+  return CVETL_OK;
+}
+
 cvetl_status cvetl_transform(cvetl_ctx* c) {
   if (!c) return CVETL_EINVAL;
   if (c->state != 1) return fail(c, CVETL_ESTATE, "cvetl_transform needs a preceding cvetl_extract");
@@ -1184,8 +1297,13 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     CK(cudaMemsetAsync(h.cnt, 0, ((size_t)cap + 1) * 4, c->st));
     CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
     if (n) {
-      LAUNCH(ST_HASH, (k_hash_count<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
-                          c->jid, c->lat, c->lon, c->spd, n, h, c->bt, row_slot, c->dstate)));
+      const int U = c->tune.row_unroll;
+#define HASH(U_) k_hash_count<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
+    c->jid, c->lat, c->lon, c->spd, n, h, c->bt, row_slot, c->dstate)
+      if (U == 2) LAUNCH(ST_HASH, (HASH(2)));
+      else if (U == 8) LAUNCH(ST_HASH, (HASH(8)));
+      else LAUNCH(ST_HASH, (HASH(4)));
+#undef HASH
       LAUNCH_CHECK();
     }
     cvetl_status s = read_state(c);
@@ -1245,8 +1363,13 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("rec", nv, &rec);
   ENSURE("ridx", nv, &ridx);
   if (n) {
-    LAUNCH(ST_SCATTER, (k_scatter<<<grid_for((n + kUnroll - 1) / kUnroll, 256), 256, 0, c->st>>>(
-                           c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)));
+    const int U = c->tune.row_unroll;
+#define SCAT(U_) k_scatter<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
+    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)
+    if (U == 2) LAUNCH(ST_SCATTER, (SCAT(2)));
+    else if (U == 8) LAUNCH(ST_SCATTER, (SCAT(8)));
+    else LAUNCH(ST_SCATTER, (SCAT(4)));
+#undef SCAT
     LAUNCH_CHECK();
   }
 
@@ -1288,12 +1411,30 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("run.min", nv, &o.run_min);
   ENSURE("run.max", nv, &o.run_max);
   o.run_cap = (uint32_t)nv;
+  // work list, longest journey first, for the persistent journey kernel
+  unsigned long long *szkey, *szsorted;
+  uint32_t *order = nullptr, *work;
+  ENSURE("j.szkey", (size_t)J, &szkey);
+  ENSURE("j.work", 1, &work);
+  CK(cudaMemsetAsync(work, 0, 4, c->st));
   if (J) {
-    if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
-    } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, nullptr, JState{})));
-    }
+    LAUNCH(ST_SIZES, (k_size_keys<<<(J + 255) / 256, 256, 0, c->st>>>(jn, J, szkey)));
+    LAUNCH_CHECK();
+    cvetl_status s = sort_pairs<unsigned long long>(c, "osort", szkey, nullptr, J, 0, 32, &szsorted, &order);
+    if (s != CVETL_OK) return s;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool pers = c->tune.journey_ctas > 0;
+    const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
+    const bool f32 = c->cfg.precision == CVETL_FP32;
+#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, \
+                                                                      c->dstate, nullptr, JState{}, order, work)
+    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true)));
+    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false)));
+    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true)));
+    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false)));
+#undef JRN
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);

@@ -66,8 +66,10 @@ __device__ __forceinline__ int64_t hash_find(const Hash& h, uint64_t key) {
   return -1;
 }
 
-constexpr int kUnroll = 4;  // records per thread per iteration: independent probe chains in flight
+// U rows per thread per iteration keep U independent probe / atomic chains in flight (2, 4 or 8,
+// chosen by the tuner).
 
+template <int U>
 __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ jid,
                                                     const double* __restrict__ lat,
                                                     const double* __restrict__ lon,
@@ -76,12 +78,12 @@ __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ 
                                                     DevState* st) {
   __shared__ unsigned long long scratch[8];
   unsigned long long bad = 0;
-  const uint32_t step = gridDim.x * blockDim.x * kUnroll;
-  for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll + threadIdx.x; i0 < n; i0 += step) {
-    uint64_t id[kUnroll];
-    bool ok[kUnroll];
+  const uint32_t step = gridDim.x * blockDim.x * U;
+  for (uint32_t i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < n; i0 += step) {
+    uint64_t id[U];
+    bool ok[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint32_t i = i0 + u * blockDim.x;
       ok[u] = i < n && row_valid(lat[i], lon[i], spd[i]);
       id[u] = (i < n) ? (uint64_t)jid[i] : 0;
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ 
       }
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint32_t i = i0 + u * blockDim.x;
       uint32_t slot = kKeyInvalid;  // dropped row
       if (ok[u]) {
@@ -162,6 +164,7 @@ __global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J
 // iteration keep four atomic -> store chains in flight; each record is one 32-byte store, with
 // the point's cell x bin key computed here (this kernel waits on memory, so the keying
 // arithmetic is free) and its row index stored beside it.
+template <int U>
 __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lat,
                                                  const double* __restrict__ lon,
@@ -169,19 +172,19 @@ __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
                                                  const uint32_t* __restrict__ row_slot, uint32_t n,
                                                  Hash h, GridParams g, Batch bt, Rec* __restrict__ rec,
                                                  uint32_t* __restrict__ ridx) {
-  const uint32_t step = gridDim.x * blockDim.x * kUnroll;
-  for (uint32_t i0 = blockIdx.x * blockDim.x * kUnroll + threadIdx.x; i0 < n; i0 += step) {
-    uint32_t slot[kUnroll], pos[kUnroll];
+  const uint32_t step = gridDim.x * blockDim.x * U;
+  for (uint32_t i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < n; i0 += step) {
+    uint32_t slot[U], pos[U];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       const uint32_t i = i0 + u * blockDim.x;
       slot[u] = (i < n) ? row_slot[i] : kKeyInvalid;
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
+    for (int u = 0; u < U; ++u)
       pos[u] = (slot[u] != kKeyInvalid) ? atomicAdd(&h.aux[slot[u]], 1u) : 0u;
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < U; ++u) {
       if (slot[u] == kKeyInvalid) continue;
       const uint32_t i = i0 + u * blockDim.x;
       const int64_t t = ts[i];

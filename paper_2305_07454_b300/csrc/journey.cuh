@@ -723,14 +723,15 @@ __device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlo
   return open;
 }
 
+// One journey (rank j) by the whole CTA. Ends with every thread past its last shared-memory use
+// of this journey except the run copy-out (the caller synchronises before the next journey).
 template <class Form>
-__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
-                                                         const uint32_t* __restrict__ ridx,
-                                                         const uint32_t* __restrict__ jn,
-                                                         const uint32_t* __restrict__ joff, uint32_t J,
-                                                         Elem* scrA, Elem* scrB, GridParams g,
-                                                         JourneyOut o, DevState* st,
-                                                         const uint32_t* __restrict__ jslot, JState js) {
+__device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ rec,
+                                            const uint32_t* __restrict__ ridx,
+                                            const uint32_t* __restrict__ jn,
+                                            const uint32_t* __restrict__ joff, Elem* scrA, Elem* scrB,
+                                            const GridParams& g, const JourneyOut& o, DevState* st,
+                                            const uint32_t* __restrict__ jslot, const JState& js) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SortSmem ssort;
   __shared__ double red_d[kJBlock / 32];
@@ -745,8 +746,6 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
   __shared__ RunPart s_open;
   RunSlot* rbuf = reinterpret_cast<RunSlot*>(smem_raw + kRunBufOff);
 
-  const uint32_t j = blockIdx.x;
-  if (j >= J) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
@@ -1013,6 +1012,43 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
     o.run_min[g] = q.mn;
     o.run_max[g] = q.mx;
   }
+}
+
+// The journey kernel. Persistent: each CTA takes the next journey of the work list `order`
+// (journey ranks, longest first, so that the long journeys of an uneven batch start early and
+// the short ones fill the tail) through the work counter until the list is exhausted.
+// Otherwise CTA b takes journey order[b] (rank b without a list): the block scheduler's
+// dispatch order then gives the same longest-first start without the loop.
+template <class Form, bool Persistent>
+__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
+                                                         const uint32_t* __restrict__ ridx,
+                                                         const uint32_t* __restrict__ jn,
+                                                         const uint32_t* __restrict__ joff, uint32_t J,
+                                                         Elem* scrA, Elem* scrB, GridParams g,
+                                                         JourneyOut o, DevState* st,
+                                                         const uint32_t* __restrict__ jslot, JState js,
+                                                         const uint32_t* __restrict__ order, uint32_t* work) {
+  if (!Persistent) {
+    if (blockIdx.x < J)
+      journey_one<Form>(order ? order[blockIdx.x] : blockIdx.x, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
+    return;
+  }
+  __shared__ uint32_t s_w;
+  for (;;) {
+    if (threadIdx.x == 0) s_w = atomicAdd(work, 1u);
+    __syncthreads();
+    const uint32_t w = s_w;
+    __syncthreads();
+    if (w >= J) break;
+    journey_one<Form>(order ? order[w] : w, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
+    __syncthreads();
+  }
+}
+
+// Work list keys: the journeys by size, longest first (ties by rank).
+__global__ void k_size_keys(const uint32_t* __restrict__ jn, uint32_t J, unsigned long long* __restrict__ keys) {
+  const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < J) keys[r] = 0xFFFFFFFFull - jn[r];
 }
 
 }  // namespace cvetl
