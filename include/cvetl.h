@@ -91,6 +91,13 @@ typedef struct {
   void* stream;                      /* cudaStream_t */
   int32_t mode;                      /* CVETL_BATCH (one batch per extract) or CVETL_STREAM */
   int64_t lateness_ms;               /* stream mode: how late a record may arrive (30000) */
+  int32_t graph;                     /* batch mode, 1: after the journey count is read back, the
+                                        rest of transform and load runs as a CUDA graph, captured
+                                        on the first run of a shape (rows, journeys, kept rows,
+                                        buffers, inputs, launch shapes) and replayed when the
+                                        shape repeats; per-kernel profile times are not taken for
+                                        replays. Buffers that depend on the run count are then
+                                        sized for one run per kept point. */
 } cvetl_config;
 
 typedef struct {
@@ -173,6 +180,7 @@ typedef struct {
   int64_t launches[CVETL_MAX_STAGES];   /* kernel launches */
   int64_t total_launches;               /* all of this context's kernel launches */
   int64_t device_bytes;                 /* device memory the context holds now */
+  int64_t graph_replays;                /* CUDA graph launches (config.graph) */
 } cvetl_stats;
 
 /* Fills *cfg with the statewide defaults listed beside each field. */

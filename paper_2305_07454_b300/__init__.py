@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int32), ("materialize_points", ctypes.c_int32),
         ("profile", ctypes.c_int32), ("device", ctypes.c_int32),
         ("mem_budget_bytes", ctypes.c_size_t), ("stream", _P),
-        ("mode", ctypes.c_int32), ("lateness_ms", ctypes.c_int64),
+        ("mode", ctypes.c_int32), ("lateness_ms", ctypes.c_int64), ("graph", ctypes.c_int32),
     ]
 
 
@@ -75,7 +75,8 @@ MAX_STAGES = 32
 class Stats(ctypes.Structure):
     _fields_ = [("n_stages", ctypes.c_int32), ("name", ctypes.c_char_p * MAX_STAGES),
                 ("ms", ctypes.c_double * MAX_STAGES), ("launches", ctypes.c_int64 * MAX_STAGES),
-                ("total_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("total_launches", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64)]
 
 
 class Instance(ctypes.Structure):
@@ -426,7 +427,8 @@ class Pipeline:
         self._check(lib.cvetl_stats_get(self._h, ctypes.byref(s)))
         return {"stages": {s.name[i].decode(): {"ms": s.ms[i], "launches": int(s.launches[i])}
                            for i in range(s.n_stages)},
-                "total_launches": int(s.total_launches)}
+                "total_launches": int(s.total_launches), "device_bytes": int(s.device_bytes),
+                "graph_replays": int(s.graph_replays)}
 
     def stats_reset(self):
         self._check(lib.cvetl_stats_reset(self._h))

@@ -6,10 +6,13 @@
 
 namespace cvetl {
 
+// R_dev != nullptr (here and in k_cell_write): the run count is read from device memory and R
+// is the upper bound the grid covers.
 __global__ void k_cell_heads(const unsigned long long* __restrict__ skey, uint32_t R,
-                             uint32_t* __restrict__ head) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < R) head[i] = (i == 0 || (skey[i] >> 32) != (skey[i - 1] >> 32)) ? 1u : 0u;
+                             uint32_t* __restrict__ head, const uint32_t* __restrict__ R_dev) {
+  if (R_dev) R = min(R, *R_dev);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x)
+    head[i] = (i == 0 || (skey[i] >> 32) != (skey[i - 1] >> 32)) ? 1u : 0u;
 }
 
 struct CellOut {
@@ -26,39 +29,43 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
                              const uint32_t* __restrict__ run_cnt, const double* __restrict__ run_sum,
                              const float* __restrict__ run_min, const float* __restrict__ run_max,
                              int32_t n_rows, int32_t n_cols, Batch bt,
-                             uint32_t* __restrict__ inst_cells, CellOut o) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= R || !head[i]) return;
-  const uint32_t key = (uint32_t)(skey[i] >> 32);
-  uint32_t cnt = 0;
-  double sum = 0.0;
-  float mn = run_min[sidx[i]], mx = run_max[sidx[i]];
-  for (uint32_t m = i; m < R && (uint32_t)(skey[m] >> 32) == key; ++m) {
-    uint32_t r = sidx[m];
-    cnt += run_cnt[r];
-    sum += run_sum[r];
-    mn = fminf(mn, run_min[r]);
-    mx = fmaxf(mx, run_max[r]);
+                             uint32_t* __restrict__ inst_cells, CellOut o,
+                             const uint32_t* __restrict__ R_dev) {
+  if (R_dev) R = min(R, *R_dev);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) {
+    if (!head[i]) continue;
+    const uint32_t key = (uint32_t)(skey[i] >> 32);
+    uint32_t cnt = 0;
+    double sum = 0.0;
+    float mn = run_min[sidx[i]], mx = run_max[sidx[i]];
+    for (uint32_t m = i; m < R && (uint32_t)(skey[m] >> 32) == key; ++m) {
+      uint32_t r = sidx[m];
+      cnt += run_cnt[r];
+      sum += run_sum[r];
+      mn = fminf(mn, run_min[r]);
+      mx = fmaxf(mx, run_max[r]);
+    }
+    const uint32_t c = cidx[i];
+    uint32_t lkey = key;  // a batch reports each instance's own keys
+    int32_t nr = n_rows, nc = n_cols;
+    if (bt.n_inst) {
+      const int q = inst_of_key(bt, key);
+      lkey = key - bt.inst[q].key_off;
+      nr = bt.inst[q].n_rows;
+      nc = bt.inst[q].n_cols;
+      atomicAdd(&inst_cells[q], 1u);
+    }
+    const uint32_t cells = (uint32_t)nr * (uint32_t)nc;
+    o.key[c] = lkey;
+    o.bin[c] = (int32_t)(lkey / cells);
+    o.row[c] = (int32_t)((lkey % cells) / (uint32_t)nc);
+    o.col[c] = (int32_t)(lkey % (uint32_t)nc);
+    o.count[c] = cnt;
+    o.sum[c] = sum;
+    o.mean[c] = sum / (double)cnt;
+    o.min[c] = mn;
+    o.max[c] = mx;
   }
-  const uint32_t c = cidx[i];
-  uint32_t lkey = key;  // a batch reports each instance's own keys
-  if (bt.n_inst) {
-    const int q = inst_of_key(bt, key);
-    lkey = key - bt.inst[q].key_off;
-    n_rows = bt.inst[q].n_rows;
-    n_cols = bt.inst[q].n_cols;
-    atomicAdd(&inst_cells[q], 1u);
-  }
-  const uint32_t cells = (uint32_t)n_rows * (uint32_t)n_cols;
-  o.key[c] = lkey;
-  o.bin[c] = (int32_t)(lkey / cells);
-  o.row[c] = (int32_t)((lkey % cells) / (uint32_t)n_cols);
-  o.col[c] = (int32_t)(lkey % (uint32_t)n_cols);
-  o.count[c] = cnt;
-  o.sum[c] = sum;
-  o.mean[c] = sum / (double)cnt;
-  o.min[c] = mn;
-  o.max[c] = mx;
 }
 
 }  // namespace cvetl

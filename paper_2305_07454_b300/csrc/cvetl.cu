@@ -81,6 +81,7 @@ struct cvetl_ctx {
   std::vector<int64_t> inst_rows, inst_keys;  // first row / key of each instance, + the totals
   std::vector<int64_t> inst_cells, inst_journeys;  // first cell / journey row (after cvetl_load)
   uint32_t* inst_counts = nullptr;  // device: journeys [kMaxInst], then cells [kMaxInst]
+  uint32_t* cell_total = nullptr;   // device: the cell count of the last batch
   // stream mode
   struct {
     bool flushed = false, has_w_prev = false;
@@ -99,6 +100,25 @@ struct cvetl_ctx {
     int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
     int small_sort_max = 2048;  // pairs up to which one block sorts (0..kCtaSortMax)
   } tune;
+  // CUDA graphs of the batch path after sizing (config.graph), one per shape
+  struct GraphKey {
+    uint64_t n, J, nv, cap, gen;
+    const void* cols[5];
+    const void* inst;
+    int n_inst, precision, materialize, t0, t1, t2;
+    bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof o) == 0; }
+  };
+  struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    int64_t launches[ST_COUNT];
+  };
+  std::vector<GraphEntry> graphs;
+  bool capturing = false;       // a graph capture is in progress on the stream
+  cudaStream_t cap_stream = nullptr;  // captures run here (the legacy default stream cannot be captured)
+  int64_t cap_launches[ST_COUNT] = {};
+  uint64_t buf_gen = 0;         // bumped whenever a device buffer moves
+  int64_t graph_replays = 0;
   // statistics
   int64_t launches[ST_COUNT] = {};
   double ms[ST_COUNT] = {};
@@ -142,6 +162,10 @@ struct LaunchScope {
   int stage;
   cudaEvent_t a = nullptr, b = nullptr;
   LaunchScope(cvetl_ctx* c_, int s) : c(c_), stage(s) {
+    if (c->capturing) {  // counted when the graph is launched; no per-kernel events in a graph
+      c->cap_launches[s] += 1;
+      return;
+    }
     c->launches[s] += 1;
     c->total_launches += 1;
     if (c->cfg.profile) {
@@ -177,6 +201,8 @@ cvetl_status ensure(cvetl_ctx* c, const char* name, size_t count, T** out) {
   if (bytes == 0) bytes = 256;
   DevBuf& b = c->bufs[name];
   if (b.bytes < bytes) {
+    if (c->capturing) return fail(c, CVETL_ECUDA, "internal: buffer %s would move during a graph capture", name);
+    c->buf_gen += 1;
     size_t grow = bytes + bytes / 8;
     size_t after = c->held - b.bytes + grow;
     if (c->cfg.mem_budget_bytes && after > c->cfg.mem_budget_bytes) {
@@ -248,9 +274,11 @@ unsigned long long threshold(double xmin, double step, int k) {
 // ---- radix sort driver ----------------------------------------------------------------
 // Sorts n (key, value) pairs by bits [begin_bit, end_bit) of the key. keys is overwritten.
 // vals == nullptr means value = position. The sorted pairs are returned in *ko / *vo.
+// n_dev != nullptr: the pair count is in device memory and n is its upper bound (no host read,
+// so the sequence can be captured in a CUDA graph).
 template <typename K>
 cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, uint32_t n,
-                        int begin_bit, int end_bit, K** ko, uint32_t** vo) {
+                        int begin_bit, int end_bit, K** ko, uint32_t** vo, const uint32_t* n_dev = nullptr) {
   if (n == 0) {
     *ko = keys;
     *vo = vals;
@@ -262,7 +290,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   uint32_t *va, *vb, *hist, *status, *tiles;
   ENSURE((t + ".k2").c_str(), n, &k2);
   ENSURE((t + ".vb").c_str(), n, &vb);
-  if (n <= (uint32_t)c->tune.small_sort_max) {  // small: one block, shared memory
+  if (!n_dev && n <= (uint32_t)c->tune.small_sort_max) {  // small: one block, shared memory
     LAUNCH(ST_CTA_SORT, (k_cta_sort<K><<<1, kCtaSortBlock, cta_sort_smem<K>(), c->st>>>(
                             keys, vals, n, begin_bit, end_bit, k2, vb)));
     LAUNCH_CHECK();
@@ -279,7 +307,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   CK(cudaMemsetAsync(hist, 0, rs::kMaxPasses * rs::kRadix * 4, c->st));
   CK(cudaMemsetAsync(tiles, 0, rs::kMaxPasses * 4, c->st));
   LAUNCH(ST_SORT_HIST, (rs::k_histogram<K><<<grid_for(n, rs::kBlock, 4), rs::kBlock, 0, c->st>>>(
-                           keys, n, begin_bit, passes, hist)));
+                           keys, n, begin_bit, passes, hist, n_dev)));
   LAUNCH_CHECK();
   LAUNCH(ST_SORT_HIST, (rs::k_hist_scan<<<passes, rs::kBlock, 0, c->st>>>(hist)));
   LAUNCH_CHECK();
@@ -292,7 +320,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
     CK(cudaMemsetAsync(status, 0, (size_t)ntiles * rs::kRadix * 4, c->st));
     LAUNCH(ST_SORT_PASS, (rs::k_onesweep<K><<<ntiles, rs::kBlock, smem, c->st>>>(
                              kin, vin, kout, vout, n, begin_bit + rs::kBits * p,
-                             hist + p * rs::kRadix, status, tiles + p, &c->dstate->err)));
+                             hist + p * rs::kRadix, status, tiles + p, &c->dstate->err, n_dev)));
     LAUNCH_CHECK();
     // next pass reads what this one wrote
     K* tk = kin;
@@ -307,7 +335,10 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   return CVETL_OK;
 }
 
-cvetl_status scan_u32(cvetl_ctx* c, const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* total_dev) {
+// Exclusive prefix sum of n counts (n_dev != nullptr: the count is in device memory, n its upper
+// bound); *total_dev receives the sum.
+cvetl_status scan_u32(cvetl_ctx* c, const uint32_t* in, uint32_t n, uint32_t* out, uint32_t* total_dev,
+                      const uint32_t* n_dev = nullptr) {
   const uint32_t nb = (n + scan::kTile - 1) / scan::kTile;
   uint32_t* sums;
   ENSURE("scan.sums", nb + 1, &sums);
@@ -315,16 +346,16 @@ cvetl_status scan_u32(cvetl_ctx* c, const uint32_t* in, uint32_t n, uint32_t* ou
     CK(cudaMemsetAsync(total_dev, 0, 4, c->st));
     return CVETL_OK;
   }
-  if (nb == 1) {
+  if (nb == 1 && !n_dev) {
     LAUNCH(ST_SCAN, (scan::k_scan_small<<<1, scan::kBlock, 0, c->st>>>(in, n, out, total_dev)));
     LAUNCH_CHECK();
     return CVETL_OK;
   }
-  LAUNCH(ST_SCAN, (scan::k_tile_sums<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums)));
+  LAUNCH(ST_SCAN, (scan::k_tile_sums<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums, n_dev)));
   LAUNCH_CHECK();
   LAUNCH(ST_SCAN, (scan::k_scan_sums<<<1, scan::kBlock, 0, c->st>>>(sums, nb, total_dev)));
   LAUNCH_CHECK();
-  LAUNCH(ST_SCAN, (scan::k_apply<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums, out)));
+  LAUNCH(ST_SCAN, (scan::k_apply<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums, out, n_dev)));
   LAUNCH_CHECK();
   return CVETL_OK;
 }
@@ -427,6 +458,8 @@ cvetl_status grow_keep(cvetl_ctx* c, const char* name, size_t count, size_t keep
     *out = reinterpret_cast<T*>(b.p);
     return CVETL_OK;
   }
+  if (c->capturing) return fail(c, CVETL_ECUDA, "internal: buffer %s would move during a graph capture", name);
+  c->buf_gen += 1;
   const size_t grow = bytes + bytes / 4;
   if (c->cfg.mem_budget_bytes && c->held + grow > c->cfg.mem_budget_bytes)
     return fail(c, CVETL_EFULL, "buffer %s needs %zu more bytes; the context holds %zu of a %zu budget",
@@ -510,6 +543,7 @@ cvetl_status alloc_cell_table(cvetl_ctx* c, uint32_t cap, int gen, CellHash* ch)
 }
 
 void free_gen(cvetl_ctx* c, const char* prefix) {
+  c->buf_gen += 1;
   cudaStreamSynchronize(c->st);
   for (auto it = c->bufs.begin(); it != c->bufs.end();) {
     if (it->first.rfind(prefix, 0) == 0) {
@@ -760,7 +794,7 @@ cvetl_status stream_fold(cvetl_ctx* c) {
   ENSURE("cell.head", (size_t)R, &head);
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (R) {
-    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head)));
+    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head, nullptr)));
     LAUNCH_CHECK();
     LAUNCH(ST_CELL_WRITE, (k_cell_fold<<<(R + 255) / 256, 256, 0, c->st>>>(
                               skey, sidx, R, head, c->jo.run_cnt, c->jo.run_sum, c->jo.run_min,
@@ -855,6 +889,243 @@ cvetl_status stream_tables(cvetl_ctx* c) {
   }
   c->J = Jn;
   CK(cudaStreamSynchronize(c->st));
+  return CVETL_OK;
+}
+
+// The batch path after sizing (journey ids collected, J known): ids in order, bucket offsets,
+// the scatter, the journey kernel, then the load stage's run sort and cell table. With exact,
+// the run count is read back once and the load stage is sized by it; otherwise the load stage
+// reads the run count from device memory and is sized for the worst case (one run per kept
+// point), so that the whole sequence has no host read and can be captured in a CUDA graph.
+cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned long long* ukey,
+                         uint32_t* uslot, uint32_t J, bool exact) {
+  const uint32_t n = (uint32_t)c->n_rows;
+  if (c->bt.n_inst) CK(cudaMemsetAsync(c->inst_counts, 0, 2 * kMaxInst * 4, c->st));
+  unsigned long long* skey;
+  uint32_t* sslot;
+  {
+    cvetl_status s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot);
+    if (s != CVETL_OK) return s;
+  }
+  uint32_t *jn, *joff, *total;
+  ENSURE("j.n32", (size_t)J, &jn);
+  ENSURE("j.off32", (size_t)J, &joff);
+  ENSURE("j.total", 1, &total);
+  ENSURE("out.j_id", (size_t)J, &c->jid_sorted);
+  if (J) {
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted,
+                                                                       c->bt.n_inst ? 1 : 0, c->inst_counts)));
+    LAUNCH_CHECK();
+  }
+  {
+    cvetl_status s = scan_u32(c, jn, J, joff, total);
+    if (s != CVETL_OK) return s;
+  }
+  if (J) {
+    LAUNCH(ST_CURSORS, (k_journey_cursors<<<(J + 255) / 256, 256, 0, c->st>>>(sslot, J, joff, h)));
+    LAUNCH_CHECK();
+  }
+
+  // 3. scatter kept rows into journey buckets
+  const size_t nv = c->n_valid;
+  Rec* rec;
+  uint32_t* ridx;
+  ENSURE("rec", nv, &rec);
+  ENSURE("ridx", nv, &ridx);
+  if (n) {
+    const int U = c->tune.row_unroll;
+#define SCAT(U_) k_scatter<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
+    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)
+    if (U == 2) LAUNCH(ST_SCATTER, (SCAT(2)));
+    else if (U == 8) LAUNCH(ST_SCATTER, (SCAT(8)));
+    else LAUNCH(ST_SCATTER, (SCAT(4)));
+#undef SCAT
+    LAUNCH_CHECK();
+  }
+
+  // 4. per-journey sort, kinematics, keys, journey table, cell runs
+  Elem *scrA, *scrB;
+  ENSURE("scr.a", nv, &scrA);
+  ENSURE("scr.b", nv, &scrB);
+  JourneyOut& o = c->jo;
+  ENSURE("out.j_n", (size_t)J, &o.n);
+  ENSURE("out.j_off", (size_t)J, &o.off);
+  ENSURE("out.j_start_ts", (size_t)J, &o.start_ts);
+  ENSURE("out.j_end_ts", (size_t)J, &o.end_ts);
+  ENSURE("out.j_duration", (size_t)J, &o.duration);
+  ENSURE("out.j_dwell", (size_t)J, &o.dwell);
+  ENSURE("out.j_dist", (size_t)J, &o.dist);
+  ENSURE("out.j_slat", (size_t)J, &o.slat);
+  ENSURE("out.j_slon", (size_t)J, &o.slon);
+  ENSURE("out.j_elat", (size_t)J, &o.elat);
+  ENSURE("out.j_elon", (size_t)J, &o.elon);
+  if (c->cfg.materialize_points) {
+    ENSURE("out.p_perm", nv, &o.perm);
+    ENSURE("out.p_d", nv, &o.d);
+    ENSURE("out.p_vhat", nv, &o.vhat);
+    ENSURE("out.p_accel", nv, &o.accel);
+    ENSURE("out.p_dwell", nv, &o.dwell_pt);
+    ENSURE("out.p_key", nv, &o.key);
+    ENSURE("out.p_flags", nv, &o.flags);
+  } else {
+    o.perm = nullptr;
+    o.d = nullptr;
+    o.vhat = o.accel = nullptr;
+    o.dwell_pt = nullptr;
+    o.key = nullptr;
+    o.flags = nullptr;
+  }
+  ENSURE("run.sortkey", nv, &o.run_sortkey);
+  ENSURE("run.cnt", nv, &o.run_cnt);
+  ENSURE("run.sum", nv, &o.run_sum);
+  ENSURE("run.min", nv, &o.run_min);
+  ENSURE("run.max", nv, &o.run_max);
+  o.run_cap = (uint32_t)nv;
+  // work list, longest journey first, for the persistent journey kernel
+  unsigned long long *szkey, *szsorted;
+  uint32_t *order = nullptr, *work;
+  ENSURE("j.szkey", (size_t)J, &szkey);
+  ENSURE("j.work", 1, &work);
+  CK(cudaMemsetAsync(work, 0, 4, c->st));
+  if (J) {
+    LAUNCH(ST_SIZES, (k_size_keys<<<(J + 255) / 256, 256, 0, c->st>>>(jn, J, szkey)));
+    LAUNCH_CHECK();
+    cvetl_status s = sort_pairs<unsigned long long>(c, "osort", szkey, nullptr, J, 0, 32, &szsorted, &order);
+    if (s != CVETL_OK) return s;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool pers = c->tune.journey_ctas > 0;
+    const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
+    const bool f32 = c->cfg.precision == CVETL_FP32;
+#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, \
+                                                                      c->dstate, nullptr, JState{}, order, work)
+    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true)));
+    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false)));
+    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true)));
+    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false)));
+#undef JRN
+    LAUNCH_CHECK();
+  }
+
+  // load: runs ordered by (key, first sorted position), folded into the cell table
+  uint32_t R = (uint32_t)c->n_valid;
+  const uint32_t* Rd = &c->dstate->n_runs;
+  if (exact) {
+    cvetl_status s = read_state(c);
+    if (s != CVETL_OK) return s;
+    R = c->hstate->n_runs;
+    Rd = nullptr;
+  }
+  unsigned long long* rkey;
+  uint32_t* sidx;
+  cvetl_status s = sort_pairs<unsigned long long>(c, "rsort", c->jo.run_sortkey, nullptr, R, 0, 64, &rkey, &sidx, Rd);
+  if (s != CVETL_OK) return s;
+  uint32_t *head, *cidx, *ctotal;
+  ENSURE("cell.head", (size_t)R, &head);
+  ENSURE("cell.idx", (size_t)R, &cidx);
+  ENSURE("cell.total", 1, &ctotal);
+  if (R) {
+    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<grid_for(R, 256), 256, 0, c->st>>>(rkey, R, head, Rd)));
+    LAUNCH_CHECK();
+  }
+  if ((s = scan_u32(c, head, R, cidx, ctotal, Rd)) != CVETL_OK) return s;
+  CellOut& co = c->co;
+  ENSURE("out.c_key", (size_t)R, &co.key);
+  ENSURE("out.c_row", (size_t)R, &co.row);
+  ENSURE("out.c_col", (size_t)R, &co.col);
+  ENSURE("out.c_bin", (size_t)R, &co.bin);
+  ENSURE("out.c_count", (size_t)R, &co.count);
+  ENSURE("out.c_sum", (size_t)R, &co.sum);
+  ENSURE("out.c_mean", (size_t)R, &co.mean);
+  ENSURE("out.c_min", (size_t)R, &co.min);
+  ENSURE("out.c_max", (size_t)R, &co.max);
+  if (R) {
+    LAUNCH(ST_CELL_WRITE, (k_cell_write<<<grid_for(R, 256), 256, 0, c->st>>>(
+                              rkey, sidx, R, head, cidx, c->jo.run_cnt, c->jo.run_sum,
+                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt,
+                              c->inst_counts + kMaxInst, co, Rd)));
+    LAUNCH_CHECK();
+  }
+  c->cell_total = ctotal;
+  return CVETL_OK;
+}
+
+// post_sizing as a CUDA graph, one per shape (rows, journeys, kept rows, hash table, buffer
+// generation, input columns, batch table, precision, point columns, launch shapes). The first
+// run of a shape executes eagerly (allocating what it needs) and is then captured; later runs of
+// the shape launch the graph. A capture that fails leaves that shape eager.
+cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned long long* ukey,
+                       uint32_t* uslot, uint32_t J) {
+  cvetl_ctx::GraphKey k;
+  memset(&k, 0, sizeof k);
+  k.n = (uint64_t)c->n_rows;
+  k.J = J;
+  k.nv = c->n_valid;
+  k.cap = h.cap;
+  k.gen = c->buf_gen;
+  k.cols[0] = c->jid;
+  k.cols[1] = c->ts;
+  k.cols[2] = c->lat;
+  k.cols[3] = c->lon;
+  k.cols[4] = c->spd;
+  k.inst = c->bt.inst;
+  k.n_inst = c->bt.n_inst;
+  k.precision = c->cfg.precision;
+  k.materialize = c->cfg.materialize_points;
+  k.t0 = c->tune.journey_ctas;
+  k.t1 = c->tune.row_unroll;
+  k.t2 = c->tune.small_sort_max;
+  for (auto& g : c->graphs) {
+    if (!(g.key == k)) continue;
+    if (!g.exec) return post_sizing(c, h, row_slot, ukey, uslot, J, false);
+    CK(cudaGraphLaunch(g.exec, c->st));
+    c->graph_replays += 1;
+    for (int i = 0; i < ST_COUNT; ++i) {
+      c->launches[i] += g.launches[i];
+      c->total_launches += g.launches[i];
+    }
+    return CVETL_OK;
+  }
+  cvetl_status s = post_sizing(c, h, row_slot, ukey, uslot, J, false);
+  if (s != CVETL_OK) return s;
+  k.gen = c->buf_gen;  // the buffers as they stand after the eager run
+  cvetl_ctx::GraphEntry e;
+  e.key = k;
+  e.exec = nullptr;
+  memset(c->cap_launches, 0, sizeof c->cap_launches);
+  cudaGraph_t graph = nullptr;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+  }
+  cudaStream_t user = c->st;
+  cudaError_t ce = cudaErrorNotReady;
+  cvetl_status cs = CVETL_ECUDA;
+  if (c->cap_stream) {
+    // nothing executes during a capture, so the private stream needs no ordering with the user's
+    c->st = c->cap_stream;
+    c->capturing = true;
+    ce = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+      const std::string saved = c->err;
+      cs = post_sizing(c, h, row_slot, ukey, uslot, J, false);
+      ce = cudaStreamEndCapture(c->st, &graph);
+      if (cs != CVETL_OK) c->err = saved;  // the eager results stand
+    }
+    c->capturing = false;
+    c->st = user;
+  }
+  if (ce == cudaSuccess && cs == CVETL_OK && graph && cudaGraphInstantiate(&e.exec, graph, 0) != cudaSuccess)
+    e.exec = nullptr;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+  memcpy(e.launches, c->cap_launches, sizeof e.launches);
+  if (c->graphs.size() >= 8) {
+    if (c->graphs.front().exec) cudaGraphExecDestroy(c->graphs.front().exec);
+    c->graphs.erase(c->graphs.begin());
+  }
+  c->graphs.push_back(e);
   return CVETL_OK;
 }
 
@@ -994,6 +1265,9 @@ cvetl_status cvetl_destroy(cvetl_ctx* c) {
     cudaEventDestroy(p.second.second);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  for (auto& g : c->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return CVETL_OK;
 }
@@ -1331,115 +1605,27 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(&J, counter, 4, cudaMemcpyDeviceToHost));
   c->J = J;
-  unsigned long long* skey;
-  uint32_t* sslot;
-  {
-    cvetl_status s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot);
-    if (s != CVETL_OK) return s;
-  }
-  uint32_t *jn, *joff, *total;
-  ENSURE("j.n32", (size_t)J, &jn);
-  ENSURE("j.off32", (size_t)J, &joff);
-  ENSURE("j.total", 1, &total);
-  ENSURE("out.j_id", (size_t)J, &c->jid_sorted);
-  if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted,
-                                                                       c->bt.n_inst ? 1 : 0, c->inst_counts)));
-    LAUNCH_CHECK();
-  }
-  {
-    cvetl_status s = scan_u32(c, jn, J, joff, total);
-    if (s != CVETL_OK) return s;
-  }
-  if (J) {
-    LAUNCH(ST_CURSORS, (k_journey_cursors<<<(J + 255) / 256, 256, 0, c->st>>>(sslot, J, joff, h)));
-    LAUNCH_CHECK();
-  }
 
-  // 3. scatter kept rows into journey buckets
-  const size_t nv = c->n_valid;
-  Rec* rec;
-  uint32_t* ridx;
-  ENSURE("rec", nv, &rec);
-  ENSURE("ridx", nv, &ridx);
-  if (n) {
-    const int U = c->tune.row_unroll;
-#define SCAT(U_) k_scatter<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
-    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)
-    if (U == 2) LAUNCH(ST_SCATTER, (SCAT(2)));
-    else if (U == 8) LAUNCH(ST_SCATTER, (SCAT(8)));
-    else LAUNCH(ST_SCATTER, (SCAT(4)));
-#undef SCAT
-    LAUNCH_CHECK();
-  }
-
-  // 4. per-journey sort, kinematics, keys, journey table, cell runs
-  Elem *scrA, *scrB;
-  ENSURE("scr.a", nv, &scrA);
-  ENSURE("scr.b", nv, &scrB);
-  JourneyOut& o = c->jo;
-  ENSURE("out.j_n", (size_t)J, &o.n);
-  ENSURE("out.j_off", (size_t)J, &o.off);
-  ENSURE("out.j_start_ts", (size_t)J, &o.start_ts);
-  ENSURE("out.j_end_ts", (size_t)J, &o.end_ts);
-  ENSURE("out.j_duration", (size_t)J, &o.duration);
-  ENSURE("out.j_dwell", (size_t)J, &o.dwell);
-  ENSURE("out.j_dist", (size_t)J, &o.dist);
-  ENSURE("out.j_slat", (size_t)J, &o.slat);
-  ENSURE("out.j_slon", (size_t)J, &o.slon);
-  ENSURE("out.j_elat", (size_t)J, &o.elat);
-  ENSURE("out.j_elon", (size_t)J, &o.elon);
-  if (c->cfg.materialize_points) {
-    ENSURE("out.p_perm", nv, &o.perm);
-    ENSURE("out.p_d", nv, &o.d);
-    ENSURE("out.p_vhat", nv, &o.vhat);
-    ENSURE("out.p_accel", nv, &o.accel);
-    ENSURE("out.p_dwell", nv, &o.dwell_pt);
-    ENSURE("out.p_key", nv, &o.key);
-    ENSURE("out.p_flags", nv, &o.flags);
-  } else {
-    o.perm = nullptr;
-    o.d = nullptr;
-    o.vhat = o.accel = nullptr;
-    o.dwell_pt = nullptr;
-    o.key = nullptr;
-    o.flags = nullptr;
-  }
-  ENSURE("run.sortkey", nv, &o.run_sortkey);
-  ENSURE("run.cnt", nv, &o.run_cnt);
-  ENSURE("run.sum", nv, &o.run_sum);
-  ENSURE("run.min", nv, &o.run_min);
-  ENSURE("run.max", nv, &o.run_max);
-  o.run_cap = (uint32_t)nv;
-  // work list, longest journey first, for the persistent journey kernel
-  unsigned long long *szkey, *szsorted;
-  uint32_t *order = nullptr, *work;
-  ENSURE("j.szkey", (size_t)J, &szkey);
-  ENSURE("j.work", 1, &work);
-  CK(cudaMemsetAsync(work, 0, 4, c->st));
-  if (J) {
-    LAUNCH(ST_SIZES, (k_size_keys<<<(J + 255) / 256, 256, 0, c->st>>>(jn, J, szkey)));
-    LAUNCH_CHECK();
-    cvetl_status s = sort_pairs<unsigned long long>(c, "osort", szkey, nullptr, J, 0, 32, &szsorted, &order);
-    if (s != CVETL_OK) return s;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const bool pers = c->tune.journey_ctas > 0;
-    const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
-    const bool f32 = c->cfg.precision == CVETL_FP32;
-#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, \
-                                                                      c->dstate, nullptr, JState{}, order, work)
-    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true)));
-    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false)));
-    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true)));
-    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false)));
-#undef JRN
-    LAUNCH_CHECK();
-  }
-  cvetl_status s = read_state(c);
+  // 3. the rest of transform and load, with no host read until the end
+  cvetl_status s = c->cfg.graph ? run_graph(c, h, row_slot, ukey, uslot, J)
+                                : post_sizing(c, h, row_slot, ukey, uslot, J, true);
   if (s != CVETL_OK) return s;
+  if ((s = read_state(c)) != CVETL_OK) return s;
   c->R = c->hstate->n_runs;
+  uint32_t K = 0;
+  CK(cudaMemcpy(&K, c->cell_total, 4, cudaMemcpyDeviceToHost));
+  c->K = c->R ? K : 0;
+  if (c->bt.n_inst) {  // first journey and cell row of each instance
+    uint32_t cnt[2 * kMaxInst];
+    CK(cudaMemcpy(cnt, c->inst_counts, sizeof cnt, cudaMemcpyDeviceToHost));
+    const int m = c->bt.n_inst;
+    c->inst_journeys.assign(m + 1, 0);
+    c->inst_cells.assign(m + 1, 0);
+    for (int i = 0; i < m; ++i) {
+      c->inst_journeys[i + 1] = c->inst_journeys[i] + cnt[i];
+      c->inst_cells[i + 1] = c->inst_cells[i] + cnt[kMaxInst + i];
+    }
+  }
   c->state = 2;
   return CVETL_OK;
 }
@@ -1454,52 +1640,8 @@ cvetl_status cvetl_load(cvetl_ctx* c) {
     c->state = 3;
     return CVETL_OK;
   }
-  const uint32_t R = c->R;
-  unsigned long long* skey;
-  uint32_t* sidx;
-  cvetl_status s = sort_pairs<unsigned long long>(c, "rsort", c->jo.run_sortkey, nullptr, R, 0, 64, &skey, &sidx);
-  if (s != CVETL_OK) return s;
-  uint32_t *head, *cidx, *total;
-  ENSURE("cell.head", (size_t)R, &head);
-  ENSURE("cell.idx", (size_t)R, &cidx);
-  ENSURE("cell.total", 1, &total);
-  if (R) {
-    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head)));
-    LAUNCH_CHECK();
-  }
-  if ((s = scan_u32(c, head, R, cidx, total)) != CVETL_OK) return s;
-  CellOut& co = c->co;
-  ENSURE("out.c_key", (size_t)R, &co.key);
-  ENSURE("out.c_row", (size_t)R, &co.row);
-  ENSURE("out.c_col", (size_t)R, &co.col);
-  ENSURE("out.c_bin", (size_t)R, &co.bin);
-  ENSURE("out.c_count", (size_t)R, &co.count);
-  ENSURE("out.c_sum", (size_t)R, &co.sum);
-  ENSURE("out.c_mean", (size_t)R, &co.mean);
-  ENSURE("out.c_min", (size_t)R, &co.min);
-  ENSURE("out.c_max", (size_t)R, &co.max);
-  if (R) {
-    LAUNCH(ST_CELL_WRITE, (k_cell_write<<<(R + 255) / 256, 256, 0, c->st>>>(
-                              skey, sidx, R, head, cidx, c->jo.run_cnt, c->jo.run_sum,
-                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt,
-                              c->inst_counts + kMaxInst, co)));
-    LAUNCH_CHECK();
-  }
-  if ((s = read_state(c)) != CVETL_OK) return s;
-  uint32_t K = 0;
-  CK(cudaMemcpy(&K, total, 4, cudaMemcpyDeviceToHost));
-  c->K = R ? K : 0;
-  if (c->bt.n_inst) {  // first journey and cell row of each instance
-    uint32_t cnt[2 * kMaxInst];
-    CK(cudaMemcpy(cnt, c->inst_counts, sizeof cnt, cudaMemcpyDeviceToHost));
-    const int m = c->bt.n_inst;
-    c->inst_journeys.assign(m + 1, 0);
-    c->inst_cells.assign(m + 1, 0);
-    for (int i = 0; i < m; ++i) {
-      c->inst_journeys[i + 1] = c->inst_journeys[i] + cnt[i];
-      c->inst_cells[i + 1] = c->inst_cells[i] + cnt[kMaxInst + i];
-    }
-  }
+  // batch mode: the load stage's kernels were queued with the transform's (one sequence with
+  // a single read-back at its end); the cell table is complete here
   c->state = 3;
   return CVETL_OK;
 }
@@ -1634,6 +1776,7 @@ cvetl_status cvetl_stats_get(cvetl_ctx* c, cvetl_stats* out) {
   }
   out->total_launches = c->total_launches;
   out->device_bytes = (int64_t)c->held;
+  out->graph_replays = c->graph_replays;
   return CVETL_OK;
 }
 

@@ -1028,20 +1028,20 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
                                                          JourneyOut o, DevState* st,
                                                          const uint32_t* __restrict__ jslot, JState js,
                                                          const uint32_t* __restrict__ order, uint32_t* work) {
-  if (!Persistent) {
+  if constexpr (!Persistent) {
     if (blockIdx.x < J)
       journey_one<Form>(order ? order[blockIdx.x] : blockIdx.x, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
-    return;
-  }
-  __shared__ uint32_t s_w;
-  for (;;) {
-    if (threadIdx.x == 0) s_w = atomicAdd(work, 1u);
-    __syncthreads();
-    const uint32_t w = s_w;
-    __syncthreads();
-    if (w >= J) break;
-    journey_one<Form>(order ? order[w] : w, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
-    __syncthreads();
+  } else {
+    __shared__ uint32_t s_w;
+    for (;;) {
+      if (threadIdx.x == 0) s_w = atomicAdd(work, 1u);
+      __syncthreads();
+      const uint32_t w = s_w;
+      __syncthreads();
+      if (w >= J) break;
+      journey_one<Form>(order ? order[w] : w, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
+      __syncthreads();
+    }
   }
 }
 

@@ -95,7 +95,7 @@ extern "C" cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t
   int hb = (int)((un + rs::kBlock - 1) / rs::kBlock);
   if (hb > sms * 4) hb = sms * 4;
   rs::k_histogram<unsigned long long><<<hb, rs::kBlock, 0, st>>>(
-      (const unsigned long long*)keys_in, un, begin_bit, passes, hist);
+      (const unsigned long long*)keys_in, un, begin_bit, passes, hist, nullptr);
   rs::k_hist_scan<<<passes, rs::kBlock, 0, st>>>(hist);
   {
     cudaError_t e = cudaGetLastError();
@@ -112,7 +112,7 @@ extern "C" cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t
     CK(cudaMemsetAsync(status, 0, 4ull * ntiles * rs::kRadix, st));
     rs::k_onesweep<unsigned long long><<<ntiles, rs::kBlock, (size_t)rs::kTile * 12, st>>>(
         kin, vin, kout, vout, un, begin_bit + rs::kBits * p, hist + p * rs::kRadix, status,
-        tiles + p, err);
+        tiles + p, err, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, CVETL_ECUDA, "cvetl_sort_u64_noalloc: %s", cudaGetErrorString(e));
     kin = kout;

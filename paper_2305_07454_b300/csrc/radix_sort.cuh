@@ -28,11 +28,14 @@ __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
 }
 
 // Histograms of n_passes digits starting at begin_bit. hist: [kMaxPasses][256], zeroed.
+// n_dev != nullptr: the key count is read from device memory (n is then an upper bound).
 template <typename K>
 __global__ void __launch_bounds__(kBlock) k_histogram(const K* __restrict__ keys, uint32_t n,
                                                       int begin_bit, int n_passes,
-                                                      uint32_t* __restrict__ hist) {
+                                                      uint32_t* __restrict__ hist,
+                                                      const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t sh[kMaxPasses][kRadix];
+  if (n_dev) n = min(n, *n_dev);
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kBlock) (&sh[0][0])[i] = 0;
   __syncthreads();
   for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
@@ -56,7 +59,10 @@ __global__ void __launch_bounds__(kBlock) k_hist_scan(uint32_t* hist) {
 }
 
 // One digit pass. status: [n_tiles][256] words, zeroed; tile_ctr zeroed.
-// vin == nullptr means value = input position (iota).
+// vin == nullptr means value = input position (iota). n_dev != nullptr: the key count is read
+// from device memory and the grid covers the upper bound n; tiles are numbered in the order the
+// CTAs start, so a tile that starts past the count returns at once (no tile holding keys looks
+// back at it).
 template <typename K>
 __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
                                                      const uint32_t* __restrict__ vin,
@@ -64,7 +70,7 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
                                                      uint32_t* __restrict__ vout, uint32_t n,
                                                      int shift, const uint32_t* __restrict__ goff,
                                                      uint32_t* status, uint32_t* tile_ctr,
-                                                     uint32_t* err) {
+                                                     uint32_t* err, const uint32_t* __restrict__ n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   K* s_keys = reinterpret_cast<K*>(smem_raw);
   uint32_t* s_vals = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * kTile);
@@ -80,6 +86,10 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
   __syncthreads();
   const uint32_t tile = s_tile;
   const uint32_t base = tile * kTile;
+  if (n_dev) {
+    n = min(n, *n_dev);
+    if (base >= n && tile > 0) return;
+  }
   const uint32_t n_valid = (base < n) ? min((uint32_t)kTile, n - base) : 0u;
 
   K key[kIpt];

@@ -9,9 +9,13 @@ constexpr int kBlock = 256;
 constexpr int kRounds = 16;
 constexpr int kTile = kBlock * kRounds;
 
+// n_dev != nullptr (all three passes): the count is read from device memory, n is the upper
+// bound the grid covers.
 __global__ void __launch_bounds__(kBlock) k_tile_sums(const uint32_t* __restrict__ in, uint32_t n,
-                                                      uint32_t* __restrict__ sums) {
+                                                      uint32_t* __restrict__ sums,
+                                                      const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t scratch[kBlock / 32];
+  if (n_dev) n = min(n, *n_dev);
   uint32_t base = blockIdx.x * kTile, acc = 0;
   for (int r = 0; r < kRounds; ++r) {
     uint32_t i = base + r * kBlock + threadIdx.x;
@@ -37,8 +41,11 @@ __global__ void __launch_bounds__(kBlock) k_scan_sums(uint32_t* sums, uint32_t n
 
 __global__ void __launch_bounds__(kBlock) k_apply(const uint32_t* __restrict__ in, uint32_t n,
                                                   const uint32_t* __restrict__ sums,
-                                                  uint32_t* __restrict__ out) {
+                                                  uint32_t* __restrict__ out,
+                                                  const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t scratch[kBlock / 32 + 1];
+  if (n_dev) n = min(n, *n_dev);
+  if (blockIdx.x * kTile >= n && blockIdx.x > 0) return;
   uint32_t base = blockIdx.x * kTile, carry = sums[blockIdx.x];
   for (int r = 0; r < kRounds; ++r) {
     uint32_t i = base + r * kBlock + threadIdx.x;
