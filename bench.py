@@ -415,6 +415,168 @@ def serving(host, n, args, batch_cells, batch_ms):
     return out
 
 
+def _roofline(stages, counters, precision, n_steps_div=1.0):
+    """Roofline entry of the dominant kernel from per-stage CUDA-event times."""
+    top = max(stages, key=lambda k: stages[k]["ms"])
+    launches = max(1, stages[top]["launches"])
+    avg_ms = stages[top]["ms"] / launches
+    hbm_peak, peak_src = load_peaks()
+    if top == "journeys" and precision == "fp64":
+        gops_peak, mhz = fp64_peak_gops()
+        ops = FP64_OPS_PER_POINT * counters["n_valid"]
+        achieved = ops / (avg_ms / 1e3) / 1e9
+        return {"bound": "alu", "kernel": top, "achieved": achieved, "peak": gops_peak,
+                "unit": "G binary64 ops/s",
+                "peak_source": f"derived: {SMS} SMs x {FP64_PER_CLK_PER_SM:g} binary64 ops/clk x {mhz:g} MHz",
+                "frac": achieved / gops_peak, "ops_per_launch": ops, "avg_launch_ms": avg_ms, "traffic": None}
+    ab = algorithmic_bytes(top, counters)
+    achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
+    return {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src,
+            "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
+            "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": None}
+
+
+def _max_rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.size == 0:
+        return 0.0
+    d = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+    d[(a == 0) & (b == 0)] = 0.0
+    return float(d.max())
+
+
+def run_week(args):
+    """The batched workload: 7 days x 4 regional boxes in one batch (one pass of every kernel,
+    launch shapes from the autotuner, the post-sizing sequence replayed as a CUDA graph)."""
+    import torch
+
+    import cvgen
+    import paper_2305_07454_b300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision or "fp32"
+    recipes = cvgen.week_regions(seed=1 + rank, scale=args.scale)
+    t_gen = time.perf_counter()
+    host, grids = [], []
+    dt = {"jid": torch.int64, "ts": torch.int64, "lat": torch.float64, "lon": torch.float64,
+          "speed": torch.float32, "heading": torch.float32}
+    for r in recipes:
+        n_i = cvgen.count(r["params"])
+        h = {k: torch.empty(n_i, dtype=v, pin_memory=True) for k, v in dt.items()}
+        cvgen.generate(r["params"], out={k: v.numpy() for k, v in h.items()})
+        host.append(h)
+        grids.append({k: r[k] for k in P.GRID_KEYS})
+    t_gen = time.perf_counter() - t_gen
+    n = sum(h["jid"].shape[0] for h in host)
+    d_insts = [dict(g, **{k: h[k].to(dev, non_blocking=True) for k in COLS}) for g, h in zip(grids, host)]
+    h_insts = [dict(g, **{k: h[k] for k in COLS}) for g, h in zip(grids, host)]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    pc = P.FP32 if prec == "fp32" else P.FP64
+
+    # per-stage times of one eager run (profiled), and the FP64 form for the error report
+    with P.Pipeline(stream=stream, precision=pc, profile=1) as pe:
+        pe.extract_batch(d_insts)
+        tune_t = time.perf_counter()
+        tuning = pe.autotune(reps=2)
+        tune_t = time.perf_counter() - tune_t
+        pe.transform()
+        pe.load()
+        pe.stats_reset()
+        pe.extract_batch(d_insts)
+        pe.transform()
+        pe.load()
+        stats = pe.stats()
+        res = pe.results(to_host=True)
+        t = pe.tables()
+    counters = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_runs")}
+    counters.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
+    errors = None
+    if pc == P.FP32:
+        with P.Pipeline(stream=stream, precision=P.FP64) as p64:
+            p64.extract_batch(d_insts)
+            p64.transform()
+            p64.load()
+            ref = p64.results(to_host=True)
+        same_int = all(np.array_equal(res["cells"][k], ref["cells"][k]) for k in ("key", "count", "min", "max")) and \
+            all(np.array_equal(res["journeys"][k], ref["journeys"][k]) for k in ("id", "n", "start_ts", "end_ts", "dwell_ms"))
+        errors = {"integers_keys_counts_min_max_equal": bool(same_int),
+                  "journey_distance_max_rel": _max_rel(res["journeys"]["distance_m"], ref["journeys"]["distance_m"]),
+                  "cell_sum_max_rel": _max_rel(res["cells"]["sum"], ref["cells"]["sum"]),
+                  "cell_mean_max_rel": _max_rel(res["cells"]["mean"], ref["cells"]["mean"])}
+        del ref
+    del res
+
+    # timed: graph replays of the tuned shapes
+    pipe = P.Pipeline(stream=stream, precision=pc, graph=1)
+    pipe.tuning = {k: v for k, v in tuning.items() if k != "ms"}
+
+    def step(insts):
+        pipe.extract_batch(insts)
+        pipe.transform()
+        pipe.load()
+        pipe.tables()
+
+    for _ in range(max(args.warmup, 2)):
+        step(d_insts)
+    pipe.stats_reset()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(d_insts)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    gst = pipe.stats()
+    ms_step = ms_total / args.steps
+    value = n / (ms_step / 1e3)
+    # end to end from pinned host columns
+    e2e_steps = max(1, min(args.steps, 2))
+    step(h_insts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(h_insts)
+        out = pipe.results(to_host=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values())
+    pipe.close()
+    stages = stats["stages"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 2), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "fp64" else "f32 (binary64 coordinate differences)",
+        "data": "synthetic",
+        "config": {"workload": f"week_regions x{args.scale:g}: {len(recipes)} instances (7 days x 4 regional "
+                               f"boxes), {n} records, {counters['n_journeys']} journeys, Zipf(1.5) journey "
+                               "lengths on [10, 200000], one batch",
+                   "records": n, "instances": len(recipes), "precision": prec, "scale": args.scale,
+                   "instance_records": [int(h["jid"].shape[0]) for h in host],
+                   "l2": "inputs larger than L2 (no flush needed)", "parallelism": "1 GPU"},
+        "tuning": {**tuning, "seconds": tune_t},
+        "graph": {"replays_in_timed_steps": gst["graph_replays"], "launches_per_step": gst["total_launches"] / args.steps},
+        "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * sum(BYTES[k] for k in COLS),
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": gst["total_launches"],
+        "roofline": _roofline(stages, counters, prec),
+        "stages": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"]} for k, v in stages.items() if v["launches"]},
+        "errors_vs_fp64_form": errors,
+        "counters": counters,
+        "generation_s": t_gen,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline({k: host[0][k] for k in COLS}, int(host[0]["jid"].shape[0]), budget_s=args.cpu_budget)
+        print(json.dumps(line), flush=True)
+
+
 def _sample_journeys(host, frac_den: int):
     """Whole journeys: the records whose journey id falls in 1 of frac_den hash classes."""
     jid = host["jid"].numpy() if hasattr(host["jid"], "numpy") else host["jid"]
@@ -500,7 +662,9 @@ def main():
     ap.add_argument("--workload", default="full_day")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--input", default="columns", choices=["columns", "csv"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="fp64 for the day workloads, fp32 for week_regions unless given")
+    ap.add_argument("--scale", type=float, default=0.25, help="week_regions: instance size factor")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-feeds", type=int, default=4, help="0 skips the serving leg")
     ap.add_argument("--serve-slots", type=int, default=0, help="server slots (default: one per feed)")
@@ -508,7 +672,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "week_regions":
+        run_week(args)
     else:
+        args.precision = args.precision or "fp64"
         run_ours(args)
 
 

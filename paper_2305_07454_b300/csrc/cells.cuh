@@ -29,8 +29,7 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
                              const uint32_t* __restrict__ run_cnt, const double* __restrict__ run_sum,
                              const float* __restrict__ run_min, const float* __restrict__ run_max,
                              int32_t n_rows, int32_t n_cols, Batch bt,
-                             uint32_t* __restrict__ inst_cells, CellOut o,
-                             const uint32_t* __restrict__ R_dev) {
+                             CellOut o, const uint32_t* __restrict__ R_dev) {
   if (R_dev) R = min(R, *R_dev);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) {
     if (!head[i]) continue;
@@ -53,7 +52,6 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
       lkey = key - bt.inst[q].key_off;
       nr = bt.inst[q].n_rows;
       nc = bt.inst[q].n_cols;
-      atomicAdd(&inst_cells[q], 1u);
     }
     const uint32_t cells = (uint32_t)nr * (uint32_t)nc;
     o.key[c] = lkey;
@@ -66,6 +64,36 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
     o.min[c] = mn;
     o.max[c] = mx;
   }
+}
+
+// First journey rank and first cell row of each batch instance (out[i], out[kMaxInst + i]), by
+// binary search over the sorted journey keys (order-preserving keys of (instance, id)) and the
+// sorted run keys ((key << 32) | position; an instance's first run heads its first cell).
+// One thread per instance.
+__global__ void k_inst_begins(const unsigned long long* __restrict__ jkey, uint32_t J,
+                              const unsigned long long* __restrict__ rkey, uint32_t R,
+                              const uint32_t* __restrict__ R_dev, const uint32_t* __restrict__ cidx,
+                              const uint32_t* __restrict__ K_dev, Batch bt, uint32_t* __restrict__ out) {
+  if (R_dev) R = min(R, *R_dev);
+  const int i = threadIdx.x;
+  if (i >= bt.n_inst) return;
+  const unsigned long long jk = ((unsigned long long)i << kInstShift) ^ kSign64;
+  uint32_t lo = 0, hi = J;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jkey[mid] < jk) lo = mid + 1;
+    else hi = mid;
+  }
+  out[i] = lo;
+  const unsigned long long ck = (unsigned long long)bt.inst[i].key_off << 32;
+  lo = 0;
+  hi = R;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (rkey[mid] < ck) lo = mid + 1;
+    else hi = mid;
+  }
+  out[kMaxInst + i] = lo < R ? cidx[lo] : *K_dev;
 }
 
 }  // namespace cvetl

@@ -82,6 +82,8 @@ struct cvetl_ctx {
   std::vector<int64_t> inst_cells, inst_journeys;  // first cell / journey row (after cvetl_load)
   uint32_t* inst_counts = nullptr;  // device: journeys [kMaxInst], then cells [kMaxInst]
   uint32_t* cell_total = nullptr;   // device: the cell count of the last batch
+  uint32_t hint_distinct = 0;       // journeys of the last batch (sizes the next hash table)
+  std::vector<double> batch_key;    // the last batch's instance grids and sizes
   // stream mode
   struct {
     bool flushed = false, has_w_prev = false;
@@ -709,7 +711,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   ENSURE("j.total", 1, &total);
   ENSURE("j.idtmp", (size_t)J, &jid_tmp);
   if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0, nullptr)));
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0)));
     LAUNCH_CHECK();
   }
   if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
@@ -900,7 +902,6 @@ cvetl_status stream_tables(cvetl_ctx* c) {
 cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned long long* ukey,
                          uint32_t* uslot, uint32_t J, bool exact) {
   const uint32_t n = (uint32_t)c->n_rows;
-  if (c->bt.n_inst) CK(cudaMemsetAsync(c->inst_counts, 0, 2 * kMaxInst * 4, c->st));
   unsigned long long* skey;
   uint32_t* sslot;
   {
@@ -914,7 +915,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   ENSURE("out.j_id", (size_t)J, &c->jid_sorted);
   if (J) {
     LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted,
-                                                                       c->bt.n_inst ? 1 : 0, c->inst_counts)));
+                                                                       c->bt.n_inst ? 1 : 0)));
     LAUNCH_CHECK();
   }
   {
@@ -1043,8 +1044,12 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   if (R) {
     LAUNCH(ST_CELL_WRITE, (k_cell_write<<<grid_for(R, 256), 256, 0, c->st>>>(
                               rkey, sidx, R, head, cidx, c->jo.run_cnt, c->jo.run_sum,
-                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt,
-                              c->inst_counts + kMaxInst, co, Rd)));
+                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt, co, Rd)));
+    LAUNCH_CHECK();
+  }
+  if (c->bt.n_inst) {
+    LAUNCH(ST_CELL_WRITE, (k_inst_begins<<<1, 32, 0, c->st>>>(skey, J, rkey, R, Rd, cidx, ctotal, c->bt,
+                                                               c->inst_counts)));
     LAUNCH_CHECK();
   }
   c->cell_total = ctotal;
@@ -1360,7 +1365,15 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   ENSURE("in.lat", n, &lat);
   ENSURE("in.lon", n, &lon);
   ENSURE("in.spd", n, &spd);
-  // instance table: threshold tables and offsets
+  // instance table: threshold tables and offsets (kept from the last batch when the instances'
+  // grids, days and sizes repeat)
+  std::vector<double> key;
+  key.push_back(c->cfg.cell_deg);
+  for (int i = 0; i < n_inst; ++i) {
+    const cvetl_instance& q = inst[i];
+    key.insert(key.end(), {q.lat_min, q.lon_min, (double)q.n_rows, (double)q.n_cols, (double)q.t0_ms, (double)q.n});
+  }
+  const bool same_tables = key == c->batch_key && c->bt.n_inst == n_inst && c->bt.inst != nullptr;
   std::vector<BatchInst> bi(n_inst);
   std::vector<unsigned long long> thr;
   std::vector<size_t> thr_at(n_inst);
@@ -1379,6 +1392,7 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
     }
     c->inst_rows[i + 1] = (int64_t)(r0 + m);
     c->inst_keys[i + 1] = c->inst_keys[i] + (int64_t)q.n_rows * q.n_cols * c->cfg.n_bins;
+    if (same_tables) continue;
     thr_at[i] = thr.size();
     for (int k = 0; k <= q.n_rows; ++k) thr.push_back(threshold(q.lat_min, c->cfg.cell_deg, k));
     for (int k = 0; k <= q.n_cols; ++k) thr.push_back(threshold(q.lon_min, c->cfg.cell_deg, k));
@@ -1389,6 +1403,24 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
     bi[i].t0_ms = q.t0_ms;
     bi[i].row_begin = (uint32_t)r0;
     bi[i].key_off = (uint32_t)c->inst_keys[i];
+  }
+  if (same_tables) {
+    const Batch keep = c->bt;
+    c->jid = jid;
+    c->ts = ts;
+    c->lat = lat;
+    c->lon = lon;
+    c->spd = spd;
+    c->heading = nullptr;
+    c->n_in = rows;
+    c->n_rows = rows;
+    c->csv_malformed = 0;
+    c->J = c->R = c->K = c->n_valid = 0;
+    c->bt = keep;
+    c->inst_cells.clear();
+    c->inst_journeys.clear();
+    c->state = 1;
+    return CVETL_OK;
   }
   unsigned long long* dthr;
   BatchInst* dbi;
@@ -1405,6 +1437,7 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   CK(cudaMemcpy(dbi, bi.data(), bi.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
   c->bt.n_inst = n_inst;
   c->bt.inst = dbi;
+  c->batch_key = key;
   c->jid = jid;
   c->ts = ts;
   c->lat = lat;
@@ -1552,12 +1585,13 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   }
   const uint32_t n = (uint32_t)c->n_rows;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
-  if (c->bt.n_inst) CK(cudaMemsetAsync(c->inst_counts, 0, 2 * kMaxInst * 4, c->st));
 
   // 1. count journeys (hash table of ids), growing the table if it overflows
   // start small (2^18 slots stay hot in L2) and grow when the ids do not fit at load <= 1/2
   uint32_t cap = next_pow2(2ull * (n > 256 ? n : 256));
   if (cap > (1u << 18)) cap = 1u << 18;
+  if (c->hint_distinct)  // the last batch's journey count: skip the growth steps it needed
+    cap = std::min(next_pow2(2ull * (n > 256 ? n : 256)), std::max(cap, next_pow2(2ull * c->hint_distinct + 2)));
   Hash h{};
   uint32_t* row_slot;
   ENSURE("row.slot", (size_t)n, &row_slot);
@@ -1591,6 +1625,7 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     cap = (cap * 4ull > limit) ? limit : cap * 4;
   }
   c->n_valid = (uint32_t)(n - c->hstate->n_malformed);
+  c->hint_distinct = c->hstate->n_distinct;
 
   // 2. distinct ids in ascending order -> rank, size, bucket offset
   unsigned long long* ukey;
@@ -1619,11 +1654,11 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     uint32_t cnt[2 * kMaxInst];
     CK(cudaMemcpy(cnt, c->inst_counts, sizeof cnt, cudaMemcpyDeviceToHost));
     const int m = c->bt.n_inst;
-    c->inst_journeys.assign(m + 1, 0);
-    c->inst_cells.assign(m + 1, 0);
+    c->inst_journeys.assign(m + 1, (int64_t)c->J);
+    c->inst_cells.assign(m + 1, (int64_t)c->K);
     for (int i = 0; i < m; ++i) {
-      c->inst_journeys[i + 1] = c->inst_journeys[i] + cnt[i];
-      c->inst_cells[i + 1] = c->inst_cells[i] + cnt[kMaxInst + i];
+      c->inst_journeys[i] = cnt[i];
+      c->inst_cells[i] = cnt[kMaxInst + i];
     }
   }
   c->state = 2;

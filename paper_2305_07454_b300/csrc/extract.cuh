@@ -133,22 +133,15 @@ __global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
   }
 }
 
-// Journey rank r (ascending id): size, id (a batch's (instance, id) is unpacked, and the
-// instance's journeys counted in inst_journeys).
+// Journey rank r (ascending id): size, id (a batch's (instance, id) is unpacked).
 __global__ void k_journey_sizes(const unsigned long long* __restrict__ skey,
                                 const uint32_t* __restrict__ sslot, uint32_t J, Hash h,
-                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out,
-                                int batched, uint32_t* __restrict__ inst_journeys) {
+                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out, int batched) {
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < J) {
     jn[r] = h.cnt[sslot[r]];
     const uint64_t id = skey[r] ^ kSign64;
-    if (batched) {
-      jid_out[r] = composite_jid(id);
-      atomicAdd(&inst_journeys[id >> kInstShift], 1u);
-    } else {
-      jid_out[r] = (int64_t)id;
-    }
+    jid_out[r] = batched ? composite_jid(id) : (int64_t)id;
   }
 }
 
