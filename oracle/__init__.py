@@ -26,6 +26,7 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
 
 KEY_INVALID = 0xFFFFFFFF
 F_START, F_DUP, F_OFFGRID, F_STOP = 0x01, 0x02, 0x04, 0x08
+DXN_CARDINAL, DXN_QUADRANT = 0, 1
 
 
 def build(force: bool = False, src: str = _SRC, out: str = _SO) -> str:
@@ -48,6 +49,19 @@ class Params(ctypes.Structure):
         ("v_stop_kmh", ctypes.c_float),
         ("earth_radius_m", ctypes.c_double),
     ]
+
+
+class LatticeParams(ctypes.Structure):
+    _fields_ = [("bin_ms", ctypes.c_int64), ("n_bins", ctypes.c_int32), ("direction", ctypes.c_int32)]
+
+
+LATTICE_DTYPES = {"key": np.uint32, "bin": np.int32, "dxn": np.int32, "row": np.int32, "col": np.int32,
+                  "count": np.uint32, "sum": np.float64, "mean": np.float32, "volume": np.uint32,
+                  "mean_norm": np.float32, "volume_norm": np.float32}
+
+
+class _LatticeCells(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in LATTICE_DTYPES]
 
 
 def default_params(**kw) -> Params:
@@ -112,6 +126,12 @@ class Oracle:
         lib.orc_grid_index.restype = ctypes.c_int32
         lib.orc_time_bin.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
         lib.orc_time_bin.restype = ctypes.c_int32
+        lib.orc_direction.argtypes = [ctypes.c_float, ctypes.c_int32]
+        lib.orc_direction.restype = ctypes.c_int32
+        lib.orc_lattice.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(LatticeParams), ctypes.c_int64,
+                                    _P, _P, _P, _P, _P, _P, ctypes.POINTER(_LatticeCells),
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _P, _P]
+        lib.orc_lattice.restype = ctypes.c_int
         self.lib = lib
 
     # ---- single steps ----
@@ -123,6 +143,30 @@ class Oracle:
 
     def time_bin(self, ts, t0_ms, bin_ms, n_bins) -> int:
         return self.lib.orc_time_bin(ts, t0_ms, bin_ms, n_bins)
+
+    def direction(self, heading: float, mode: int = DXN_CARDINAL) -> int:
+        return self.lib.orc_direction(heading, mode)
+
+    def lattice(self, cols: dict, params: Params | None = None, bin_ms: int = 300000, n_bins: int = 288,
+                direction: int = DXN_CARDINAL) -> dict:
+        """The 8-channel lattice of the kept rows (needs a heading column)."""
+        p = params or default_params()
+        lp = LatticeParams(bin_ms=bin_ms, n_bins=n_bins, direction=direction)
+        a = {k: np.ascontiguousarray(cols[k], dtype=dt) for k, dt in
+             (("jid", np.int64), ("ts", np.int64), ("lat", np.float64), ("lon", np.float64),
+              ("speed", np.float32), ("heading", np.float32))}
+        n = int(a["jid"].shape[0])
+        out = {k: np.empty(max(n, 1), dt) for k, dt in LATTICE_DTYPES.items()}
+        sc = _LatticeCells(**{k: v.ctypes.data for k, v in out.items()})
+        nc, nd = ctypes.c_int64(), ctypes.c_int64()
+        mn, mx = np.zeros(8, np.float32), np.zeros(8, np.float32)
+        rc = self.lib.orc_lattice(ctypes.byref(p), ctypes.byref(lp), n, *[a[k].ctypes.data for k in
+                                  ("jid", "ts", "lat", "lon", "speed", "heading")], ctypes.byref(sc),
+                                  ctypes.byref(nc), ctypes.byref(nd), mn.ctypes.data, mx.ctypes.data)
+        if rc != 0:
+            raise RuntimeError(f"orc_lattice failed ({rc})")
+        return {"cells": {k: v[:nc.value] for k, v in out.items()}, "n_dropped": int(nd.value),
+                "ch_min": mn, "ch_max": mx}
 
     def parse_decimal(self, s: str):
         b = s.encode()

@@ -343,3 +343,113 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
   free(spd);
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Lattice: the paper stores each 5-minute batch as an image of 8 channels, speed and     */
+/* volume in the four cardinal directions (Results, the channel images; Algorithm 2,     */
+/* step 3, direction = heading // dxn_step), with volume as the count of unique journeys */
+/* (Table 3, "Reduction - Count Unique (Volume)") and min-max normalised channels        */
+/* (Table 3, "Normalize"; the paper names the operation without a formula: min-max per   */
+/* channel over its occupied cells is the reading). Speed is the mean point speed.       */
+/* ------------------------------------------------------------------------------------ */
+
+/* Cardinal reading: a heading within 45 degrees of north is N, and so on clockwise. The   */
+/* printed heading // 90 gives quadrants that are not centred on the cardinal directions; */
+/* it is kept as ORC_DXN_QUADRANT.                                                        */
+int32_t orc_direction(float heading, int32_t mode) {
+  const double h = (double)heading;
+  if (!isfinite(h)) return -1;
+  double r = fmod(h + (mode == ORC_DXN_CARDINAL ? 45.0 : 0.0), 360.0);
+  if (r < 0.0) r += 360.0;
+  if (r >= 360.0) r = 0.0;
+  return (int32_t)floor(r / 90.0);
+}
+
+static const uint32_t* g_lkey;
+
+/* Order lattice entries (input indices) by (lattice key, journey id, input index). */
+static int cmp_lkey_jid_idx(const void* a, const void* b) {
+  uint32_t i = *(const uint32_t*)a, j = *(const uint32_t*)b;
+  if (g_lkey[i] != g_lkey[j]) return g_lkey[i] < g_lkey[j] ? -1 : 1;
+  if (g_jid[i] != g_jid[j]) return g_jid[i] < g_jid[j] ? -1 : 1;
+  return i < j ? -1 : (i > j ? 1 : 0);
+}
+
+int orc_lattice(const orc_params* p, const orc_lattice_params* lp, int64_t n, const int64_t* jid,
+                const int64_t* ts, const double* lat, const double* lon, const float* speed,
+                const float* heading, orc_lattice_cells* out, int64_t* n_cells, int64_t* n_dropped,
+                float* ch_min, float* ch_max) {
+  if (!p || !lp || n < 0 || n > 0xFFFFFFFELL || !out || !n_cells || !n_dropped || !ch_min || !ch_max) return 1;
+  if (lp->bin_ms <= 0 || lp->n_bins <= 0 || p->n_rows <= 0 || p->n_cols <= 0) return 1;
+  if ((uint64_t)lp->n_bins * 4u * (uint64_t)p->n_rows * (uint64_t)p->n_cols > 0xFFFFFFFFull) return 1;
+  uint32_t* lkey = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+  uint32_t* ent = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+  if (!lkey || !ent) { free(lkey); free(ent); return 2; }
+  int64_t m = 0, dropped = 0;
+  /* 1. Key every kept row: (bin, direction, row, col) unrolled, like the cell key. */
+  for (int64_t i = 0; i < n; i++) {
+    if (!valid_record(lat[i], lon[i], speed[i])) continue;
+    const int32_t d = orc_direction(heading[i], lp->direction);
+    const int32_t b = orc_time_bin(ts[i], p->t0_ms, lp->bin_ms, lp->n_bins);
+    const int32_t r = orc_grid_index(lat[i], p->lat_min, p->cell_deg, p->n_rows);
+    const int32_t c = orc_grid_index(lon[i], p->lon_min, p->cell_deg, p->n_cols);
+    if (d < 0 || b < 0 || r < 0 || c < 0) { dropped++; continue; }
+    lkey[i] = (((uint32_t)b * 4u + (uint32_t)d) * (uint32_t)p->n_rows + (uint32_t)r) * (uint32_t)p->n_cols + (uint32_t)c;
+    ent[m++] = (uint32_t)i;
+  }
+  /* 2. Group by key; inside a key by journey, then input order. */
+  g_lkey = lkey;
+  g_jid = jid;
+  qsort(ent, (size_t)m, sizeof(uint32_t), cmp_lkey_jid_idx);
+  /* 3. Per key: count, speed sum in that order, mean, unique journeys. */
+  int64_t k = 0;
+  for (int64_t a = 0; a < m;) {
+    const uint32_t key = lkey[ent[a]];
+    uint32_t cnt = 0, vol = 0;
+    double sum = 0.0;
+    int64_t e = a;
+    for (; e < m && lkey[ent[e]] == key; e++) {
+      const uint32_t i = ent[e];
+      const float s = (speed[i] == 0.0f) ? 0.0f : speed[i];
+      cnt += 1;
+      sum += (double)s;
+      if (e == a || jid[ent[e - 1]] != jid[i]) vol += 1;
+    }
+    const uint32_t cells = (uint32_t)p->n_rows * (uint32_t)p->n_cols;
+    out->key[k] = key;
+    out->bin[k] = (int32_t)(key / (cells * 4u));
+    out->dxn[k] = (int32_t)((key / cells) % 4u);
+    out->row[k] = (int32_t)((key % cells) / (uint32_t)p->n_cols);
+    out->col[k] = (int32_t)(key % (uint32_t)p->n_cols);
+    out->count[k] = cnt;
+    out->sum[k] = sum;
+    out->mean[k] = (float)(sum / (double)cnt);
+    out->volume[k] = vol;
+    k++;
+    a = e;
+  }
+  /* 4. Min-max per channel (2d: mean speed, 2d + 1: volume) over the occupied cells. */
+  int seen[8] = {0};
+  for (int c = 0; c < 8; c++) ch_min[c] = ch_max[c] = 0.0f;
+  for (int64_t q = 0; q < k; q++) {
+    const int d = out->dxn[q];
+    const float v[2] = {out->mean[q], (float)out->volume[q]};
+    for (int t = 0; t < 2; t++) {
+      const int c = 2 * d + t;
+      if (!seen[c] || v[t] < ch_min[c]) ch_min[c] = v[t];
+      if (!seen[c] || v[t] > ch_max[c]) ch_max[c] = v[t];
+      seen[c] = 1;
+    }
+  }
+  for (int64_t q = 0; q < k; q++) {
+    const int d = out->dxn[q];
+    const float mn0 = ch_min[2 * d], mx0 = ch_max[2 * d], mn1 = ch_min[2 * d + 1], mx1 = ch_max[2 * d + 1];
+    out->mean_norm[q] = (mx0 > mn0) ? (out->mean[q] - mn0) / (mx0 - mn0) : 0.0f;
+    out->volume_norm[q] = (mx1 > mn1) ? ((float)out->volume[q] - mn1) / (mx1 - mn1) : 0.0f;
+  }
+  *n_cells = k;
+  *n_dropped = dropped;
+  free(lkey);
+  free(ent);
+  return 0;
+}

@@ -121,6 +121,41 @@ int orc_run(const orc_params* p, int64_t n,
             const float* speed,
             orc_points* pts, orc_journeys* jr, orc_cells* cl, orc_counters* cnt);
 
+/* ---- Lattice (the paper's 8-channel spatio-temporal image; Results, the 5-minute channel
+ * images of speed and volume in four cardinal directions; Algorithm 2, step 3; Table 3,
+ * "Count Unique (Volume)" and "Normalize"). */
+#define ORC_DXN_CARDINAL 0 /* floor(((h + 45) mod 360) / 90): 0 N, 1 E, 2 S, 3 W (reading) */
+#define ORC_DXN_QUADRANT 1 /* floor((h mod 360) / 90): Algorithm 2's heading // 90 as printed */
+
+/* Direction channel of a heading in degrees; -1 for a non-finite heading. */
+int32_t orc_direction(float heading, int32_t mode);
+
+typedef struct {
+  int64_t bin_ms;     /* lattice time bin, from the run's t0_ms (300000: 5 minutes) */
+  int32_t n_bins;     /* 288 for a day of 5-minute bins */
+  int32_t direction;  /* ORC_DXN_* */
+} orc_lattice_params;
+
+/* One row per occupied (bin, direction, row, col), ascending key; capacity >= kept rows. */
+typedef struct {
+  uint32_t* key;      /* ((bin * 4 + dxn) * n_rows + row) * n_cols + col */
+  int32_t *bin, *dxn, *row, *col;
+  uint32_t* count;    /* points */
+  double* sum;        /* speed sum, sequential in (journey id, input index) order */
+  float* mean;        /* (float)(sum / count): channel 2 * dxn */
+  uint32_t* volume;   /* distinct journeys: channel 2 * dxn + 1 */
+  float* mean_norm;   /* min-max normalised per channel over the occupied cells */
+  float* volume_norm;
+} orc_lattice_cells;
+
+/* The lattice of the kept rows (the same row rule as orc_run) that have a finite heading and
+ * fall inside the grid and the lattice's bins. ch_min / ch_max: per channel over its
+ * occupied cells (0 for a channel without cells). Returns 0 on success. */
+int orc_lattice(const orc_params* p, const orc_lattice_params* lp, int64_t n, const int64_t* jid,
+                const int64_t* ts, const double* lat, const double* lon, const float* speed,
+                const float* heading, orc_lattice_cells* out, int64_t* n_cells, int64_t* n_dropped,
+                float* ch_min, float* ch_max);
+
 #ifdef __cplusplus
 }
 #endif

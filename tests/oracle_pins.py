@@ -350,6 +350,113 @@ def pin_invalid_records(o):
     assert r["counters"]["n_valid"] == 2 and r["counters"]["n_out_of_grid"] == 1  # lat 35.0
 
 
+# ---- lattice (8 channels: mean speed and unique journeys in four directions) ----------
+T0 = 1620518400000
+
+
+def pin_direction_sectors(o):
+    """Cardinal reading: within 45 deg of north is N (0), then E, S, W clockwise; the printed
+    heading // 90 (quadrant reading) starts each sector at a multiple of 90 deg."""
+    card = {0.0: 0, 44.9: 0, 45.0: 1, 90.0: 1, 134.9: 1, 135.0: 2, 180.0: 2, 224.9: 2, 225.0: 3,
+            270.0: 3, 314.9: 3, 315.0: 0, 359.9: 0, 360.0: 0, -10.0: 0, -45.0: 0, -45.1: 3, 405.0: 1}
+    for h, d in card.items():
+        assert o.direction(h, 0) == d, ("cardinal", h, o.direction(h, 0), d)
+    quad = {0.0: 0, 89.9: 0, 90.0: 1, 179.9: 1, 180.0: 2, 270.0: 3, 359.9: 3, -0.5: 3, 360.0: 0}
+    for h, d in quad.items():
+        assert o.direction(h, 1) == d, ("quadrant", h, o.direction(h, 1), d)
+    assert o.direction(float("nan"), 0) == -1 and o.direction(float("inf"), 1) == -1
+
+
+def _lattice_case(seed=7):
+    """Points at cell centres with known (bin, direction, row, col): several journeys share
+    cells, journeys re-enter a cell within a bin, some points have no heading or fall outside
+    the bins. Returns the columns and the expected groups built from the construction."""
+    rng = np.random.default_rng(seed)
+    rows, cols_, bins = 460, 670, 288
+    heads = [0.0, 90.0, 180.0, 270.0]  # sector centres: directions 0..3
+    recs, expect = [], {}
+    idx = 0
+    for j in range(40):
+        jid = int(rng.integers(0, 2 ** 31))
+        for _ in range(int(rng.integers(1, 30))):
+            b, d = int(rng.integers(0, 3)), int(rng.integers(0, 4))
+            r, c = int(rng.integers(100, 103)), int(rng.integers(200, 202))
+            ts = T0 + b * 300000 + int(rng.integers(0, 300000))
+            lat, lon = 36.0 + 0.01 * r + 0.005, -95.8 + 0.01 * c + 0.005
+            spd = float(np.float32(rng.uniform(0, 120)))
+            kind = rng.random()
+            h = heads[d] if kind > 0.1 else float("nan")
+            if kind < 0.05:
+                ts = T0 + bins * 300000 + 1  # after the lattice's last bin
+            recs.append((jid, ts, lat, lon, spd, h))
+            if kind > 0.1:
+                key = ((b * 4 + d) * rows + r) * cols_ + c
+                expect.setdefault(key, []).append((jid, idx, spd))
+            idx += 1
+    order = rng.permutation(len(recs))
+    recs = [recs[i] for i in order]
+    pos = {int(old): new for new, old in enumerate(order)}
+    for key in expect:
+        expect[key] = [(jid, pos[i], spd) for jid, i, spd in expect[key]]
+    cols = {"jid": np.array([r[0] for r in recs], np.int64), "ts": np.array([r[1] for r in recs], np.int64),
+            "lat": np.array([r[2] for r in recs]), "lon": np.array([r[3] for r in recs]),
+            "speed": np.array([r[4] for r in recs], np.float32), "heading": np.array([r[5] for r in recs], np.float32)}
+    return cols, expect
+
+
+def pin_lattice_bruteforce(o):
+    """Per (bin, direction, cell): point count, speed sum (in journey, input order), mean,
+    unique journeys; per channel min-max normalisation over the occupied cells."""
+    cols, expect = _lattice_case()
+    L = o.lattice(cols)
+    c = L["cells"]
+    keys = sorted(expect)
+    assert list(c["key"]) == keys
+    n_kept = sum(len(v) for v in expect.values())
+    assert int(c["count"].sum()) == n_kept and L["n_dropped"] == len(cols["jid"]) - n_kept
+    mean, vol = [], []
+    for q, key in enumerate(keys):
+        pts = sorted(expect[key], key=lambda t: (t[0], t[1]))
+        s = 0.0
+        for _, _, spd in pts:
+            s += spd
+        assert c["count"][q] == len(pts) and c["sum"][q] == s
+        assert c["volume"][q] == len({t[0] for t in pts})
+        assert c["mean"][q] == np.float32(s / len(pts))
+        assert c["dxn"][q] == (key // (460 * 670)) % 4
+        mean.append(np.float32(s / len(pts)))
+        vol.append(np.float32(len({t[0] for t in pts})))
+    assert max(vol) > 1  # journeys share cells
+    for ch in range(8):
+        sel = [q for q, key in enumerate(keys) if (key // (460 * 670)) % 4 == ch // 2]
+        v = [(mean if ch % 2 == 0 else vol)[q] for q in sel]
+        mn, mx = (min(v), max(v)) if v else (np.float32(0), np.float32(0))
+        assert L["ch_min"][ch] == mn and L["ch_max"][ch] == mx, (ch, L["ch_min"][ch], mn, L["ch_max"][ch], mx)
+        out = c["mean_norm" if ch % 2 == 0 else "volume_norm"]
+        for q, x in zip(sel, v):
+            want = np.float32((x - mn) / (mx - mn)) if mx > mn else np.float32(0)
+            assert out[q] == want
+
+
+def pin_lattice_invariants(o):
+    """On a generated day: conservation, volume <= count, means inside [min, max] of the
+    speeds, normalised channels inside [0, 1] and reaching both ends."""
+    import cvgen
+
+    cols = cvgen.generate(cvgen.params("small_day", seed=5, n_journeys=400))
+    L = o.lattice(cols)
+    c = L["cells"]
+    kept = int((np.isfinite(cols["lat"]) & (np.abs(cols["lat"]) <= 90)).sum())
+    assert int(c["count"].sum()) + L["n_dropped"] == kept
+    assert (c["volume"] <= c["count"]).all() and (c["volume"] >= 1).all()
+    assert (c["mean_norm"] >= 0).all() and (c["mean_norm"] <= 1).all()
+    for d in range(4):
+        sel = c["dxn"] == d
+        if sel.sum() > 1 and L["ch_max"][2 * d] > L["ch_min"][2 * d]:
+            assert c["mean_norm"][sel].min() == 0 and c["mean_norm"][sel].max() == 1
+
+
 CPU_PINS = [pin_haversine_closed_forms, pin_grid_index, pin_time_bin, pin_parse_fields, pin_table1,
-            pin_bruteforce_orders, pin_kinematics_hand, pin_invalid_records]
+            pin_bruteforce_orders, pin_kinematics_hand, pin_invalid_records, pin_direction_sectors,
+            pin_lattice_bruteforce, pin_lattice_invariants]
 DATA_PINS = [pin_invariants, pin_library_cross_check, pin_csv_roundtrip]

@@ -38,6 +38,13 @@ MUTANTS = {
     "lat_range_180": ("!(fabs(la) <= 90.0)", "!(fabs(la) <= 180.0)"),
     "cell_sum_first_only": ("cl->sum[c] += (double)s;", "if (cl->count[c] == 1) cl->sum[c] += (double)s;"),
     "cell_min_as_max": ("if (s < cl->min[c]) cl->min[c] = s;", "if (s > cl->min[c]) cl->min[c] = s;"),
+    "direction_no_offset": ("fmod(h + (mode == ORC_DXN_CARDINAL ? 45.0 : 0.0), 360.0)", "fmod(h, 360.0)"),
+    "direction_negative_unwrapped": ("  if (r < 0.0) r += 360.0;\n  if (r >= 360.0) r = 0.0;", "  if (r >= 360.0) r = 0.0;"),
+    "volume_counts_points": ("if (e == a || jid[ent[e - 1]] != jid[i]) vol += 1;", "vol += 1;"),
+    "lattice_sum_by_point_order": ("  if (g_jid[i] != g_jid[j]) return g_jid[i] < g_jid[j] ? -1 : 1;\n  return i < j ? -1 : (i > j ? 1 : 0);\n}\n\nint orc_lattice",
+                                   "  return i < j ? -1 : (i > j ? 1 : 0);\n}\n\nint orc_lattice"),
+    "normalise_global": ("const float mn0 = ch_min[2 * d], mx0 = ch_max[2 * d],", "const float mn0 = ch_min[0], mx0 = ch_max[0],"),
+    "lattice_key_dir_bin_swapped": ("lkey[i] = (((uint32_t)b * 4u + (uint32_t)d)", "lkey[i] = (((uint32_t)d * 4u + (uint32_t)b)"),
 }
 
 
