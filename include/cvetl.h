@@ -291,6 +291,52 @@ cvetl_status cvetl_tuning_set(cvetl_ctx* ctx, const cvetl_tuning* t);
  * left as they were. */
 cvetl_status cvetl_autotune(cvetl_ctx* ctx, int32_t reps, cvetl_tuning* out, double* ms_best);
 
+/* Lattice (the paper's multidimensional spatio-temporal output: each lattice time bin is an
+ * image of 8 channels, speed and volume in the four cardinal directions, Results; direction
+ * by Algorithm 2, step 3; volume as unique journeys, Table 3 "Count Unique (Volume)"; min-max
+ * normalised channels, Table 3 "Normalize"). Channel 2d is the mean point speed and channel
+ * 2d + 1 the number of unique journeys of direction d in a cell and lattice bin. */
+enum {
+  CVETL_DXN_CARDINAL = 0, /* floor(((heading + 45) mod 360) / 90): 0 N, 1 E, 2 S, 3 W */
+  CVETL_DXN_QUADRANT = 1  /* floor((heading mod 360) / 90), the printed heading // 90 */
+};
+
+typedef struct {
+  int64_t bin_ms;     /* lattice bin from config.t0_ms (300000: 5 minutes) */
+  int32_t n_bins;     /* 288 */
+  int32_t direction;  /* CVETL_DXN_* */
+  int32_t dense;      /* 1: also write the dense tensor (n_bins * 8 * n_rows * n_cols floats) */
+  int32_t normalize;  /* 1: the dense tensor holds the normalised channels */
+} cvetl_lattice_config;
+
+typedef struct {
+  /* occupied (bin, direction, cell), ascending key = ((bin * 4 + dxn) * n_rows + row) * n_cols + col */
+  int64_t n_cells;
+  const uint32_t* key;
+  const int32_t *bin, *dxn, *row, *col;
+  const uint32_t* count;    /* points */
+  const double* sum;        /* speed sum, in (journey, extracted-row) order */
+  const float* mean;        /* (float)(sum / count) */
+  const uint32_t* volume;   /* unique journeys */
+  const float* mean_norm;   /* (mean - min) / (max - min) of its channel over the occupied cells, 0 if max = min */
+  const float* volume_norm;
+  int64_t n_dropped;        /* kept rows without a finite heading or outside the grid or the lattice bins */
+  const float* dense;       /* [n_bins][8][n_rows][n_cols] (zero where unoccupied), or NULL */
+  int32_t n_bins;
+  float ch_min[8], ch_max[8]; /* per channel over its occupied cells (0 for an empty channel) */
+} cvetl_lattice;
+
+void cvetl_lattice_config_default(cvetl_lattice_config* lc);
+
+/* Builds the lattice of the last batch (batch mode, one instance, after cvetl_load; the
+ * extracted rows need headings: binary columns with a heading column, or CSV). Kept rows are
+ * keyed by lattice bin, direction and cell (the same thresholds as the cell keys) and grouped
+ * with the library's radix sort by (key, journey rank), ties in extracted-row order; one thread
+ * per cell then folds its points in that order. Device arrays stay valid until the next
+ * cvetl_extract or cvetl_lattice_build. CVETL_ESTATE before cvetl_load; CVETL_EINVAL for a
+ * stream context, a batch of instances, missing headings or a bad configuration. */
+cvetl_status cvetl_lattice_build(cvetl_ctx* ctx, const cvetl_lattice_config* lc, cvetl_lattice* out);
+
 /* Stream mode (config.mode = CVETL_STREAM; the paper runs batches only, this serves windows of
  * records as they arrive). Per window: cvetl_extract appends the window's rows (binary columns)
  * to a pending store on the device; cvetl_transform finalises every pending point whose

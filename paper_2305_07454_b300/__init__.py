@@ -94,6 +94,24 @@ class Tuning(ctypes.Structure):
                 ("small_sort_max", ctypes.c_int32)]
 
 
+DXN_CARDINAL, DXN_QUADRANT = 0, 1
+
+
+class LatticeConfig(ctypes.Structure):
+    _fields_ = [("bin_ms", ctypes.c_int64), ("n_bins", ctypes.c_int32), ("direction", ctypes.c_int32),
+                ("dense", ctypes.c_int32), ("normalize", ctypes.c_int32)]
+
+
+_LATTICE = [("key", "<u4"), ("bin", "<i4"), ("dxn", "<i4"), ("row", "<i4"), ("col", "<i4"), ("count", "<u4"),
+            ("sum", "<f8"), ("mean", "<f4"), ("volume", "<u4"), ("mean_norm", "<f4"), ("volume_norm", "<f4")]
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = ([("n_cells", ctypes.c_int64)] + [(k, _P) for k, _ in _LATTICE]
+                + [("n_dropped", ctypes.c_int64), ("dense", _P), ("n_bins", ctypes.c_int32),
+                   ("ch_min", ctypes.c_float * 8), ("ch_max", ctypes.c_float * 8)])
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_size_t)]
@@ -130,6 +148,9 @@ def _load():
     lib.cvetl_extract_batch.argtypes = [_P, ctypes.POINTER(Instance), ctypes.c_int32, ctypes.c_int32]
     _I64P = ctypes.POINTER(ctypes.c_int64)
     lib.cvetl_batch_ranges.argtypes = [_P, _I64P, _I64P, _I64P, _I64P, ctypes.c_int32]
+    lib.cvetl_lattice_config_default.argtypes = [ctypes.POINTER(LatticeConfig)]
+    lib.cvetl_lattice_config_default.restype = None
+    lib.cvetl_lattice_build.argtypes = [_P, ctypes.POINTER(LatticeConfig), ctypes.POINTER(Lattice)]
     lib.cvetl_tuning_get.argtypes = [_P, ctypes.POINTER(Tuning)]
     lib.cvetl_tuning_set.argtypes = [_P, ctypes.POINTER(Tuning)]
     lib.cvetl_autotune.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double)]
@@ -146,7 +167,7 @@ def _load():
     for f in ("cvetl_create", "cvetl_extract", "cvetl_transform", "cvetl_load", "cvetl_results",
               "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
               "cvetl_extract_batch", "cvetl_batch_ranges", "cvetl_tuning_get", "cvetl_tuning_set",
-              "cvetl_autotune", "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
+              "cvetl_autotune", "cvetl_lattice_build", "cvetl_server_create", "cvetl_server_add_feed", "cvetl_server_submit",
               "cvetl_server_submit_flush", "cvetl_server_wait", "cvetl_server_drain",
               "cvetl_server_feed", "cvetl_server_destroy"):
         getattr(lib, f).restype = ctypes.c_int
@@ -160,7 +181,7 @@ EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_trans
            "cvetl_results", "cvetl_flush", "cvetl_stats_get", "cvetl_stats_reset", "cvetl_destroy",
            "cvetl_last_error", "cvetl_version", "cvetl_sort_u64_noalloc", "cvetl_extract_batch",
            "cvetl_batch_ranges", "cvetl_tuning_get", "cvetl_tuning_set", "cvetl_autotune",
-           "cvetl_server_create",
+           "cvetl_lattice_config_default", "cvetl_lattice_build", "cvetl_server_create",
            "cvetl_server_add_feed", "cvetl_server_submit", "cvetl_server_submit_flush",
            "cvetl_server_wait", "cvetl_server_drain", "cvetl_server_feed", "cvetl_server_destroy",
            "cvetl_server_last_error")
@@ -206,6 +227,13 @@ def _columns_input(cols: dict, window_end_ms: int = 0):
         if v.dtype != dt or not v.is_contiguous() or v.dim() != 1:
             raise ValueError(f"column {k} must be a contiguous 1-D {dt} tensor")
         ts.append(v)
+    hd = cols.get("heading")
+    if hd is not None:
+        if isinstance(hd, np.ndarray):
+            hd = torch.from_numpy(np.ascontiguousarray(hd))
+        if hd.dtype != torch.float32 or not hd.is_contiguous() or hd.dim() != 1:
+            raise ValueError("column heading must be a contiguous 1-D torch.float32 tensor")
+        ts.append(hd)
     n = ts[0].shape[0]
     if any(t.shape[0] != n for t in ts):
         raise ValueError("columns differ in length")
@@ -215,7 +243,8 @@ def _columns_input(cols: dict, window_end_ms: int = 0):
     on_device = dev.pop()
     inp = Input(kind=IN_COLUMNS, on_device=int(on_device), n=n,
                 jid=ts[0].data_ptr(), ts=ts[1].data_ptr(), lat=ts[2].data_ptr(),
-                lon=ts[3].data_ptr(), speed=ts[4].data_ptr(), heading=None,
+                lon=ts[3].data_ptr(), speed=ts[4].data_ptr(),
+                heading=ts[5].data_ptr() if hd is not None else None,
                 window_end_ms=int(window_end_ms))
     return inp, ts
 
@@ -346,6 +375,33 @@ class Pipeline:
         t, ms = Tuning(), ctypes.c_double()
         self._check(lib.cvetl_autotune(self._h, int(reps), ctypes.byref(t), ctypes.byref(ms)))
         return {**{k: int(getattr(t, k)) for k, _ in Tuning._fields_}, "ms": float(ms.value)}
+
+    def lattice(self, to_host: bool = True, **cfg) -> dict:
+        """The 8-channel lattice of the last batch (after load): the occupied cells, the dense
+        [n_bins, 8, n_rows, n_cols] tensor (a zero-copy device tensor, or None), the channel
+        extremes and the count of dropped rows. cfg: bin_ms, n_bins, direction, dense, normalize."""
+        torch = self._torch
+        lc = LatticeConfig()
+        lib.cvetl_lattice_config_default(ctypes.byref(lc))
+        for k, v in cfg.items():
+            setattr(lc, k, v)
+        L = Lattice()
+        self._check(lib.cvetl_lattice_build(self._h, ctypes.byref(lc), ctypes.byref(L)))
+
+        def view(ptr, n, ty):
+            if n == 0 or not ptr:
+                return np.empty(0, np.dtype(ty)) if to_host else None
+            a = torch.as_tensor(_DeviceArray(ptr, n, ty), device="cuda")
+            return a.cpu().numpy() if to_host else a
+
+        out = {"cells": {k: view(getattr(L, k), L.n_cells, ty) for k, ty in _LATTICE},
+               "n_dropped": int(L.n_dropped), "ch_min": np.array(L.ch_min[:], np.float32),
+               "ch_max": np.array(L.ch_max[:], np.float32), "dense": None}
+        if L.dense:
+            shape = (int(L.n_bins), 8, int(self.config.n_rows), int(self.config.n_cols))
+            n = int(np.prod(shape))
+            out["dense"] = torch.as_tensor(_DeviceArray(L.dense, n, "<f4"), device="cuda").view(shape)
+        return out
 
     def extract_csv(self, text):
         """CSV text as bytes / numpy uint8 (host) or a uint8 torch tensor (host or device)."""

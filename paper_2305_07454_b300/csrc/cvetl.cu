@@ -24,6 +24,7 @@
 #include "cells.cuh"
 #include "csv.cuh"
 #include "stream.cuh"
+#include "lattice.cuh"
 
 using namespace cvetl;
 
@@ -32,13 +33,13 @@ namespace {
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
   ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
-  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_COUNT
+  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
                                      "csv_count", "csv_parse", "stream_append", "stream_split",
-                                     "stream_tables", "cta_sort"};
+                                     "stream_tables", "cta_sort", "lattice"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -75,6 +76,7 @@ struct cvetl_ctx {
   // outputs
   JourneyOut jo{};
   CellOut co{};
+  LatticeOut lattice{};
   int64_t* jid_sorted = nullptr;
   // batch of instances (cvetl_extract_batch); bt.n_inst = 0 for one instance
   Batch bt{};
@@ -83,6 +85,8 @@ struct cvetl_ctx {
   uint32_t* inst_counts = nullptr;  // device: journeys [kMaxInst], then cells [kMaxInst]
   uint32_t* cell_total = nullptr;   // device: the cell count of the last batch
   uint32_t hint_distinct = 0;       // journeys of the last batch (sizes the next hash table)
+  uint32_t* slot_rank = nullptr;    // journey rank of each hash slot (last batch)
+  uint32_t* row_slot = nullptr;     // hash slot of each extracted row (last batch)
   std::vector<double> batch_key;    // the last batch's instance grids and sizes
   // stream mode
   struct {
@@ -711,7 +715,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   ENSURE("j.total", 1, &total);
   ENSURE("j.idtmp", (size_t)J, &jid_tmp);
   if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0)));
+    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0, nullptr)));
     LAUNCH_CHECK();
   }
   if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
@@ -902,6 +906,8 @@ cvetl_status stream_tables(cvetl_ctx* c) {
 cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned long long* ukey,
                          uint32_t* uslot, uint32_t J, bool exact) {
   const uint32_t n = (uint32_t)c->n_rows;
+  ENSURE("hash.rank", (size_t)h.cap + 1, &c->slot_rank);
+  c->row_slot = row_slot;
   unsigned long long* skey;
   uint32_t* sslot;
   {
@@ -915,7 +921,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   ENSURE("out.j_id", (size_t)J, &c->jid_sorted);
   if (J) {
     LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, c->jid_sorted,
-                                                                       c->bt.n_inst ? 1 : 0)));
+                                                                       c->bt.n_inst ? 1 : 0, c->slot_rank)));
     LAUNCH_CHECK();
   }
   {
@@ -1325,10 +1331,17 @@ cvetl_status cvetl_extract(cvetl_ctx* c, const cvetl_input* in) {
     c->lon = lon;
     c->spd = spd;
   }
+  const float* heading = in->heading;
+  if (heading && !in->on_device) {
+    float* hd;
+    ENSURE("in.heading", n, &hd);
+    if (n) CK(cudaMemcpyAsync(hd, in->heading, n * 4, cudaMemcpyHostToDevice, c->st));
+    heading = hd;
+  }
   c->n_in = in->n;
   c->n_rows = in->n;
   c->csv_malformed = 0;
-  c->heading = in->heading;
+  c->heading = heading;
   c->bt = Batch{};
   c->J = c->R = c->K = c->n_valid = 0;
   c->state = 1;
@@ -1570,6 +1583,133 @@ cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, doubl
   if (st != CVETL_OK) return st;
   if (out) cvetl_tuning_get(c, out);
   if (ms_best) *ms_best = best_ms;
+  return CVETL_OK;
+}
+
+void cvetl_lattice_config_default(cvetl_lattice_config* lc) {
+  if (!lc) return;
+  memset(lc, 0, sizeof(*lc));
+  lc->bin_ms = 300000;
+  lc->n_bins = 288;
+  lc->direction = CVETL_DXN_CARDINAL;
+  lc->dense = 1;
+  lc->normalize = 0;
+}
+
+cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, cvetl_lattice* out) {
+  if (!c) return CVETL_EINVAL;
+  if (!lc || !out) return fail(c, CVETL_EINVAL, "cvetl_lattice_build: NULL argument");
+  if (c->cfg.mode != CVETL_BATCH || c->bt.n_inst) return fail(c, CVETL_EINVAL, "the lattice is built for a single batch");
+  if (c->state < 3) return fail(c, CVETL_ESTATE, "cvetl_lattice_build needs a preceding cvetl_load");
+  if (!c->heading) return fail(c, CVETL_EINVAL, "the lattice needs the heading column");
+  if (lc->bin_ms <= 0 || lc->n_bins <= 0 || (lc->direction != CVETL_DXN_CARDINAL && lc->direction != CVETL_DXN_QUADRANT))
+    return fail(c, CVETL_EINVAL, "lattice bins must be positive and the direction a CVETL_DXN_* value");
+  const uint64_t cells = (uint64_t)c->cfg.n_rows * (uint64_t)c->cfg.n_cols;
+  if ((uint64_t)lc->n_bins * 4u * cells > 0xFFFFFFFFull)
+    return fail(c, CVETL_EINVAL, "n_bins * 4 * n_rows * n_cols must stay below 2^32");
+  cudaSetDevice(c->cfg.device);
+  const uint32_t n = (uint32_t)c->n_rows, J = c->J;
+  LatticeParams lp;
+  lp.bin_ms = lc->bin_ms;
+  lp.n_bins = lc->n_bins;
+  lp.direction = lc->direction;
+  lp.rank_bits = std::max(1, 64 - __builtin_clzll((unsigned long long)std::max<uint32_t>(J, 2) - 1));
+  unsigned __int128 span = (unsigned __int128)(uint64_t)lc->n_bins * (uint64_t)lc->bin_ms;
+  lp.t_span = span > (unsigned __int128)~0ull ? ~0ull : (unsigned long long)span;
+  const uint64_t max_lk = (uint64_t)lc->n_bins * 4u * cells - 1;
+  const int end_bit = std::min(64, (max_lk ? 64 - __builtin_clzll(max_lk) : 1) + lp.rank_bits);
+  unsigned long long *keys, *ctr;
+  ENSURE("lat.keys", (size_t)n, &keys);
+  ENSURE("lat.ctr", 4, &ctr);
+  CK(cudaMemsetAsync(ctr, 0, 32, c->st));
+  if (n) {
+    LAUNCH(ST_LATTICE, (k_lattice_keys<<<grid_for(n, 256), 256, 0, c->st>>>(
+                           c->row_slot, c->slot_rank, c->ts, c->lat, c->lon, c->heading, n, c->gp, lp, keys, ctr)));
+    LAUNCH_CHECK();
+  }
+  unsigned long long* skey;
+  uint32_t* srow;
+  cvetl_status s = sort_pairs<unsigned long long>(c, "lsort", keys, nullptr, n, 0, end_bit, &skey, &srow);
+  if (s != CVETL_OK) return s;
+  unsigned long long dropped = 0;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&dropped, ctr, 8, cudaMemcpyDeviceToHost));
+  const uint32_t m = (uint32_t)((uint64_t)c->n_valid - dropped);
+  uint32_t *head, *cidx, *total, *chan;
+  ENSURE("lat.head", (size_t)m, &head);
+  ENSURE("lat.idx", (size_t)m, &cidx);
+  ENSURE("lat.total", 1, &total);
+  ENSURE("lat.chan", 16, &chan);
+  CK(cudaMemsetAsync(chan, 0xFF, 32, c->st));
+  CK(cudaMemsetAsync(chan + 8, 0, 32, c->st));
+  if (m) {
+    LAUNCH(ST_LATTICE, (k_lattice_heads<<<grid_for(m, 256), 256, 0, c->st>>>(skey, m, lp.rank_bits, head)));
+    LAUNCH_CHECK();
+  }
+  if ((s = scan_u32(c, head, m, cidx, total)) != CVETL_OK) return s;
+  LatticeOut& lo = c->lattice;
+  ENSURE("lat.o_key", (size_t)m, &lo.key);
+  ENSURE("lat.o_bin", (size_t)m, &lo.bin);
+  ENSURE("lat.o_dxn", (size_t)m, &lo.dxn);
+  ENSURE("lat.o_row", (size_t)m, &lo.row);
+  ENSURE("lat.o_col", (size_t)m, &lo.col);
+  ENSURE("lat.o_count", (size_t)m, &lo.count);
+  ENSURE("lat.o_sum", (size_t)m, &lo.sum);
+  ENSURE("lat.o_mean", (size_t)m, &lo.mean);
+  ENSURE("lat.o_volume", (size_t)m, &lo.volume);
+  ENSURE("lat.o_mean_norm", (size_t)m, &lo.mean_norm);
+  ENSURE("lat.o_volume_norm", (size_t)m, &lo.volume_norm);
+  if (m) {
+    LAUNCH(ST_LATTICE, (k_lattice_fold<<<grid_for(m, 256), 256, 0, c->st>>>(
+                           skey, srow, m, head, cidx, c->spd, lp.rank_bits, c->cfg.n_rows, c->cfg.n_cols, lo, chan)));
+    LAUNCH_CHECK();
+  }
+  uint32_t K = 0;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&K, total, 4, cudaMemcpyDeviceToHost));
+  if (!m) K = 0;
+  float* dense = nullptr;
+  if (lc->dense) {
+    const size_t cnt = (size_t)lc->n_bins * 8u * cells;
+    ENSURE("lat.dense", cnt, &dense);
+    CK(cudaMemsetAsync(dense, 0, cnt * 4, c->st));
+  }
+  if (K) {
+    LAUNCH(ST_LATTICE, (k_lattice_norm<<<grid_for(K, 256), 256, 0, c->st>>>(K, chan, lo, c->cfg.n_rows, c->cfg.n_cols,
+                                                                            dense, lc->normalize ? 1 : 0)));
+    LAUNCH_CHECK();
+  }
+  uint32_t ch[16];
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(ch, chan, sizeof ch, cudaMemcpyDeviceToHost));
+  if ((s = read_state(c)) != CVETL_OK) return s;
+  memset(out, 0, sizeof(*out));
+  out->n_cells = K;
+  out->key = lo.key;
+  out->bin = lo.bin;
+  out->dxn = lo.dxn;
+  out->row = lo.row;
+  out->col = lo.col;
+  out->count = lo.count;
+  out->sum = lo.sum;
+  out->mean = lo.mean;
+  out->volume = lo.volume;
+  out->mean_norm = lo.mean_norm;
+  out->volume_norm = lo.volume_norm;
+  out->n_dropped = (int64_t)dropped;
+  out->dense = dense;
+  out->n_bins = lc->n_bins;
+  for (int k = 0; k < 8; ++k) {
+    const bool seen = ch[k] != 0xFFFFFFFFu;
+    auto dec = [](uint32_t u) {
+      uint32_t b = (u & 0x80000000u) ? (u ^ 0x80000000u) : ~u;
+      float f;
+      memcpy(&f, &b, 4);
+      return f;
+    };
+    out->ch_min[k] = seen ? dec(ch[k]) : 0.0f;
+    out->ch_max[k] = seen ? dec(ch[8 + k]) : 0.0f;
+  }
   return CVETL_OK;
 }
 

@@ -134,12 +134,15 @@ __global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
 }
 
 // Journey rank r (ascending id): size, id (a batch's (instance, id) is unpacked).
+// slot_rank (may be null) receives each hash slot's journey rank.
 __global__ void k_journey_sizes(const unsigned long long* __restrict__ skey,
                                 const uint32_t* __restrict__ sslot, uint32_t J, Hash h,
-                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out, int batched) {
+                                uint32_t* __restrict__ jn, int64_t* __restrict__ jid_out, int batched,
+                                uint32_t* __restrict__ slot_rank) {
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < J) {
     jn[r] = h.cnt[sslot[r]];
+    if (slot_rank) slot_rank[sslot[r]] = r;
     const uint64_t id = skey[r] ^ kSign64;
     jid_out[r] = batched ? composite_jid(id) : (int64_t)id;
   }

@@ -1,0 +1,160 @@
+// lattice.cuh — the 8-channel spatio-temporal lattice: per lattice time bin, direction and cell,
+// the mean point speed and the number of unique journeys (channels 2d and 2d + 1 of direction
+// d), min-max normalised per channel, optionally written densely as [bin][8][row][col].
+// (Results: the 5-minute channel images of speed and volume in four cardinal directions;
+// Algorithm 2, step 3: direction = heading // dxn_step; Table 3: "Count Unique (Volume)",
+// "Normalize".)
+#pragma once
+#include "common.cuh"
+#include "keying.cuh"
+
+namespace cvetl {
+
+struct LatticeParams {
+  int64_t bin_ms;
+  int32_t n_bins;
+  int32_t direction;   // 0 cardinal: floor(((h + 45) mod 360) / 90); 1 quadrant: floor((h mod 360) / 90)
+  int32_t rank_bits;   // bits of the journey rank in the sort key
+  unsigned long long t_span;  // n_bins * bin_ms (saturated)
+};
+
+// Direction channel of a heading (binary64 arithmetic on the float32 heading, as defined);
+// -1 for a non-finite heading.
+__device__ __forceinline__ int lattice_direction(float heading, int mode) {
+  const double h = (double)heading;
+  if (!isfinite(h)) return -1;
+  double r = fmod(h + (mode == 0 ? 45.0 : 0.0), 360.0);
+  if (r < 0.0) r += 360.0;
+  if (r >= 360.0) r = 0.0;
+  return (int)floor(r / 90.0);
+}
+
+// Sort key of every row: (lattice key << rank_bits) | journey rank for a kept row that has a
+// lattice position, all-ones otherwise (sorted last). Dropped kept rows are counted.
+__global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict__ row_slot,
+                                                      const uint32_t* __restrict__ slot_rank,
+                                                      const int64_t* __restrict__ ts,
+                                                      const double* __restrict__ lat,
+                                                      const double* __restrict__ lon,
+                                                      const float* __restrict__ heading, uint32_t n,
+                                                      GridParams g, LatticeParams lp,
+                                                      unsigned long long* __restrict__ keys,
+                                                      unsigned long long* n_dropped) {
+  __shared__ unsigned long long scratch[8];
+  unsigned long long dropped = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long k = ~0ull;
+    const uint32_t slot = row_slot[i];
+    if (slot != kKeyInvalid) {
+      const int d = lattice_direction(heading[i], lp.direction);
+      const int r = grid_index(lat[i], g.row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
+      const int c = grid_index(lon[i], g.col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
+      const int64_t t = ts[i];
+      const unsigned long long off = (unsigned long long)t - (unsigned long long)g.t0_ms;
+      if (d < 0 || r < 0 || c < 0 || t < g.t0_ms || off >= lp.t_span) {
+        ++dropped;
+      } else {
+        const unsigned long long b = off / (unsigned long long)lp.bin_ms;
+        const unsigned long long lk =
+            ((b * 4ull + (unsigned long long)d) * (unsigned long long)g.n_rows + (unsigned long long)r) *
+                (unsigned long long)g.n_cols + (unsigned long long)c;
+        k = (lk << lp.rank_bits) | (unsigned long long)slot_rank[slot];
+      }
+    }
+    keys[i] = k;
+  }
+  const unsigned long long s = block_sum<256, unsigned long long>(dropped, scratch);
+  if (threadIdx.x == 0 && s) atomicAdd(n_dropped, s);
+}
+
+__global__ void k_lattice_heads(const unsigned long long* __restrict__ skey, uint32_t m, int rank_bits,
+                                uint32_t* __restrict__ head) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    head[i] = (i == 0 || (skey[i] >> rank_bits) != (skey[i - 1] >> rank_bits)) ? 1u : 0u;
+}
+
+struct LatticeOut {
+  uint32_t* key;
+  int32_t *bin, *dxn, *row, *col;
+  uint32_t* count;
+  double* sum;
+  float* mean;
+  uint32_t* volume;
+  float *mean_norm, *volume_norm;
+};
+
+__device__ __forceinline__ uint32_t ord_f32(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float from_ord_f32(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u ^ 0x80000000u) : ~u);
+}
+
+// One thread per lattice cell (segment head): the segment's points in (journey, row) order
+// give the count, the speed sum in that order, the mean and the unique journeys; the channel
+// extremes go to chan[0..7] (min) and chan[8..15] (max) as order-preserving words.
+__global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, const uint32_t* __restrict__ srow,
+                               uint32_t m, const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx,
+                               const float* __restrict__ spd, int rank_bits, int32_t n_rows, int32_t n_cols,
+                               LatticeOut o, uint32_t* __restrict__ chan) {
+  const unsigned long long rmask = (1ull << rank_bits) - 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    if (!head[i]) continue;
+    const unsigned long long lk = skey[i] >> rank_bits;
+    uint32_t cnt = 0, vol = 0;
+    double sum = 0.0;
+    unsigned long long prev_rank = ~0ull;
+    for (uint32_t e = i; e < m && (skey[e] >> rank_bits) == lk; ++e) {
+      const float s = spd[srow[e]];
+      cnt += 1;
+      sum += (double)(((__float_as_uint(s) & 0x7FFFFFFFu) == 0) ? 0.0f : s);
+      const unsigned long long rk = skey[e] & rmask;
+      if (rk != prev_rank) vol += 1;
+      prev_rank = rk;
+    }
+    const uint32_t q = cidx[i];
+    const uint32_t key = (uint32_t)lk, cells = (uint32_t)n_rows * (uint32_t)n_cols;
+    const int d = (int)((key / cells) % 4u);
+    const float mean = (float)(sum / (double)cnt);
+    o.key[q] = key;
+    o.bin[q] = (int32_t)(key / (cells * 4u));
+    o.dxn[q] = d;
+    o.row[q] = (int32_t)((key % cells) / (uint32_t)n_cols);
+    o.col[q] = (int32_t)(key % (uint32_t)n_cols);
+    o.count[q] = cnt;
+    o.sum[q] = sum;
+    o.mean[q] = mean;
+    o.volume[q] = vol;
+    atomicMin(&chan[2 * d], ord_f32(mean));
+    atomicMax(&chan[8 + 2 * d], ord_f32(mean));
+    atomicMin(&chan[2 * d + 1], ord_f32((float)vol));
+    atomicMax(&chan[8 + 2 * d + 1], ord_f32((float)vol));
+  }
+}
+
+// Min-max normalisation per channel and, when dense != nullptr, the dense tensor
+// [n_bins][8][n_rows][n_cols] (zeroed beforehand; channels of the normalised values when
+// normalized, of the raw values otherwise).
+__global__ void k_lattice_norm(uint32_t K, const uint32_t* __restrict__ chan, LatticeOut o, int32_t n_rows,
+                               int32_t n_cols, float* __restrict__ dense, int normalized) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+    const int d = o.dxn[q];
+    const float mn0 = from_ord_f32(chan[2 * d]), mx0 = from_ord_f32(chan[8 + 2 * d]);
+    const float mn1 = from_ord_f32(chan[2 * d + 1]), mx1 = from_ord_f32(chan[8 + 2 * d + 1]);
+    const float mean = o.mean[q], vol = (float)o.volume[q];
+    const float mn = (mx0 > mn0) ? (mean - mn0) / (mx0 - mn0) : 0.0f;
+    const float vn = (mx1 > mn1) ? (vol - mn1) / (mx1 - mn1) : 0.0f;
+    o.mean_norm[q] = mn;
+    o.volume_norm[q] = vn;
+    if (dense) {
+      const size_t plane = (size_t)n_rows * (size_t)n_cols;
+      const size_t at = ((size_t)o.bin[q] * 8u + (size_t)(2 * d)) * plane + (size_t)o.row[q] * (size_t)n_cols +
+                        (size_t)o.col[q];
+      dense[at] = normalized ? mn : mean;
+      dense[at + plane] = normalized ? vn : vol;
+    }
+  }
+}
+
+}  // namespace cvetl
