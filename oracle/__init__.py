@@ -88,7 +88,7 @@ class _Journeys(ctypes.Structure):
 
 
 class _Cells(ctypes.Structure):
-    _fields_ = [(n, _P) for n in ("key", "row", "col", "bin", "count", "sum", "mean", "min", "max")]
+    _fields_ = [(n, _P) for n in ("key", "row", "col", "bin", "count", "sum", "mean", "min", "max", "volume")]
 
 
 class _Counters(ctypes.Structure):
@@ -103,7 +103,7 @@ JOURNEY_DTYPES = dict(jid=np.int64, n=np.int64, start_ts=np.int64, end_ts=np.int
                       start_lat=np.float64, start_lon=np.float64, end_lat=np.float64,
                       end_lon=np.float64)
 CELL_DTYPES = dict(key=np.uint32, row=np.int32, col=np.int32, bin=np.int32, count=np.uint32,
-                   sum=np.float64, mean=np.float64, min=np.float32, max=np.float32)
+                   sum=np.float64, mean=np.float64, min=np.float32, max=np.float32, volume=np.uint32)
 
 
 class Oracle:

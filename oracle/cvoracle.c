@@ -302,9 +302,9 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
   }
   cnt->n_journeys = nj;
 
-  /* 11. Cell x bin aggregates over valid keys, in key order (groupby count / sum / mean,
-   * Table 3; min and max added). Sorted positions are stably ordered by key, so the sum
-   * runs over each key's points in (journey, time) order. */
+  /* 11. Cell x bin aggregates over valid keys, in key order (groupby count / sum / mean and
+   * count unique journeys, Table 3; min and max added). Sorted positions are stably ordered
+   * by key, so the sum runs over each key's points in (journey, time) order. */
   uint32_t* byk = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(nv > 0 ? nv : 1));
   if (!byk) { free(order); free(spd); return 2; }
   int64_t m = 0;
@@ -327,9 +327,12 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
       cl->sum[nc] = 0.0;
       cl->min[nc] = s;
       cl->max[nc] = s;
+      cl->volume[nc] = 0;
       nc++;
     }
     int64_t c = nc - 1;
+    /* a key's points come in (journey, time) order: a new journey starts at each change */
+    if (cl->count[c] == 0 || jid[order[byk[t - 1]]] != jid[order[k]]) cl->volume[c] += 1;
     cl->count[c] += 1;
     cl->sum[c] += (double)s;
     if (s < cl->min[c]) cl->min[c] = s;

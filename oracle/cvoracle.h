@@ -82,6 +82,7 @@ typedef struct {
   double* mean;
   float* min;
   float* max;
+  uint32_t* volume; /* unique journeys (Table 3, "Reduction - Count Unique (Volume)") */
 } orc_cells;
 
 typedef struct {

@@ -254,6 +254,12 @@ def pin_library_cross_check(o, cols):
     assert np.array_equal(np.maximum.reduceat(ss, first), cl["max"])
     sums = np.add.reduceat(ss.astype(np.float64), first)
     assert np.all(np.abs(sums - cl["sum"]) <= 1e-12 * np.abs(sums) + 1e-9)
+    # unique journeys per key: distinct (key, journey) pairs counted per key
+    jj = cols["jid"][p["perm"]][ok][o2]
+    pairs = np.unique(np.stack([kk.astype(np.int64), jj]), axis=1)
+    uk2, vol = np.unique(pairs[0], return_counts=True)
+    assert np.array_equal(uk2, cl["key"].astype(np.int64)) and np.array_equal(vol, cl["volume"])
+    assert (cl["volume"] <= cl["count"]).all()
 
 
 def _independent_groups(cols):

@@ -44,6 +44,7 @@ MUTANTS = {
     "lattice_sum_by_point_order": ("  if (g_jid[i] != g_jid[j]) return g_jid[i] < g_jid[j] ? -1 : 1;\n  return i < j ? -1 : (i > j ? 1 : 0);\n}\n\nint orc_lattice",
                                    "  return i < j ? -1 : (i > j ? 1 : 0);\n}\n\nint orc_lattice"),
     "normalise_global": ("const float mn0 = ch_min[2 * d], mx0 = ch_max[2 * d],", "const float mn0 = ch_min[0], mx0 = ch_max[0],"),
+    "cell_volume_counts_points": ("if (cl->count[c] == 0 || jid[order[byk[t - 1]]] != jid[order[k]]) cl->volume[c] += 1;", "cl->volume[c] += 1;"),
     "lattice_key_dir_bin_swapped": ("lkey[i] = (((uint32_t)b * 4u + (uint32_t)d)", "lkey[i] = (((uint32_t)d * 4u + (uint32_t)b)"),
 }
 
