@@ -131,6 +131,7 @@ typedef struct {
   const double* cell_mean;
   const float* cell_min;
   const float* cell_max;
+  const uint32_t* cell_volume;  /* unique journeys (Table 3, count unique); NULL in stream mode */
   /* journey table, ascending journey id (device pointers, n_journeys rows) */
   int64_t n_journeys;
   const int64_t* j_id;

@@ -48,7 +48,7 @@ class Input(ctypes.Structure):
 
 
 _CELL = [("key", "<u4"), ("row", "<i4"), ("col", "<i4"), ("bin", "<i4"), ("count", "<u4"),
-         ("sum", "<f8"), ("mean", "<f8"), ("min", "<f4"), ("max", "<f4")]
+         ("sum", "<f8"), ("mean", "<f8"), ("min", "<f4"), ("max", "<f4"), ("volume", "<u4")]
 _JOURNEY = [("id", "<i8"), ("n", "<i8"), ("offset", "<i8"), ("start_ts", "<i8"), ("end_ts", "<i8"),
             ("duration_ms", "<i8"), ("distance_m", "<f8"), ("dwell_ms", "<i8"),
             ("start_lat", "<f8"), ("start_lon", "<f8"), ("end_lat", "<f8"), ("end_lon", "<f8")]

@@ -21,7 +21,19 @@ struct CellOut {
   uint32_t* count;
   double *sum, *mean;
   float *min, *max;
+  uint32_t* volume;  // unique journeys (batch mode)
 };
+
+// Rank of the journey whose sorted points contain position pos (joff: J ascending offsets).
+__device__ __forceinline__ uint32_t journey_of(const uint32_t* __restrict__ joff, uint32_t J, uint32_t pos) {
+  uint32_t lo = 0, hi = J;  // last offset <= pos
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (joff[mid] <= pos) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
                              const uint32_t* __restrict__ sidx, uint32_t R,
@@ -29,20 +41,27 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
                              const uint32_t* __restrict__ run_cnt, const double* __restrict__ run_sum,
                              const float* __restrict__ run_min, const float* __restrict__ run_max,
                              int32_t n_rows, int32_t n_cols, Batch bt,
-                             CellOut o, const uint32_t* __restrict__ R_dev) {
+                             CellOut o, const uint32_t* __restrict__ R_dev,
+                             const uint32_t* __restrict__ joff, uint32_t J) {
   if (R_dev) R = min(R, *R_dev);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) {
     if (!head[i]) continue;
     const uint32_t key = (uint32_t)(skey[i] >> 32);
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, vol = 0, prev_j = 0xFFFFFFFFu;
     double sum = 0.0;
     float mn = run_min[sidx[i]], mx = run_max[sidx[i]];
+    // runs of a key come by first sorted position, so one journey's runs are adjacent
     for (uint32_t m = i; m < R && (uint32_t)(skey[m] >> 32) == key; ++m) {
       uint32_t r = sidx[m];
       cnt += run_cnt[r];
       sum += run_sum[r];
       mn = fminf(mn, run_min[r]);
       mx = fmaxf(mx, run_max[r]);
+      if (o.volume) {
+        const uint32_t jr = journey_of(joff, J, (uint32_t)skey[m]);
+        vol += jr != prev_j;
+        prev_j = jr;
+      }
     }
     const uint32_t c = cidx[i];
     uint32_t lkey = key;  // a batch reports each instance's own keys
@@ -63,6 +82,7 @@ __global__ void k_cell_write(const unsigned long long* __restrict__ skey,
     o.mean[c] = sum / (double)cnt;
     o.min[c] = mn;
     o.max[c] = mx;
+    if (o.volume) o.volume[c] = vol;
   }
 }
 

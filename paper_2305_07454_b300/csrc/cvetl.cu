@@ -1047,10 +1047,12 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   ENSURE("out.c_mean", (size_t)R, &co.mean);
   ENSURE("out.c_min", (size_t)R, &co.min);
   ENSURE("out.c_max", (size_t)R, &co.max);
+  ENSURE("out.c_volume", (size_t)R, &co.volume);
   if (R) {
     LAUNCH(ST_CELL_WRITE, (k_cell_write<<<grid_for(R, 256), 256, 0, c->st>>>(
                               rkey, sidx, R, head, cidx, c->jo.run_cnt, c->jo.run_sum,
-                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt, co, Rd)));
+                              c->jo.run_min, c->jo.run_max, c->cfg.n_rows, c->cfg.n_cols, c->bt, co, Rd,
+                              joff, J)));
     LAUNCH_CHECK();
   }
   if (c->bt.n_inst) {
@@ -1851,6 +1853,7 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
     r->cell_key = co.key; r->cell_row = co.row; r->cell_col = co.col; r->cell_bin = co.bin;
     r->cell_count = co.count; r->cell_sum = co.sum; r->cell_mean = co.mean;
     r->cell_min = co.min; r->cell_max = co.max;
+    r->cell_volume = nullptr;  // unique journeys are not kept across windows
     const JourneyOut& o = c->jo;
     r->n_journeys = c->J;
     r->j_id = c->jid_sorted; r->j_n = o.n; r->j_offset = o.off; r->j_start_ts = o.start_ts;
@@ -1882,6 +1885,7 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
   r->cell_mean = co.mean;
   r->cell_min = co.min;
   r->cell_max = co.max;
+  r->cell_volume = co.volume;
   const JourneyOut& o = c->jo;
   r->n_journeys = c->J;
   r->j_id = c->jid_sorted;

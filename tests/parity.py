@@ -58,6 +58,8 @@ def compare(gpu: dict, orc: dict, points: bool = True, rel: float = REL, counter
     g, o = gpu["cells"], orc["cells"]
     for k in ("key", "row", "col", "bin", "count", "min", "max"):
         exact("cell " + k, g[k], o[k])
+    if g.get("volume") is not None and g["volume"].shape == g["key"].shape:  # batch mode
+        exact("cell volume", g["volume"], o["volume"])
     close("cell sum", g["sum"], o["sum"], rel)
     close("cell mean", g["mean"], o["mean"], rel)
     if points:
