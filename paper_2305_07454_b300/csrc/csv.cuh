@@ -159,6 +159,133 @@ __device__ bool parse_row(const unsigned char* p, int len, int64_t& jid, int64_t
   return true;
 }
 
+// ---- byte-parallel helpers (SWAR: several bytes per 32- or 64-bit word)
+// Bit i of the result is set when byte i of w equals c (exact per byte: no borrow between bytes).
+__device__ __forceinline__ uint32_t byte_eq_mask4(uint32_t w, uint32_t c4) {
+  const uint32_t x = w ^ c4;
+  const uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;  // 0x80 where x's byte is 0
+  return ((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u);
+}
+
+// 8 bytes at byte offset pos of a 16-byte aligned shared buffer (two aligned loads + shift).
+__device__ __forceinline__ unsigned long long load8(const unsigned char* s, int pos) {
+  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(s + (pos & ~7));
+  const int sh = (pos & 7) * 8;
+  const unsigned long long lo = w[0];
+  if (sh == 0) return lo;
+  return (lo >> sh) | (w[1] << (64 - sh));
+}
+
+// The value of n (1..8) ASCII decimal digits held in the low n bytes of x (first digit in the
+// lowest byte), or false if one of them is not a digit. The digits are moved to the top bytes
+// and the bottom bytes filled with '0', then pairs, quads and the octet are combined by
+// multiply-and-shift inside the word.
+__device__ __forceinline__ bool digits8(unsigned long long x, int n, unsigned long long& v) {
+  const int sh = 8 * (8 - n);
+  x = sh ? ((x << sh) | (0x3030303030303030ull >> (64 - sh))) : x;
+  const unsigned long long t = x - 0x3030303030303030ull;  // digit values (a byte below '0' sets its top bit)
+  if (((x + 0x4646464646464646ull) | t) & 0x8080808080808080ull) return false;  // some byte outside '0'..'9'
+  unsigned long long y = (t * 10 + (t >> 8)) & 0x00FF00FF00FF00FFull;      // 2-digit lanes
+  y = (y * 100 + (y >> 16)) & 0x0000FFFF0000FFFFull;                      // 4-digit lanes
+  v = (y * 10000 + (y >> 32)) & 0xFFFFFFFFull;                            // 8 digits
+  return true;
+}
+
+// The value of the n (1..18) digits at s[pos, pos + n): a leading chunk of 1..8 digits, then
+// chunks of 8.
+__device__ __forceinline__ bool digits_at(const unsigned char* s, int pos, int n, unsigned long long& v) {
+  const int m = n - ((n - 1) >> 3) * 8;
+  unsigned long long acc, d;
+  if (!digits8(load8(s, pos), m, acc)) return false;
+  for (pos += m, n -= m; n > 0; pos += 8, n -= 8) {
+    if (!digits8(load8(s, pos), 8, d)) return false;
+    acc = acc * 100000000ull + d;
+  }
+  v = acc;
+  return true;
+}
+
+// Fields of one line of the staged window by the separator masks: an integer field.
+__device__ __forceinline__ bool int_field(const unsigned char* s, int a, int b, long long& out) {
+  bool neg = false;
+  if (a < b && s[a] == '-') {
+    neg = true;
+    ++a;
+  }
+  const int n = b - a;
+  if (n < 1 || n > 18) return false;
+  unsigned long long v;
+  if (!digits_at(s, a, n, v)) return false;
+  out = neg ? -(long long)v : (long long)v;
+  return true;
+}
+
+// A decimal field -?[0-9]+(\.[0-9]+)? with at most 15 digits.
+__device__ __forceinline__ bool dec_field(const unsigned char* s, int a, int b, double& out) {
+  bool neg = false;
+  if (a < b && s[a] == '-') {
+    neg = true;
+    ++a;
+  }
+  const int len = b - a;
+  if (len < 1 || len > 16) return false;  // 15 digits and one '.'
+  // position of the first '.' (if any) in the field
+  int dot = -1;
+  {
+    const unsigned long long w0 = load8(s, a), w1 = load8(s, a + 8);
+    const uint32_t m = byte_eq_mask4((uint32_t)w0, 0x2E2E2E2Eu) | (byte_eq_mask4((uint32_t)(w0 >> 32), 0x2E2E2E2Eu) << 4) |
+                       (byte_eq_mask4((uint32_t)w1, 0x2E2E2E2Eu) << 8) | (byte_eq_mask4((uint32_t)(w1 >> 32), 0x2E2E2E2Eu) << 12);
+    const uint32_t in = m & ((1u << len) - 1u);
+    if (in) dot = __ffs(in) - 1;
+  }
+  const int ni = dot < 0 ? len : dot, nf = dot < 0 ? 0 : len - dot - 1;
+  if (ni < 1 || (dot >= 0 && nf < 1) || ni + nf > 15) return false;
+  unsigned long long hi, lo = 0;
+  if (!digits_at(s, a, ni, hi)) return false;
+  if (nf && !digits_at(s, a + ni + 1, nf, lo)) return false;  // a second '.' is not a digit
+  const unsigned long long M = hi * (kPow5[nf] << nf) + lo;  // hi * 10^nf + lo < 10^15
+  const double v = dec_to_f64(M, nf);
+  out = neg ? -v : v;
+  return true;
+}
+
+// One line [a, e) of the staged window, fields located with the comma mask.
+__device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const uint32_t* cm, int a, int e,
+                                                  int64_t& jid, int64_t& ts, double& lat, double& lon,
+                                                  float& spd, float& hd) {
+  if (e > a && s[e - 1] == '\r') --e;
+  if (e == a) return false;
+  int sep[6];
+  int nsep = 0;
+  for (int w = a >> 5; w <= ((e - 1) >> 5) && nsep < 6; ++w) {
+    uint32_t m = cm[w];
+    const int lo = w << 5;
+    if (lo < a) m &= ~0u << (a - lo);
+    if (lo + 32 > e) m &= (e - lo >= 32) ? ~0u : ((1u << (e - lo)) - 1u);
+    while (m && nsep < 6) {
+      sep[nsep++] = lo + __ffs(m) - 1;
+      m &= m - 1;
+    }
+  }
+  if (nsep != 5) return false;
+  long long iv0, iv1;
+  double d0, d1, d2, d3;
+  if (!int_field(s, a, sep[0], iv0) || !int_field(s, sep[0] + 1, sep[1], iv1)) return false;
+  if (!dec_field(s, sep[1] + 1, sep[2], d0) || !dec_field(s, sep[2] + 1, sep[3], d1) ||
+      !dec_field(s, sep[3] + 1, sep[4], d2) || !dec_field(s, sep[4] + 1, e, d3))
+    return false;
+  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  if (((unsigned long long)__double_as_longlong(d0) & kAbs) > 0x4056800000000000ull) return false;
+  if (((unsigned long long)__double_as_longlong(d1) & kAbs) > 0x4066800000000000ull) return false;
+  jid = iv0;
+  ts = iv1;
+  lat = d0;
+  lon = d1;
+  spd = __double2float_rn(d2);
+  hd = __double2float_rn(d3);
+  return true;
+}
+
 struct CsvOut {
   int64_t *jid, *ts;
   double *lat, *lon;
@@ -192,13 +319,17 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_count(const unsigned char* __
 }
 
 // Pass 2: parse. Tiles are taken in order (ticket); each tile publishes its count of kept rows
-// and looks back over earlier tiles for its first output row, so rows keep file order.
+// and looks back over earlier tiles for its first output row, so rows keep file order (the last
+// tile's inclusive count is the number of kept rows). Inside a tile, one pass turns the bytes
+// into newline and comma bit masks; line starts, line ends and field separators then come from
+// the masks, and the digits are read eight at a time.
 __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __restrict__ buf,
                                                          unsigned long long len, uint32_t n_tiles,
                                                          CsvOut out, uint32_t cap,
                                                          uint32_t* status, uint32_t* tile_ctr,
                                                          DevState* st) {
-  __shared__ __align__(16) unsigned char s_buf[kCsvTile + kCsvHalo];
+  __shared__ __align__(16) unsigned char s_buf[kCsvTile + kCsvHalo + 32];
+  __shared__ uint32_t s_nl[(kCsvTile + kCsvHalo) / 32 + 1], s_cm[(kCsvTile + kCsvHalo) / 32 + 1];
   __shared__ uint16_t s_start[kCsvTile];
   __shared__ uint32_t s_scan[kCsvBlock / 32 + 1];
   __shared__ uint32_t s_tile, s_base;
@@ -211,23 +342,61 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   const unsigned long long base = (unsigned long long)tile * kCsvTile;
   const int tlen = (int)min((unsigned long long)kCsvTile, len - base);
   const int wlen = (int)min((unsigned long long)(kCsvTile + kCsvHalo), len - base);
-  // stage the tile (+ halo) in shared memory: 16-byte loads (base is 16-byte aligned)
+  // stage the tile (+ halo) in shared memory: 16-byte loads (base is 16-byte aligned); zero the
+  // 32 bytes after the window (the word loads of the parser may read into them)
   for (int o = tid * 16; o < wlen; o += kCsvBlock * 16) {
     if (o + 16 <= wlen) *reinterpret_cast<uint4*>(s_buf + o) = *reinterpret_cast<const uint4*>(buf + base + o);
     else
       for (int q = o; q < wlen; ++q) s_buf[q] = buf[base + q];
   }
+  if (tid < 32) s_buf[wlen + tid] = 0;
   if (tid == 0) s_prev = (base == 0) ? (unsigned char)'\n' : buf[base - 1];
   __syncthreads();
-  // line starts inside the tile: each thread scans 64 bytes
-  constexpr int kPer = kCsvTile / kCsvBlock;
-  const int c0 = tid * kPer, c1 = min(tlen, c0 + kPer);
+  // newline and comma bit masks of the window, one bit per byte: each thread classifies one
+  // 4-byte word, eight lanes' nibbles combine into a 32-bit mask word
+  const int nmask = (wlen + 31) / 32;
+  for (int q0 = tid & ~31; q0 < nmask * 8; q0 += kCsvBlock) {  // warp-uniform trip count
+    const int q = q0 + (tid & 31);
+    const bool have = q < nmask * 8;  // groups of 8 lanes are all in or all out
+    const uint32_t w = have ? reinterpret_cast<const uint32_t*>(s_buf)[q] : 0u;
+    uint32_t nl = byte_eq_mask4(w, 0x0A0A0A0Au) << ((q & 7) * 4);
+    uint32_t cm = byte_eq_mask4(w, 0x2C2C2C2Cu) << ((q & 7) * 4);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      nl |= __shfl_xor_sync(0xffffffffu, nl, o);
+      cm |= __shfl_xor_sync(0xffffffffu, cm, o);
+    }
+    if (have && (q & 7) == 0) {
+      s_nl[q >> 3] = nl;
+      s_cm[q >> 3] = cm;
+    }
+  }
+  __syncthreads();
+  // line starts inside the tile (a byte after a newline): 2 mask words per thread
+  const int tw = (tlen + 31) / 32;
+  uint32_t smask[2];
   uint32_t cnt = 0;
-  for (int p = c0; p < c1; ++p) cnt += ((p == 0 ? s_prev : s_buf[p - 1]) == '\n');
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int w = tid * 2 + u;
+    uint32_t m = 0;
+    if (w < tw) {
+      m = (s_nl[w] << 1) | (w ? (s_nl[w - 1] >> 31) : (s_prev == '\n' ? 1u : 0u));
+      if ((w + 1) * 32 > tlen) m &= (tlen - w * 32 >= 32) ? ~0u : ((1u << (tlen - w * 32)) - 1u);
+    }
+    smask[u] = m;
+    cnt += __popc(m);
+  }
   uint32_t total;
   uint32_t r = block_excl_scan<kCsvBlock>(cnt, s_scan, &total);
-  for (int p = c0; p < c1; ++p)
-    if ((p == 0 ? s_prev : s_buf[p - 1]) == '\n') s_start[r++] = (uint16_t)p;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    uint32_t m = smask[u];
+    while (m) {
+      s_start[r++] = (uint16_t)((tid * 2 + u) * 32 + __ffs(m) - 1);
+      m &= m - 1;
+    }
+  }
   __syncthreads();
   const int nstart = (int)total;
   // parse the lines starting here; keep up to kCsvRounds per thread in registers
@@ -238,20 +407,24 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   bool ok[kCsvRounds];
   uint32_t mine = 0;
   auto parse_at = [&](int i, int64_t& a, int64_t& b, double& c, double& d, float& e, float& f) -> bool {
-    const int s = s_start[i];
-    int q = s;
-    while (q < wlen && s_buf[q] != '\n') ++q;
-    if (q < wlen || base + wlen == len) return parse_row(s_buf + s, q - s, a, b, c, d, e, f);
+    const int st = s_start[i];
+    // the line's end: the next newline bit at or after its start
+    int w = st >> 5;
+    uint32_t m = s_nl[w] & (~0u << (st & 31));
+    while (!m && ++w < nmask) m = s_nl[w];
+    if (m) return parse_line_masked(s_buf, s_cm, st, w * 32 + __ffs(m) - 1, a, b, c, d, e, f);
+    if (base + wlen == len) return parse_line_masked(s_buf, s_cm, st, wlen, a, b, c, d, e, f);
     // the line runs past the staged window: read it from global memory
-    unsigned long long g = base + q;
+    unsigned long long g = base + wlen;
     while (g < len && buf[g] != '\n') ++g;
-    return parse_row(buf + base + s, (int)(g - (base + s)), a, b, c, d, e, f);
+    return parse_row(buf + base + st, (int)(g - (base + st)), a, b, c, d, e, f);
   };
+  const int rounds = (nstart + kCsvBlock - 1) / kCsvBlock;  // block-uniform
   if (in_regs) {
 #pragma unroll
     for (int u = 0; u < kCsvRounds; ++u) {
       const int i = tid + u * kCsvBlock;
-      ok[u] = (i < nstart) && parse_at(i, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
+      ok[u] = (u < rounds) && (i < nstart) && parse_at(i, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
       mine += ok[u];
     }
   } else {
@@ -289,8 +462,6 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
       st_relaxed_u32(status + tile, (2u << 30) | (excl + tile_valid));
     }
     s_base = excl;
-    atomicAdd(&st->n_lines, (unsigned long long)nstart);
-    if ((uint32_t)nstart > tile_valid) atomicAdd(&st->n_malformed, (unsigned long long)(nstart - tile_valid));
   }
   __syncthreads();
   // write the kept rows in file order (line i of the tile before line i + 1)
@@ -310,6 +481,7 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   if (in_regs) {
 #pragma unroll
     for (int u = 0; u < kCsvRounds; ++u) {
+      if (u >= rounds) break;  // block-uniform: the scans below stay collective
       uint32_t round_total;
       const uint32_t rk = block_excl_scan<kCsvBlock>(ok[u] ? 1u : 0u, s_scan, &round_total);
       if (ok[u]) put(pos + rk, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);

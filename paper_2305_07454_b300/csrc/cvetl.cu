@@ -409,8 +409,11 @@ cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
     LAUNCH_CHECK();
   }
   unsigned long long newlines = 0;
+  unsigned char last = '\n';
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(&newlines, nl, 8, cudaMemcpyDeviceToHost));
+  if (len) CK(cudaMemcpy(&last, buf + len - 1, 1, cudaMemcpyDeviceToHost));
+  const size_t n_lines = (size_t)newlines + (last != '\n' ? 1u : 0u);  // the last line may lack '\n'
   const size_t cap = len ? (size_t)newlines + 1 : 0;
   if (cap > (size_t)CVETL_MAX_RECORDS) return fail(c, CVETL_EINVAL, "the text holds more than %lld lines", (long long)CVETL_MAX_RECORDS);
   int64_t *jid, *ts;
@@ -437,9 +440,12 @@ cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
   }
   cvetl_status s = read_state(c);
   if (s != CVETL_OK) return s;
-  c->n_in = (int64_t)c->hstate->n_lines;
-  c->csv_malformed = (int64_t)c->hstate->n_malformed;
-  c->n_rows = c->n_in - c->csv_malformed;
+  uint32_t kept = 0;  // the last tile's inclusive count of kept rows
+  if (n_tiles) CK(cudaMemcpy(&kept, status + n_tiles - 1, 4, cudaMemcpyDeviceToHost));
+  kept &= (1u << 30) - 1;
+  c->n_in = (int64_t)n_lines;
+  c->csv_malformed = (int64_t)n_lines - (int64_t)kept;
+  c->n_rows = kept;
   c->jid = jid;
   c->ts = ts;
   c->lat = lat;

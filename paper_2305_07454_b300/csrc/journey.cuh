@@ -203,7 +203,27 @@ __device__ __forceinline__ Cos64 cos64(double lat, const CosEntry* __restrict__ 
   return c;
 }
 
-__device__ __forceinline__ bool tiny_deg(double x) { return fabs(x) < kTinyDeg; }
+// |x| < kTinyDeg on the bit patterns (an integer compare, not a binary64 one; NaN fails).
+__device__ __forceinline__ bool tiny_deg(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) < 0x3F977318FC504817ull;  // 0.0229
+}
+
+// double -> float rounded to nearest even by the bit layout when the result is a normal float
+// (the implied speed's distance; other values take the conversion instruction).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FF);
+  if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  uint32_t keep = (uint32_t)(m >> 29);
+  const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
+  keep += (rest > half || (rest == half && (keep & 1u))) ? 1u : 0u;
+  // a mantissa carry moves into the exponent (and to infinity past the largest float)
+  return __uint_as_float((hi & 0x80000000u) | (((uint32_t)(e - 1023 + 127) << 23) + keep));
+}
+__device__ __forceinline__ float to_f32(double x) { return f64_to_f32_rn(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
 
 __device__ __forceinline__ double haversine64(double la1, double lo1, const Cos64& c1, double la2,
                                               double lo2, const Cos64& c2, const GridParams& g) {
@@ -882,7 +902,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
         if (dt > 0) {
           // stored as float32: computed in float32 from the binary64 distance
           const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : (float)dt;
-          vh = (float)d * (3600.0f / fdt);
+          vh = to_f32(d) * (3600.0f / fdt);
           ac = (cur.spd - p_spd) / (0.0036f * fdt);
         }
         if (p_spd < g.v_stop && cur.spd < g.v_stop) {
