@@ -79,7 +79,7 @@ _P = ctypes.c_void_p
 
 
 class _Points(ctypes.Structure):
-    _fields_ = [(n, _P) for n in ("perm", "d", "vhat", "accel", "dwell", "key", "flags")]
+    _fields_ = [(n, _P) for n in ("perm", "d", "vhat", "accel", "dwell", "key", "flags", "stop_ms", "accel_v")]
 
 
 class _Journeys(ctypes.Structure):
@@ -97,7 +97,7 @@ class _Counters(ctypes.Structure):
 
 
 POINT_DTYPES = dict(perm=np.uint32, d=np.float64, vhat=np.float64, accel=np.float64,
-                    dwell=np.int64, key=np.uint32, flags=np.uint8)
+                    dwell=np.int64, key=np.uint32, flags=np.uint8, stop_ms=np.int64, accel_v=np.float64)
 JOURNEY_DTYPES = dict(jid=np.int64, n=np.int64, start_ts=np.int64, end_ts=np.int64,
                       duration_ms=np.int64, distance_m=np.float64, dwell_ms=np.int64,
                       start_lat=np.float64, start_lon=np.float64, end_lat=np.float64,

@@ -227,11 +227,14 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
   qsort(order, (size_t)nv, sizeof(uint32_t), cmp_jid_ts_idx);
 
   const double R = p->earth_radius_m;
+  int64_t run_stop = 0;     /* dwell of the current run of stop steps */
+  double v_prev = 0.0;      /* implied speed of the previous step, m/s */
+  int v_prev_ok = 0;        /* the previous step had dt > 0 */
   for (int64_t k = 0; k < nv; k++) {
     uint32_t i = order[k];
     pts->perm[k] = i;
     uint8_t f = 0;
-    double d = 0.0, vh = 0.0, ac = 0.0;
+    double d = 0.0, vh = 0.0, ac = 0.0, av = 0.0;
     int64_t dwell = 0;
     /* 4. Journey start / step. */
     int start = (k == 0) || (jid[order[k - 1]] != jid[i]);
@@ -255,6 +258,24 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
         f |= ORC_F_STOP;
         dwell = dt;
       }
+      /* Run-length dwell (reading): the time since the current stop began is the dwell summed
+       * over the consecutive stop steps ending here. Acceleration from the implied speeds
+       * (reading): the difference of this step's and the previous step's implied speed in m/s
+       * over this step's dt, when both steps have dt > 0. */
+      run_stop = (f & ORC_F_STOP) ? run_stop + dwell : 0;
+      if (dt > 0) {
+        const double dt_s = (double)dt / 1000.0;
+        const double v = d / dt_s;
+        if (v_prev_ok) av = (v - v_prev) / dt_s;
+        v_prev = v;
+        v_prev_ok = 1;
+      } else {
+        v_prev_ok = 0;
+      }
+    }
+    if (start) {
+      run_stop = 0;
+      v_prev_ok = 0;
     }
     /* 9. Key: Algorithm 2 bins unrolled into one global index. */
     int32_t r = orc_grid_index(lat[i], p->lat_min, p->cell_deg, p->n_rows);
@@ -275,6 +296,8 @@ int orc_run(const orc_params* p, int64_t n, const int64_t* jid, const int64_t* t
     pts->dwell[k] = dwell;
     pts->key[k] = key;
     pts->flags[k] = f;
+    pts->stop_ms[k] = run_stop;
+    pts->accel_v[k] = av;
   }
 
   /* 10. Journey summaries, in journey-id order, sequential sums in sorted order. */

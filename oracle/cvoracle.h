@@ -54,6 +54,8 @@ typedef struct {
   int64_t* dwell;   /* dwell time of the step, ms */
   uint32_t* key;    /* unrolled cell x bin key, or ORC_KEY_INVALID */
   uint8_t* flags;   /* ORC_F_* */
+  int64_t* stop_ms; /* time since the current stop began: dwell summed over the run of stop steps */
+  double* accel_v;  /* acceleration from the implied speeds, m/s^2 (0 unless both steps have dt > 0) */
 } orc_points;
 
 /* Journey table, one row per distinct journey id, ascending id. Capacity >= n_valid. */

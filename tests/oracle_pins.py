@@ -462,7 +462,34 @@ def pin_lattice_invariants(o):
             assert c["mean_norm"][sel].min() == 0 and c["mean_norm"][sel].max() == 1
 
 
+def pin_run_length_dwell_and_speed_acceleration(o):
+    """Time since a stop began (dwell summed over consecutive stop steps, reset at a moving step
+    and at a journey start) and acceleration from implied speeds on a meridian (closed form)."""
+    t = 1620532122000
+    deg = lambda m: math.degrees(m / R)  # metres along a meridian
+    lat = [37.0]
+    for v in (10.0, 12.0, 14.0):  # 1 s steps at 10, 12, 14 m/s
+        lat.append(lat[-1] + deg(v))
+    lat += [lat[-1]] * 2  # a duplicate, then a 1 s step at rest
+    n1 = len(lat)
+    cols = dict(jid=np.array([7] * n1 + [8] * 7 + [9] * 2, np.int64),
+                ts=np.array([t + 1000 * i for i in range(4)] + [t + 3000, t + 4000] +
+                            [t + 1000 * i for i in range(7)] + [t, t + 1000], np.int64),
+                lat=np.array(lat + [38.0] * 7 + [38.5] * 2),
+                lon=np.full(n1 + 9, -92.5),
+                speed=np.array([30, 30, 30, 30, 30, 30] + [5, 0, 0, 0, 5, 0, 0] + [0, 0], np.float32))
+    p = o.run(cols)["points"]
+    a = p["accel_v"]
+    assert a[0] == 0 and a[1] == 0  # no previous implied speed
+    assert abs(a[2] - 2.0) < 1e-6 and abs(a[3] - 2.0) < 1e-6
+    assert a[4] == 0 and a[5] == 0  # a zero-dt step breaks the chain on both sides
+    assert list(p["stop_ms"][n1:n1 + 7]) == [0, 0, 1000, 2000, 0, 0, 1000]
+    assert list(p["stop_ms"][n1 + 7:]) == [0, 1000]  # a new journey starts a new run
+    assert (p["stop_ms"][:n1] == 0).all()
+
+
 CPU_PINS = [pin_haversine_closed_forms, pin_grid_index, pin_time_bin, pin_parse_fields, pin_table1,
             pin_bruteforce_orders, pin_kinematics_hand, pin_invalid_records, pin_direction_sectors,
+            pin_run_length_dwell_and_speed_acceleration,
             pin_lattice_bruteforce, pin_lattice_invariants]
 DATA_PINS = [pin_invariants, pin_library_cross_check, pin_csv_roundtrip]

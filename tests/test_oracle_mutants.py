@@ -45,6 +45,8 @@ MUTANTS = {
                                    "  return i < j ? -1 : (i > j ? 1 : 0);\n}\n\nint orc_lattice"),
     "normalise_global": ("const float mn0 = ch_min[2 * d], mx0 = ch_max[2 * d],", "const float mn0 = ch_min[0], mx0 = ch_max[0],"),
     "cell_volume_counts_points": ("if (cl->count[c] == 0 || jid[order[byk[t - 1]]] != jid[order[k]]) cl->volume[c] += 1;", "cl->volume[c] += 1;"),
+    "stop_run_not_reset": ("run_stop = (f & ORC_F_STOP) ? run_stop + dwell : 0;", "run_stop = run_stop + dwell;"),
+    "speed_accel_in_kmh": ("const double v = d / dt_s;", "const double v = d / dt_s * 3.6;"),
     "lattice_key_dir_bin_swapped": ("lkey[i] = (((uint32_t)b * 4u + (uint32_t)d)", "lkey[i] = (((uint32_t)d * 4u + (uint32_t)b)"),
 }
 
