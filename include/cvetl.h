@@ -155,6 +155,9 @@ typedef struct {
   const int64_t* p_dwell;  /* dwell of the step, ms */
   const uint32_t* p_key;   /* unrolled cell x bin key or CVETL_KEY_INVALID */
   const uint8_t* p_flags;  /* CVETL_F_* */
+  const int64_t* p_stop_ms; /* time since the current stop began: dwell summed over consecutive stop steps */
+  const float* p_accel_v;   /* acceleration from the implied speeds of this and the previous step, m/s^2
+                               (binary64, 0 unless both steps have dt > 0) */
   /* extracted columns (device; the CSV path's parsed rows, or the caller's columns), n_extracted rows */
   int64_t n_extracted;
   const int64_t* x_jid;

@@ -53,7 +53,7 @@ _JOURNEY = [("id", "<i8"), ("n", "<i8"), ("offset", "<i8"), ("start_ts", "<i8"),
             ("duration_ms", "<i8"), ("distance_m", "<f8"), ("dwell_ms", "<i8"),
             ("start_lat", "<f8"), ("start_lon", "<f8"), ("end_lat", "<f8"), ("end_lon", "<f8")]
 _POINT = [("perm", "<u4"), ("d", "<f8"), ("vhat", "<f4"), ("accel", "<f4"), ("dwell", "<i8"),
-          ("key", "<u4"), ("flags", "|u1")]
+          ("key", "<u4"), ("flags", "|u1"), ("stop_ms", "<i8"), ("accel_v", "<f4")]
 _EXTRACTED = [("jid", "<i8"), ("ts", "<i8"), ("lat", "<f8"), ("lon", "<f8"), ("speed", "<f4"),
               ("heading", "<f4")]
 _COUNTERS = ["n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_too_late", "n_runs"]

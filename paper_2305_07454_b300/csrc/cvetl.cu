@@ -33,13 +33,13 @@ namespace {
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
   ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
-  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_COUNT
+  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_POINT_EXTRAS, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
                                      "csv_count", "csv_parse", "stream_append", "stream_split",
-                                     "stream_tables", "cta_sort", "lattice"};
+                                     "stream_tables", "cta_sort", "lattice", "point_extras"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -980,6 +980,8 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     ENSURE("out.p_dwell", nv, &o.dwell_pt);
     ENSURE("out.p_key", nv, &o.key);
     ENSURE("out.p_flags", nv, &o.flags);
+    ENSURE("out.p_stop_ms", nv, &o.stop_ms);
+    ENSURE("out.p_accel_v", nv, &o.accel_v);
   } else {
     o.perm = nullptr;
     o.d = nullptr;
@@ -987,6 +989,8 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     o.dwell_pt = nullptr;
     o.key = nullptr;
     o.flags = nullptr;
+    o.stop_ms = nullptr;
+    o.accel_v = nullptr;
   }
   ENSURE("run.sortkey", nv, &o.run_sortkey);
   ENSURE("run.cnt", nv, &o.run_cnt);
@@ -1019,6 +1023,11 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false)));
 #undef JRN
     LAUNCH_CHECK();
+    if (o.perm) {  // features over earlier points of a journey (materialised points)
+      LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(
+                              jn, joff, J, c->ts, o.perm, o.d, o.dwell_pt, o.flags, o.stop_ms, o.accel_v)));
+      LAUNCH_CHECK();
+    }
   }
 
   // load: runs ordered by (key, first sorted position), folded into the cell table
@@ -1915,6 +1924,8 @@ cvetl_status cvetl_results(cvetl_ctx* c, cvetl_tables* r) {
     r->p_dwell = o.dwell_pt;
     r->p_key = o.key;
     r->p_flags = o.flags;
+    r->p_stop_ms = o.stop_ms;
+    r->p_accel_v = o.accel_v;
   }
   r->n_malformed = c->csv_malformed + (int64_t)c->hstate->n_malformed;
   r->n_valid = c->n_valid;

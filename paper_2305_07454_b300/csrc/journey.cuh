@@ -28,6 +28,8 @@ struct JourneyOut {
   int64_t* dwell_pt;
   uint32_t* key;
   uint8_t* flags;
+  int64_t* stop_ms;  // time since the current stop began
+  float* accel_v;    // acceleration from the implied speeds
   // cell runs
   unsigned long long* run_sortkey;  // (key << 32) | sorted position of the run's first point
   uint32_t* run_cnt;
@@ -1069,6 +1071,66 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
 __global__ void k_size_keys(const uint32_t* __restrict__ jn, uint32_t J, unsigned long long* __restrict__ keys) {
   const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < J) keys[r] = 0xFFFFFFFFull - jn[r];
+}
+
+// Per-point features that need a journey's earlier points (materialised points only): the time
+// since the current stop began (dwell summed over consecutive stop steps: a segmented scan,
+// reset at every step that is not a stop, which includes the journey's first point) and the
+// acceleration from the implied speeds of this and the previous step (both with dt > 0),
+// evaluated in binary64 from the step distances and stored as float32. One warp per journey,
+// 32 points at a time, the scan carried from chunk to chunk.
+__global__ void __launch_bounds__(256) k_point_extras(const uint32_t* __restrict__ jn,
+                                                      const uint32_t* __restrict__ joff, uint32_t J,
+                                                      const int64_t* __restrict__ ts,
+                                                      const uint32_t* __restrict__ perm,
+                                                      const double* __restrict__ d,
+                                                      const int64_t* __restrict__ dwell,
+                                                      const uint8_t* __restrict__ flags,
+                                                      int64_t* __restrict__ stop_ms,
+                                                      float* __restrict__ accel_v) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < J; j += nwarps) {
+    const uint32_t off = joff[j], n = jn[j];
+    long long carry = 0;
+    for (uint32_t b = 0; b < n; b += 32) {
+      const uint32_t k = b + lane, g = off + k;
+      long long v = 0;
+      uint32_t reset = 1;
+      float av = 0.0f;
+      if (k < n) {
+        if (flags[g] & kFStop) {
+          v = dwell[g];
+          reset = 0;
+        }
+        if (k >= 2) {
+          const int64_t t0 = ts[perm[g - 2]], t1 = ts[perm[g - 1]], t2 = ts[perm[g]];
+          const int64_t dt1 = (int64_t)((unsigned long long)t1 - (unsigned long long)t0);
+          const int64_t dt2 = (int64_t)((unsigned long long)t2 - (unsigned long long)t1);
+          if (dt1 > 0 && dt2 > 0) {
+            const double s1 = (double)dt1 / 1000.0, s2 = (double)dt2 / 1000.0;
+            av = (float)((d[g] / s2 - d[g - 1] / s1) / s2);
+          }
+        }
+      }
+      // inclusive segmented scan: the sum since the last reset at or before this lane
+#pragma unroll
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const long long pv = __shfl_up_sync(0xffffffffu, v, o2);
+        const uint32_t pr = __shfl_up_sync(0xffffffffu, reset, o2);
+        if (lane >= o2 && !reset) {
+          v += pv;
+          reset = pr;
+        }
+      }
+      const long long out = reset ? v : v + carry;  // no reset in this chunk up to here: continue the run
+      if (k < n) {
+        stop_ms[g] = out;
+        accel_v[g] = av;
+      }
+      carry = __shfl_sync(0xffffffffu, out, 31);
+    }
+  }
 }
 
 }  // namespace cvetl

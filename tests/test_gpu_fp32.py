@@ -48,7 +48,7 @@ def test_fp32_small_day(orc, small_day):
     # everything that is not floating point is identical to the binary64 form
     import parity
 
-    for k in ("perm", "key", "flags", "dwell"):
+    for k in ("perm", "key", "flags", "dwell", "stop_ms"):
         parity.exact("point " + k, g["points"][k], o["points"][k])
     for k in ("id", "n", "offset", "start_ts", "end_ts", "duration_ms", "dwell_ms"):
         parity.exact("journey " + k, g["journeys"][k], o["journeys"]["jid" if k == "id" else k]
