@@ -146,11 +146,10 @@ def fp64_peak_gops():
     return SMS * FP64_PER_CLK_PER_SM * mhz / 1e3, mhz
 
 
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP64 journey
-# kernel from an ncu capture of the tenth-day workload (14,637,283 records: 868.4 MB read,
-# 77.8 MB written), scaled by records to the workload's launch; reported only for the kernel
-# that was captured (set to None when the kernel changes until it is captured again).
-TRAFFIC_PER_RECORD = {"journeys": (868.384512e6 + 77.815296e6) / 14637283}
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record of a kernel,
+# from an ncu capture of that kernel as it stands, scaled by records to the workload's launch;
+# empty until the current kernels are captured.
+TRAFFIC_PER_RECORD: dict = {}
 
 
 def run_ours(args):

@@ -35,15 +35,14 @@ struct DevState {
   uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
 };
 
-// One extracted record, bucketed by journey (32 bytes, one DRAM sector). The record's row index
-// (the tie-break of equal timestamps, and the materialised permutation) travels in a parallel
-// uint32 array at the same bucket position.
+// One extracted record, bucketed by journey: 32 bytes, one DRAM sector, written by one store
+// (a separate 4-byte array would take a partial-sector write per record at a random address).
 struct __align__(32) Rec {
   int64_t ts;
   double lat;
   double lon;
   float spd;     // canonical speed (+0.0 for -0.0)
-  uint32_t key;  // the point's cell x bin key (Algorithm 2), kKeyInvalid off the grid
+  uint32_t idx;  // extracted-row index: the tie-break of equal timestamps, the materialised permutation
 };
 static_assert(sizeof(Rec) == 32, "Rec must be one 32-byte sector");
 

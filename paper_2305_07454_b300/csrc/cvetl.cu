@@ -588,14 +588,11 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
   const size_t need = (size_t)ss.n_pending + n;
   int64_t* pj;
   Rec* pr;
-  uint32_t* pi;
-  char nj[32], nr[32], ni[32];
+  char nj[32], nr[32];
   snprintf(nj, sizeof nj, "sp.jid%d", ss.side);
   snprintf(nr, sizeof nr, "sp.rec%d", ss.side);
-  snprintf(ni, sizeof ni, "sp.idx%d", ss.side);
   GROW(nj, need, ss.n_pending, &pj);
   GROW(nr, need, ss.n_pending, &pr);
-  GROW(ni, need, ss.n_pending, &pi);
   const int64_t* jid = in->jid;
   const int64_t* ts = in->ts;
   const double* lat = in->lat;
@@ -621,8 +618,7 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
   if (n) {
     LAUNCH(ST_STREAM_APPEND, (k_stream_append<<<grid_for(n, 256), 256, 0, c->st>>>(
                                  jid, ts, lat, lon, spd, (uint32_t)n, ss.arrival, ss.w_prev,
-                                 ss.has_w_prev ? 1 : 0, pj, pr, pi, ss.n_pending, (uint32_t)need, c->gp,
-                                 c->dstate)));
+                                 ss.has_w_prev ? 1 : 0, pj, pr, ss.n_pending, (uint32_t)need, c->dstate)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
@@ -673,22 +669,17 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   const uint32_t np = ss.n_pending;
   int64_t *pj, *qj;
   Rec *pr, *qr, *fr;
-  uint32_t *pi, *qi, *fi, *fs;
-  char n1[32], n2[32], n3[32];
+  uint32_t* fs;
+  char n1[32], n2[32];
   snprintf(n1, sizeof n1, "sp.jid%d", ss.side);
   snprintf(n2, sizeof n2, "sp.rec%d", ss.side);
-  snprintf(n3, sizeof n3, "sp.idx%d", ss.side);
   GROW(n1, np, np, &pj);
   GROW(n2, np, np, &pr);
-  GROW(n3, np, np, &pi);
   snprintf(n1, sizeof n1, "sp.jid%d", ss.side ^ 1);
   snprintf(n2, sizeof n2, "sp.rec%d", ss.side ^ 1);
-  snprintf(n3, sizeof n3, "sp.idx%d", ss.side ^ 1);
   GROW(n1, np, 0, &qj);
   GROW(n2, np, 0, &qr);
-  GROW(n3, np, 0, &qi);
   ENSURE("sf.rec", np, &fr);
-  ENSURE("sf.idx", np, &fi);
   ENSURE("sf.slot", np, &fs);
   // journeys touched by the window, ascending id: bucket offsets
   unsigned long long* ukey;
@@ -698,7 +689,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (np) {
     LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
-                                pj, pr, pi, np, wm, all ? 1 : 0, h, qj, qr, qi, fr, fi, fs, c->dstate)));
+                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
     LAUNCH_CHECK();
     LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate)));
     LAUNCH_CHECK();
@@ -730,11 +721,9 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
     LAUNCH_CHECK();
   }
   Rec* rec;
-  uint32_t* ridx;
   ENSURE("rec", nf, &rec);
-  ENSURE("ridx", nf, &ridx);
   if (nf) {
-    LAUNCH(ST_SCATTER, (k_stream_scatter<<<grid_for(nf, 256), 256, 0, c->st>>>(fr, fi, fs, nf, h, rec, ridx)));
+    LAUNCH(ST_SCATTER, (k_stream_scatter<<<grid_for(nf, 256), 256, 0, c->st>>>(fr, fs, nf, h, rec)));
     LAUNCH_CHECK();
   }
   Elem *scrA, *scrB;
@@ -751,9 +740,9 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (J) {
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, Batch{}, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
+      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, Batch{}, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
     }
     LAUNCH_CHECK();
   }
@@ -942,13 +931,11 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   // 3. scatter kept rows into journey buckets
   const size_t nv = c->n_valid;
   Rec* rec;
-  uint32_t* ridx;
   ENSURE("rec", nv, &rec);
-  ENSURE("ridx", nv, &ridx);
   if (n) {
     const int U = c->tune.row_unroll;
 #define SCAT(U_) k_scatter<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
-    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->gp, c->bt, rec, ridx)
+    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)
     if (U == 2) LAUNCH(ST_SCATTER, (SCAT(2)));
     else if (U == 8) LAUNCH(ST_SCATTER, (SCAT(8)));
     else LAUNCH(ST_SCATTER, (SCAT(4)));
@@ -1015,7 +1002,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     const bool pers = c->tune.journey_ctas > 0;
     const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
     const bool f32 = c->cfg.precision == CVETL_FP32;
-#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, ridx, jn, joff, J, scrA, scrB, c->gp, o, \
+#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, c->bt, o, \
                                                                       c->dstate, nullptr, JState{}, order, work)
     if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true)));
     else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false)));
@@ -1256,6 +1243,7 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.bin_ms = cfg->bin_ms;
   unsigned __int128 span = (unsigned __int128)(uint64_t)cfg->n_bins * (uint64_t)cfg->bin_ms;
   g.t_span = span > (unsigned __int128)~0ull ? ~0ull : (unsigned long long)span;
+  g.bin_magic = cfg->bin_ms == 1 ? 0ull : ~0ull / (unsigned long long)cfg->bin_ms + 1ull;  // ceil(2^64 / bin_ms)
   g.v_stop = cfg->v_stop_kmh;
   g.radius_m = cfg->earth_radius_m;
   g.asin_c1 = 2.0 * cfg->earth_radius_m;

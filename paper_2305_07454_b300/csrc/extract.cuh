@@ -156,18 +156,17 @@ __global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J
 
 // Every kept row goes to its journey's bucket (the order inside a bucket is arbitrary; the
 // journey kernel sorts it by (timestamp, row index)). The counting pass left each row's hash
-// slot (or kKeyInvalid for a dropped row), so no probe is needed here. Four rows per thread per
-// iteration keep four atomic -> store chains in flight; each record is one 32-byte store, with
-// the point's cell x bin key computed here (this kernel waits on memory, so the keying
-// arithmetic is free) and its row index stored beside it.
+// slot (or kKeyInvalid for a dropped row), so no probe is needed here. U rows per thread per
+// iteration keep U atomic -> store chains in flight. Each record, with its row index, is one
+// 32-byte store at the bucket cursor: consecutive cursor positions of a journey are written in
+// the order the atomics hand them out, so L2 assembles whole lines before writing them back.
 template <int U>
 __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lat,
                                                  const double* __restrict__ lon,
                                                  const float* __restrict__ spd,
                                                  const uint32_t* __restrict__ row_slot, uint32_t n,
-                                                 Hash h, GridParams g, Batch bt, Rec* __restrict__ rec,
-                                                 uint32_t* __restrict__ ridx) {
+                                                 Hash h, Rec* __restrict__ rec) {
   const uint32_t step = gridDim.x * blockDim.x * U;
   for (uint32_t i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < n; i0 += step) {
     uint32_t slot[U], pos[U];
@@ -183,19 +182,14 @@ __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
     for (int u = 0; u < U; ++u) {
       if (slot[u] == kKeyInvalid) continue;
       const uint32_t i = i0 + u * blockDim.x;
-      const int64_t t = ts[i];
-      const double la = lat[i], lo = lon[i];
-      const uint32_t key = bt.n_inst ? batch_cell_key(la, lo, t, g, bt.inst[inst_of_row(bt, i)])
-                                     : cell_key(la, lo, t, g);
-      const unsigned long long a = (unsigned long long)t;
-      const unsigned long long b = (unsigned long long)__double_as_longlong(la);
-      const unsigned long long c = (unsigned long long)__double_as_longlong(lo);
+      const unsigned long long a = (unsigned long long)ts[i];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(lat[i]);
+      const unsigned long long c = (unsigned long long)__double_as_longlong(lon[i]);
       const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(spd[i])) |
-                                   ((unsigned long long)key << 32);
+                                   ((unsigned long long)i << 32);
       asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + pos[u]), "l"(a), "l"(b),
                    "l"(c), "l"(d)
                    : "memory");
-      ridx[pos[u]] = i;
     }
   }
 }

@@ -80,14 +80,13 @@ __device__ __forceinline__ void bitonic_smem(Elem* E, int P) {
   }
 }
 
-__device__ __forceinline__ void load_elems(Elem* E, const Rec* __restrict__ R, const uint32_t* __restrict__ RI,
-                                           int base, int m, int P) {
+__device__ __forceinline__ void load_elems(Elem* E, const Rec* __restrict__ R, int base, int m, int P) {
   for (int i = threadIdx.x; i < P; i += kJBlock) {
     Elem e;
     if (i < m) {
       const Rec* r = R + base + i;
       e.t = (unsigned long long)r->ts ^ kSign64;
-      e.idx = RI[base + i];
+      e.idx = r->idx;
       e.pos = (uint32_t)(base + i);
     } else {
       e.t = ~0ull;
@@ -113,13 +112,12 @@ __device__ __forceinline__ int merge_path(const Elem* A, int la, const Elem* B, 
 // Sorts a journey by (timestamp, row) pairs: shared-memory bitonic sort of kEChunk chunks, then rounds
 // of CTA-wide merge-path merges between two global scratch buffers. Returns the buffer
 // holding the sorted elements.
-__device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, const uint32_t* __restrict__ RI, int n,
-                                Elem* A, Elem* B) {
+__device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem* A, Elem* B) {
   for (int c0 = 0; c0 < n; c0 += kEChunk) {
     int m = min(kEChunk, n - c0);
     int P = 1;
     while (P < m) P <<= 1;
-    load_elems(E, R, RI, c0, m, P);
+    load_elems(E, R, c0, m, P);
     bitonic_smem(E, P);
     for (int i = threadIdx.x; i < m; i += kJBlock) A[c0 + i] = E[i];
     __syncthreads();
@@ -473,7 +471,7 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
 
 // Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
 // slot (arbitrary) here; reorder each such group by extracted-row index.
-__device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const uint32_t* __restrict__ RI) {
+__device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
   const unsigned long long mask = (1ull << pos_bits) - 1;
   for (int k = threadIdx.x; k < n; k += kJBlock) {
     const unsigned long long t = K[k] >> pos_bits;
@@ -483,9 +481,9 @@ __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const uint3
       while (e < n && (K[e] >> pos_bits) == t) ++e;
       for (int i = k + 1; i < e; ++i) {  // insertion sort by row index
         const unsigned long long v = K[i];
-        const uint32_t vi = RI[v & mask];
+        const uint32_t vi = R[v & mask].idx;
         int q = i - 1;
-        while (q >= k && RI[K[q] & mask] > vi) {
+        while (q >= k && R[K[q] & mask].idx > vi) {
           K[q + 1] = K[q];
           --q;
         }
@@ -749,10 +747,10 @@ __device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlo
 // of this journey except the run copy-out (the caller synchronises before the next journey).
 template <class Form>
 __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ rec,
-                                            const uint32_t* __restrict__ ridx,
                                             const uint32_t* __restrict__ jn,
                                             const uint32_t* __restrict__ joff, Elem* scrA, Elem* scrB,
-                                            const GridParams& g, const JourneyOut& o, DevState* st,
+                                            const GridParams& g, const Batch& bt, const JourneyOut& o,
+                                            DevState* st,
                                             const uint32_t* __restrict__ jslot, const JState& js) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SortSmem ssort;
@@ -772,8 +770,9 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
-  const uint32_t* RI = ridx + off;  // row index of each bucket position
   const bool small = n <= kJCap;
+  // the grid and day the journey's points are keyed on (a journey lies in one batch instance)
+  const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, R[0].idx) : nullptr;
   // stream mode: the journey continues from its state (last point, open run, running sums)
   const bool stream = js.n != nullptr;
   const uint32_t slot = stream ? jslot[j] : 0u;
@@ -829,12 +828,12 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       __syncthreads();
       K = cta_radix_sort(GA, GB, n, nbits, ssort);
     }
-    fix_ties(K, n, pos_bits, RI);
+    fix_ties(K, n, pos_bits, R);
     sortedK = K;
   } else {
     // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
     if (tid == 0) atomicAdd(&st->n_big, 1u);
-    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, RI, n, scrA + off, scrB + off);
+    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
   }
   const unsigned long long pmask = (1ull << pos_bits) - 1;
 
@@ -859,7 +858,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       p_lon = q.lon;
       p_spd = q.spd;
       p_cos = Form::cosine(q.lat, g);
-      run.key = q.key;
+      run.key = point_key(q.lat, q.lon, q.ts, g, bi);
       run.mn = __int_as_float(0x7F800000);   // +inf
       run.mx = __int_as_float((int)0xFF800000u);  // -inf
       in_pre = true;  // an empty fragment of the previous thread's run
@@ -879,13 +878,12 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     Rec nxt = R[nxt_p];
     for (int k = k0; k < k1; ++k) {
       const Rec cur = nxt;
-      const uint32_t cur_p = nxt_p;
       if (k + 1 < k1) {
         nxt_p = radix ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos;
         nxt = R[nxt_p];
       }
       const typename Form::Cos ccur = Form::cosine(cur.lat, g);
-      const uint32_t key = cur.key;
+      const uint32_t key = point_key(cur.lat, cur.lon, cur.ts, g, bi);
       uint8_t fl = 0;
       typename Form::Dist d = 0;
       float vh = 0.0f, ac = 0.0f;
@@ -915,7 +913,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       if (key == kKeyInvalid) fl |= kFOffgrid;
       if (o.perm) {
         const uint32_t gp = off + (uint32_t)k;
-        o.perm[gp] = RI[cur_p];
+        o.perm[gp] = cur.idx;
         o.d[gp] = (double)d;
         o.vhat[gp] = vh;
         o.accel[gp] = ac;
@@ -1043,16 +1041,16 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
 // dispatch order then gives the same longest-first start without the loop.
 template <class Form, bool Persistent>
 __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
-                                                         const uint32_t* __restrict__ ridx,
                                                          const uint32_t* __restrict__ jn,
                                                          const uint32_t* __restrict__ joff, uint32_t J,
-                                                         Elem* scrA, Elem* scrB, GridParams g,
+                                                         Elem* scrA, Elem* scrB, GridParams g, Batch bt,
                                                          JourneyOut o, DevState* st,
                                                          const uint32_t* __restrict__ jslot, JState js,
                                                          const uint32_t* __restrict__ order, uint32_t* work) {
   if constexpr (!Persistent) {
     if (blockIdx.x < J)
-      journey_one<Form>(order ? order[blockIdx.x] : blockIdx.x, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
+      journey_one<Form>(order ? order[blockIdx.x] : blockIdx.x, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot,
+                        js);
   } else {
     __shared__ uint32_t s_w;
     for (;;) {
@@ -1061,7 +1059,7 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       const uint32_t w = s_w;
       __syncthreads();
       if (w >= J) break;
-      journey_one<Form>(order ? order[w] : w, rec, ridx, jn, joff, scrA, scrB, g, o, st, jslot, js);
+      journey_one<Form>(order ? order[w] : w, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot, js);
       __syncthreads();
     }
   }

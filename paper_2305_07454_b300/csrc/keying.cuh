@@ -1,6 +1,6 @@
 // keying.cuh — the grid / time-bin key of Algorithm 2 (row, column and bin by floor division,
-// unrolled into one positional index), shared by the kernels that key points: the scatter of
-// the batch path and the append of the stream path.
+// unrolled into one positional index), computed per point by the journey kernel (batch and
+// stream paths) and, with a direction channel, by the lattice.
 #pragma once
 #include "common.cuh"
 
@@ -18,6 +18,7 @@ struct GridParams {
   int32_t n_rows, n_cols, n_bins;
   int64_t t0_ms, bin_ms;
   unsigned long long t_span;  // n_bins * bin_ms, saturated
+  unsigned long long bin_magic;  // ceil(2^64 / bin_ms) (0 for bin_ms = 1): see bin_of
   float v_stop;
   double radius_m;
   const CosEntry* cos_tab;  // k = -9000..9000
@@ -42,15 +43,35 @@ __device__ __forceinline__ float leading_f32(double x) {
   return __int_as_float((int)(sign | ((uint32_t)(e - 1023 + 127) << 23) | mant));
 }
 
+// n >= 1. The cell is the r with thr[r] <= u < thr[r + 1]; both bounds of the estimate are
+// loaded together, and a step past either end of the table means off the grid.
 __device__ __forceinline__ int grid_index(double x, const unsigned long long* __restrict__ thr,
                                           int n, float xmin_f, float inv_f) {
-  unsigned long long u = ord_f64(x);
-  if (u < __ldg(&thr[0]) || u >= __ldg(&thr[n])) return -1;
+  const unsigned long long u = ord_f64(x);
   int r = __float2int_rd((leading_f32(x) - xmin_f) * inv_f);
   r = max(0, min(n - 1, r));
-  while (r > 0 && u < __ldg(&thr[r])) --r;
-  while (r < n - 1 && u >= __ldg(&thr[r + 1])) ++r;
+  unsigned long long lo = __ldg(&thr[r]), hi = __ldg(&thr[r + 1]);
+  while (u < lo) {
+    if (r == 0) return -1;
+    --r;
+    hi = lo;
+    lo = __ldg(&thr[r]);
+  }
+  while (u >= hi) {
+    if (r == n - 1) return -1;
+    ++r;
+    lo = hi;
+    hi = __ldg(&thr[r + 1]);
+  }
   return r;
+}
+
+// floor(off / bin_ms) for off < t_span. Below 2^32 by one multiply-high with c = ceil(2^64 / d):
+// floor(x / d) = floor(c x / 2^64) for every 32-bit x and 32-bit d (Lemire, Kaser and Kurz,
+// "Faster remainder by direct computation", 2019, with 64-bit fractions for 32-bit words).
+__device__ __forceinline__ uint32_t bin_of(unsigned long long off, const GridParams& g) {
+  if (g.t_span <= 0xFFFFFFFFull) return g.bin_magic ? (uint32_t)__umul64hi(g.bin_magic, off) : (uint32_t)off;
+  return (uint32_t)(off / (unsigned long long)g.bin_ms);
 }
 
 // bin = floor((ts - t0) / bin_ms) when 0 <= bin < n_bins, else -1 (exact integer arithmetic).
@@ -58,8 +79,7 @@ __device__ __forceinline__ int time_bin(int64_t ts, const GridParams& g) {
   if (ts < g.t0_ms) return -1;
   unsigned long long off = (unsigned long long)ts - (unsigned long long)g.t0_ms;
   if (off >= g.t_span) return -1;
-  if (g.t_span <= 0xFFFFFFFFull) return (int)((uint32_t)off / (uint32_t)g.bin_ms);
-  return (int)(off / (unsigned long long)g.bin_ms);
+  return (int)bin_of(off, g);
 }
 
 __device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts, const GridParams& g) {
@@ -132,9 +152,15 @@ __device__ __forceinline__ uint32_t batch_cell_key(double lat, double lon, int64
   if (r < 0 || c < 0 || ts < bi.t0_ms) return kKeyInvalid;
   const unsigned long long off = (unsigned long long)ts - (unsigned long long)bi.t0_ms;
   if (off >= g.t_span) return kKeyInvalid;
-  const int b = (g.t_span <= 0xFFFFFFFFull) ? (int)((uint32_t)off / (uint32_t)g.bin_ms)
-                                            : (int)(off / (unsigned long long)g.bin_ms);
+  const int b = (int)bin_of(off, g);
   return bi.key_off + ((uint32_t)b * (uint32_t)bi.n_rows + (uint32_t)r) * (uint32_t)bi.n_cols + (uint32_t)c;
+}
+
+// The key of a point: of the single instance described by g (bi == nullptr) or of batch
+// instance *bi.
+__device__ __forceinline__ uint32_t point_key(double lat, double lon, int64_t ts, const GridParams& g,
+                                              const BatchInst* bi) {
+  return bi ? batch_cell_key(lat, lon, ts, g, *bi) : cell_key(lat, lon, ts, g);
 }
 
 }  // namespace cvetl

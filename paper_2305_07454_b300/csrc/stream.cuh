@@ -14,10 +14,9 @@
 
 namespace cvetl {
 
-// Appends the window's kept rows to the pending store after its first p_base entries (arrival
-// index = arrival_base + row, kept in p_idx; the record carries the point's cell x bin key;
-// st->n_pending counts the appended rows); rows whose timestamp is below the previous watermark
-// are dropped as too late.
+// Appends the window's kept rows to the pending store after its first p_base entries (the
+// record carries its arrival index arrival_base + row; st->n_pending counts the appended rows);
+// rows whose timestamp is below the previous watermark are dropped as too late.
 __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict__ jid,
                                                        const int64_t* __restrict__ ts,
                                                        const double* __restrict__ lat,
@@ -25,9 +24,8 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
                                                        const float* __restrict__ spd, uint32_t n,
                                                        uint32_t arrival_base, int64_t w_prev,
                                                        int has_w_prev, int64_t* __restrict__ p_jid,
-                                                       Rec* __restrict__ p_rec,
-                                                       uint32_t* __restrict__ p_idx, uint32_t p_base,
-                                                       uint32_t p_cap, GridParams g, DevState* st) {
+                                                       Rec* __restrict__ p_rec, uint32_t p_base,
+                                                       uint32_t p_cap, DevState* st) {
   __shared__ unsigned long long scratch[8];
   unsigned long long bad = 0, late = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -53,9 +51,8 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
     r.lat = la;
     r.lon = lo;
     r.spd = canon_speed(sp);
-    r.key = cell_key(la, lo, t, g);
+    r.idx = arrival_base + i;
     p_rec[o] = r;
-    p_idx[o] = arrival_base + i;
   }
   const unsigned long long b = block_sum<256, unsigned long long>(bad, scratch);
   const unsigned long long l = block_sum<256, unsigned long long>(late, scratch);
@@ -69,12 +66,10 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
 // slot and the count per journey; st->n_final), the rest to the next pending store
 // (st->n_pending).
 __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict__ p_jid,
-                                                      const Rec* __restrict__ p_rec,
-                                                      const uint32_t* __restrict__ p_idx, uint32_t n,
+                                                      const Rec* __restrict__ p_rec, uint32_t n,
                                                       int64_t wm, int finalize_all, Hash h,
                                                       int64_t* __restrict__ q_jid, Rec* __restrict__ q_rec,
-                                                      uint32_t* __restrict__ q_idx, Rec* __restrict__ f_rec,
-                                                      uint32_t* __restrict__ f_idx,
+                                                      Rec* __restrict__ f_rec,
                                                       uint32_t* __restrict__ f_slot, DevState* st) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Rec r = p_rec[i];
@@ -88,13 +83,11 @@ __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict_
       atomicAdd(&h.cnt[s], 1u);
       const uint32_t o = atomicAdd(&st->n_final, 1u);
       f_rec[o] = r;
-      f_idx[o] = p_idx[i];
       f_slot[o] = (uint32_t)s;
     } else {
       const uint32_t o = atomicAdd(&st->n_pending, 1u);
       q_jid[o] = id;
       q_rec[o] = r;
-      q_idx[o] = p_idx[i];
     }
   }
 }
@@ -113,14 +106,11 @@ __global__ void k_stream_touched(Hash h, unsigned long long* __restrict__ ukey,
 }
 
 __global__ void __launch_bounds__(256) k_stream_scatter(const Rec* __restrict__ f_rec,
-                                                        const uint32_t* __restrict__ f_idx,
                                                         const uint32_t* __restrict__ f_slot,
-                                                        uint32_t n, Hash h, Rec* __restrict__ rec,
-                                                        uint32_t* __restrict__ ridx) {
+                                                        uint32_t n, Hash h, Rec* __restrict__ rec) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t pos = atomicAdd(&h.aux[f_slot[i]], 1u);
     rec[pos] = f_rec[i];
-    ridx[pos] = f_idx[i];
   }
 }
 

@@ -161,6 +161,18 @@ def test_cell_edges_exactly(orc):
     compare(run_gpu(cols), orc.run(cols))
 
 
+@pytest.mark.parametrize("bin_ms,n_bins", [(1, 13000), (7, 9000), (1000, 7200), (60000, 1440),
+                                            (2 ** 31 - 1, 2), (2 ** 32 + 5, 1)])
+def test_time_bins_of_any_width(orc, bin_ms, n_bins):
+    """Algorithm 2's time bin, floor((ts - t0) / bin_ms), for bin widths from 1 ms to past 2^32
+    ms: spans below 2^32 take the multiply-high division, wider ones the 64-bit division."""
+    import oracle
+
+    cols = synth([300, 1000, 37, 5000], seed=11)
+    cfg = dict(bin_ms=bin_ms, n_bins=n_bins, t0_ms=int(cols["ts"].min()) - 5)
+    compare(run_gpu(cols, **cfg), orc.run(cols, oracle.default_params(**cfg)))
+
+
 def test_aggregates_only_mode_matches(orc, small_day):
     g = run_gpu(small_day, materialize=False)
     assert "points" not in g
