@@ -206,8 +206,9 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out);
  * '\n'); a row is exactly six ','-separated fields jid,ts,lat,lon,speed,heading; jid and ts
  * match -?[0-9]{1,18}; the others match -?[0-9]+(\.[0-9]+)? with at most 15 digits and take the
  * binary64 value nearest to the decimal (speed and heading then rounded to float32);
- * |lat| <= 90 and |lon| <= 180. Any other line (empty lines included) is counted in
- * n_malformed and dropped; n_in counts lines. Kept rows keep file order as their row index.
+ * |lat| <= 90 and |lon| <= 180. Every line is a row and its row index is its line number
+ * (0-based, file order); any other line (empty lines included) becomes the row
+ * (0, 0, NaN, NaN, NaN, NaN), which is dropped and counted in n_malformed; n_in counts lines.
  * Replaces the context's previous batch. Returns CVETL_EINVAL for NULL columns or
  * n outside [0, CVETL_MAX_RECORDS], CVETL_EFULL if the budget is exceeded. */
 cvetl_status cvetl_extract(cvetl_ctx* ctx, const cvetl_input* in);

@@ -182,7 +182,8 @@ class Oracle:
 
     # ---- extract ----
     def parse_csv(self, buf: np.ndarray | bytes):
-        """Returns (columns dict, n_lines, n_malformed)."""
+        """Returns (columns dict, n_lines, n_malformed): one row per line, malformed lines as
+        rows (0, 0, NaN, NaN, NaN, NaN) that the extract drops."""
         if isinstance(buf, (bytes, bytearray)):
             buf = np.frombuffer(bytes(buf), dtype=np.uint8)
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
@@ -191,13 +192,13 @@ class Oracle:
                     lat=np.empty(cap, np.float64), lon=np.empty(cap, np.float64),
                     speed=np.empty(cap, np.float32), heading=np.empty(cap, np.float32))
         nl, nm = ctypes.c_int64(), ctypes.c_int64()
-        kept = self.lib.orc_parse_csv(buf.ctypes.data, buf.shape[0], cap,
+        rows = self.lib.orc_parse_csv(buf.ctypes.data, buf.shape[0], cap,
                                       *[cols[c].ctypes.data for c in
                                         ("jid", "ts", "lat", "lon", "speed", "heading")],
                                       ctypes.byref(nl), ctypes.byref(nm))
-        if kept < 0:
+        if rows < 0:
             raise RuntimeError("orc_parse_csv: capacity too small")
-        return {k: v[:kept].copy() for k, v in cols.items()}, int(nl.value), int(nm.value)
+        return {k: v[:rows].copy() for k, v in cols.items()}, int(nl.value), int(nm.value)
 
     # ---- whole path ----
     def run(self, cols: dict, params: Params | None = None) -> dict:

@@ -106,28 +106,30 @@ static int parse_row(const char* s, int64_t len, int64_t* jid, int64_t* ts, doub
 int64_t orc_parse_csv(const char* buf, int64_t len, int64_t cap, int64_t* jid, int64_t* ts,
                       double* lat, double* lon, float* speed, float* heading,
                       int64_t* n_lines, int64_t* n_malformed) {
-  int64_t kept = 0, lines = 0, bad = 0;
+  int64_t lines = 0, bad = 0;
   int64_t b = 0;
   while (b < len) {
     int64_t e = b;
     while (e < len && buf[e] != '\n') e++;
-    lines++;
+    if (lines >= cap) return -1; /* the caller's columns are too short */
     int64_t j, t;
     double la, lo;
     float sp, hd;
     if (parse_row(buf + b, e - b, &j, &t, &la, &lo, &sp, &hd)) {
-      if (kept >= cap) return -1; /* the caller's columns are too short */
-      jid[kept] = j; ts[kept] = t; lat[kept] = la; lon[kept] = lo;
-      speed[kept] = sp; heading[kept] = hd;
-      kept++;
+      jid[lines] = j; ts[lines] = t; lat[lines] = la; lon[lines] = lo;
+      speed[lines] = sp; heading[lines] = hd;
     } else {
+      /* a record without a position: the extract drops it as malformed */
+      jid[lines] = 0; ts[lines] = 0; lat[lines] = NAN; lon[lines] = NAN;
+      speed[lines] = NAN; heading[lines] = NAN;
       bad++;
     }
+    lines++;
     b = e + 1; /* skip the '\n'; a final line without '\n' ends at len */
   }
   *n_lines = lines;
   *n_malformed = bad;
-  return kept;
+  return lines;
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -103,9 +103,10 @@ int orc_parse_decimal(const char* s, int64_t len, double* out);
 /* Integer field -> int64, per the CSV grammar. */
 int orc_parse_integer(const char* s, int64_t len, int64_t* out);
 
-/* Parse CSV text. Writes kept rows (file order) to the columns, which must have room for
- * every line. Returns the number of kept rows (-1 if cap is too small); *n_lines and
- * *n_malformed are set. */
+/* Parse CSV text. Every line is a row, in file order (its extracted-row index is its line
+ * number); a line that breaks the grammar becomes the row (0, 0, NaN, NaN, NaN, NaN), which
+ * the extract drops as malformed. The columns must have room for every line. Returns the
+ * number of rows (-1 if cap is too small); *n_lines and *n_malformed are set. */
 int64_t orc_parse_csv(const char* buf, int64_t len, int64_t cap,
                       int64_t* jid, int64_t* ts, double* lat, double* lon,
                       float* speed, float* heading,

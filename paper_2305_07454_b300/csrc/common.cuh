@@ -30,7 +30,6 @@ struct DevState {
   unsigned long long n_malformed;
   unsigned long long n_dup;
   unsigned long long n_offgrid;
-  unsigned long long n_lines;  // CSV: lines in the text
   unsigned long long n_too_late;  // stream mode: records older than the previous watermark
   uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
 };

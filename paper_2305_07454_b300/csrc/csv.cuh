@@ -7,7 +7,11 @@
 //   value    = the binary64 value nearest to M / 10^k (M the digits as an integer, k the number
 //              of fraction digits), i.e. one round-to-nearest division of two exact binary64s
 //   range    = |lat| <= 90 and |lon| <= 180; speed and heading are rounded to float32
-// A row breaking any rule is dropped and counted as malformed.
+// Every line is a row, in file order, and its extracted-row index is its line number; a line
+// breaking any rule becomes the row (0, 0, NaN, NaN, NaN, NaN), which the extract drops and
+// counts as malformed. Row i's place in the columns is then known from the line starts alone:
+// tile t's first row is the number of line starts before it (a prefix sum of per-tile counts),
+// so tiles are parsed independently, with no ordering between them.
 //
 // Decimal conversion uses no floating-point division: M / 10^k = (M / 5^k) * 2^-k, and
 // M / 5^k is computed exactly as an integer quotient of M * 2^t (128-bit) by 5^k through a
@@ -21,7 +25,6 @@ namespace cvetl {
 constexpr int kCsvTile = 12288;  // bytes per tile (multiple of 16)
 constexpr int kCsvHalo = 1024;   // bytes past the tile kept in shared memory (lines crossing its end)
 constexpr int kCsvBlock = 256;
-constexpr int kCsvRounds = 4;    // lines per thread kept in registers (tiles of <= 1024 lines)
 
 __constant__ unsigned long long kPow5[16] = {1ull, 5ull, 25ull, 125ull, 625ull, 3125ull, 15625ull,
                                              78125ull, 390625ull, 1953125ull, 9765625ull,
@@ -292,53 +295,56 @@ struct CsvOut {
   float *speed, *heading;
 };
 
-// Pass 1: count '\n' bytes; the number of lines is at most that count + 1.
-__global__ void __launch_bounds__(kCsvBlock) k_csv_count(const unsigned char* __restrict__ buf,
-                                                         unsigned long long len,
-                                                         unsigned long long* __restrict__ n_lines) {
-  __shared__ unsigned long long scratch[kCsvBlock / 32];
-  unsigned long long c = 0;
-  const unsigned long long stride = (unsigned long long)gridDim.x * kCsvBlock * 16;
-  for (unsigned long long b0 = ((unsigned long long)blockIdx.x * kCsvBlock + threadIdx.x) * 16; b0 < len;
-       b0 += stride) {
-    if (b0 + 16 <= len) {
-      const uint4 v = *reinterpret_cast<const uint4*>(buf + b0);
-      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+// Pass 1: line starts per tile. Byte b starts a line when b = 0 or byte b - 1 is '\n', so a
+// tile's count is its newlines, less one for a newline in its last byte, plus one for a newline
+// just before it (or for the first tile).
+__global__ void __launch_bounds__(kCsvBlock) k_csv_tile_lines(const unsigned char* __restrict__ buf,
+                                                              unsigned long long len, uint32_t n_tiles,
+                                                              uint32_t* __restrict__ lines,
+                                                              unsigned long long* __restrict__ total) {
+  __shared__ uint32_t scratch[kCsvBlock / 32];
+  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const unsigned long long base = (unsigned long long)t * kCsvTile;
+    const unsigned long long end = min(base + (unsigned long long)kCsvTile, len);
+    uint32_t c = 0;
+    for (unsigned long long b0 = base + threadIdx.x * 16ull; b0 < end; b0 += kCsvBlock * 16ull) {
+      if (b0 + 16 <= end) {
+        const uint4 v = *reinterpret_cast<const uint4*>(buf + b0);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t x = w[q] ^ 0x0A0A0A0Au;  // bytes equal to '\n' become 0
-        c += __popc((x - 0x01010101u) & ~x & 0x80808080u);
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t x = w[q] ^ 0x0A0A0A0Au;  // bytes equal to '\n' become 0
+          c += __popc((x - 0x01010101u) & ~x & 0x80808080u);
+        }
+      } else {
+        for (unsigned long long p = b0; p < end; ++p) c += buf[p] == '\n';
       }
-    } else {
-      for (unsigned long long p = b0; p < len; ++p) c += buf[p] == '\n';
+    }
+    c = block_sum<kCsvBlock, uint32_t>(c, scratch);  // ends with a barrier: scratch is free again
+    if (threadIdx.x == 0) {
+      const uint32_t before = (base == 0) ? 1u : (buf[base - 1] == '\n' ? 1u : 0u);
+      const uint32_t l = c - (buf[end - 1] == '\n' ? 1u : 0u) + before;
+      lines[t] = l;
+      atomicAdd(total, (unsigned long long)l);  // 64-bit: the caller checks the 32-bit prefix sums
     }
   }
-  // (line starts <= newlines + 1: the caller sizes its columns with that bound)
-  c = block_sum<kCsvBlock, unsigned long long>(c, scratch);
-  if (threadIdx.x == 0 && c) atomicAdd(n_lines, c);
 }
 
-// Pass 2: parse. Tiles are taken in order (ticket); each tile publishes its count of kept rows
-// and looks back over earlier tiles for its first output row, so rows keep file order (the last
-// tile's inclusive count is the number of kept rows). Inside a tile, one pass turns the bytes
-// into newline and comma bit masks; line starts, line ends and field separators then come from
-// the masks, and the digits are read eight at a time.
+// Pass 2: parse tile blockIdx.x, whose first row is tile_row[blockIdx.x]. One pass turns the
+// staged bytes into newline and comma bit masks; line starts, line ends and field separators
+// then come from the masks, and the digits are read eight at a time. Line i of the tile is row
+// tile_row + i: consecutive threads write consecutive rows.
 __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __restrict__ buf,
-                                                         unsigned long long len, uint32_t n_tiles,
-                                                         CsvOut out, uint32_t cap,
-                                                         uint32_t* status, uint32_t* tile_ctr,
-                                                         DevState* st) {
+                                                         unsigned long long len,
+                                                         const uint32_t* __restrict__ tile_row, CsvOut out,
+                                                         uint32_t cap, DevState* st) {
   __shared__ __align__(16) unsigned char s_buf[kCsvTile + kCsvHalo + 32];
   __shared__ uint32_t s_nl[(kCsvTile + kCsvHalo) / 32 + 1], s_cm[(kCsvTile + kCsvHalo) / 32 + 1];
   __shared__ uint16_t s_start[kCsvTile];
   __shared__ uint32_t s_scan[kCsvBlock / 32 + 1];
-  __shared__ uint32_t s_tile, s_base;
   __shared__ unsigned char s_prev;
   const int tid = threadIdx.x;
-  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  if (tile >= n_tiles) return;
+  const uint32_t tile = blockIdx.x;
   const unsigned long long base = (unsigned long long)tile * kCsvTile;
   const int tlen = (int)min((unsigned long long)kCsvTile, len - base);
   const int wlen = (int)min((unsigned long long)(kCsvTile + kCsvHalo), len - base);
@@ -399,74 +405,32 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   }
   __syncthreads();
   const int nstart = (int)total;
-  // parse the lines starting here; keep up to kCsvRounds per thread in registers
-  const bool in_regs = nstart <= kCsvRounds * kCsvBlock;
-  int64_t vj[kCsvRounds], vt[kCsvRounds];
-  double vla[kCsvRounds], vlo[kCsvRounds];
-  float vs[kCsvRounds], vh[kCsvRounds];
-  bool ok[kCsvRounds];
-  uint32_t mine = 0;
-  auto parse_at = [&](int i, int64_t& a, int64_t& b, double& c, double& d, float& e, float& f) -> bool {
-    const int st = s_start[i];
+  const uint32_t row0 = tile_row[tile];
+  for (int i = tid; i < nstart; i += kCsvBlock) {
+    const int sl = s_start[i];
     // the line's end: the next newline bit at or after its start
-    int w = st >> 5;
-    uint32_t m = s_nl[w] & (~0u << (st & 31));
+    int w = sl >> 5;
+    uint32_t m = s_nl[w] & (~0u << (sl & 31));
     while (!m && ++w < nmask) m = s_nl[w];
-    if (m) return parse_line_masked(s_buf, s_cm, st, w * 32 + __ffs(m) - 1, a, b, c, d, e, f);
-    if (base + wlen == len) return parse_line_masked(s_buf, s_cm, st, wlen, a, b, c, d, e, f);
-    // the line runs past the staged window: read it from global memory
-    unsigned long long g = base + wlen;
-    while (g < len && buf[g] != '\n') ++g;
-    return parse_row(buf + base + st, (int)(g - (base + st)), a, b, c, d, e, f);
-  };
-  const int rounds = (nstart + kCsvBlock - 1) / kCsvBlock;  // block-uniform
-  if (in_regs) {
-#pragma unroll
-    for (int u = 0; u < kCsvRounds; ++u) {
-      const int i = tid + u * kCsvBlock;
-      ok[u] = (u < rounds) && (i < nstart) && parse_at(i, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
-      mine += ok[u];
+    int64_t a, b;
+    double c, d;
+    float e, f;
+    bool ok;
+    if (m) {
+      ok = parse_line_masked(s_buf, s_cm, sl, w * 32 + __ffs(m) - 1, a, b, c, d, e, f);
+    } else if (base + wlen == len) {
+      ok = parse_line_masked(s_buf, s_cm, sl, wlen, a, b, c, d, e, f);
+    } else {  // the line runs past the staged window: read it from global memory
+      unsigned long long g = base + wlen;
+      while (g < len && buf[g] != '\n') ++g;
+      ok = parse_row(buf + base + sl, (int)(g - (base + sl)), a, b, c, d, e, f);
     }
-  } else {
-    for (int i = tid; i < nstart; i += kCsvBlock) {
-      int64_t a, b;
-      double c, d;
-      float e, f;
-      mine += parse_at(i, a, b, c, d, e, f);
+    if (!ok) {  // a row without a position
+      a = b = 0;
+      c = d = __longlong_as_double(0x7FF8000000000000ll);
+      e = f = __int_as_float(0x7FC00000);
     }
-  }
-  uint32_t tile_valid;
-  block_excl_scan<kCsvBlock>(mine, s_scan, &tile_valid);
-  // look back for the first output row of this tile
-  if (tid == 0) {
-    uint32_t excl = 0;
-    if (tile == 0) {
-      st_relaxed_u32(status, (2u << 30) | tile_valid);
-    } else {
-      st_relaxed_u32(status + tile, (1u << 30) | tile_valid);
-      for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
-        uint32_t s = ld_relaxed_u32(status + p);
-        int spins = 0;
-        while ((s >> 30) == 0) {
-          if (++spins > (1 << 22)) break;
-          __nanosleep(32);
-          s = ld_relaxed_u32(status + p);
-        }
-        if ((s >> 30) == 0) {
-          atomicOr(&st->err, kErrLookbackTimeout);
-          break;
-        }
-        excl += s & ((1u << 30) - 1);
-        if ((s >> 30) == 2u) break;
-      }
-      st_relaxed_u32(status + tile, (2u << 30) | (excl + tile_valid));
-    }
-    s_base = excl;
-  }
-  __syncthreads();
-  // write the kept rows in file order (line i of the tile before line i + 1)
-  uint32_t pos = s_base;
-  auto put = [&](uint32_t o, int64_t a, int64_t b, double c, double d, float e, float f) {
+    const uint32_t o = row0 + (uint32_t)i;
     if (o < cap) {
       out.jid[o] = a;
       out.ts[o] = b;
@@ -476,28 +440,6 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
       out.heading[o] = f;
     } else {
       atomicOr(&st->err, kErrCapacity);
-    }
-  };
-  if (in_regs) {
-#pragma unroll
-    for (int u = 0; u < kCsvRounds; ++u) {
-      if (u >= rounds) break;  // block-uniform: the scans below stay collective
-      uint32_t round_total;
-      const uint32_t rk = block_excl_scan<kCsvBlock>(ok[u] ? 1u : 0u, s_scan, &round_total);
-      if (ok[u]) put(pos + rk, vj[u], vt[u], vla[u], vlo[u], vs[u], vh[u]);
-      pos += round_total;
-    }
-  } else {  // a tile of very short lines: parse again
-    for (int i0 = 0; i0 < nstart; i0 += kCsvBlock) {
-      const int i = i0 + tid;
-      int64_t a = 0, b = 0;
-      double c = 0.0, d = 0.0;
-      float e = 0.f, f = 0.f;
-      const bool v = (i < nstart) && parse_at(i, a, b, c, d, e, f);
-      uint32_t round_total;
-      const uint32_t rk = block_excl_scan<kCsvBlock>(v ? 1u : 0u, s_scan, &round_total);
-      if (v) put(pos + rk, a, b, c, d, e, f);
-      pos += round_total;
     }
   }
 }

@@ -386,8 +386,8 @@ uint32_t next_pow2(uint64_t v) {
 
 }  // namespace
 
-// CSV text -> parsed columns on the device (count pass sizes the columns; parse pass keeps
-// file order through a decoupled look-back over tiles).
+// CSV text -> parsed columns on the device: line starts per tile, their prefix sum (each
+// tile's first row; the total sizes the columns), then the tiles are parsed independently.
 cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
   const size_t len = in->csv_len;
   if (len && !in->csv) return fail(c, CVETL_EINVAL, "cvetl_extract: NULL csv");
@@ -401,51 +401,51 @@ cvetl_status extract_csv(cvetl_ctx* c, const cvetl_input* in) {
     CK(cudaMemcpyAsync(d, in->csv, len, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
     buf = d;
   }
-  unsigned long long* nl;
-  ENSURE("csv.newlines", 1, &nl);
-  CK(cudaMemsetAsync(nl, 0, 8, c->st));
-  if (len) {
-    LAUNCH(ST_CSV_COUNT, (k_csv_count<<<grid_for((len + 15) / 16, kCsvBlock), kCsvBlock, 0, c->st>>>(buf, len, nl)));
+  const uint32_t n_tiles = (uint32_t)((len + kCsvTile - 1) / kCsvTile);
+  uint32_t *tile_lines, *tile_row, *total;
+  unsigned long long* total64;
+  ENSURE("csv.tile_lines", (size_t)n_tiles, &tile_lines);
+  ENSURE("csv.tile_row", (size_t)n_tiles, &tile_row);
+  ENSURE("csv.lines", 1, &total);
+  ENSURE("csv.lines64", 1, &total64);
+  CK(cudaMemsetAsync(total64, 0, 8, c->st));
+  if (n_tiles) {
+    LAUNCH(ST_CSV_COUNT, (k_csv_tile_lines<<<grid_for((size_t)n_tiles * kCsvBlock, kCsvBlock), kCsvBlock, 0, c->st>>>(
+                             buf, len, n_tiles, tile_lines, total64)));
     LAUNCH_CHECK();
   }
-  unsigned long long newlines = 0;
-  unsigned char last = '\n';
+  {
+    cvetl_status s = scan_u32(c, tile_lines, n_tiles, tile_row, total);
+    if (s != CVETL_OK) return s;
+  }
+  unsigned long long lines64 = 0;
+  CK(cudaMemcpyAsync(&lines64, total64, 8, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  CK(cudaMemcpy(&newlines, nl, 8, cudaMemcpyDeviceToHost));
-  if (len) CK(cudaMemcpy(&last, buf + len - 1, 1, cudaMemcpyDeviceToHost));
-  const size_t n_lines = (size_t)newlines + (last != '\n' ? 1u : 0u);  // the last line may lack '\n'
-  const size_t cap = len ? (size_t)newlines + 1 : 0;
-  if (cap > (size_t)CVETL_MAX_RECORDS) return fail(c, CVETL_EINVAL, "the text holds more than %lld lines", (long long)CVETL_MAX_RECORDS);
+  if (lines64 > (unsigned long long)CVETL_MAX_RECORDS)  // (also keeps the 32-bit row offsets exact)
+    return fail(c, CVETL_EINVAL, "the text holds more than %lld lines", (long long)CVETL_MAX_RECORDS);
+  const uint32_t n_lines = (uint32_t)lines64;
   int64_t *jid, *ts;
   double *lat, *lon;
   float *spd, *hd;
-  ENSURE("csv.jid", cap, &jid);
-  ENSURE("csv.ts", cap, &ts);
-  ENSURE("csv.lat", cap, &lat);
-  ENSURE("csv.lon", cap, &lon);
-  ENSURE("csv.spd", cap, &spd);
-  ENSURE("csv.hd", cap, &hd);
-  const uint32_t n_tiles = (uint32_t)((len + kCsvTile - 1) / kCsvTile);
-  uint32_t *status, *tiles;
-  ENSURE("csv.status", (size_t)n_tiles + 1, &status);
-  ENSURE("csv.tiles", 1, &tiles);
-  CK(cudaMemsetAsync(status, 0, ((size_t)n_tiles + 1) * 4, c->st));
-  CK(cudaMemsetAsync(tiles, 0, 4, c->st));
+  ENSURE("csv.jid", n_lines, &jid);
+  ENSURE("csv.ts", n_lines, &ts);
+  ENSURE("csv.lat", n_lines, &lat);
+  ENSURE("csv.lon", n_lines, &lon);
+  ENSURE("csv.spd", n_lines, &spd);
+  ENSURE("csv.hd", n_lines, &hd);
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (n_tiles) {
     CsvOut o{jid, ts, lat, lon, spd, hd};
-    LAUNCH(ST_CSV_PARSE, (k_csv_parse<<<n_tiles, kCsvBlock, 0, c->st>>>(buf, len, n_tiles, o, (uint32_t)cap,
-                                                                         status, tiles, c->dstate)));
+    LAUNCH(ST_CSV_PARSE, (k_csv_parse<<<n_tiles, kCsvBlock, 0, c->st>>>(buf, len, tile_row, o, n_lines, c->dstate)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
   if (s != CVETL_OK) return s;
-  uint32_t kept = 0;  // the last tile's inclusive count of kept rows
-  if (n_tiles) CK(cudaMemcpy(&kept, status + n_tiles - 1, 4, cudaMemcpyDeviceToHost));
-  kept &= (1u << 30) - 1;
+  // malformed lines are rows without a position: the extract counts them with the other
+  // dropped rows
   c->n_in = (int64_t)n_lines;
-  c->csv_malformed = (int64_t)n_lines - (int64_t)kept;
-  c->n_rows = kept;
+  c->csv_malformed = 0;
+  c->n_rows = n_lines;
   c->jid = jid;
   c->ts = ts;
   c->lat = lat;
