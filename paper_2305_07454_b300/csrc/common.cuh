@@ -56,6 +56,27 @@ __host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
   return (b & kSign64) ? ~b : (b | kSign64);
 }
 
+// double -> float rounded to nearest even by the bit layout when the result is a normal float
+// (other values take the conversion instruction, which runs on the binary64 pipe).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FF);
+  if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  uint32_t keep = (uint32_t)(m >> 29);
+  const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
+  keep += (rest > half || (rest == half && (keep & 1u))) ? 1u : 0u;
+  // a mantissa carry moves into the exponent (and to infinity past the largest float)
+  return __uint_as_float((hi & 0x80000000u) | (((uint32_t)(e - 1023 + 127) << 23) + keep));
+}
+// The same, with zeros (frequent among parsed speeds) also kept off the binary64 pipe.
+__device__ __forceinline__ float f64_to_f32_rn_z(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  if ((b << 1) == 0) return __uint_as_float((uint32_t)(b >> 32));  // +-0
+  return f64_to_f32_rn(x);
+}
+
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
   k *= 0xff51afd7ed558ccdull;

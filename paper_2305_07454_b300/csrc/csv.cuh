@@ -13,10 +13,10 @@
 // tile t's first row is the number of line starts before it (a prefix sum of per-tile counts),
 // so tiles are parsed independently, with no ordering between them.
 //
-// Decimal conversion uses no floating-point division: M / 10^k = (M / 5^k) * 2^-k, and
-// M / 5^k is computed exactly as an integer quotient of M * 2^t (128-bit) by 5^k through a
-// 128-bit reciprocal ceil(2^128 / 5^k) with one correction step; the 55-57-bit quotient and its
-// remainder then give the round-to-nearest-even binary64 result directly.
+// Decimal conversion uses no floating-point division and no binary64 arithmetic:
+// M / 10^k = (M / 5^k) * 2^-k, and q = floor(M * 2^t / 5^k) (55-57 bits) comes from one 64 x 64
+// multiply-high of the left-justified M by a 64-bit reciprocal of 5^k, corrected once with the
+// exact remainder; q and the remainder then give the round-to-nearest-even binary64 result.
 #pragma once
 #include "common.cuh"
 
@@ -30,54 +30,42 @@ __constant__ unsigned long long kPow5[16] = {1ull, 5ull, 25ull, 125ull, 625ull, 
                                              78125ull, 390625ull, 1953125ull, 9765625ull,
                                              48828125ull, 244140625ull, 1220703125ull,
                                              6103515625ull, 30517578125ull};
-// ceil(2^128 / 5^k) as {high 64 bits, low 64 bits}
-__constant__ unsigned long long kRecip5[16][2] = {
-    {0ull, 0ull},  // k = 0: no division
-    {0x3333333333333333ull, 0x3333333333333334ull},
-    {0x0a3d70a3d70a3d70ull, 0xa3d70a3d70a3d70bull},
-    {0x020c49ba5e353f7cull, 0xed916872b020c49cull},
-    {0x0068db8bac710cb2ull, 0x95e9e1b089a02753ull},
-    {0x0014f8b588e368f0ull, 0x8461f9f01b866e44ull},
-    {0x000431bde82d7b63ull, 0x4dad31fcd24e160eull},
-    {0x0000d6bf94d5e57aull, 0x42bc3d329076046aull},
-    {0x00002af31dc46118ull, 0x73bf3f70834acdafull},
-    {0x0000089705f4136bull, 0x4a59731680a88f8aull},
-    {0x000001b7cdfd9d7bull, 0xdbab7d6ae6881cb6ull},
-    {0x00000057f5ff85e5ull, 0x92557f7bc7b4d28bull},
-    {0x000000119799812dull, 0xea11197f27f0f6e9ull},
-    {0x0000000384b84d09ull, 0x2ed0384ca19697c9ull},
-    {0x00000000b424dc35ull, 0x095cd80f538484c2ull},
-    {0x0000000024075f3dull, 0xceac2b3643e74dc1ull},
+// floor(2^(63 + Ld) / 5^k), Ld the bit length of 5^k: a reciprocal in [2^63, 2^64)
+__constant__ unsigned long long kRecip5[16] = {
+    0ull,  // k = 0: no division
+    0xccccccccccccccccull, 0xa3d70a3d70a3d70aull, 0x83126e978d4fdf3bull, 0xd1b71758e219652bull,
+    0xa7c5ac471b478423ull, 0x8637bd05af6c69b5ull, 0xd6bf94d5e57a42bcull, 0xabcc77118461cefcull,
+    0x89705f4136b4a597ull, 0xdbe6fecebdedd5beull, 0xafebff0bcb24aafeull, 0x8cbccc096f5088cbull,
+    0xe12e13424bb40e13ull, 0xb424dc35095cd80full, 0x901d7cf73ab0acd9ull,
 };
 
-typedef unsigned __int128 u128;
-
-// floor(a * b / 2^128) from 64-bit limbs
-__device__ __forceinline__ u128 mulhi128(u128 a, u128 b) {
-  const unsigned long long a0 = (unsigned long long)a, a1 = (unsigned long long)(a >> 64);
-  const unsigned long long b0 = (unsigned long long)b, b1 = (unsigned long long)(b >> 64);
-  const u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
-  const u128 mid = (p00 >> 64) + (unsigned long long)p01 + (unsigned long long)p10;
-  return p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+// The binary64 value of an integer M < 2^53 (exact), by its bit layout.
+__device__ __forceinline__ double u53_to_f64(unsigned long long M) {
+  if (M == 0) return 0.0;
+  const int L = 64 - __clzll((long long)M);
+  const unsigned long long mant = M << (53 - L);  // leading bit at position 52
+  return __longlong_as_double((long long)(((unsigned long long)(1022 + L) << 52) | (mant & ((1ull << 52) - 1))));
 }
 
 // The binary64 value nearest to M / 10^k (ties to even), M < 10^15, 0 <= k <= 15.
+// With L, Ld the bit lengths of M and d = 5^k and t = 56 + Ld - L, q = floor(M 2^t / d) lies in
+// [2^55, 2^57). Mn = M 2^(64 - L) and R = floor(2^(63 + Ld) / d) give hi = floor(Mn R / 2^64) in
+// (M 2^(t+7) / d - 2, M 2^(t+7) / d], so hi >> 7 is q or q - 1; the remainder
+// M 2^t - q d lies in [0, 2d) (below 2^36), so 64-bit wrapping arithmetic computes it exactly.
 __device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
   if (M == 0) return 0.0;
-  if (k == 0) return __ull2double_rn(M);  // exact: M < 2^53
+  if (k == 0) return u53_to_f64(M);
   const unsigned long long d = kPow5[k];
   const int L = 64 - __clzll((long long)M), Ld = 64 - __clzll((long long)d);
-  const int t = 56 + Ld - L;  // x / d lies in [2^55, 2^57)
-  const u128 x = (u128)M << t;
-  const u128 R = ((u128)kRecip5[k][0] << 64) | kRecip5[k][1];
-  unsigned long long q = (unsigned long long)mulhi128(x, R);  // q or q + 1
-  __int128 r = (__int128)x - (__int128)((u128)q * d);
-  if (r < 0) {
-    q -= 1;
-    r += d;
+  const int t = 56 + Ld - L;
+  unsigned long long q = __umul64hi(M << (64 - L), kRecip5[k]) >> 7;
+  unsigned long long r = (t >= 64 ? 0ull : (M << t)) - q * d;
+  if (r >= d) {
+    q += 1;
+    r -= d;
   }
   const int b = 64 - __clzll((long long)q);
-  int s = b - 53;  // 3 or 4 bits below the binary64 significand
+  int s = b - 53;  // 2 to 4 bits below the binary64 significand
   unsigned long long mant = q >> s;
   const unsigned long long low = q & ((1ull << s) - 1), half = 1ull << (s - 1);
   if (low > half || (low == half && (r != 0 || (mant & 1)))) mant += 1;
@@ -87,6 +75,10 @@ __device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
   }
   const int e = 52 + s - t - k;
   return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ double negate_if(double v, bool neg) {
+  return neg ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull) : v;
 }
 
 __device__ __forceinline__ bool is_digit(unsigned c) { return c - '0' <= 9u; }
@@ -146,8 +138,7 @@ __device__ bool parse_row(const unsigned char* p, int len, int64_t& jid, int64_t
     } else if (i != len) {
       return false;
     }
-    const double v = dec_to_f64(M, nf);
-    dv[f] = neg ? -v : v;
+    dv[f] = negate_if(dec_to_f64(M, nf), neg);
   }
   // |lat| <= 90, |lon| <= 180 (on the bit patterns)
   const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
@@ -157,17 +148,19 @@ __device__ bool parse_row(const unsigned char* p, int len, int64_t& jid, int64_t
   ts = iv[1];
   lat = dv[0];
   lon = dv[1];
-  spd = __double2float_rn(dv[2]);
-  hd = __double2float_rn(dv[3]);
+  spd = f64_to_f32_rn_z(dv[2]);
+  hd = f64_to_f32_rn_z(dv[3]);
   return true;
 }
 
 // ---- byte-parallel helpers (SWAR: several bytes per 32- or 64-bit word)
-// Bit i of the result is set when byte i of w equals c (exact per byte: no borrow between bytes).
-__device__ __forceinline__ uint32_t byte_eq_mask4(uint32_t w, uint32_t c4) {
+// Bit j (0..3) set when byte j of w equals the byte repeated in c4. The zero-byte test leaves
+// bit 7 of each matching byte, and one multiply by 1 + 2^7 + 2^14 + 2^21 moves bits 7, 15, 23
+// and 31 to bits 28..31 (the partial products land on distinct bits, so nothing carries).
+__device__ __forceinline__ uint32_t byte_eq_nibble(uint32_t w, uint32_t c4) {
   const uint32_t x = w ^ c4;
-  const uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;  // 0x80 where x's byte is 0
-  return ((z >> 7) & 1u) | ((z >> 14) & 2u) | ((z >> 21) & 4u) | ((z >> 28) & 8u);
+  const uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+  return (z * 0x00204081u) >> 28;
 }
 
 // 8 bytes at byte offset pos of a 16-byte aligned shared buffer (two aligned loads + shift).
@@ -223,42 +216,52 @@ __device__ __forceinline__ bool int_field(const unsigned char* s, int a, int b, 
   return true;
 }
 
-// A decimal field -?[0-9]+(\.[0-9]+)? with at most 15 digits.
+// A decimal field -?[0-9]+(\.[0-9]+)? with at most 15 digits. Its (at most 16) bytes are
+// loaded as two words once: the '.' is found by a byte compare, removed by shifting the bytes
+// above it down, and the remaining digit string is converted eight digits at a time.
 __device__ __forceinline__ bool dec_field(const unsigned char* s, int a, int b, double& out) {
-  bool neg = false;
-  if (a < b && s[a] == '-') {
-    neg = true;
-    ++a;
-  }
+  const bool neg = a < b && s[a] == '-';
+  if (neg) ++a;
   const int len = b - a;
   if (len < 1 || len > 16) return false;  // 15 digits and one '.'
-  // position of the first '.' (if any) in the field
-  int dot = -1;
-  {
-    const unsigned long long w0 = load8(s, a), w1 = load8(s, a + 8);
-    const uint32_t m = byte_eq_mask4((uint32_t)w0, 0x2E2E2E2Eu) | (byte_eq_mask4((uint32_t)(w0 >> 32), 0x2E2E2E2Eu) << 4) |
-                       (byte_eq_mask4((uint32_t)w1, 0x2E2E2E2Eu) << 8) | (byte_eq_mask4((uint32_t)(w1 >> 32), 0x2E2E2E2Eu) << 12);
-    const uint32_t in = m & ((1u << len) - 1u);
-    if (in) dot = __ffs(in) - 1;
+  unsigned long long lo = load8(s, a), hi = load8(s, a + 8);  // bytes [a, a + 16)
+  const uint32_t dm = (byte_eq_nibble((uint32_t)lo, 0x2E2E2E2Eu) | (byte_eq_nibble((uint32_t)(lo >> 32), 0x2E2E2E2Eu) << 4) |
+                       (byte_eq_nibble((uint32_t)hi, 0x2E2E2E2Eu) << 8) |
+                       (byte_eq_nibble((uint32_t)(hi >> 32), 0x2E2E2E2Eu) << 12)) &
+                      ((1u << len) - 1u);
+  int n = len, nf = 0;
+  if (dm) {
+    const int dot = __ffs(dm) - 1;
+    nf = len - dot - 1;
+    if (dot == 0 || nf == 0) return false;  // digits on both sides of the '.'
+    n = len - 1;
+    const unsigned long long slo = (lo >> 8) | (hi << 56), shi = hi >> 8;  // all bytes one down
+    if (dot < 8) {
+      const unsigned long long keep = (1ull << (8 * dot)) - 1;
+      lo = (lo & keep) | (slo & ~keep);
+      hi = shi;
+    } else {
+      const unsigned long long keep = (1ull << (8 * (dot - 8))) - 1;
+      hi = (hi & keep) | (shi & ~keep);
+    }
   }
-  const int ni = dot < 0 ? len : dot, nf = dot < 0 ? 0 : len - dot - 1;
-  if (ni < 1 || (dot >= 0 && nf < 1) || ni + nf > 15) return false;
-  unsigned long long hi, lo = 0;
-  if (!digits_at(s, a, ni, hi)) return false;
-  if (nf && !digits_at(s, a + ni + 1, nf, lo)) return false;  // a second '.' is not a digit
-  const unsigned long long M = hi * (kPow5[nf] << nf) + lo;  // hi * 10^nf + lo < 10^15
-  const double v = dec_to_f64(M, nf);
-  out = neg ? -v : v;
+  if (n > 15) return false;
+  unsigned long long M;  // the n digits, bytes [0, n) of (lo, hi); a second '.' is not a digit
+  if (n <= 8) {
+    if (!digits8(lo, n, M)) return false;
+  } else {
+    const int k = n - 8;  // leading digits, then the last eight
+    unsigned long long v;
+    if (!digits8(lo, k, M) || !digits8((lo >> (8 * k)) | (hi << (64 - 8 * k)), 8, v)) return false;
+    M = M * 100000000ull + v;
+  }
+  out = negate_if(dec_to_f64(M, nf), neg);
   return true;
 }
 
-// One line [a, e) of the staged window, fields located with the comma mask.
-__device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const uint32_t* cm, int a, int e,
-                                                  int64_t& jid, int64_t& ts, double& lat, double& lon,
-                                                  float& spd, float& hd) {
-  if (e > a && s[e - 1] == '\r') --e;
-  if (e == a) return false;
-  int sep[6];
+// The five ',' of a line longer than 64 bytes, from the comma mask (a rare path: kept out of
+// line so that the common path below holds its positions in registers).
+__device__ __noinline__ bool long_line_seps(const uint32_t* cm, int a, int e, int* sep) {
   int nsep = 0;
   for (int w = a >> 5; w <= ((e - 1) >> 5) && nsep < 6; ++w) {
     uint32_t m = cm[w];
@@ -270,7 +273,33 @@ __device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const 
       m &= m - 1;
     }
   }
-  if (nsep != 5) return false;
+  return nsep == 5;
+}
+
+// One line [a, e) of the staged window, fields located with the comma mask.
+__device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const uint32_t* cm, int a, int e,
+                                                  int64_t& jid, int64_t& ts, double& lat, double& lon,
+                                                  float& spd, float& hd) {
+  if (e > a && s[e - 1] == '\r') --e;
+  if (e == a) return false;
+  int sep[5];
+  if (e - a <= 64) {  // the comma bits of bytes [a, a + 64) from three mask words
+    const int w = a >> 5, sh = a & 31;
+    unsigned long long m = (((unsigned long long)cm[w + 1] << 32) | cm[w]) >> sh;
+    if (sh) m |= (unsigned long long)cm[w + 2] << (64 - sh);
+    if (e - a < 64) m &= (1ull << (e - a)) - 1;
+    if (__popcll(m) != 5) return false;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      sep[k] = a + __ffsll((long long)m) - 1;
+      m &= m - 1;
+    }
+  } else {
+    int s6[6];
+    if (!long_line_seps(cm, a, e, s6)) return false;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sep[k] = s6[k];
+  }
   long long iv0, iv1;
   double d0, d1, d2, d3;
   if (!int_field(s, a, sep[0], iv0) || !int_field(s, sep[0] + 1, sep[1], iv1)) return false;
@@ -284,8 +313,8 @@ __device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const 
   ts = iv1;
   lat = d0;
   lon = d1;
-  spd = __double2float_rn(d2);
-  hd = __double2float_rn(d3);
+  spd = f64_to_f32_rn_z(d2);
+  hd = f64_to_f32_rn_z(d3);
   return true;
 }
 
@@ -339,7 +368,7 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
                                                          const uint32_t* __restrict__ tile_row, CsvOut out,
                                                          uint32_t cap, DevState* st) {
   __shared__ __align__(16) unsigned char s_buf[kCsvTile + kCsvHalo + 32];
-  __shared__ uint32_t s_nl[(kCsvTile + kCsvHalo) / 32 + 1], s_cm[(kCsvTile + kCsvHalo) / 32 + 1];
+  __shared__ uint32_t s_nl[(kCsvTile + kCsvHalo) / 32 + 2], s_cm[(kCsvTile + kCsvHalo) / 32 + 2];
   __shared__ uint16_t s_start[kCsvTile];
   __shared__ uint32_t s_scan[kCsvBlock / 32 + 1];
   __shared__ unsigned char s_prev;
@@ -348,35 +377,48 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   const unsigned long long base = (unsigned long long)tile * kCsvTile;
   const int tlen = (int)min((unsigned long long)kCsvTile, len - base);
   const int wlen = (int)min((unsigned long long)(kCsvTile + kCsvHalo), len - base);
-  // stage the tile (+ halo) in shared memory: 16-byte loads (base is 16-byte aligned); zero the
-  // 32 bytes after the window (the word loads of the parser may read into them)
-  for (int o = tid * 16; o < wlen; o += kCsvBlock * 16) {
-    if (o + 16 <= wlen) *reinterpret_cast<uint4*>(s_buf + o) = *reinterpret_cast<const uint4*>(buf + base + o);
-    else
-      for (int q = o; q < wlen; ++q) s_buf[q] = buf[base + q];
-  }
-  if (tid < 32) s_buf[wlen + tid] = 0;
-  if (tid == 0) s_prev = (base == 0) ? (unsigned char)'\n' : buf[base - 1];
-  __syncthreads();
-  // newline and comma bit masks of the window, one bit per byte: each thread classifies one
-  // 4-byte word, eight lanes' nibbles combine into a 32-bit mask word
+  // stage the window (tile + halo) and build its newline and comma masks, one bit per byte:
+  // thread t takes the 32-byte chunks t, t + kCsvBlock, ... (16-byte loads: base is 16-byte
+  // aligned), stores the bytes to shared memory and derives the two mask words from its
+  // registers. The bytes after the window are zero (the word loads of the parser may read 32
+  // bytes past a field), and so are the two mask words after the last.
   const int nmask = (wlen + 31) / 32;
-  for (int q0 = tid & ~31; q0 < nmask * 8; q0 += kCsvBlock) {  // warp-uniform trip count
-    const int q = q0 + (tid & 31);
-    const bool have = q < nmask * 8;  // groups of 8 lanes are all in or all out
-    const uint32_t w = have ? reinterpret_cast<const uint32_t*>(s_buf)[q] : 0u;
-    uint32_t nl = byte_eq_mask4(w, 0x0A0A0A0Au) << ((q & 7) * 4);
-    uint32_t cm = byte_eq_mask4(w, 0x2C2C2C2Cu) << ((q & 7) * 4);
+  for (int ch = tid; ch < nmask; ch += kCsvBlock) {
+    const int o = ch * 32;
+    uint32_t w[8];
+    if (o + 32 <= wlen) {
+      const uint4 v0 = *reinterpret_cast<const uint4*>(buf + base + o);
+      const uint4 v1 = *reinterpret_cast<const uint4*>(buf + base + o + 16);
+      w[0] = v0.x; w[1] = v0.y; w[2] = v0.z; w[3] = v0.w;
+      w[4] = v1.x; w[5] = v1.y; w[6] = v1.z; w[7] = v1.w;
+    } else {
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      nl |= __shfl_xor_sync(0xffffffffu, nl, o);
-      cm |= __shfl_xor_sync(0xffffffffu, cm, o);
+      for (int q = 0; q < 8; ++q) {
+        uint32_t x = 0;
+        for (int bb = 0; bb < 4; ++bb) {
+          const int p = o + 4 * q + bb;
+          if (p < wlen) x |= (uint32_t)buf[base + p] << (8 * bb);
+        }
+        w[q] = x;
+      }
     }
-    if (have && (q & 7) == 0) {
-      s_nl[q >> 3] = nl;
-      s_cm[q >> 3] = cm;
+    *reinterpret_cast<uint4*>(s_buf + o) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(s_buf + o + 16) = make_uint4(w[4], w[5], w[6], w[7]);
+    uint32_t nl = 0, cm = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      nl |= byte_eq_nibble(w[q], 0x0A0A0A0Au) << (4 * q);
+      cm |= byte_eq_nibble(w[q], 0x2C2C2C2Cu) << (4 * q);
     }
+    s_nl[ch] = nl;
+    s_cm[ch] = cm;
   }
+  if (tid < 32) s_buf[nmask * 32 + tid] = 0;
+  if (tid < 2) {
+    s_nl[nmask + tid] = 0;
+    s_cm[nmask + tid] = 0;
+  }
+  if (tid == 0) s_prev = (base == 0) ? (unsigned char)'\n' : buf[base - 1];
   __syncthreads();
   // line starts inside the tile (a byte after a newline): 2 mask words per thread
   const int tw = (tlen + 31) / 32;

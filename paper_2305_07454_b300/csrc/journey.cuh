@@ -208,20 +208,6 @@ __device__ __forceinline__ bool tiny_deg(double x) {
   return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) < 0x3F977318FC504817ull;  // 0.0229
 }
 
-// double -> float rounded to nearest even by the bit layout when the result is a normal float
-// (the implied speed's distance; other values take the conversion instruction).
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const uint32_t hi = (uint32_t)(b >> 32);
-  const int e = (int)((hi >> 20) & 0x7FF);
-  if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  uint32_t keep = (uint32_t)(m >> 29);
-  const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
-  keep += (rest > half || (rest == half && (keep & 1u))) ? 1u : 0u;
-  // a mantissa carry moves into the exponent (and to infinity past the largest float)
-  return __uint_as_float((hi & 0x80000000u) | (((uint32_t)(e - 1023 + 127) << 23) + keep));
-}
 __device__ __forceinline__ float to_f32(double x) { return f64_to_f32_rn(x); }
 __device__ __forceinline__ float to_f32(float x) { return x; }
 

@@ -135,3 +135,36 @@ def test_decimal_conversion_is_correctly_rounded(orc):
     exact("heading", got["heading"], want["heading"])
     assert np.array_equal(got["lat"], np.array(lats))
     assert np.array_equal(got["speed"], np.array(spds).astype(np.float32))
+
+
+def test_decimal_edge_values(orc):
+    """Decimals at the ends of the grammar: 14 fraction digits after a 0 (the widest shift),
+    15 integer digits (the exact integer path), zeros with fraction digits, negative zero,
+    trailing zeros, 16-digit and malformed fields; each against CPython's correctly rounded
+    float()."""
+    vals = ["0.00000000000001", "0.00000000000009", "0.10000000000000", "-0.00000000000001",
+            "999999999999999", "99999999999999.9", "0.99999999999999", "1.00000000000000",
+            "0.0", "-0.0", "0.1", "0.2", "0.3", "2.675", "1.005", "179.999999999999",
+            "123456789.012345", "0.5", "1.5", "2.5", "4503599627370.49", "9007199254740.99",
+            "16777216.5", "16777217", "3.40282346638528", "0.000000000000001", "1e3", "1.2.3"]
+    lines = [f"{i},{1620518400000 + i},37.5,{v if _num(v) is not None and abs(_num(v)) <= 180 else '-92.5'},"
+             f"{v},{v}".encode() for i, v in enumerate(vals)]
+    text = b"\n".join(lines)
+    want, _, _ = orc.parse_csv(text)
+    got, _ = gpu_csv(text, materialize=False)
+    for k in ("lon", "speed", "heading"):
+        exact(k, got[k], want[k])
+    for i, v in enumerate(vals):
+        if _num(v) is None:
+            assert np.isnan(got["speed"][i]), v
+        else:
+            assert got["speed"][i] == np.float32(float(v)) and np.signbit(got["speed"][i]) == v.startswith("-"), v
+
+
+def _num(v):
+    """The value of a field of the decimal grammar (at most 15 digits), else None."""
+    import re
+
+    if not re.fullmatch(r"-?[0-9]+(\.[0-9]+)?", v) or sum(ch.isdigit() for ch in v) > 15:
+        return None
+    return float(v)
