@@ -126,6 +126,8 @@ def algorithmic_bytes(stage: str, c: dict) -> float:
         "scatter": 32.0 * nin + 32.0 * nv,              # ts, lat, lon, speed, slot read; records written
         "journeys": 32.0 * nv + 28.0 * R + 96.0 * J,    # records read; runs and journey rows written
         "cell_write": 28.0 * R + 44.0 * c["n_cells"],
+        "csv_count": float(c.get("csv_bytes", 0)),                  # the text read
+        "csv_parse": float(c.get("csv_bytes", 0)) + 40.0 * nin,    # the text read; six columns written
     }.get(stage, 0.0)
 
 
@@ -199,7 +201,7 @@ def run_ours(args):
     # launch shapes from the library's autotuner on this workload (outside the timed region)
     extract_dev(pipe)
     t_tune = time.perf_counter()
-    tuning = pipe.autotune(reps=2)
+    tuning = pipe.autotune(reps=2) if args.autotune else {**pipe.tuning, "ms": None}
     tuning["seconds"] = time.perf_counter() - t_tune
     for _ in range(args.warmup):
         run_dev(pipe)
@@ -221,6 +223,8 @@ def run_ours(args):
     counters = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid",
                                                  "n_dup", "n_runs")}
     counters.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
+    if csv_host is not None:
+        counters["csv_bytes"] = int(csv_host.numel())
     if world > 1:
         tt = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -690,6 +694,8 @@ def main():
     ap.add_argument("--scale", type=float, default=0.25, help="week_regions: instance size factor")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-feeds", type=int, default=4, help="0 skips the serving leg")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="0 keeps the library's default launch shapes (a fixed launch order for ncu)")
     ap.add_argument("--serve-slots", type=int, default=0, help="server slots (default: one per feed)")
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     args = ap.parse_args()

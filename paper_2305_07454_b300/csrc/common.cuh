@@ -45,10 +45,24 @@ struct __align__(32) Rec {
 };
 static_assert(sizeof(Rec) == 32, "Rec must be one 32-byte sector");
 
+// The bit pattern of a double, moved through PTX so that integer operations on it stay integer
+// operations: the compiler otherwise recognises sign-bit masks of a reinterpreted double as
+// binary64 negations and absolute values, which run on the binary64 pipe.
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  unsigned long long b;
+  asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+  return b;
+}
+__device__ __forceinline__ double dfrom(unsigned long long b) {
+  double x;
+  asm("mov.b64 %0, %1;" : "=d"(x) : "l"(b));
+  return x;
+}
+
 // Order-preserving map of a double onto uint64 (for finite values and +-inf).
 __host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
 #ifdef __CUDA_ARCH__
-  uint64_t b = (uint64_t)__double_as_longlong(x);
+  uint64_t b = dbits(x);
 #else
   uint64_t b;
   memcpy(&b, &x, 8);
@@ -56,13 +70,17 @@ __host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
   return (b & kSign64) ? ~b : (b | kSign64);
 }
 
+// The conversion instruction (it runs on the binary64 pipe), out of line so that the compiler
+// cannot turn the rare branch that needs it into a conversion on every call.
+__device__ __noinline__ float f64_to_f32_rare(double x) { return (float)x; }
+
 // double -> float rounded to nearest even by the bit layout when the result is a normal float
-// (other values take the conversion instruction, which runs on the binary64 pipe).
+// (other values take the conversion instruction).
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long b = dbits(x);
   const uint32_t hi = (uint32_t)(b >> 32);
   const int e = (int)((hi >> 20) & 0x7FF);
-  if (e < 1023 - 126 || e > 1023 + 127) return (float)x;
+  if (e < 1023 - 126 || e > 1023 + 127) return f64_to_f32_rare(x);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   uint32_t keep = (uint32_t)(m >> 29);
   const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
@@ -72,7 +90,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double x) {
 }
 // The same, with zeros (frequent among parsed speeds) also kept off the binary64 pipe.
 __device__ __forceinline__ float f64_to_f32_rn_z(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long b = dbits(x);
   if ((b << 1) == 0) return __uint_as_float((uint32_t)(b >> 32));  // +-0
   return f64_to_f32_rn(x);
 }

@@ -78,7 +78,7 @@ __device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
 }
 
 __device__ __forceinline__ double negate_if(double v, bool neg) {
-  return neg ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull) : v;
+  return neg ? dfrom(dbits(v) ^ 0x8000000000000000ull) : v;
 }
 
 __device__ __forceinline__ bool is_digit(unsigned c) { return c - '0' <= 9u; }
@@ -142,8 +142,8 @@ __device__ bool parse_row(const unsigned char* p, int len, int64_t& jid, int64_t
   }
   // |lat| <= 90, |lon| <= 180 (on the bit patterns)
   const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
-  if (((unsigned long long)__double_as_longlong(dv[0]) & kAbs) > 0x4056800000000000ull) return false;
-  if (((unsigned long long)__double_as_longlong(dv[1]) & kAbs) > 0x4066800000000000ull) return false;
+  if ((dbits(dv[0]) & kAbs) > 0x4056800000000000ull) return false;
+  if ((dbits(dv[1]) & kAbs) > 0x4066800000000000ull) return false;
   jid = iv[0];
   ts = iv[1];
   lat = dv[0];
@@ -307,8 +307,8 @@ __device__ __forceinline__ bool parse_line_masked(const unsigned char* s, const 
       !dec_field(s, sep[3] + 1, sep[4], d2) || !dec_field(s, sep[4] + 1, e, d3))
     return false;
   const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
-  if (((unsigned long long)__double_as_longlong(d0) & kAbs) > 0x4056800000000000ull) return false;
-  if (((unsigned long long)__double_as_longlong(d1) & kAbs) > 0x4066800000000000ull) return false;
+  if ((dbits(d0) & kAbs) > 0x4056800000000000ull) return false;
+  if ((dbits(d1) & kAbs) > 0x4066800000000000ull) return false;
   jid = iv0;
   ts = iv1;
   lat = d0;

@@ -24,8 +24,8 @@ __device__ __forceinline__ bool row_valid(double lat, double lon, float spd) {
   const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
   const unsigned long long b90 = 0x4056800000000000ull;   // 90.0
   const unsigned long long b180 = 0x4066800000000000ull;  // 180.0
-  unsigned long long la = (unsigned long long)__double_as_longlong(lat) & kAbs;
-  unsigned long long lo = (unsigned long long)__double_as_longlong(lon) & kAbs;
+  unsigned long long la = dbits(lat) & kAbs;
+  unsigned long long lo = dbits(lon) & kAbs;
   uint32_t sp = (uint32_t)__float_as_int(spd) & 0x7FFFFFFFu;
   return la <= b90 && lo <= b180 && sp < 0x7F800000u;
 }

@@ -205,7 +205,7 @@ __device__ __forceinline__ Cos64 cos64(double lat, const CosEntry* __restrict__ 
 
 // |x| < kTinyDeg on the bit patterns (an integer compare, not a binary64 one; NaN fails).
 __device__ __forceinline__ bool tiny_deg(double x) {
-  return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) < 0x3F977318FC504817ull;  // 0.0229
+  return (dbits(x) & 0x7FFFFFFFFFFFFFFFull) < 0x3F977318FC504817ull;  // 0.0229
 }
 
 __device__ __forceinline__ float to_f32(double x) { return f64_to_f32_rn(x); }

@@ -33,7 +33,7 @@ struct GridParams {
 // that table: no floating-point division, bit-exact with the binary64 definition. A float
 // estimate from the double's leading bits picks the table entry; one or two compares fix it.
 __device__ __forceinline__ float leading_f32(double x) {
-  uint64_t b = (uint64_t)__double_as_longlong(x);
+  uint64_t b = dbits(x);
   uint32_t hi = (uint32_t)(b >> 32);
   uint32_t sign = hi & 0x80000000u;
   int e = (int)((hi >> 20) & 0x7FF);
