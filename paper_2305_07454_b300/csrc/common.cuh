@@ -74,6 +74,11 @@ __host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
 // cannot turn the rare branch that needs it into a conversion on every call.
 __device__ __noinline__ float f64_to_f32_rare(double x) { return (float)x; }
 
+// 64-bit integer -> float conversions run on the binary64 pipe too: the rare wide cases call
+// these, out of line for the same reason.
+__device__ __noinline__ float u64_to_f32_rz_rare(unsigned long long x) { return __ull2float_rz(x); }
+__device__ __noinline__ float i64_to_f32_rare(long long x) { return (float)x; }
+
 // double -> float rounded to nearest even by the bit layout when the result is a normal float
 // (other values take the conversion instruction).
 __device__ __forceinline__ float f64_to_f32_rn(double x) {

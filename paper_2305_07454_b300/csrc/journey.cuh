@@ -338,7 +338,7 @@ constexpr int kMaxBucket = 48;
 // Bucket of a time offset t in [0, span]: a journey spanning under 2^32 ms (any real one)
 // converts through 32 bits, which gives the same float as the 64-bit conversion.
 __device__ __forceinline__ int time_bucket(unsigned long long t, bool narrow, float scale, int nb) {
-  const float f = narrow ? __uint2float_rz((uint32_t)t) : __ull2float_rz(t);
+  const float f = narrow ? __uint2float_rz((uint32_t)t) : u64_to_f32_rz_rare(t);
   return min(nb - 1, (int)(f * scale));
 }
 
@@ -609,7 +609,7 @@ struct StitchSmem {
 // is sorted) and written out with one global allocation per journey; a journey with more runs
 // than the buffer holds emits the rest directly.
 struct __align__(8) RunSlot {
-  double sum;
+  float s, c;  // compensated speed sum, folded into binary64 at the copy-out (not in the walk)
   uint32_t key, cnt, start;
   float mn, mx;
   uint32_t pad;
@@ -623,18 +623,18 @@ static_assert(kEChunk * 16 <= kRunBufOff, "fallback pair chunks must not overlap
 __device__ __forceinline__ void run_put(RunSlot* buf, uint32_t* nbuf, const JourneyOut& o, DevState* st,
                                         const RunPart& r) {
   if (r.key == kKeyInvalid || r.cnt == 0) return;
-  const double sum = (double)r.s + (double)r.c;
   const uint32_t i = atomicAdd(nbuf, 1u);
   if (i < (uint32_t)kRunBuf) {
     RunSlot& q = buf[i];
-    q.sum = sum;
+    q.s = r.s;
+    q.c = r.c;
     q.key = r.key;
     q.cnt = r.cnt;
     q.start = r.start;
     q.mn = r.mn;
     q.mx = r.mx;
   } else {
-    emit_run(o, st, r.key, r.cnt, sum, r.mn, r.mx, r.start);
+    emit_run(o, st, r.key, r.cnt, (double)r.s + (double)r.c, r.mn, r.mx, r.start);
   }
 }
 
@@ -887,7 +887,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
         d = Form::distance(p_lat, p_lon, p_cos, cur.lat, cur.lon, ccur, g);
         if (dt > 0) {
           // stored as float32: computed in float32 from the binary64 distance
-          const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : (float)dt;
+          const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : i64_to_f32_rare(dt);
           vh = to_f32(d) * (3600.0f / fdt);
           ac = (cur.spd - p_spd) / (0.0036f * fdt);
         }
@@ -1014,7 +1014,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     const RunSlot q = rbuf[i];
     o.run_sortkey[g] = ((unsigned long long)q.key << 32) | q.start;
     o.run_cnt[g] = q.cnt;
-    o.run_sum[g] = q.sum;
+    o.run_sum[g] = (double)q.s + (double)q.c;
     o.run_min[g] = q.mn;
     o.run_max[g] = q.mx;
   }
