@@ -59,6 +59,21 @@ __device__ __forceinline__ double dfrom(unsigned long long b) {
   return x;
 }
 
+// float -> double by the bit layout, exact for every float (denormals included), without a
+// conversion instruction on the binary64 pipe.
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xFFu, man = b & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if (ex == 0xFFu) return dfrom(sign | 0x7FF0000000000000ull | ((unsigned long long)man << 29));
+  if (ex == 0) {
+    if (man == 0) return dfrom(sign);
+    const int L = 32 - __clz((int)man);  // man = 1.x * 2^(L-1): the value is 2^(L-150) * 1.x
+    return dfrom(sign | ((unsigned long long)(873 + L) << 52) | (((unsigned long long)man << (53 - L)) & 0xFFFFFFFFFFFFFull));
+  }
+  return dfrom(sign | ((unsigned long long)(ex + 896) << 52) | ((unsigned long long)man << 29));
+}
+
 // Order-preserving map of a double onto uint64 (for finite values and +-inf).
 __host__ __device__ __forceinline__ uint64_t ord_f64(double x) {
 #ifdef __CUDA_ARCH__

@@ -1621,20 +1621,24 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
   lp.rank_bits = std::max(1, 64 - __builtin_clzll((unsigned long long)std::max<uint32_t>(J, 2) - 1));
   unsigned __int128 span = (unsigned __int128)(uint64_t)lc->n_bins * (uint64_t)lc->bin_ms;
   lp.t_span = span > (unsigned __int128)~0ull ? ~0ull : (unsigned long long)span;
+  lp.bin_magic = lc->bin_ms == 1 ? 0ull : ~0ull / (unsigned long long)lc->bin_ms + 1ull;
   const uint64_t max_lk = (uint64_t)lc->n_bins * 4u * cells - 1;
   const int end_bit = std::min(64, (max_lk ? 64 - __builtin_clzll(max_lk) : 1) + lp.rank_bits);
   unsigned long long *keys, *ctr;
+  uint32_t* vals;
   ENSURE("lat.keys", (size_t)n, &keys);
+  ENSURE("lat.vals", (size_t)n, &vals);
   ENSURE("lat.ctr", 4, &ctr);
   CK(cudaMemsetAsync(ctr, 0, 32, c->st));
   if (n) {
     LAUNCH(ST_LATTICE, (k_lattice_keys<<<grid_for(n, 256), 256, 0, c->st>>>(
-                           c->row_slot, c->slot_rank, c->ts, c->lat, c->lon, c->heading, n, c->gp, lp, keys, ctr)));
+                           c->row_slot, c->slot_rank, c->ts, c->lat, c->lon, c->heading, n, c->spd, c->gp, lp, keys,
+                           vals, ctr)));
     LAUNCH_CHECK();
   }
   unsigned long long* skey;
-  uint32_t* srow;
-  cvetl_status s = sort_pairs<unsigned long long>(c, "lsort", keys, nullptr, n, 0, end_bit, &skey, &srow);
+  uint32_t* sspd;  // the points' speeds in lattice order
+  cvetl_status s = sort_pairs<unsigned long long>(c, "lsort", keys, vals, n, 0, end_bit, &skey, &sspd);
   if (s != CVETL_OK) return s;
   unsigned long long dropped = 0;
   CK(cudaStreamSynchronize(c->st));
@@ -1652,6 +1656,12 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
     LAUNCH_CHECK();
   }
   if ((s = scan_u32(c, head, m, cidx, total)) != CVETL_OK) return s;
+  uint32_t* start;
+  ENSURE("lat.start", (size_t)m + 1, &start);
+  if (m) {
+    LAUNCH(ST_LATTICE, (k_lattice_starts<<<grid_for(m, 256), 256, 0, c->st>>>(head, cidx, m, total, start)));
+    LAUNCH_CHECK();
+  }
   LatticeOut& lo = c->lattice;
   ENSURE("lat.o_key", (size_t)m, &lo.key);
   ENSURE("lat.o_bin", (size_t)m, &lo.bin);
@@ -1666,7 +1676,7 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
   ENSURE("lat.o_volume_norm", (size_t)m, &lo.volume_norm);
   if (m) {
     LAUNCH(ST_LATTICE, (k_lattice_fold<<<grid_for(m, 256), 256, 0, c->st>>>(
-                           skey, srow, m, head, cidx, c->spd, lp.rank_bits, c->cfg.n_rows, c->cfg.n_cols, lo, chan)));
+                           skey, sspd, start, total, lp.rank_bits, c->cfg.n_rows, c->cfg.n_cols, lo, chan)));
     LAUNCH_CHECK();
   }
   uint32_t K = 0;

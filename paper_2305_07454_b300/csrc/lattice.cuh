@@ -15,18 +15,36 @@ struct LatticeParams {
   int32_t n_bins;
   int32_t direction;   // 0 cardinal: floor(((h + 45) mod 360) / 90); 1 quadrant: floor((h mod 360) / 90)
   int32_t rank_bits;   // bits of the journey rank in the sort key
-  unsigned long long t_span;  // n_bins * bin_ms (saturated)
+  unsigned long long t_span;     // n_bins * bin_ms (saturated)
+  unsigned long long bin_magic;  // ceil(2^64 / bin_ms) (0 for bin_ms = 1)
 };
 
-// Direction channel of a heading (binary64 arithmetic on the float32 heading, as defined);
-// -1 for a non-finite heading.
-__device__ __forceinline__ int lattice_direction(float heading, int mode) {
+// Direction channel of a heading by the definition, binary64 arithmetic on the float32
+// heading; -1 for a non-finite heading. (Out of line: only headings outside the usual range
+// take it.)
+__device__ __noinline__ int lattice_direction_exact(float heading, int mode) {
   const double h = (double)heading;
   if (!isfinite(h)) return -1;
   double r = fmod(h + (mode == 0 ? 45.0 : 0.0), 360.0);
   if (r < 0.0) r += 360.0;
   if (r >= 360.0) r = 0.0;
   return (int)floor(r / 90.0);
+}
+
+// The same for the headings of the usual range by float32 compares. For a cardinal h in
+// [-45, 315) (quadrant: [0, 360)), r = h + 45 (h) lies in [0, 360) where the remainder is r
+// itself, h + 45 is exact in binary64 wherever it decides a sector, and floor(r / 90) of the
+// correctly rounded quotient is the number of the edges 90, 180, 270 that r reaches (a quotient
+// just below an integer k never rounds up to k: its distance to k exceeds half an ulp of k), so
+// the sector is the number of edges h reaches.
+__device__ __forceinline__ int lattice_direction(float heading, int mode) {
+  if (mode == 0) {
+    if (heading >= -45.0f && heading < 315.0f)
+      return (heading >= 45.0f) + (heading >= 135.0f) + (heading >= 225.0f);
+  } else if (heading >= 0.0f && heading < 360.0f) {
+    return (heading >= 90.0f) + (heading >= 180.0f) + (heading >= 270.0f);
+  }
+  return lattice_direction_exact(heading, mode);
 }
 
 // Sort key of every row: (lattice key << rank_bits) | journey rank for a kept row that has a
@@ -37,8 +55,9 @@ __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict
                                                       const double* __restrict__ lat,
                                                       const double* __restrict__ lon,
                                                       const float* __restrict__ heading, uint32_t n,
-                                                      GridParams g, LatticeParams lp,
-                                                      unsigned long long* __restrict__ keys,
+                                                      const float* __restrict__ spd, GridParams g,
+                                                      LatticeParams lp, unsigned long long* __restrict__ keys,
+                                                      uint32_t* __restrict__ vals,
                                                       unsigned long long* n_dropped) {
   __shared__ unsigned long long scratch[8];
   unsigned long long dropped = 0;
@@ -54,7 +73,9 @@ __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict
       if (d < 0 || r < 0 || c < 0 || t < g.t0_ms || off >= lp.t_span) {
         ++dropped;
       } else {
-        const unsigned long long b = off / (unsigned long long)lp.bin_ms;
+        const unsigned long long b = (lp.t_span <= 0xFFFFFFFFull)
+                                         ? (lp.bin_magic ? __umul64hi(lp.bin_magic, off) : off)
+                                         : off / (unsigned long long)lp.bin_ms;
         const unsigned long long lk =
             ((b * 4ull + (unsigned long long)d) * (unsigned long long)g.n_rows + (unsigned long long)r) *
                 (unsigned long long)g.n_cols + (unsigned long long)c;
@@ -62,6 +83,7 @@ __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict
       }
     }
     keys[i] = k;
+    vals[i] = __float_as_uint(spd[i]);  // the sort's payload: the speed, read in lattice order
   }
   const unsigned long long s = block_sum<256, unsigned long long>(dropped, scratch);
   if (threadIdx.x == 0 && s) atomicAdd(n_dropped, s);
@@ -91,29 +113,36 @@ __device__ __forceinline__ float from_ord_f32(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u ^ 0x80000000u) : ~u);
 }
 
-// One thread per lattice cell (segment head): the segment's points in (journey, row) order
-// give the count, the speed sum in that order, the mean and the unique journeys; the channel
-// extremes go to chan[0..7] (min) and chan[8..15] (max) as order-preserving words.
-__global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, const uint32_t* __restrict__ srow,
-                               uint32_t m, const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx,
-                               const float* __restrict__ spd, int rank_bits, int32_t n_rows, int32_t n_cols,
-                               LatticeOut o, uint32_t* __restrict__ chan) {
+// Cell starts: start[cidx[i]] = i for every segment head i, and start[K] = m.
+__global__ void k_lattice_starts(const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx, uint32_t m,
+                                 const uint32_t* __restrict__ K, uint32_t* __restrict__ start) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (head[i]) start[cidx[i]] = i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[*K] = m;
+}
+
+// One thread per lattice cell: its points in (journey, row) order give the count, the speed sum
+// in that order (binary64, one add per point as defined), the mean and the unique journeys; the
+// channel extremes go to chan[0..7] (min) and chan[8..15] (max) as order-preserving words.
+__global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, const uint32_t* __restrict__ sspd,
+                               const uint32_t* __restrict__ start, const uint32_t* __restrict__ Kp, int rank_bits,
+                               int32_t n_rows, int32_t n_cols, LatticeOut o, uint32_t* __restrict__ chan) {
+  const uint32_t K = *Kp;
   const unsigned long long rmask = (1ull << rank_bits) - 1;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    if (!head[i]) continue;
-    const unsigned long long lk = skey[i] >> rank_bits;
-    uint32_t cnt = 0, vol = 0;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+    const uint32_t e0 = start[q], e1 = start[q + 1];
+    const unsigned long long lk = skey[e0] >> rank_bits;
+    uint32_t vol = 0;
     double sum = 0.0;
     unsigned long long prev_rank = ~0ull;
-    for (uint32_t e = i; e < m && (skey[e] >> rank_bits) == lk; ++e) {
-      const float s = spd[srow[e]];
-      cnt += 1;
-      sum += (double)(((__float_as_uint(s) & 0x7FFFFFFFu) == 0) ? 0.0f : s);
+    for (uint32_t e = e0; e < e1; ++e) {
+      const float sp = __uint_as_float(sspd[e]);
+      sum += f32_to_f64_exact(((__float_as_uint(sp) & 0x7FFFFFFFu) == 0) ? 0.0f : sp);
       const unsigned long long rk = skey[e] & rmask;
-      if (rk != prev_rank) vol += 1;
+      vol += (rk != prev_rank) ? 1u : 0u;
       prev_rank = rk;
     }
-    const uint32_t q = cidx[i];
+    const uint32_t cnt = e1 - e0;
     const uint32_t key = (uint32_t)lk, cells = (uint32_t)n_rows * (uint32_t)n_cols;
     const int d = (int)((key / cells) % 4u);
     const float mean = (float)(sum / (double)cnt);

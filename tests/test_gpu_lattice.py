@@ -126,3 +126,29 @@ def test_lattice_errors(small_day):
         with pytest.raises(P.CvetlError) as e:
             p.lattice()
         assert e.value.status == P.EINVAL
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_headings_at_sector_edges(orc, direction):
+    """Headings on and next to every sector edge, far outside [0, 360), tiny, signed zero,
+    infinite and NaN: the float32 fast path and the out-of-line binary64 path against the
+    oracle's definition."""
+    edges = [-405.0, -360.0, -315.0, -270.0, -225.0, -180.0, -135.0, -90.0, -45.0, 0.0, 45.0, 90.0,
+             135.0, 180.0, 225.0, 270.0, 315.0, 360.0, 405.0, 720.0]
+    h = []
+    for e in edges:
+        f = np.float32(e)
+        h += [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+    h += [np.float32(v) for v in (-0.0, 1e-30, -1e-30, 1e-45, -1e-45, 1e30, -1e30, 3.4e38, -3.4e38)]
+    h += [np.float32(np.inf), np.float32(-np.inf), np.float32(np.nan)]
+    h = np.array(h, np.float32)
+    n = h.shape[0]
+    rng = np.random.default_rng(21)
+    cols = dict(jid=rng.integers(0, 5, n).astype(np.int64),
+                ts=(1620518400000 + rng.integers(0, 86_400_000, n)).astype(np.int64),
+                lat=38.0 + rng.uniform(0, 0.05, n), lon=-92.0 + rng.uniform(0, 0.05, n),
+                speed=rng.uniform(0, 100, n).astype(np.float32), heading=h)
+    g = gpu_lattice(cols, **SMALL, direction=direction, dense=0)
+    o = orc.lattice(cols, **SMALL, direction=direction)
+    check(g, o)
+    assert g["n_dropped"] == 3  # the non-finite headings
