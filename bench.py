@@ -233,28 +233,54 @@ def run_ours(args):
     value = n * world * args.steps / (ms_total / 1e3)
 
     # ---- end to end through the C ABI with host inputs ------------------------------------
-    e2e_steps = max(1, min(args.steps, 3))
-    pipe_h = P.Pipeline(stream=stream, precision=prec)
+    # Two pipelines, each on its own stream and host thread (the library calls release the
+    # GIL), take alternate steps: one step's host->device copy of its pinned inputs overlaps
+    # the other's kernels and result read-back. Every step copies its inputs and reads its
+    # tables back into pinned host buffers inside the timed region.
+    import threading
 
-    def run_host():
+    e2e_per_pipe = max(1, min(args.steps, 3))
+    pipes_h = [P.Pipeline(stream=torch.cuda.Stream(device=dev), precision=prec) for _ in range(2)]
+    host_outs = [ph.host_tables(cells=counters["n_cells"], journeys=counters["n_journeys"]) for ph in pipes_h]
+    last = [None, None]
+
+    def run_host(i):
+        ph = pipes_h[i]
         if csv_host is None:
-            pipe_h.extract({k: host[k] for k in COLS})
+            ph.extract({k: host[k] for k in COLS})
         else:
-            pipe_h.extract_csv(csv_host)
-        pipe_h.transform()
-        pipe_h.load()
-        return pipe_h.results(to_host=True)
+            ph.extract_csv(csv_host)
+        ph.transform()
+        ph.load()
+        last[i] = ph.results(to_host=True, out=host_outs[i])
 
-    run_host()
+    for i in range(2):
+        run_host(i)
     barrier()
+    errors = []
+
+    def worker(i):
+        try:
+            for _ in range(e2e_per_pipe):
+                run_host(i)
+        except Exception as exc:  # reported after the join
+            errors.append(exc)
+
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        out = run_host()
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = (time.perf_counter() - t0) / (2 * e2e_per_pipe)
+    if errors:
+        raise errors[0]
+    out = last[0]
     h2d = sum(BYTES[k] for k in COLS) * n if csv_host is None else int(csv_host.numel())
     d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values()) + 8 * 6
-    pipe_h.close()
+    for ph in pipes_h:
+        ph.close()
 
     # the 8-channel lattice of the day (5-minute bins, dense [288, 8, 460, 670] float32 tensor)
     lat_ms = []
@@ -317,7 +343,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (no flush needed)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "e2e": {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "pipelines": 2},
         "gpu_launches": stats["total_launches"],
         "tuning": tuning,
         "roofline": roofline,
@@ -565,11 +591,14 @@ def run_week(args):
     # end to end from pinned host columns
     e2e_steps = max(1, min(args.steps, 2))
     step(h_insts)
+    t = pipe.tables()
+    host_out = pipe.host_tables(cells=int(t.n_cells), journeys=int(t.n_journeys))
+    pipe.results(to_host=True, out=host_out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         step(h_insts)
-        out = pipe.results(to_host=True)
+        out = pipe.results(to_host=True, out=host_out)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values())

@@ -453,30 +453,49 @@ class Pipeline:
         self._check(lib.cvetl_results(self._h, ctypes.byref(t)))
         return t
 
-    def results(self, to_host: bool = True) -> dict:
+    def results(self, to_host: bool = True, out: "HostTables | None" = None) -> dict:
         """Cells, journeys, per-point columns (if materialised) and counters. to_host=False
-        returns zero-copy device tensors valid until the next extract."""
+        returns zero-copy device tensors valid until the next extract. With out (pinned host
+        buffers from host_tables()), the columns are copied into them on the pipeline's stream
+        with one synchronisation, and the returned arrays are views of out, valid until out is
+        reused."""
         torch = self._torch
         t = self.tables()
 
-        def view(ptr, n, typestr):
+        def dev(ptr, n, typestr):
             if n == 0 or not ptr:
                 np_dt = np.dtype(typestr)
-                arr = torch.empty(0, dtype=torch.from_numpy(np.empty(0, np_dt)).dtype, device="cuda")
-            else:
-                arr = torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
-            return arr.cpu().numpy() if to_host else arr
+                return torch.empty(0, dtype=torch.from_numpy(np.empty(0, np_dt)).dtype, device="cuda")
+            return torch.as_tensor(_DeviceArray(ptr, n, typestr), device="cuda")
 
-        out = {
-            "cells": {k: view(getattr(t, "cell_" + k), t.n_cells, ty) for k, ty in _CELL},
-            "journeys": {k: view(getattr(t, "j_" + k), t.n_journeys, ty) for k, ty in _JOURNEY},
-            "counters": {k: int(getattr(t, k)) for k in _COUNTERS},
-        }
+        parts = {"cells": ("cell_", _CELL, t.n_cells), "journeys": ("j_", _JOURNEY, t.n_journeys)}
         if t.n_points and t.p_perm:
-            out["points"] = {k: view(getattr(t, "p_" + k), t.n_points, ty) for k, ty in _POINT}
-        out["counters"]["n_journeys"] = int(t.n_journeys)
-        out["counters"]["n_cells"] = int(t.n_cells)
-        return out
+            parts["points"] = ("p_", _POINT, t.n_points)
+        res = {}
+        if to_host and out is not None:
+            with torch.cuda.stream(self.stream):
+                for part, (pre, cols, n) in parts.items():
+                    res[part] = {}
+                    for k, ty in cols:
+                        buf = out.get(part, k, n)
+                        if n:
+                            buf.copy_(dev(getattr(t, pre + k), n, ty), non_blocking=True)
+                        res[part][k] = buf.numpy()
+            self.stream.synchronize()
+        else:
+            for part, (pre, cols, n) in parts.items():
+                res[part] = {}
+                for k, ty in cols:
+                    arr = dev(getattr(t, pre + k), n, ty)
+                    res[part][k] = arr.cpu().numpy() if to_host else arr
+        res["counters"] = {k: int(getattr(t, k)) for k in _COUNTERS}
+        res["counters"]["n_journeys"] = int(t.n_journeys)
+        res["counters"]["n_cells"] = int(t.n_cells)
+        return res
+
+    def host_tables(self, cells: int, journeys: int, points: int = 0) -> "HostTables":
+        """Pinned host buffers for results(out=...) with room for the given table sizes."""
+        return HostTables(cells, journeys, points)
 
     def stats(self) -> dict:
         s = Stats()
@@ -494,6 +513,30 @@ class Pipeline:
         self.transform()
         self.load()
         return self.results(to_host=to_host)
+
+
+class HostTables:
+    """Pinned host buffers for Pipeline.results(out=...): one per result column, grown on
+    demand (a larger table reallocates that column)."""
+
+    def __init__(self, cells: int, journeys: int, points: int = 0):
+        import torch
+
+        self._torch = torch
+        self._cap = {"cells": cells, "journeys": journeys, "points": points}
+        self._bufs = {}
+
+    def get(self, part: str, name: str, n: int):
+        torch = self._torch
+        cols = {"cells": _CELL, "journeys": _JOURNEY, "points": _POINT}[part]
+        ty = dict(cols)[name]
+        b = self._bufs.get((part, name))
+        if b is None or b.shape[0] < n:
+            cap = max(n, self._cap[part])
+            dt = torch.from_numpy(np.empty(0, np.dtype(ty))).dtype
+            b = torch.empty(cap, dtype=dt, pin_memory=True)
+            self._bufs[(part, name)] = b
+        return b[:n]
 
 
 class Server:

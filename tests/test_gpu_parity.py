@@ -210,3 +210,23 @@ def test_stats_count_launches(small_day):
         s = p.stats()
     assert s["total_launches"] > 10
     assert s["stages"]["journeys"]["launches"] == 1 and s["stages"]["journeys"]["ms"] > 0
+
+
+def test_results_into_pinned_buffers(small_day):
+    """results(out=...) fills pinned host buffers with the same tables as the plain host copy,
+    and buffers smaller than a table grow."""
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    t = {k: torch.from_numpy(np.ascontiguousarray(small_day[k])).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
+    with P.Pipeline(materialize_points=1) as p:
+        p.run(t, to_host=False)
+        a = p.results(to_host=True)
+        host = p.host_tables(cells=1, journeys=1, points=1)
+        b = p.results(to_host=True, out=host)
+        assert b["cells"]["key"].shape == a["cells"]["key"].shape
+        for part in ("cells", "journeys", "points"):
+            for k in a[part]:
+                exact(part + " " + k, b[part][k], a[part][k])
+        assert b["counters"] == a["counters"]
