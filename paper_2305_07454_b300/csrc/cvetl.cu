@@ -33,13 +33,15 @@ namespace {
 enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
   ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
-  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_POINT_EXTRAS, ST_COUNT
+  ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_POINT_EXTRAS, ST_LATTICE_KEYS,
+  ST_LATTICE_FOLD, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
                                      "csv_count", "csv_parse", "stream_append", "stream_split",
-                                     "stream_tables", "cta_sort", "lattice", "point_extras"};
+                                     "stream_tables", "cta_sort", "lattice", "point_extras", "lattice_keys",
+                                     "lattice_fold"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -1631,7 +1633,7 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
   ENSURE("lat.ctr", 4, &ctr);
   CK(cudaMemsetAsync(ctr, 0, 32, c->st));
   if (n) {
-    LAUNCH(ST_LATTICE, (k_lattice_keys<<<grid_for(n, 256), 256, 0, c->st>>>(
+    LAUNCH(ST_LATTICE_KEYS, (k_lattice_keys<<<grid_for(n, 256), 256, 0, c->st>>>(
                            c->row_slot, c->slot_rank, c->ts, c->lat, c->lon, c->heading, n, c->spd, c->gp, lp, keys,
                            vals, ctr)));
     LAUNCH_CHECK();
@@ -1674,15 +1676,23 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
   ENSURE("lat.o_volume", (size_t)m, &lo.volume);
   ENSURE("lat.o_mean_norm", (size_t)m, &lo.mean_norm);
   ENSURE("lat.o_volume_norm", (size_t)m, &lo.volume_norm);
-  if (m) {
-    LAUNCH(ST_LATTICE, (k_lattice_fold<<<grid_for(m, 256), 256, 0, c->st>>>(
-                           skey, sspd, start, total, lp.rank_bits, c->cfg.n_rows, c->cfg.n_cols, lo, chan)));
-    LAUNCH_CHECK();
-  }
   uint32_t K = 0;
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(&K, total, 4, cudaMemcpyDeviceToHost));
   if (!m) K = 0;
+  if (K) {
+    // cells longest first, so that the lanes of a warp fold cells of about the same length
+    unsigned long long *lkey, *lsorted;
+    uint32_t* order;
+    ENSURE("lat.lenkey", (size_t)K, &lkey);
+    LAUNCH(ST_LATTICE, (k_lattice_len_keys<<<grid_for(K, 256), 256, 0, c->st>>>(start, total, lkey)));
+    LAUNCH_CHECK();
+    if ((s = sort_pairs<unsigned long long>(c, "lorder", lkey, nullptr, K, 32, 64, &lsorted, &order)) != CVETL_OK)
+      return s;
+    LAUNCH(ST_LATTICE_FOLD, (k_lattice_fold<<<grid_for(K, 256), 256, 0, c->st>>>(
+                           skey, sspd, start, order, total, lp.rank_bits, c->cfg.n_rows, c->cfg.n_cols, lo, chan)));
+    LAUNCH_CHECK();
+  }
   float* dense = nullptr;
   if (lc->dense) {
     const size_t cnt = (size_t)lc->n_bins * 8u * cells;

@@ -48,7 +48,10 @@ __device__ __forceinline__ int lattice_direction(float heading, int mode) {
 }
 
 // Sort key of every row: (lattice key << rank_bits) | journey rank for a kept row that has a
-// lattice position, all-ones otherwise (sorted last). Dropped kept rows are counted.
+// lattice position, all-ones otherwise (sorted last); the speed is the sort's payload. Dropped
+// kept rows are counted. Four rows per thread per iteration: their columns and their journeys'
+// ranks are loaded before any of them is keyed, so the loads overlap.
+constexpr int kLatRows = 4;
 __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict__ row_slot,
                                                       const uint32_t* __restrict__ slot_rank,
                                                       const int64_t* __restrict__ ts,
@@ -61,29 +64,50 @@ __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict
                                                       unsigned long long* n_dropped) {
   __shared__ unsigned long long scratch[8];
   unsigned long long dropped = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    unsigned long long k = ~0ull;
-    const uint32_t slot = row_slot[i];
-    if (slot != kKeyInvalid) {
-      const int d = lattice_direction(heading[i], lp.direction);
-      const int r = grid_index(lat[i], g.row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
-      const int c = grid_index(lon[i], g.col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
-      const int64_t t = ts[i];
-      const unsigned long long off = (unsigned long long)t - (unsigned long long)g.t0_ms;
-      if (d < 0 || r < 0 || c < 0 || t < g.t0_ms || off >= lp.t_span) {
-        ++dropped;
-      } else {
-        const unsigned long long b = (lp.t_span <= 0xFFFFFFFFull)
-                                         ? (lp.bin_magic ? __umul64hi(lp.bin_magic, off) : off)
-                                         : off / (unsigned long long)lp.bin_ms;
-        const unsigned long long lk =
-            ((b * 4ull + (unsigned long long)d) * (unsigned long long)g.n_rows + (unsigned long long)r) *
-                (unsigned long long)g.n_cols + (unsigned long long)c;
-        k = (lk << lp.rank_bits) | (unsigned long long)slot_rank[slot];
-      }
+  const uint32_t step = gridDim.x * blockDim.x * kLatRows;
+  for (uint32_t i0 = blockIdx.x * blockDim.x * kLatRows + threadIdx.x; i0 < n; i0 += step) {
+    uint32_t slot[kLatRows], rank[kLatRows];
+    float hd[kLatRows], sp[kLatRows];
+    double la[kLatRows], lo[kLatRows];
+    int64_t t[kLatRows];
+#pragma unroll
+    for (int u = 0; u < kLatRows; ++u) {
+      const uint32_t i = i0 + u * blockDim.x;
+      const bool in = i < n;
+      slot[u] = in ? row_slot[i] : kKeyInvalid;
+      hd[u] = in ? heading[i] : 0.0f;
+      sp[u] = in ? spd[i] : 0.0f;
+      la[u] = in ? lat[i] : 0.0;
+      lo[u] = in ? lon[i] : 0.0;
+      t[u] = in ? ts[i] : 0;
     }
-    keys[i] = k;
-    vals[i] = __float_as_uint(spd[i]);  // the sort's payload: the speed, read in lattice order
+#pragma unroll
+    for (int u = 0; u < kLatRows; ++u) rank[u] = (slot[u] != kKeyInvalid) ? slot_rank[slot[u]] : 0u;
+#pragma unroll
+    for (int u = 0; u < kLatRows; ++u) {
+      const uint32_t i = i0 + u * blockDim.x;
+      if (i >= n) break;
+      unsigned long long k = ~0ull;
+      if (slot[u] != kKeyInvalid) {
+        const int d = lattice_direction(hd[u], lp.direction);
+        const int r = grid_index(la[u], g.row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
+        const int c = grid_index(lo[u], g.col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
+        const unsigned long long off = (unsigned long long)t[u] - (unsigned long long)g.t0_ms;
+        if (d < 0 || r < 0 || c < 0 || t[u] < g.t0_ms || off >= lp.t_span) {
+          ++dropped;
+        } else {
+          const unsigned long long b = (lp.t_span <= 0xFFFFFFFFull)
+                                           ? (lp.bin_magic ? __umul64hi(lp.bin_magic, off) : off)
+                                           : off / (unsigned long long)lp.bin_ms;
+          const unsigned long long lk =
+              ((b * 4ull + (unsigned long long)d) * (unsigned long long)g.n_rows + (unsigned long long)r) *
+                  (unsigned long long)g.n_cols + (unsigned long long)c;
+          k = (lk << lp.rank_bits) | (unsigned long long)rank[u];
+        }
+      }
+      keys[i] = k;
+      vals[i] = __float_as_uint(sp[u]);  // the sort's payload: the speed, read in lattice order
+    }
   }
   const unsigned long long s = block_sum<256, unsigned long long>(dropped, scratch);
   if (threadIdx.x == 0 && s) atomicAdd(n_dropped, s);
@@ -121,15 +145,32 @@ __global__ void k_lattice_starts(const uint32_t* __restrict__ head, const uint32
   if (blockIdx.x == 0 && threadIdx.x == 0) start[*K] = m;
 }
 
+// Sort keys of the cells by length, longest first (ties by cell).
+__global__ void k_lattice_len_keys(const uint32_t* __restrict__ start, const uint32_t* __restrict__ Kp,
+                                   unsigned long long* __restrict__ lkey) {
+  const uint32_t K = *Kp;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x)
+    lkey[q] = ((unsigned long long)(0xFFFFFFFFu - (start[q + 1] - start[q])) << 32) | q;
+}
+
 // One thread per lattice cell: its points in (journey, row) order give the count, the speed sum
 // in that order (binary64, one add per point as defined), the mean and the unique journeys; the
 // channel extremes go to chan[0..7] (min) and chan[8..15] (max) as order-preserving words.
+// Cells are taken in the order `order` (longest first), so that the lanes of a warp fold
+// cells of about the same length; each cell's own points keep their order.
 __global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, const uint32_t* __restrict__ sspd,
-                               const uint32_t* __restrict__ start, const uint32_t* __restrict__ Kp, int rank_bits,
-                               int32_t n_rows, int32_t n_cols, LatticeOut o, uint32_t* __restrict__ chan) {
+                               const uint32_t* __restrict__ start, const uint32_t* __restrict__ order,
+                               const uint32_t* __restrict__ Kp, int rank_bits, int32_t n_rows, int32_t n_cols,
+                               LatticeOut o, uint32_t* __restrict__ chan) {
+  // channel extremes of this block's cells, merged into chan once per block (the 16 words of
+  // chan would otherwise take four contended global atomics per cell)
+  __shared__ uint32_t s_chan[16];
+  if (threadIdx.x < 16) s_chan[threadIdx.x] = threadIdx.x < 8 ? 0xFFFFFFFFu : 0u;
+  __syncthreads();
   const uint32_t K = *Kp;
   const unsigned long long rmask = (1ull << rank_bits) - 1;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < K; q += gridDim.x * blockDim.x) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < K; w += gridDim.x * blockDim.x) {
+    const uint32_t q = order ? order[w] : w;
     const uint32_t e0 = start[q], e1 = start[q + 1];
     const unsigned long long lk = skey[e0] >> rank_bits;
     uint32_t vol = 0;
@@ -155,10 +196,16 @@ __global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, cons
     o.sum[q] = sum;
     o.mean[q] = mean;
     o.volume[q] = vol;
-    atomicMin(&chan[2 * d], ord_f32(mean));
-    atomicMax(&chan[8 + 2 * d], ord_f32(mean));
-    atomicMin(&chan[2 * d + 1], ord_f32((float)vol));
-    atomicMax(&chan[8 + 2 * d + 1], ord_f32((float)vol));
+    atomicMin(&s_chan[2 * d], ord_f32(mean));
+    atomicMax(&s_chan[8 + 2 * d], ord_f32(mean));
+    atomicMin(&s_chan[2 * d + 1], ord_f32((float)vol));
+    atomicMax(&s_chan[8 + 2 * d + 1], ord_f32((float)vol));
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    if (s_chan[threadIdx.x] != 0xFFFFFFFFu) atomicMin(&chan[threadIdx.x], s_chan[threadIdx.x]);
+  } else if (threadIdx.x < 16) {
+    if (s_chan[threadIdx.x] != 0u) atomicMax(&chan[threadIdx.x], s_chan[threadIdx.x]);
   }
 }
 
