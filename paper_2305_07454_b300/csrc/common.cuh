@@ -144,6 +144,17 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// atomicAdd(ctr, 1) for each lane that calls it, as one atomic per warp (the lanes of a warp
+// that reach it together): returns the lane's own slot, in lane order.
+__device__ __forceinline__ uint32_t warp_inc(uint32_t* ctr) {
+  const uint32_t active = __activemask();
+  const int leader = __ffs(active) - 1;
+  uint32_t base = 0;
+  if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(ctr, (uint32_t)__popc(active));
+  base = __shfl_sync(active, base, leader);
+  return base + (uint32_t)__popc(active & lanemask_lt());
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_tile_lines(const unsigned cha
                                                               uint32_t* __restrict__ lines,
                                                               unsigned long long* __restrict__ total) {
   __shared__ uint32_t scratch[kCsvBlock / 32];
+  unsigned long long block_lines = 0;  // (thread 0) added to *total once
   for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const unsigned long long base = (unsigned long long)t * kCsvTile;
     const unsigned long long end = min(base + (unsigned long long)kCsvTile, len);
@@ -354,9 +355,10 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_tile_lines(const unsigned cha
       const uint32_t before = (base == 0) ? 1u : (buf[base - 1] == '\n' ? 1u : 0u);
       const uint32_t l = c - (buf[end - 1] == '\n' ? 1u : 0u) + before;
       lines[t] = l;
-      atomicAdd(total, (unsigned long long)l);  // 64-bit: the caller checks the 32-bit prefix sums
+      block_lines += l;
     }
   }
+  if (threadIdx.x == 0 && block_lines) atomicAdd(total, block_lines);  // 64-bit: the caller checks the 32-bit prefix sums
 }
 
 // Pass 2: parse tile blockIdx.x, whose first row is tile_row[blockIdx.x]. One pass turns the

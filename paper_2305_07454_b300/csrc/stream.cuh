@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
       ++late;
       continue;
     }
-    const uint32_t o = p_base + atomicAdd(&st->n_pending, 1u);
+    const uint32_t o = p_base + warp_inc(&st->n_pending);
     if (o >= p_cap) {
       atomicOr(&st->err, kErrCapacity);
       continue;
@@ -81,11 +81,11 @@ __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict_
         continue;
       }
       atomicAdd(&h.cnt[s], 1u);
-      const uint32_t o = atomicAdd(&st->n_final, 1u);
+      const uint32_t o = warp_inc(&st->n_final);
       f_rec[o] = r;
       f_slot[o] = (uint32_t)s;
     } else {
-      const uint32_t o = atomicAdd(&st->n_pending, 1u);
+      const uint32_t o = warp_inc(&st->n_pending);
       q_jid[o] = id;
       q_rec[o] = r;
     }
