@@ -36,11 +36,16 @@ __device__ __noinline__ int lattice_direction_exact(float heading, int mode) {
 // itself, h + 45 is exact in binary64 wherever it decides a sector, and floor(r / 90) of the
 // correctly rounded quotient is the number of the edges 90, 180, 270 that r reaches (a quotient
 // just below an integer k never rounds up to k: its distance to k exceeds half an ulp of k), so
-// the sector is the number of edges h reaches.
+// the sector is the number of edges h reaches. A cardinal h in [315, 405) has the remainder
+// h + 45 - 360 in [0, 90) (sector 0); one in [-405, -45) has h + 405 (exact: |h| >= 45, so h
+// needs no bits below 2^-18), whose sector counts the edges -315, -225, -135 that h reaches.
 __device__ __forceinline__ int lattice_direction(float heading, int mode) {
   if (mode == 0) {
     if (heading >= -45.0f && heading < 315.0f)
       return (heading >= 45.0f) + (heading >= 135.0f) + (heading >= 225.0f);
+    if (heading >= 315.0f && heading < 405.0f) return 0;
+    if (heading >= -405.0f && heading < -45.0f)
+      return (heading >= -315.0f) + (heading >= -225.0f) + (heading >= -135.0f);
   } else if (heading >= 0.0f && heading < 360.0f) {
     return (heading >= 90.0f) + (heading >= 180.0f) + (heading >= 270.0f);
   }
