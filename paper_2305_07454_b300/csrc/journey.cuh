@@ -741,7 +741,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SortSmem ssort;
   __shared__ double red_d[kJBlock / 32];
-  __shared__ long long red_i[kJBlock / 32];
+  __shared__ long long red_i[3][kJBlock / 32];
   __shared__ unsigned long long s_tmin, s_tmax;
   __shared__ int s_flag;
   __shared__ int64_t s_first_ts, s_last_ts;
@@ -941,10 +941,28 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     }
   }
   // 3. journey sums in a fixed order; stitch run fragments across thread ranges in order
-  const double sd = block_sum<kJBlock, double>(dist.value(), red_d);
-  const long long sw = block_sum<kJBlock, long long>(dwell_sum, red_i);
-  const long long sdup = block_sum<kJBlock, long long>(n_dup, red_i);
-  const long long soff = block_sum<kJBlock, long long>(n_off, red_i);
+  // (the four block sums in one pass: each value takes the warp tree and then the warps in
+  // order, as block_sum does; the totals are valid in thread 0)
+  double sd = warp_sum(dist.value());
+  long long sw = warp_sum(dwell_sum), sdup = warp_sum(n_dup), soff = warp_sum(n_off);
+  if (lane == 0) {
+    red_d[tid >> 5] = sd;
+    red_i[0][tid >> 5] = sw;
+    red_i[1][tid >> 5] = sdup;
+    red_i[2][tid >> 5] = soff;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    sd = 0.0;
+    sw = sdup = soff = 0;
+#pragma unroll
+    for (int w = 0; w < kJBlock / 32; ++w) {
+      sd += red_d[w];
+      sw += red_i[0][w];
+      sdup += red_i[1][w];
+      soff += red_i[2][w];
+    }
+  }
   StitchSmem& ss = *reinterpret_cast<StitchSmem*>(smem_raw);  // the sort buffers are done
   ss.pre[tid] = pre;
   ss.suf[tid] = run;
