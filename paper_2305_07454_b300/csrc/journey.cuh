@@ -330,9 +330,9 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
 // bucket. Timestamps of a journey are spread almost evenly over its span (regular sampling),
 // so with about one bucket per point the buckets hold a few keys each and the sort is O(n).
 // bucket(t) = min(nb - 1, floor(float(t) * nb / (span + 1))) is non-decreasing in t, so the
-// buckets' concatenation is in key order once each bucket is sorted. Returns false, with the
-// keys untouched in A, when some bucket holds more than kMaxBucket keys (then the caller uses
-// the radix sort). cnt: nb counters in shared memory. The sorted keys end in B.
+// buckets' concatenation is in key order once each bucket is sorted. Returns false when some
+// bucket holds more than kMaxBucket keys (then the caller uses the radix sort). cnt: nb
+// counters in shared memory. The sorted keys end in B.
 constexpr int kMaxBucket = 48;
 
 // Bucket of a time offset t in [0, span]: a journey spanning under 2^32 ms (any real one)
@@ -342,62 +342,8 @@ __device__ __forceinline__ int time_bucket(unsigned long long t, bool narrow, fl
   return min(nb - 1, (int)(f * scale));
 }
 
-__device__ bool cta_bucket_sort(const unsigned long long* A, unsigned long long* B, int n, int pos_bits,
-                                unsigned long long span, uint32_t* cnt, int nb, uint32_t* scan_scratch,
-                                int* flag) {
-  const int tid = threadIdx.x;
-  const float scale = (float)nb / ((float)span + 1.0f);
-  const bool narrow = span <= 0xFFFFFFFFull;
-  for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < n; i += kJBlock) {
-    const int b = time_bucket(A[i] >> pos_bits, narrow, scale, nb);
-    atomicAdd(&cnt[b], 1u);
-  }
-  __syncthreads();
-  // exclusive scan of the counters; each thread owns a contiguous chunk
-  const int chunk = (nb + kJBlock - 1) / kJBlock;
-  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
-  uint32_t sum = 0, mx = 0;
-  for (int i = c0; i < c1; ++i) {
-    sum += cnt[i];
-    mx = max(mx, cnt[i]);
-  }
-  if (tid == 0) *flag = 0;
-  uint32_t base = block_excl_scan<kJBlock>(sum, scan_scratch, nullptr);
-  if (mx > (uint32_t)kMaxBucket) *flag = 1;
-  for (int i = c0; i < c1; ++i) {
-    const uint32_t v = cnt[i];
-    cnt[i] = base;
-    base += v;
-  }
-  __syncthreads();
-  if (*flag) return false;
-  for (int i = tid; i < n; i += kJBlock) {
-    const unsigned long long k = A[i];
-    const int b = time_bucket(k >> pos_bits, narrow, scale, nb);
-    B[atomicAdd(&cnt[b], 1u)] = k;
-  }
-  __syncthreads();
-  // cnt[b] is now the end of bucket b; sort each bucket by key value
-  for (int b = tid; b < nb; b += kJBlock) {
-    const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
-    for (int i = lo + 1; i < hi; ++i) {
-      const unsigned long long v = B[i];
-      int q = i - 1;
-      while (q >= lo && B[q] > v) {
-        B[q + 1] = B[q];
-        --q;
-      }
-      B[q + 1] = v;
-    }
-  }
-  __syncthreads();
-  return true;
-}
-
-// The same counting sort, with the keys rebuilt from the journey's records on each pass
-// (the records stay in L2), so that only the output buffer B takes shared memory.
+// The keys are rebuilt from the journey's records on each pass (the records stay in L2), so
+// that only the output buffer B takes shared memory.
 __device__ __forceinline__ unsigned long long rec_key(const Rec* __restrict__ R, int i,
                                                       unsigned long long tmin, int pos_bits) {
   return ((((unsigned long long)R[i].ts ^ kSign64) - tmin) << pos_bits) | (unsigned long long)i;
