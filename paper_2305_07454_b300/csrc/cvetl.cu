@@ -106,6 +106,7 @@ struct cvetl_ctx {
   struct {
     int journey_ctas = 0;      // persistent journey CTAs per SM (1..3); 0: one CTA per journey
     int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
+    int row_block = 256;       // threads per block of the counting pass and the scatter
     int small_sort_max = 2048;  // pairs up to which one block sorts (0..kCtaSortMax)
   } tune;
   // CUDA graphs of the batch path after sizing (config.graph), one per shape
@@ -935,12 +936,17 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   Rec* rec;
   ENSURE("rec", nv, &rec);
   if (n) {
-    const int U = c->tune.row_unroll;
-#define SCAT(U_) k_scatter<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
+    const int U = c->tune.row_unroll, NT = c->tune.row_block;
+#define SCAT(U_, NT_) k_scatter<U_, NT_><<<grid_for((n + U_ - 1) / U_, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
     c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)
-    if (U == 2) LAUNCH(ST_SCATTER, (SCAT(2)));
-    else if (U == 8) LAUNCH(ST_SCATTER, (SCAT(8)));
-    else LAUNCH(ST_SCATTER, (SCAT(4)));
+#define SCAT_NT(U_)                                                    \
+    if (NT == 128) LAUNCH(ST_SCATTER, (SCAT(U_, 128)));                \
+    else if (NT == 512) LAUNCH(ST_SCATTER, (SCAT(U_, 512)));           \
+    else LAUNCH(ST_SCATTER, (SCAT(U_, 256)));
+    if (U == 2) { SCAT_NT(2) }
+    else if (U == 8) { SCAT_NT(8) }
+    else { SCAT_NT(4) }
+#undef SCAT_NT
 #undef SCAT
     LAUNCH_CHECK();
   }
@@ -1091,7 +1097,7 @@ cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned
   k.precision = c->cfg.precision;
   k.materialize = c->cfg.materialize_points;
   k.t0 = c->tune.journey_ctas;
-  k.t1 = c->tune.row_unroll;
+  k.t1 = c->tune.row_unroll * 1024 + c->tune.row_block;
   k.t2 = c->tune.small_sort_max;
   for (auto& g : c->graphs) {
     if (!(g.key == k)) continue;
@@ -1494,6 +1500,7 @@ cvetl_status cvetl_tuning_get(cvetl_ctx* c, cvetl_tuning* out) {
   if (!out) return fail(c, CVETL_EINVAL, "cvetl_tuning_get: NULL output");
   out->journey_ctas = c->tune.journey_ctas;
   out->row_unroll = c->tune.row_unroll;
+  out->row_block = c->tune.row_block;
   out->small_sort_max = c->tune.small_sort_max;
   return CVETL_OK;
 }
@@ -1504,10 +1511,13 @@ cvetl_status cvetl_tuning_set(cvetl_ctx* c, const cvetl_tuning* t) {
   if (t->journey_ctas < 0 || t->journey_ctas > 3) return fail(c, CVETL_EINVAL, "journey_ctas must be in [0, 3]");
   if (t->row_unroll != 2 && t->row_unroll != 4 && t->row_unroll != 8)
     return fail(c, CVETL_EINVAL, "row_unroll must be 2, 4 or 8");
+  if (t->row_block != 128 && t->row_block != 256 && t->row_block != 512)
+    return fail(c, CVETL_EINVAL, "row_block must be 128, 256 or 512");
   if (t->small_sort_max < 0 || t->small_sort_max > (int32_t)kCtaSortMax)
     return fail(c, CVETL_EINVAL, "small_sort_max must be in [0, %u]", kCtaSortMax);
   c->tune.journey_ctas = t->journey_ctas;
   c->tune.row_unroll = t->row_unroll;
+  c->tune.row_block = t->row_block;
   c->tune.small_sort_max = t->small_sort_max;
   return CVETL_OK;
 }
@@ -1559,13 +1569,13 @@ cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, doubl
   auto best = c->tune;
   double best_ms = 0.0;
   if ((st = measure(&best_ms)) == CVETL_OK) {
-    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048};
-    for (int field = 0; field < 3 && st == CVETL_OK; ++field) {
-      const int* cand = field == 0 ? ctas : field == 1 ? unroll : smax;
-      const int nc = field == 1 ? 3 : 4;
+    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048}, block[] = {128, 256, 512};
+    for (int field = 0; field < 4 && st == CVETL_OK; ++field) {
+      const int* cand = field == 0 ? ctas : field == 1 ? unroll : field == 2 ? smax : block;
+      const int nc = (field == 1 || field == 3) ? 3 : 4;
       for (int k = 0; k < nc && st == CVETL_OK; ++k) {
         auto t = best;
-        int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : t.small_sort_max;
+        int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : field == 2 ? t.small_sort_max : t.row_block;
         if (f == cand[k]) continue;
         f = cand[k];
         c->tune = t;
@@ -1770,12 +1780,17 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
     CK(cudaMemsetAsync(h.cnt, 0, ((size_t)cap + 1) * 4, c->st));
     CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
     if (n) {
-      const int U = c->tune.row_unroll;
-#define HASH(U_) k_hash_count<U_><<<grid_for((n + U_ - 1) / U_, 256), 256, 0, c->st>>>( \
+      const int U = c->tune.row_unroll, NT = c->tune.row_block;
+#define HASH(U_, NT_) k_hash_count<U_, NT_><<<grid_for((n + U_ - 1) / U_, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
     c->jid, c->lat, c->lon, c->spd, n, h, c->bt, row_slot, c->dstate)
-      if (U == 2) LAUNCH(ST_HASH, (HASH(2)));
-      else if (U == 8) LAUNCH(ST_HASH, (HASH(8)));
-      else LAUNCH(ST_HASH, (HASH(4)));
+#define HASH_NT(U_)                                                    \
+      if (NT == 128) LAUNCH(ST_HASH, (HASH(U_, 128)));                 \
+      else if (NT == 512) LAUNCH(ST_HASH, (HASH(U_, 512)));            \
+      else LAUNCH(ST_HASH, (HASH(U_, 256)));
+      if (U == 2) { HASH_NT(2) }
+      else if (U == 8) { HASH_NT(8) }
+      else { HASH_NT(4) }
+#undef HASH_NT
 #undef HASH
       LAUNCH_CHECK();
     }

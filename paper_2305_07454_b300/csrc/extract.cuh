@@ -66,17 +66,17 @@ __device__ __forceinline__ int64_t hash_find(const Hash& h, uint64_t key) {
   return -1;
 }
 
-// U rows per thread per iteration keep U independent probe / atomic chains in flight (2, 4 or 8,
-// chosen by the tuner).
+// U rows per thread per iteration keep U independent probe / atomic chains in flight (2, 4 or 8)
+// in blocks of NT threads (128, 256 or 512), both chosen by the tuner.
 
-template <int U>
-__global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ jid,
+template <int U, int NT>
+__global__ void __launch_bounds__(NT) k_hash_count(const int64_t* __restrict__ jid,
                                                     const double* __restrict__ lat,
                                                     const double* __restrict__ lon,
                                                     const float* __restrict__ spd, uint32_t n,
                                                     Hash h, Batch bt, uint32_t* __restrict__ row_slot,
                                                     DevState* st) {
-  __shared__ unsigned long long scratch[8];
+  __shared__ unsigned long long scratch[NT / 32];
   unsigned long long bad = 0;
   const uint32_t step = gridDim.x * blockDim.x * U;
   for (uint32_t i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < n; i0 += step) {
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_hash_count(const int64_t* __restrict__ 
       if (i < n) row_slot[i] = slot;
     }
   }
-  unsigned long long b = block_sum<256, unsigned long long>(bad, scratch);
+  unsigned long long b = block_sum<NT, unsigned long long>(bad, scratch);
   if (threadIdx.x == 0 && b) atomicAdd(&st->n_malformed, b);
 }
 
@@ -160,8 +160,8 @@ __global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J
 // iteration keep U atomic -> store chains in flight. Each record, with its row index, is one
 // 32-byte store at the bucket cursor: consecutive cursor positions of a journey are written in
 // the order the atomics hand them out, so L2 assembles whole lines before writing them back.
-template <int U>
-__global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ ts,
+template <int U, int NT>
+__global__ void __launch_bounds__(NT) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lat,
                                                  const double* __restrict__ lon,
                                                  const float* __restrict__ spd,
