@@ -55,6 +55,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def over_ranks(maxes, sums, world: int, device="cpu"):
+    """The job's figures over the ranks of a replica run: the largest of each value in `maxes`
+    (times: the slowest rank decides) and the total of each value in `sums` (records). One
+    process per GPU; the process group (NCCL on GPUs, gloo on CPU) is already initialised."""
+    maxes, sums = [float(v) for v in maxes], [int(v) for v in sums]
+    if world == 1:
+        return maxes, sums
+    import torch
+    import torch.distributed as dist
+
+    tm = torch.tensor(maxes, dtype=torch.float64, device=device)
+    ts = torch.tensor(sums, dtype=torch.int64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return [float(v) for v in tm.tolist()], [int(v) for v in ts.tolist()]
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
 
@@ -232,12 +249,9 @@ def run_ours(args):
     counters.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
     if csv_host is not None:
         counters["csv_bytes"] = int(csv_host.numel())
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    (ms_total,), (n_job,) = over_ranks([ms_total], [n], world, dev)
     ms_step = ms_total / args.steps
-    value = n * world * args.steps / (ms_total / 1e3)
+    value = n_job * args.steps / (ms_total / 1e3)
 
     # ---- end to end through the C ABI with host inputs ------------------------------------
     # Two pipelines, each on its own stream and host thread (the library calls release the
@@ -283,6 +297,7 @@ def run_ours(args):
     e2e_s = (time.perf_counter() - t0) / (2 * e2e_per_pipe)
     if errors:
         raise errors[0]
+    (e2e_s,), _ = over_ranks([e2e_s], [], world, dev)
     out = last[0]
     h2d = sum(BYTES[k] for k in COLS) * n if csv_host is None else int(csv_host.numel())
     d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values()) + 8 * 6
@@ -348,8 +363,9 @@ def run_ours(args):
                                   f"CSV text ({int(csv_host.numel())} bytes, 0.5% malformed rows)")
                                + ", fully shuffled", "records": n, "journeys": J, "input": args.input, "precision": args.precision,
                    "l2": "inputs larger than L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-        "e2e": {"value": n * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   **({"records_all_ranks": n_job} if world > 1 else {})},
+        "e2e": {"value": n_job / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "pipelines": 2},
         "gpu_launches": stats["total_launches"],
         "tuning": tuning,

@@ -1,0 +1,61 @@
+"""The replica path of bench.py on CPU: two gloo ranks combine their figures the way the GPU
+ranks do (the slowest rank's time, the records of all ranks), and the reference arm does its
+work on rank 0 only."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, local = bench.dist_env()
+    maxes, sums = bench.over_ranks([10.0 + 5 * rank, 0.5 - 0.1 * rank], [1000 + rank, 7], w)
+    out.put((rank, r, w, local, maxes, sums))
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_over_ranks_with_gloo(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, r, w, local, maxes, sums in got:
+        assert (r, w, local) == (rank, world, rank)
+        assert maxes == [10.0 + 5 * (world - 1), 0.5]
+        assert sums == [sum(1000 + k for k in range(world)), 7 * world]
+
+
+def test_one_rank_needs_no_group():
+    assert bench.over_ranks([3.5], [12], 1) == ([3.5], [12])
+
+
+def test_reference_arm_works_on_rank_zero_only(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class Args:
+        workload, steps, warmup = "small_day", 1, 1
+
+    assert bench.run_reference(Args()) is None
+    assert capsys.readouterr().out == ""
