@@ -32,7 +32,26 @@ struct DevState {
   unsigned long long n_offgrid;
   unsigned long long n_too_late;  // stream mode: records older than the previous watermark
   uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
+  // largest key and largest complemented key among the collected journey ids: the ids' sort
+  // covers only the bits below the highest bit where the smallest and largest key differ
+  unsigned long long key_max, key_nmin;
 };
+
+// Folds every lane's largest and smallest key into DevState's key_max / key_nmin (one atomic
+// pair per warp). All lanes of the warp call it; has = false lanes contribute nothing.
+__device__ __forceinline__ void warp_key_span(bool has, unsigned long long kmax, unsigned long long kmin,
+                                              DevState* st) {
+  unsigned long long mx = has ? kmax : 0ull, nmn = has ? ~kmin : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    nmn = max(nmn, __shfl_xor_sync(0xffffffffu, nmn, o));
+  }
+  if ((threadIdx.x & 31) == 0 && (mx | nmn)) {
+    atomicMax(&st->key_max, mx);
+    atomicMax(&st->key_nmin, nmn);
+  }
+}
 
 // One extracted record, bucketed by journey: 32 bytes, one DRAM sector, written by one store
 // (a separate 4-byte array would take a partial-sector write per record at a random address).

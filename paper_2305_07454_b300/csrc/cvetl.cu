@@ -89,6 +89,7 @@ struct cvetl_ctx {
   uint32_t hint_distinct = 0;       // journeys of the last batch (sizes the next hash table)
   uint32_t* slot_rank = nullptr;    // journey rank of each hash slot (last batch)
   uint32_t* row_slot = nullptr;     // hash slot of each extracted row (last batch)
+  int id_bits = 64;                 // bits the journey-id sort covers (from the ids' key span)
   std::vector<double> batch_key;    // the last batch's instance grids and sizes
   // stream mode
   struct {
@@ -114,7 +115,7 @@ struct cvetl_ctx {
     uint64_t n, J, nv, cap, gen;
     const void* cols[5];
     const void* inst;
-    int n_inst, precision, materialize, t0, t1, t2;
+    int n_inst, precision, materialize, t0, t1, t2, id_bits;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof o) == 0; }
   };
   struct GraphEntry {
@@ -367,6 +368,15 @@ cvetl_status scan_u32(cvetl_ctx* c, const uint32_t* in, uint32_t n, uint32_t* ou
   LAUNCH(ST_SCAN, (scan::k_apply<<<nb, scan::kBlock, 0, c->st>>>(in, n, sums, out, n_dev)));
   LAUNCH_CHECK();
   return CVETL_OK;
+}
+
+// Bits the journey-id sort must cover: up to the highest bit where the smallest and largest
+// collected key differ (the keys agree above it). Reads DevState's key span.
+int key_span_bits(cvetl_ctx* c) {
+  unsigned long long span[2] = {0, 0};
+  if (cudaMemcpy(span, &c->dstate->key_max, sizeof span, cudaMemcpyDeviceToHost) != cudaSuccess) return 64;
+  const unsigned long long diff = span[0] ^ ~span[1];
+  return diff ? 64 - __builtin_clzll(diff) : 1;
 }
 
 cvetl_status read_state(cvetl_ctx* c) {
@@ -707,7 +717,8 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   const uint32_t J = c->hstate->n_touched;
   unsigned long long* skey;
   uint32_t* sslot;
-  if ((s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot)) != CVETL_OK) return s;
+  if ((s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, key_span_bits(c), &skey, &sslot)) != CVETL_OK)
+    return s;
   uint32_t *jn, *joff, *total;
   int64_t* jid_tmp;
   ENSURE("j.n32", (size_t)J, &jn);
@@ -909,7 +920,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   unsigned long long* skey;
   uint32_t* sslot;
   {
-    cvetl_status s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, 64, &skey, &sslot);
+    cvetl_status s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, c->id_bits, &skey, &sslot);
     if (s != CVETL_OK) return s;
   }
   uint32_t *jn, *joff, *total;
@@ -1099,6 +1110,7 @@ cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned
   k.t0 = c->tune.journey_ctas;
   k.t1 = c->tune.row_unroll * 1024 + c->tune.row_block;
   k.t2 = c->tune.small_sort_max;
+  k.id_bits = c->id_bits;
   for (auto& g : c->graphs) {
     if (!(g.key == k)) continue;
     if (!g.exec) return post_sizing(c, h, row_slot, ukey, uslot, J, false);
@@ -1814,12 +1826,14 @@ cvetl_status cvetl_transform(cvetl_ctx* c) {
   ENSURE("j.uslot", (size_t)c->hstate->n_distinct + 1, &uslot);
   ENSURE("j.counter", 1, &counter);
   CK(cudaMemsetAsync(counter, 0, 4, c->st));
-  LAUNCH(ST_COLLECT, (k_collect_slots<<<grid_for((size_t)cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, counter)));
+  LAUNCH(ST_COLLECT, (k_collect_slots<<<grid_for((size_t)cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, counter,
+                                                                                        c->dstate)));
   LAUNCH_CHECK();
   uint32_t J = 0;
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(&J, counter, 4, cudaMemcpyDeviceToHost));
   c->J = J;
+  c->id_bits = key_span_bits(c);
 
   // 3. the rest of transform and load, with no host read until the end
   cvetl_status s = c->cfg.graph ? run_graph(c, h, row_slot, ukey, uslot, J)

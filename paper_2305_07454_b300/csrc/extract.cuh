@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(NT) k_hash_count(const int64_t* __restrict__ j
 
 // Distinct ids (as order-preserving keys) and their slots, in arbitrary order.
 __global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
-                                uint32_t* __restrict__ uslot, uint32_t* counter) {
+                                uint32_t* __restrict__ uslot, uint32_t* counter, DevState* st) {
+  unsigned long long kmax = 0, knmin = 0;  // this thread's span of keys
+  bool any = false;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= h.cap; s += gridDim.x * blockDim.x) {
     bool occ;
     uint64_t id;
@@ -127,10 +129,15 @@ __global__ void k_collect_slots(Hash h, unsigned long long* __restrict__ ukey,
     }
     if (occ) {
       uint32_t i = atomicAdd(counter, 1u);
-      ukey[i] = id ^ kSign64;  // signed order as unsigned order
+      const unsigned long long k = id ^ kSign64;  // signed order as unsigned order
+      ukey[i] = k;
       uslot[i] = s;
+      kmax = max(kmax, k);
+      knmin = max(knmin, ~k);
+      any = true;
     }
   }
+  warp_key_span(any, kmax, ~knmin, st);
 }
 
 // Journey rank r (ascending id): size, id (a batch's (instance, id) is unpacked).

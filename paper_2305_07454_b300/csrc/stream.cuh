@@ -96,13 +96,20 @@ __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict_
 // keys.
 __global__ void k_stream_touched(Hash h, unsigned long long* __restrict__ ukey,
                                  uint32_t* __restrict__ uslot, DevState* st) {
+  unsigned long long kmax = 0, knmin = 0;  // this thread's span of keys
+  bool any = false;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= h.cap; s += gridDim.x * blockDim.x) {
     if (h.cnt[s] == 0) continue;
     const uint64_t id = (s < h.cap) ? h.keys[s] : kHashEmpty;
     const uint32_t i = atomicAdd(&st->n_touched, 1u);
-    ukey[i] = id ^ kSign64;
+    const unsigned long long k = id ^ kSign64;
+    ukey[i] = k;
     uslot[i] = s;
+    kmax = max(kmax, k);
+    knmin = max(knmin, ~k);
+    any = true;
   }
+  warp_key_span(any, kmax, ~knmin, st);
 }
 
 __global__ void __launch_bounds__(256) k_stream_scatter(const Rec* __restrict__ f_rec,
