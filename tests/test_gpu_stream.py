@@ -45,6 +45,23 @@ def test_stream_equals_batch(orc, small_day):
     compare(g, o, points=False)
 
 
+def test_stream_with_ids_over_the_full_int64_range(orc, small_day):
+    """Journey ids at the ends of int64, -1 (the hash table's empty pattern) and random full-range
+    values: each window's id sort covers all the bits the ids span."""
+    rng = np.random.default_rng(31)
+    ids = np.unique(small_day["jid"])
+    extremes = np.array([np.iinfo(np.int64).min, np.iinfo(np.int64).min + 1, -1, 0, 1,
+                         np.iinfo(np.int64).max - 1, np.iinfo(np.int64).max], np.int64)
+    new = np.concatenate([extremes, rng.integers(np.iinfo(np.int64).min, np.iinfo(np.int64).max, ids.shape[0],
+                                                 dtype=np.int64)])[: ids.shape[0]]
+    assert np.unique(new).shape[0] == ids.shape[0]
+    cols = dict(small_day, jid=new[np.searchsorted(ids, small_day["jid"])])
+    wins = windows(cols, arrivals(cols, 3))
+    g = stream_run(wins)
+    o = orc.run({k: np.concatenate([c[k] for c, _ in wins]) for k in cols})
+    compare(g, o, points=False)
+
+
 def test_stream_drops_records_beyond_the_lateness(orc, small_day):
     wins = windows(small_day, arrivals(small_day, 2, late_frac=0.05, max_delay=120000))
     kept = expected_drops(wins)
