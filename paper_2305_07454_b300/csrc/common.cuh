@@ -27,6 +27,7 @@ struct DevState {
   uint32_t n_cells;
   uint32_t n_big;       // journeys taking the chunked-sort path
   uint32_t n_touched;   // stream mode: journeys with points finalised by this window
+  uint32_t n_long;      // stream mode: of those, the ones above the 64-thread journey kernel's limit
   unsigned long long n_malformed;
   unsigned long long n_dup;
   unsigned long long n_offgrid;

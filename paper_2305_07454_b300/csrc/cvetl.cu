@@ -109,6 +109,7 @@ struct cvetl_ctx {
     int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
     int row_block = 256;       // threads per block of the counting pass and the scatter
     int small_sort_max = 2048;  // pairs up to which one block sorts (0..kCtaSortMax)
+    int small_journey_max = 512;  // journeys of up to this many points take 64-thread CTAs (0: none)
   } tune;
   // CUDA graphs of the batch path after sizing (config.graph), one per shape
   struct GraphKey {
@@ -704,7 +705,9 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
     LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
                                 pj, pr, np, wm, all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
     LAUNCH_CHECK();
-    LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate)));
+    const uint32_t lim = (uint32_t)std::min(c->tune.small_journey_max, kJSmallMax);
+    LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate,
+                                                                                              lim)));
     LAUNCH_CHECK();
   }
   cvetl_status s = read_state(c);
@@ -714,7 +717,7 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   ss.n_journeys += c->hstate->n_distinct;
   ss.side ^= 1;
   ss.n_pending = nq;
-  const uint32_t J = c->hstate->n_touched;
+  const uint32_t J = c->hstate->n_touched, n_long = c->hstate->n_long;
   unsigned long long* skey;
   uint32_t* sslot;
   if ((s = sort_pairs<unsigned long long>(c, "jsort", ukey, uslot, J, 0, key_span_bits(c), &skey, &sslot)) != CVETL_OK)
@@ -753,11 +756,20 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   c->jo = o;
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (J) {
+    // a window's journey fragments are mostly short: each kernel shape launches only when the
+    // window holds journeys of its range (n_long of the J above the 64-thread limit)
+    const uint32_t split = (uint32_t)c->tune.small_journey_max;
+    const bool big = !split || n_long > 0, small = split && n_long < J;
+#define JRN(F, NT, SM) k_journeys<F, false, NT><<<J, NT, SM, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, Batch{}, o, \
+                                                                       c->dstate, sslot, ss.js, nullptr, nullptr, split)
     if (c->cfg.precision == CVETL_FP32) {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp32Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, Batch{}, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
+      if (big) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, kJBlock, kJSmem)));
+      if (small) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, kJSmallBlock, kJSmallSmem)));
     } else {
-      LAUNCH(ST_JOURNEYS, (k_journeys<Fp64Form, false><<<J, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, Batch{}, o, c->dstate, sslot, ss.js, nullptr, nullptr)));
+      if (big) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, kJBlock, kJSmem)));
+      if (small) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, kJSmallBlock, kJSmallSmem)));
     }
+#undef JRN
     LAUNCH_CHECK();
   }
   if (all) {  // end of the stream: close every open run
@@ -1021,12 +1033,16 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     const bool pers = c->tune.journey_ctas > 0;
     const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
     const bool f32 = c->cfg.precision == CVETL_FP32;
-#define JRN(F, P) k_journeys<F, P><<<grid, kJBlock, kJSmem, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, c->bt, o, \
-                                                                      c->dstate, nullptr, JState{}, order, work)
-    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true)));
-    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false)));
-    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true)));
-    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false)));
+    // journeys of up to `split` points (at most 512) to the 64-thread shape, the rest first
+    const uint32_t split = (uint32_t)c->tune.small_journey_max;
+#define JRN(F, P, NT, SM, G) k_journeys<F, P, NT><<<G, NT, SM, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, c->bt, o, \
+                                                                      c->dstate, nullptr, JState{}, order, work, split)
+    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true, kJBlock, kJSmem, grid)));
+    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false, kJBlock, kJSmem, grid)));
+    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true, kJBlock, kJSmem, grid)));
+    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false, kJBlock, kJSmem, grid)));
+    if (split && f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false, kJSmallBlock, kJSmallSmem, J)));
+    else if (split) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false, kJSmallBlock, kJSmallSmem, J)));
 #undef JRN
     LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)
@@ -1109,7 +1125,7 @@ cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned
   k.materialize = c->cfg.materialize_points;
   k.t0 = c->tune.journey_ctas;
   k.t1 = c->tune.row_unroll * 1024 + c->tune.row_block;
-  k.t2 = c->tune.small_sort_max;
+  k.t2 = c->tune.small_sort_max * 1024 + c->tune.small_journey_max;
   k.id_bits = c->id_bits;
   for (auto& g : c->graphs) {
     if (!(g.key == k)) continue;
@@ -1270,10 +1286,10 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
   g.dist_k = cfg->earth_radius_m * (3.141592653589793 / 180.0);
-  if (cudaFuncSetAttribute(k_journeys<Fp64Form, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journeys<Fp32Form, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journeys<Fp64Form, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journeys<Fp32Form, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+  if (cudaFuncSetAttribute(k_journeys<Fp64Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp32Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp64Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journeys<Fp32Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1514,6 +1530,7 @@ cvetl_status cvetl_tuning_get(cvetl_ctx* c, cvetl_tuning* out) {
   out->row_unroll = c->tune.row_unroll;
   out->row_block = c->tune.row_block;
   out->small_sort_max = c->tune.small_sort_max;
+  out->small_journey_max = c->tune.small_journey_max;
   return CVETL_OK;
 }
 
@@ -1527,10 +1544,13 @@ cvetl_status cvetl_tuning_set(cvetl_ctx* c, const cvetl_tuning* t) {
     return fail(c, CVETL_EINVAL, "row_block must be 128, 256 or 512");
   if (t->small_sort_max < 0 || t->small_sort_max > (int32_t)kCtaSortMax)
     return fail(c, CVETL_EINVAL, "small_sort_max must be in [0, %u]", kCtaSortMax);
+  if (t->small_journey_max < 0 || t->small_journey_max > kJSmallMax)
+    return fail(c, CVETL_EINVAL, "small_journey_max must be in [0, %d]", kJSmallMax);
   c->tune.journey_ctas = t->journey_ctas;
   c->tune.row_unroll = t->row_unroll;
   c->tune.row_block = t->row_block;
   c->tune.small_sort_max = t->small_sort_max;
+  c->tune.small_journey_max = t->small_journey_max;
   return CVETL_OK;
 }
 
@@ -1581,13 +1601,17 @@ cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, doubl
   auto best = c->tune;
   double best_ms = 0.0;
   if ((st = measure(&best_ms)) == CVETL_OK) {
-    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048}, block[] = {128, 256, 512};
-    for (int field = 0; field < 4 && st == CVETL_OK; ++field) {
-      const int* cand = field == 0 ? ctas : field == 1 ? unroll : field == 2 ? smax : block;
-      const int nc = (field == 1 || field == 3) ? 3 : 4;
+    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048}, block[] = {128, 256, 512},
+              jmax[] = {0, 128, 256, 512};
+    const int* cands[] = {ctas, unroll, smax, block, jmax};
+    const int ncand[] = {4, 3, 4, 3, 4};
+    for (int field = 0; field < 5 && st == CVETL_OK; ++field) {
+      const int* cand = cands[field];
+      const int nc = ncand[field];
       for (int k = 0; k < nc && st == CVETL_OK; ++k) {
         auto t = best;
-        int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : field == 2 ? t.small_sort_max : t.row_block;
+        int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : field == 2 ? t.small_sort_max
+                 : field == 3 ? t.row_block : t.small_journey_max;
         if (f == cand[k]) continue;
         f = cand[k];
         c->tune = t;

@@ -7,15 +7,31 @@
 
 namespace cvetl {
 
-constexpr int kJBlock = 256;   // threads per journey CTA
-constexpr int kJCap = 4096;    // records sorted in shared memory in one piece
+// Two launch shapes of the journey kernel: 256 threads take journeys of any length; 64 threads
+// take journeys of up to 512 points, with four times as many journeys resident per SM (a short
+// journey leaves most of a 256-thread CTA idle through its sort and stitch barriers).
+template <int NT>
+struct JShape;
+template <>
+struct JShape<256> {
+  static constexpr int kCap = 4096;     // records sorted in shared memory in one piece
+  static constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memory chunk (fallback)
+  static constexpr int kRunBuf = 512;   // closed runs staged in shared memory
+  static constexpr int kMinBlocks = 3;
+};
+template <>
+struct JShape<64> {
+  static constexpr int kCap = 512;
+  static constexpr int kEChunk = 256;
+  static constexpr int kRunBuf = 128;
+  static constexpr int kMinBlocks = 12;
+};
+constexpr int kJBlock = 256;   // threads per journey CTA (the shape for journeys of any length)
+constexpr int kJSmallBlock = 64;
+constexpr int kJCap = JShape<kJBlock>::kCap;
+constexpr int kJSmallMax = JShape<kJSmallBlock>::kCap;  // longest journey of the 64-thread shape
 constexpr int kBucketsBig = 12288;  // time buckets for journeys above kJCap (counters in shared memory)
-constexpr int kEChunk = 2048;  // (timestamp, row) pairs sorted per shared-memory chunk (fallback)
-// dynamic shared memory of the journey kernel: a kJCap key buffer + kJCap bucket counters, or
-// (journeys above kJCap, keys in global scratch) kBucketsBig counters
-constexpr int kJSmem = kJCap * 8 + kJCap * 4;
-static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
-static_assert(kEChunk * 16 <= kJSmem, "fallback pair chunks must fit the dynamic shared memory");
+static_assert(kJSmallBlock % 32 == 0 && kJBlock % kJSmallBlock == 0, "walk ranges: whole warps");
 
 struct JourneyOut {
   // journey table, indexed by rank
@@ -61,10 +77,11 @@ __device__ __forceinline__ double haversine_m(double la1, double lo1, double la2
 }
 
 // ---------------------------------------------------------------- in-CTA sorting
+template <int NT>
 __device__ __forceinline__ void bitonic_smem(Elem* E, int P) {
   for (int k = 2; k <= P; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += kJBlock) {
+      for (int i = threadIdx.x; i < P; i += NT) {
         int ixj = i ^ j;
         if (ixj > i) {
           Elem a = E[i], b = E[ixj];
@@ -80,8 +97,9 @@ __device__ __forceinline__ void bitonic_smem(Elem* E, int P) {
   }
 }
 
+template <int NT>
 __device__ __forceinline__ void load_elems(Elem* E, const Rec* __restrict__ R, int base, int m, int P) {
-  for (int i = threadIdx.x; i < P; i += kJBlock) {
+  for (int i = threadIdx.x; i < P; i += NT) {
     Elem e;
     if (i < m) {
       const Rec* r = R + base + i;
@@ -112,14 +130,16 @@ __device__ __forceinline__ int merge_path(const Elem* A, int la, const Elem* B, 
 // Sorts a journey by (timestamp, row) pairs: shared-memory bitonic sort of kEChunk chunks, then rounds
 // of CTA-wide merge-path merges between two global scratch buffers. Returns the buffer
 // holding the sorted elements.
+template <int NT>
 __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem* A, Elem* B) {
+  constexpr int kEChunk = JShape<NT>::kEChunk;
   for (int c0 = 0; c0 < n; c0 += kEChunk) {
     int m = min(kEChunk, n - c0);
     int P = 1;
     while (P < m) P <<= 1;
-    load_elems(E, R, c0, m, P);
-    bitonic_smem(E, P);
-    for (int i = threadIdx.x; i < m; i += kJBlock) A[c0 + i] = E[i];
+    load_elems<NT>(E, R, c0, m, P);
+    bitonic_smem<NT>(E, P);
+    for (int i = threadIdx.x; i < m; i += NT) A[c0 + i] = E[i];
     __syncthreads();
   }
   Elem *src = A, *dst = B;
@@ -130,8 +150,8 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem*
       int total = la + lb;
       const Elem* SA = src + a0;
       const Elem* SB = SA + la;
-      int d0 = (int)((long long)total * threadIdx.x / kJBlock);
-      int d1 = (int)((long long)total * (threadIdx.x + 1) / kJBlock);
+      int d0 = (int)((long long)total * threadIdx.x / NT);
+      int d1 = (int)((long long)total * (threadIdx.x + 1) / NT);
       int i = merge_path(SA, la, SB, lb, d0), j = d0 - i;
       for (int o = d0; o < d1; ++o) {
         if (i < la && (j >= lb || elem_less(SA[i], SB[j]))) dst[a0 + o] = SA[i++];
@@ -254,6 +274,19 @@ struct SortSmem {
   uint32_t scan[kJBlock / 32 + 1];
 };
 
+// static shared memory of the in-CTA sorts: the radix sort's with 256 threads, the bucket sort's
+// scan scratch alone with 64
+template <int NT>
+struct JSort {
+  struct Smem {
+    uint32_t scan[NT / 32 + 1];
+  };
+};
+template <>
+struct JSort<kJBlock> {
+  typedef SortSmem Smem;
+};
+
 __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned long long* B, int n,
                                               int nbits, SortSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -349,20 +382,21 @@ __device__ __forceinline__ unsigned long long rec_key(const Rec* __restrict__ R,
   return ((((unsigned long long)R[i].ts ^ kSign64) - tmin) << pos_bits) | (unsigned long long)i;
 }
 
+template <int NT>
 __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long long tmin, int pos_bits,
                                     unsigned long long* B, int n, unsigned long long span,
                                     uint32_t* cnt, int nb, uint32_t* scan_scratch, int* flag) {
   const int tid = threadIdx.x;
   const float scale = (float)nb / ((float)span + 1.0f);
   const bool narrow = span <= 0xFFFFFFFFull;
-  for (int i = tid; i < nb; i += kJBlock) cnt[i] = 0;
+  for (int i = tid; i < nb; i += NT) cnt[i] = 0;
   __syncthreads();
-  for (int i = tid; i < n; i += kJBlock) {
+  for (int i = tid; i < n; i += NT) {
     const int b = time_bucket(rec_key(R, i, tmin, pos_bits) >> pos_bits, narrow, scale, nb);
     atomicAdd(&cnt[b], 1u);
   }
   __syncthreads();
-  const int chunk = (nb + kJBlock - 1) / kJBlock;
+  const int chunk = (nb + NT - 1) / NT;
   const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
   uint32_t sum = 0, mx = 0;
   for (int i = c0; i < c1; ++i) {
@@ -370,7 +404,7 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
     mx = max(mx, cnt[i]);
   }
   if (tid == 0) *flag = 0;
-  uint32_t base = block_excl_scan<kJBlock>(sum, scan_scratch, nullptr);
+  uint32_t base = block_excl_scan<NT>(sum, scan_scratch, nullptr);
   if (mx > (uint32_t)kMaxBucket) *flag = 1;
   for (int i = c0; i < c1; ++i) {
     const uint32_t v = cnt[i];
@@ -379,13 +413,13 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
   }
   __syncthreads();
   if (*flag) return false;
-  for (int i = tid; i < n; i += kJBlock) {
+  for (int i = tid; i < n; i += NT) {
     const unsigned long long k = rec_key(R, i, tmin, pos_bits);
     const int b = time_bucket(k >> pos_bits, narrow, scale, nb);
     B[atomicAdd(&cnt[b], 1u)] = k;
   }
   __syncthreads();
-  for (int b = tid; b < nb; b += kJBlock) {
+  for (int b = tid; b < nb; b += NT) {
     const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
     for (int i = lo + 1; i < hi; ++i) {
       const unsigned long long v = B[i];
@@ -403,9 +437,10 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
 
 // Keys are ((ts - tmin) << pos_bits) | slot. Points with equal timestamps are ordered by the
 // slot (arbitrary) here; reorder each such group by extracted-row index.
+template <int NT>
 __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* __restrict__ R) {
   const unsigned long long mask = (1ull << pos_bits) - 1;
-  for (int k = threadIdx.x; k < n; k += kJBlock) {
+  for (int k = threadIdx.x; k < n; k += NT) {
     const unsigned long long t = K[k] >> pos_bits;
     const bool lead = (k == 0 || (K[k - 1] >> pos_bits) != t) && (k + 1 < n && (K[k + 1] >> pos_bits) == t);
     if (lead) {
@@ -544,11 +579,12 @@ __device__ __forceinline__ void run_merge(RunPart& r, const RunPart& q) {
   r.mx = fmaxf(r.mx, q.mx);
 }
 
+template <int NT>
 struct StitchSmem {
-  RunPart pre[kJBlock];  // run continuing from the previous thread's range (cnt 0: none)
-  RunPart suf[kJBlock];  // run open at the end of the range
-  uint8_t has[kJBlock];  // the thread had points
-  uint8_t cont[kJBlock]; // the whole range continued the previous thread's run
+  RunPart pre[NT];  // run continuing from the previous thread's range (cnt 0: none)
+  RunPart suf[NT];  // run open at the end of the range
+  uint8_t has[NT];  // the thread had points
+  uint8_t cont[NT]; // the whole range continued the previous thread's run
 };
 
 // Closed runs are staged in shared memory (the bucket counters' space, free once the journey
@@ -560,17 +596,32 @@ struct __align__(8) RunSlot {
   float mn, mx;
   uint32_t pad;
 };
-constexpr int kRunBuf = 512;
-constexpr int kRunBufOff = kJCap * 8;  // after the sort keys of a journey of up to kJCap points
-static_assert(kRunBufOff + kRunBuf * (int)sizeof(RunSlot) <= kJSmem, "run buffer must fit");
-static_assert((int)sizeof(StitchSmem) <= kRunBufOff, "stitch arrays must not overlap the run buffer");
-static_assert(kEChunk * 16 <= kRunBufOff, "fallback pair chunks must not overlap the run buffer");
 
+// Dynamic shared memory of the journey kernel: the sort keys of a journey of up to kCap points,
+// then its kCap bucket counters; once the journey is sorted the run buffer takes the counters'
+// space (and the stitch arrays the keys'). Journeys above kCap (256 threads only) keep their
+// keys in global scratch and use the whole space for kBucketsBig counters.
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+template <int NT>
+__host__ __device__ constexpr int jrunbuf_off() {
+  return cmax(cmax(JShape<NT>::kCap * 8, JShape<NT>::kEChunk * 16), (int)sizeof(StitchSmem<NT>));
+}
+template <int NT>
+__host__ __device__ constexpr int jsmem() {
+  return cmax(JShape<NT>::kCap * 12, jrunbuf_off<NT>() + JShape<NT>::kRunBuf * (int)sizeof(RunSlot));
+}
+constexpr int kJSmem = jsmem<kJBlock>();
+constexpr int kJSmallSmem = jsmem<kJSmallBlock>();
+static_assert(kJSmem == kJCap * 12, "journey kernel shared memory as sized for 256 threads");
+static_assert(kBucketsBig * 4 <= kJSmem, "bucket counters must fit the dynamic shared memory");
+static_assert(JShape<kJSmallBlock>::kCap * 12 <= kJSmallSmem, "keys and counters must fit");
+
+template <int NT>
 __device__ __forceinline__ void run_put(RunSlot* buf, uint32_t* nbuf, const JourneyOut& o, DevState* st,
                                         const RunPart& r) {
   if (r.key == kKeyInvalid || r.cnt == 0) return;
   const uint32_t i = atomicAdd(nbuf, 1u);
-  if (i < (uint32_t)kRunBuf) {
+  if (i < (uint32_t)JShape<NT>::kRunBuf) {
     RunSlot& q = buf[i];
     q.s = r.s;
     q.c = r.c;
@@ -591,7 +642,7 @@ __device__ __forceinline__ void run_put(RunSlot* buf, uint32_t* nbuf, const Jour
 // associatively (continue.continue = continue with X1 + X2; continue.reset = reset with
 // X1 + X2; reset.continue = reset with S1 + X2; reset.reset = reset keeping X1, S2, the run
 // S1 + X2 in between being emitted by its owner), so one warp scans them: each lane folds
-// kJBlock / 32 consecutive threads, an exclusive warp scan gives each lane its incoming open
+// NT / 32 consecutive threads, an exclusive warp scan gives each lane its incoming open
 // run, and each lane then replays its threads, emitting as the serial order would.
 __device__ __forceinline__ RunPart run_empty() {
   return RunPart{kKeyInvalid, 0u, 0u, 0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
@@ -642,10 +693,12 @@ __device__ __forceinline__ RunMap shfl_up_map(const RunMap& f, int d) {
   return o;
 }
 
-// Called by warp 0 only. Returns, in lane 31, the run open after the journey's last point.
-__device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlot* buf, uint32_t* nbuf,
-                               const JourneyOut& o, DevState* st) {
-  constexpr int kPer = kJBlock / 32;
+// Called by warp 0 only, over the nr walk ranges (a multiple of 32). Returns, in lane 31, the
+// run open after the journey's last point.
+template <int NT>
+__device__ RunPart stitch_runs(const StitchSmem<NT>& ss, int nr, const RunPart& init, RunSlot* buf,
+                               uint32_t* nbuf, const JourneyOut& o, DevState* st) {
+  const int kPer = nr / 32;
   const int lane = threadIdx.x & 31, t0 = lane * kPer;
   RunMap f{0u, run_empty(), run_empty()};
 #pragma unroll 1
@@ -668,7 +721,7 @@ __device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlo
     if (ss.cont[t]) {
       open = rp_merge(open, ss.pre[t]);
     } else {
-      run_put(buf, nbuf, o, st, rp_merge(open, ss.pre[t]));
+      run_put<NT>(buf, nbuf, o, st, rp_merge(open, ss.pre[t]));
       open = ss.suf[t];
     }
   }
@@ -677,7 +730,7 @@ __device__ RunPart stitch_runs(const StitchSmem& ss, const RunPart& init, RunSlo
 
 // One journey (rank j) by the whole CTA. Ends with every thread past its last shared-memory use
 // of this journey except the run copy-out (the caller synchronises before the next journey).
-template <class Form>
+template <class Form, int NT>
 __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ rec,
                                             const uint32_t* __restrict__ jn,
                                             const uint32_t* __restrict__ joff, Elem* scrA, Elem* scrB,
@@ -685,9 +738,10 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
                                             DevState* st,
                                             const uint32_t* __restrict__ jslot, const JState& js) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ SortSmem ssort;
-  __shared__ double red_d[kJBlock / 32];
-  __shared__ long long red_i[3][kJBlock / 32];
+  constexpr int kCap = JShape<NT>::kCap, kRunBuf = JShape<NT>::kRunBuf;
+  __shared__ typename JSort<NT>::Smem ssort;
+  __shared__ double red_d[NT / 32];
+  __shared__ long long red_i[3][NT / 32];
   __shared__ unsigned long long s_tmin, s_tmax;
   __shared__ int s_flag;
   __shared__ int64_t s_first_ts, s_last_ts;
@@ -696,13 +750,14 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   __shared__ uint32_t s_last_key;
   __shared__ uint32_t s_nbuf, s_base;
   __shared__ RunPart s_open;
+  constexpr int kRunBufOff = jrunbuf_off<NT>();
   RunSlot* rbuf = reinterpret_cast<RunSlot*>(smem_raw + kRunBufOff);
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int n = (int)jn[j];
   const uint32_t off = joff[j];
   const Rec* R = rec + off;
-  const bool small = n <= kJCap;
+  const bool small = n <= kCap;  // always, with 64 threads
   // the grid and day the journey's points are keyed on (a journey lies in one batch instance)
   const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, R[0].idx) : nullptr;
   // stream mode: the journey continues from its state (last point, open run, running sums)
@@ -713,7 +768,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   // 1. order the bucket by (timestamp, row index)
   // 1a. range of the timestamps (as order-preserving keys)
   unsigned long long lo = ~0ull, hi = 0ull;
-  for (int i = tid; i < n; i += kJBlock) {
+  for (int i = tid; i < n; i += NT) {
     const unsigned long long t = (unsigned long long)R[i].ts ^ kSign64;
     lo = min(lo, t);
     hi = max(hi, t);
@@ -737,41 +792,53 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   const unsigned long long tmin = s_tmin;
   const int pos_bits = max(1, bits_for((unsigned long long)(n > 1 ? n - 1 : 1)));
   const int nbits = pos_bits + bits_for(s_tmax - tmin);
-  const bool radix = nbits <= 64;
+  // keyed: the sort keys below fit 64 bits and the journey was sorted by them; otherwise it is
+  // sorted as (timestamp, row) pairs
+  bool keyed = nbits <= 64;
   const unsigned long long* sortedK = nullptr;
   const Elem* sortedE = nullptr;
-  if (radix) {
+  if (keyed) {
     // 1b. keys ((ts - tmin) << pos_bits) | slot: counting sort by time bucket into shared memory
-    // (global scratch above kJCap); radix sort through global scratch when buckets are crowded;
-    // ties by row index
+    // (global scratch above kCap); when buckets are crowded, a radix sort through global scratch
+    // (256 threads) or the pair sort (64 threads); ties by row index
     unsigned long long* KB = small ? reinterpret_cast<unsigned long long*>(smem_raw)
                                    : reinterpret_cast<unsigned long long*>(scrB + off);
-    uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + kJCap * sizeof(unsigned long long))
+    uint32_t* cnt = small ? reinterpret_cast<uint32_t*>(smem_raw + kCap * sizeof(unsigned long long))
                           : reinterpret_cast<uint32_t*>(smem_raw);
     const int nb = small ? max(1, n) : min(n, kBucketsBig);
-    unsigned long long* K;
+    unsigned long long* K = nullptr;
     if (n <= kBucketsBig * 8 &&
-        cta_bucket_sort_rec(R, tmin, pos_bits, KB, n, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
+        cta_bucket_sort_rec<NT>(R, tmin, pos_bits, KB, n, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
       K = KB;
-    } else {
+    } else if constexpr (NT == kJBlock) {
       unsigned long long* GA = reinterpret_cast<unsigned long long*>(scrA + off);
       unsigned long long* GB = reinterpret_cast<unsigned long long*>(scrB + off);
-      for (int i = tid; i < n; i += kJBlock) GA[i] = rec_key(R, i, tmin, pos_bits);
+      for (int i = tid; i < n; i += NT) GA[i] = rec_key(R, i, tmin, pos_bits);
       __syncthreads();
       K = cta_radix_sort(GA, GB, n, nbits, ssort);
+    } else {
+      keyed = false;
     }
-    fix_ties(K, n, pos_bits, R);
-    sortedK = K;
-  } else {
-    // timestamps spanning more than 2^(64 - pos_bits) ms: compare (timestamp, row) pairs
-    if (tid == 0) atomicAdd(&st->n_big, 1u);
-    sortedE = sort_big(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
+    if (keyed) {
+      fix_ties<NT>(K, n, pos_bits, R);
+      sortedK = K;
+    }
+  }
+  if (!keyed) {
+    // timestamps spanning more than 2^(64 - pos_bits) ms (counted), or crowded buckets with
+    // 64 threads: compare (timestamp, row) pairs
+    if (tid == 0 && nbits > 64) atomicAdd(&st->n_big, 1u);
+    sortedE = sort_big<NT>(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
   }
   const unsigned long long pmask = (1ull << pos_bits) - 1;
 
   // 2. walk: thread t owns the sorted positions [k0, k1) and visits them in order; the
   // predecessor stays in registers, runs of equal keys accumulate in the thread
-  const int k0 = (int)((long long)n * tid / kJBlock), k1 = (int)((long long)n * (tid + 1) / kJBlock);
+  // The ranges, and with them every rounding of the journey's sums, depend on n alone: a journey
+  // of up to 512 points is walked as 64 ranges by either kernel shape, a longer one as 256.
+  const int nr = (NT == kJSmallBlock || n <= kJSmallMax) ? kJSmallBlock : NT;
+  const int k0 = tid < nr ? (int)((long long)n * tid / nr) : n;
+  const int k1 = tid < nr ? (int)((long long)n * (tid + 1) / nr) : n;
   typename Form::Acc dist;
   long long dwell_sum = 0, n_dup = 0, n_off = 0;
   RunPart pre{kKeyInvalid, 0u, 0u, 0.f, 0.f, 0.f, 0.f};
@@ -784,7 +851,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     typename Form::Cos p_cos{};
     float p_spd = 0.0f;
     if (k0 > 0) {  // predecessor: the previous thread's last point
-      const Rec q = R[radix ? (uint32_t)(sortedK[k0 - 1] & pmask) : sortedE[k0 - 1].pos];
+      const Rec q = R[keyed ? (uint32_t)(sortedK[k0 - 1] & pmask) : sortedE[k0 - 1].pos];
       p_ts = q.ts;
       p_lat = q.lat;
       p_lon = q.lon;
@@ -806,12 +873,12 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       in_pre = true;
     }
     // the next record is loaded one point ahead, so its latency overlaps this point's work
-    uint32_t nxt_p = radix ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos;
+    uint32_t nxt_p = keyed ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos;
     Rec nxt = R[nxt_p];
     for (int k = k0; k < k1; ++k) {
       const Rec cur = nxt;
       if (k + 1 < k1) {
-        nxt_p = radix ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos;
+        nxt_p = keyed ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos;
         nxt = R[nxt_p];
       }
       const typename Form::Cos ccur = Form::cosine(cur.lat, g);
@@ -868,7 +935,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
           pre = run;
           in_pre = false;
         } else {
-          run_put(rbuf, &s_nbuf, o, st, run);
+          run_put<NT>(rbuf, &s_nbuf, o, st, run);
         }
       }
       run = RunPart{key, 1u, off + (uint32_t)k, cur.spd, 0.f, cur.spd, cur.spd};
@@ -902,14 +969,14 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     sd = 0.0;
     sw = sdup = soff = 0;
 #pragma unroll
-    for (int w = 0; w < kJBlock / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
       sd += red_d[w];
       sw += red_i[0][w];
       sdup += red_i[1][w];
       soff += red_i[2][w];
     }
   }
-  StitchSmem& ss = *reinterpret_cast<StitchSmem*>(smem_raw);  // the sort buffers are done
+  StitchSmem<NT>& ss = *reinterpret_cast<StitchSmem<NT>*>(smem_raw);  // the sort buffers are done
   ss.pre[tid] = pre;
   ss.suf[tid] = run;
   ss.has[tid] = k0 < k1;
@@ -920,7 +987,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     const RunPart init = has_prev ? RunPart{js.l_key[slot], js.r_cnt[slot], off, js.r_s[slot], js.r_c[slot],
                                             js.r_mn[slot], js.r_mx[slot]}
                                   : run_empty();
-    const RunPart open = stitch_runs(ss, init, rbuf, &s_nbuf, o, st);
+    const RunPart open = stitch_runs<NT>(ss, nr, init, rbuf, &s_nbuf, o, st);
     if (tid == 31) s_open = open;
   }
   __syncthreads();
@@ -948,7 +1015,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       js.r_mn[slot] = open.mn;
       js.r_mx[slot] = open.mx;
     } else {
-      run_put(rbuf, &s_nbuf, o, st, open);
+      run_put<NT>(rbuf, &s_nbuf, o, st, open);
       o.n[j] = n;
       o.off[j] = off;
       o.start_ts[j] = s_first_ts;
@@ -969,7 +1036,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   __syncthreads();
   // the staged runs, written out together
   const uint32_t nb = min(s_nbuf, (uint32_t)kRunBuf), base = s_base;
-  for (uint32_t i = tid; i < nb; i += kJBlock) {
+  for (uint32_t i = tid; i < nb; i += NT) {
     const uint32_t g = base + i;
     if (g >= o.run_cap) {
       atomicOr(&st->err, kErrCapacity);
@@ -989,19 +1056,29 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
 // the short ones fill the tail) through the work counter until the list is exhausted.
 // Otherwise CTA b takes journey order[b] (rank b without a list): the block scheduler's
 // dispatch order then gives the same longest-first start without the loop.
-template <class Form, bool Persistent>
-__global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__ rec,
-                                                         const uint32_t* __restrict__ jn,
-                                                         const uint32_t* __restrict__ joff, uint32_t J,
-                                                         Elem* scrA, Elem* scrB, GridParams g, Batch bt,
-                                                         JourneyOut o, DevState* st,
-                                                         const uint32_t* __restrict__ jslot, JState js,
-                                                         const uint32_t* __restrict__ order, uint32_t* work) {
+// split > 0 shares the journeys between the two shapes: those of up to min(split, 512) points
+// go to the 64-thread kernel (which takes the list from its short end), the rest to the
+// 256-thread kernel; each skips the other's journeys. Both run over the same list.
+template <int NT>
+__device__ __forceinline__ bool journey_mine(uint32_t n, uint32_t split) {
+  const uint32_t lim = min(split, (uint32_t)kJSmallMax);
+  if constexpr (NT == kJBlock) return split == 0 || n > lim;
+  else return n <= lim;
+}
+
+template <class Form, bool Persistent, int NT>
+__global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
+    const Rec* __restrict__ rec, const uint32_t* __restrict__ jn, const uint32_t* __restrict__ joff, uint32_t J,
+    Elem* scrA, Elem* scrB, GridParams g, Batch bt, JourneyOut o, DevState* st,
+    const uint32_t* __restrict__ jslot, JState js, const uint32_t* __restrict__ order, uint32_t* work,
+    uint32_t split) {
   if constexpr (!Persistent) {
-    if (blockIdx.x < J)
-      journey_one<Form>(order ? order[blockIdx.x] : blockIdx.x, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot,
-                        js);
+    if (blockIdx.x >= J) return;
+    const uint32_t w = (NT == kJBlock) ? blockIdx.x : J - 1 - blockIdx.x;
+    const uint32_t j = order ? order[w] : blockIdx.x;
+    if (journey_mine<NT>(jn[j], split)) journey_one<Form, NT>(j, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot, js);
   } else {
+    static_assert(!Persistent || NT == kJBlock, "persistent CTAs take the 256-thread shape");
     __shared__ uint32_t s_w;
     for (;;) {
       if (threadIdx.x == 0) s_w = atomicAdd(work, 1u);
@@ -1009,7 +1086,12 @@ __global__ void __launch_bounds__(kJBlock, 3) k_journeys(const Rec* __restrict__
       const uint32_t w = s_w;
       __syncthreads();
       if (w >= J) break;
-      journey_one<Form>(order ? order[w] : w, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot, js);
+      const uint32_t j = order ? order[w] : w;
+      if (!journey_mine<NT>(jn[j], split)) {
+        if (order) break;  // longest first: the rest of the list is the 64-thread kernel's
+        continue;
+      }
+      journey_one<Form, NT>(j, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot, js);
       __syncthreads();
     }
   }

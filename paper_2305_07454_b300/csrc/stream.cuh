@@ -94,12 +94,16 @@ __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict_
 
 // Journeys touched by this window (count > 0; st->n_touched), with their ids as order-preserving
 // keys.
+// lim > 0: also counts the journeys with more than lim points in this window (n_long), which
+// tells the host whether the 256-thread journey kernel has work.
 __global__ void k_stream_touched(Hash h, unsigned long long* __restrict__ ukey,
-                                 uint32_t* __restrict__ uslot, DevState* st) {
+                                 uint32_t* __restrict__ uslot, DevState* st, uint32_t lim) {
   unsigned long long kmax = 0, knmin = 0;  // this thread's span of keys
   bool any = false;
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s <= h.cap; s += gridDim.x * blockDim.x) {
-    if (h.cnt[s] == 0) continue;
+    const uint32_t cnt = h.cnt[s];
+    if (cnt == 0) continue;
+    if (lim && cnt > lim) warp_inc(&st->n_long);
     const uint64_t id = (s < h.cap) ? h.keys[s] : kHashEmpty;
     const uint32_t i = atomicAdd(&st->n_touched, 1u);
     const unsigned long long k = id ^ kSign64;

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 T0 = 1620518400000
 
 
-def run_gpu(cols, device=True, materialize=True, **cfg):
+def run_gpu(cols, device=True, materialize=True, tuning=None, **cfg):
     import torch
 
     import paper_2305_07454_b300 as P
@@ -21,6 +21,8 @@ def run_gpu(cols, device=True, materialize=True, **cfg):
     if device:
         t = {k: v.cuda() for k, v in t.items()}
     with P.Pipeline(materialize_points=int(materialize), **cfg) as p:
+        if tuning:
+            p.tuning = tuning
         return p.run(t)
 
 
@@ -117,6 +119,35 @@ def test_one_long_journey_many_chunks(orc):
     compare(run_gpu(cols), orc.run(cols))
 
 
+SHORT_SIZES = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 512, 513, 4097]
+
+
+@pytest.mark.parametrize("split", [0, 128, 512])
+@pytest.mark.parametrize("dup_frac", [0.01, 0.6])
+def test_short_journeys_in_64_thread_ctas(orc, split, dup_frac):
+    """Journeys of up to `split` points take the 64-thread journey kernel, the rest the
+    256-thread one; sizes around the 64-thread walk's ranges and the shape limits, and, at
+    dup_frac 0.6, time buckets crowded past the bucket sort's limit (the 64-thread kernel then
+    sorts (timestamp, row) pairs)."""
+    cols = synth(SHORT_SIZES * 3, seed=17 + split, dup_frac=dup_frac)
+    compare(run_gpu(cols, tuning=dict(small_journey_max=split)), orc.run(cols))
+
+
+def test_timestamps_spanning_the_int64_range(orc):
+    """Timestamps spread over the whole int64 range: the sort keys (time offset and bucket
+    position) no longer fit 64 bits and every journey is sorted as (timestamp, row) pairs, in both
+    kernel shapes (steps of about 2^60 ms; every point falls outside the day's bins)."""
+    rng = np.random.default_rng(23)
+    sizes = [3, 60, 200, 511, 900, 5000]
+    cols = synth(sizes, seed=23)
+    ts = rng.integers(np.iinfo(np.int64).min, np.iinfo(np.int64).max, cols["ts"].shape[0], dtype=np.int64)
+    ts[:2] = [np.iinfo(np.int64).min, np.iinfo(np.int64).max]
+    cols["ts"] = ts
+    o = orc.run(cols)
+    for split in (0, 512):
+        compare(run_gpu(cols, tuning=dict(small_journey_max=split)), o)
+
+
 def test_duplicate_heavy_ties_follow_input_order(orc):
     cols = synth([300, 5000], seed=5, dup_frac=0.5)
     compare(run_gpu(cols), orc.run(cols))
@@ -208,8 +239,9 @@ def test_stats_count_launches(small_day):
     with P.Pipeline(profile=1) as p:
         p.run(t, to_host=False)
         s = p.stats()
+        per_run = 2 if p.tuning["small_journey_max"] else 1  # the 256- and 64-thread journey kernels
     assert s["total_launches"] > 10
-    assert s["stages"]["journeys"]["launches"] == 1 and s["stages"]["journeys"]["ms"] > 0
+    assert s["stages"]["journeys"]["launches"] == per_run and s["stages"]["journeys"]["ms"] > 0
 
 
 def test_results_into_pinned_buffers(small_day):

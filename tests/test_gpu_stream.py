@@ -11,12 +11,14 @@ from streams import LATE, arrivals, windows
 
 pytestmark = pytest.mark.gpu
 
-def stream_run(wins, precision=0, stream=None, lateness=LATE):
+def stream_run(wins, precision=0, stream=None, lateness=LATE, tuning=None):
     import torch
 
     import paper_2305_07454_b300 as P
 
     with P.Pipeline(stream=stream, mode=P.STREAM, lateness_ms=lateness, precision=precision) as p:
+        if tuning:
+            p.tuning = tuning
         for cols, end in wins:
             t = {k: torch.from_numpy(cols[k]).cuda() for k in ("jid", "ts", "lat", "lon", "speed")}
             p.push_window(t, end)
@@ -36,10 +38,13 @@ def expected_drops(wins, lateness=LATE):
     return {k: np.concatenate([c[k] for c in keep]) for k in keep[0]}
 
 
-def test_stream_equals_batch(orc, small_day):
+@pytest.mark.parametrize("split", [0, 512])
+def test_stream_equals_batch(orc, small_day, split):
+    """Each window's journey fragments are short: with split 512 nearly all of them take the
+    64-thread journey kernel, continuing their journeys' state across windows."""
     wins = windows(small_day, arrivals(small_day, 1))
     assert len(wins) > 100
-    g = stream_run(wins)
+    g = stream_run(wins, tuning=dict(small_journey_max=split))
     o = orc.run({k: np.concatenate([c[k] for c, _ in wins]) for k in small_day})
     assert g["counters"]["n_too_late"] == 0
     compare(g, o, points=False)
