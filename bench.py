@@ -165,17 +165,28 @@ def fp64_peak_gops():
     return SMS * FP64_PER_CLK_PER_SM * mhz / 1e3, mhz
 
 
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record of a kernel,
+# Per-pass DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record of a stage,
 # from one ncu capture of the tenth-day workload (14,637,283 records) with the kernels as they
-# stand, scaled by records to the workload's launch (the full day is too large to capture under
-# the profiler's size rule); FP64 form, column or CSV input. Empty a kernel's entry when it
-# changes, until it is captured again.
+# stand, scaled by records to the workload's pass (the full day is too large to capture under
+# the profiler's size rule); FP64 form, column or CSV input. The journeys entry adds its two
+# kernel shapes (256- and 64-thread CTAs). Empty a stage's entry when its kernels change, until
+# they are captured again.
 TRAFFIC_PER_RECORD = {
-    "journeys": (825.795840e6 + 66.695936e6) / 14637283,
-    "scatter": (468.868096e6 + 428.238336e6) / 14637283,
-    "hash_count": (410.956800e6 + 48.372736e6) / 14637283,
+    "journeys": (827.050496e6 + 68.221696e6 + 3.345408e6 + 0.0) / 14637283,
+    "scatter": (468.913152e6 + 428.840448e6) / 14637283,
+    "hash_count": (410.996736e6 + 48.926464e6) / 14637283,
     "csv_parse": (856.018944e6 + 549.557760e6) / 14637283,
 }
+
+
+def unit_launches(stage, launches, steps):
+    """Number of passes over the stage's algorithmic work in `launches`. Every stage's launch is
+    one pass, except the journeys stage: its two kernel shapes (journeys of up to 512 points in
+    64-thread CTAs, the rest in 256-thread CTAs) share one pass over all points per step, so its
+    time per pass is the sum of both launches."""
+    if stage == "journeys":
+        return max(1, steps)
+    return max(1, launches)
 
 
 def run_ours(args):
@@ -323,8 +334,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel ---------------------------------------------------
     stages = stats["stages"]
     top = max(stages, key=lambda s: stages[s]["ms"])
-    launches = max(1, stages[top]["launches"])
-    avg_ms = stages[top]["ms"] / launches
+    avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], args.steps)
     hbm_peak, peak_src = load_peaks()
     tpr = TRAFFIC_PER_RECORD.get(top) if args.precision != "fp32" else None
     traffic = tpr * counters["n_valid"] if tpr else None
@@ -345,7 +355,8 @@ def run_ours(args):
                     "peak_source": peak_src, "unit": "GB/s",
                     "frac": (achieved / hbm_peak) if achieved else None,
                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
-    step_bytes = sum(algorithmic_bytes(s, counters) * v["launches"] / args.steps for s, v in stages.items())
+    step_bytes = sum(algorithmic_bytes(s, counters) * unit_launches(s, v["launches"], args.steps) / args.steps
+                     for s, v in stages.items() if v["launches"])
     hbm_step = {"algorithmic_bytes_per_step": step_bytes,
                 "achieved": step_bytes / (ms_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": step_bytes / (ms_step / 1e3) / 1e9 / hbm_peak}
@@ -492,10 +503,9 @@ def serving(host, n, args, batch_cells, batch_ms):
 
 
 def _roofline(stages, counters, precision, n_steps_div=1.0):
-    """Roofline entry of the dominant kernel from per-stage CUDA-event times."""
+    """Roofline entry of the dominant kernel from per-stage CUDA-event times (per step)."""
     top = max(stages, key=lambda k: stages[k]["ms"])
-    launches = max(1, stages[top]["launches"])
-    avg_ms = stages[top]["ms"] / launches
+    avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], 1)
     hbm_peak, peak_src = load_peaks()
     if top == "journeys" and precision == "fp64":
         gops_peak, mhz = fp64_peak_gops()
