@@ -84,6 +84,26 @@ def test_host_instances_and_one_instance_batch(orc):
             exact(f"{part} {k}", one[part][k], plain[part][k])
 
 
+def test_empty_malformed_and_single_row_instances(orc):
+    """Degenerate instances between ordinary ones: no rows, only malformed rows (NaN latitude)
+    and a single row; every instance's slice equals the oracle on that instance alone."""
+    import paper_2305_07454_b300 as P
+
+    base = make(seed=9, days=1)
+    a, b, c, d = base[:4]
+    empty = dict(a, **{k: a[k][:0].copy() for k in COLS})
+    bad = dict(b, lat=np.full_like(b["lat"], np.nan))
+    one = dict(c, **{k: c[k][:1].copy() for k in COLS})
+    insts = [a, empty, bad, one, d]
+    with P.Pipeline(materialize_points=1) as p:
+        res = p.run_batch(on_device(insts))
+        tot = res[0]["batch_counters"]
+    check_instances(orc, insts, res)
+    assert tot["n_malformed"] == sum(orc.run({k: q[k] for k in COLS}, oracle_params(q))["counters"]["n_malformed"]
+                                     for q in insts) >= b["jid"].shape[0]
+    assert [r["journeys"]["n"].shape[0] for r in res[1:4]] == [0, 0, 1]
+
+
 def test_same_ids_in_two_instances_are_two_journeys(orc):
     import paper_2305_07454_b300 as P
 

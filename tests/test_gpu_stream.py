@@ -78,6 +78,31 @@ def test_stream_drops_records_beyond_the_lateness(orc, small_day):
     compare(g, o, points=False)
 
 
+def test_stream_empty_and_late_only_windows(orc, small_day):
+    """Windows with no rows (one repeating the previous window's end, one taking the next
+    window's end early, which makes part of that window late) and a window whose rows are all
+    below the watermark: the tables equal the oracle over the kept rows; drops are counted."""
+    wins = windows(small_day, arrivals(small_day, 4))
+    empty = {k: v[:0].copy() for k, v in wins[0][0].items()}
+    late = {k: v[:40].copy() for k, v in wins[5][0].items()}
+    seq = []
+    for i, (cols, end) in enumerate(wins):
+        seq.append((cols, end))
+        if i == 10:
+            seq.append((empty, end))
+        if i == 20:
+            seq.append((late, end))
+        if i == 30:
+            seq.append((empty, wins[i + 1][1]))
+    kept = expected_drops(seq)
+    n_late = sum(c["ts"].shape[0] for c, _ in seq) - kept["ts"].shape[0]
+    g = stream_run(seq)
+    assert n_late > 40 and g["counters"]["n_too_late"] == n_late
+    o = orc.run(kept)
+    g["counters"]["n_in"] -= n_late
+    compare(g, o, points=False)
+
+
 def test_stream_float32_form(orc, small_day):
     import paper_2305_07454_b300 as P
 
