@@ -128,7 +128,7 @@ class TicketInfo(ctypes.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libcvetl.so is not built ({LIB_PATH}); run "
-                          "`python -m paper_2305_07454_b300.build` (nvcc, sm_103a)")
+                          "`python paper_2305_07454_b300/build.py` (nvcc, sm_103a)")
     lib = ctypes.CDLL(LIB_PATH)
     lib.cvetl_config_default.argtypes = [ctypes.POINTER(Config)]
     lib.cvetl_config_default.restype = None
