@@ -642,8 +642,8 @@ __device__ __forceinline__ void run_put(RunSlot* buf, uint32_t* nbuf, const Jour
 // associatively (continue.continue = continue with X1 + X2; continue.reset = reset with
 // X1 + X2; reset.continue = reset with S1 + X2; reset.reset = reset keeping X1, S2, the run
 // S1 + X2 in between being emitted by its owner), so one warp scans them: each lane folds
-// NT / 32 consecutive threads, an exclusive warp scan gives each lane its incoming open
-// run, and each lane then replays its threads, emitting as the serial order would.
+// nr / 32 consecutive walk ranges (nr = 64 or 256), an exclusive warp scan gives each lane its
+// incoming open run, and each lane then replays its ranges, emitting as the serial order would.
 __device__ __forceinline__ RunPart run_empty() {
   return RunPart{kKeyInvalid, 0u, 0u, 0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
 }
