@@ -2,22 +2,27 @@
 //
 // The multi-pass device-wide radix sort costs two launches and a memset per 8-bit digit, which
 // dominates small sorts (the journeys and runs of one stream window: hundreds to a few
-// thousand pairs). Here one block loads the pairs into shared memory, pads to a power of two
-// and runs a bitonic network on (key bits [begin_bit, end_bit), input position): positions are
-// distinct, so the network yields exactly the stable order, then writes keys and values out.
-// The network does O(n log^2 n) work on one SM: above a few thousand pairs the device-wide sort
-// is faster, hence the limit.
+// thousand pairs). Here one block loads the pairs into shared memory and runs an LSD radix sort
+// there: it first finds which key bits differ between the pairs (an OR and an AND over the
+// keys) and runs a counting pass only for the 8-bit digits that hold such a bit; a digit that is
+// the same in every key would leave the order unchanged. Each pass ranks a warp's keys by warp
+// match (as the journey kernel's radix sort does), sums the warps' digit counts in order, and
+// scatters; every pass is stable, so the result is the stable order by the key bits
+// [begin_bit, end_bit), equal keys in input order.
 #pragma once
 #include "common.cuh"
 
 namespace cvetl {
 
-constexpr uint32_t kCtaSortMax = 2048;
+constexpr uint32_t kCtaSortMax = 4096;
 constexpr int kCtaSortBlock = 1024;
+constexpr int kCtaSortWarps = kCtaSortBlock / 32;
+constexpr int kCtaSortPer = (int)kCtaSortMax / kCtaSortBlock;  // keys per thread per pass
 
+// Two key buffers, two value buffers, and the warps' digit counters (uint16, warp-major).
 template <typename K>
 constexpr size_t cta_sort_smem() {
-  return (size_t)kCtaSortMax * (sizeof(K) + 4);
+  return (size_t)kCtaSortMax * 2 * (sizeof(K) + 4) + (size_t)kCtaSortWarps * 256 * 2;
 }
 
 // Sorts n <= kCtaSortMax pairs by bits [begin_bit, end_bit) of the key. vin == nullptr means
@@ -30,44 +35,112 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
                                                              K* __restrict__ kout,
                                                              uint32_t* __restrict__ vout) {
   extern __shared__ __align__(16) unsigned char smem[];
-  K* sk = reinterpret_cast<K*>(smem);
-  uint32_t* sp = reinterpret_cast<uint32_t*>(sk + kCtaSortMax);
-  const uint32_t N = n < 2 ? 2u : (1u << (32 - __clz(n - 1)));
+  K* ka = reinterpret_cast<K*>(smem);
+  K* kb = ka + kCtaSortMax;
+  uint32_t* va = reinterpret_cast<uint32_t*>(kb + kCtaSortMax);
+  uint32_t* vb = va + kCtaSortMax;
+  uint16_t* wcnt = reinterpret_cast<uint16_t*>(vb + kCtaSortMax);  // [warp][digit]
+  __shared__ uint32_t qsum[4 * 256];  // per quarter of the warps and digit: counts, then offsets
+  __shared__ uint32_t base[256];      // first output position of each digit
+  __shared__ uint32_t scan[kCtaSortBlock / 32 + 1];
+  __shared__ K s_or, s_and;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int width = end_bit - begin_bit;
   const K mask = width >= (int)(8 * sizeof(K)) ? ~(K)0 : (((K)1 << width) - 1);
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-    sk[i] = i < n ? kin[i] : (K)0;
-    sp[i] = i;
+  if (tid == 0) {
+    s_or = (K)0;
+    s_and = ~(K)0;
   }
   __syncthreads();
-  // a < b in (padding last, key bits, position)
-  auto less = [&](K ka, uint32_t pa, K kb, uint32_t pb) {
-    if (pa >= n) return false;
-    if (pb >= n) return true;
-    const K a = (ka >> begin_bit) & mask, b = (kb >> begin_bit) & mask;
-    return a < b || (a == b && pa < pb);
-  };
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint32_t l = i ^ j;
-        if (l <= i) continue;
-        const K ka = sk[i], kb = sk[l];
-        const uint32_t pa = sp[i], pb = sp[l];
-        const bool up = (i & k) == 0;
-        if (up ? less(kb, pb, ka, pa) : less(ka, pa, kb, pb)) {
-          sk[i] = kb;
-          sk[l] = ka;
-          sp[i] = pb;
-          sp[l] = pa;
-        }
-      }
-      __syncthreads();
-    }
+  K o = (K)0, a = ~(K)0;
+  for (uint32_t i = tid; i < n; i += kCtaSortBlock) {
+    const K k = kin[i];
+    ka[i] = k;
+    va[i] = vin ? vin[i] : i;
+    const K d = (k >> begin_bit) & mask;
+    o |= d;
+    a &= d;
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    kout[i] = sk[i];
-    vout[i] = vin ? vin[sp[i]] : sp[i];
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    o |= __shfl_xor_sync(0xffffffffu, o, s);
+    a &= __shfl_xor_sync(0xffffffffu, a, s);
+  }
+  if (lane == 0) {
+    atomicOr(&s_or, o);
+    atomicAnd(&s_and, a);
+  }
+  __syncthreads();
+  const K vary = s_or ^ s_and;  // bits that differ between some two keys
+  K *src = ka, *dst = kb;
+  uint32_t *vs = va, *vd = vb;
+  for (int shift = 0; shift < width; shift += 8) {
+    if (((vary >> shift) & (K)255) == (K)0) continue;  // uniform digit: the pass keeps the order
+    for (int i = tid; i < kCtaSortWarps * 256 / 2; i += kCtaSortBlock) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
+    __syncthreads();
+    // warp w ranks keys [w * 32 * kCtaSortPer, (w + 1) * 32 * kCtaSortPer), 32 at a time in order
+    K key[kCtaSortPer];
+    uint32_t val[kCtaSortPer], dg[kCtaSortPer], rank[kCtaSortPer];
+#pragma unroll
+    for (int r = 0; r < kCtaSortPer; ++r) {
+      const uint32_t idx = (uint32_t)(warp * 32 * kCtaSortPer + r * 32 + lane);
+      const bool in = idx < n;
+      key[r] = in ? src[idx] : (K)0;
+      val[r] = in ? vs[idx] : 0u;
+      const uint32_t d = in ? (uint32_t)((((key[r] >> begin_bit) & mask) >> shift) & (K)255) : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = in ? (uint32_t)wcnt[warp * 256 + d] : 0u;
+      __syncwarp();
+      if (in && lane == __ffs(peers) - 1) wcnt[warp * 256 + d] = (uint16_t)(before + __popc(peers));
+      __syncwarp();
+      dg[r] = d;
+      rank[r] = before + __popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    {  // digit d, quarter q of the warps: exclusive offsets inside the quarter, quarter totals
+      const int d = tid & 255, q = tid >> 8;
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = q * (kCtaSortWarps / 4); w < (q + 1) * (kCtaSortWarps / 4); ++w) {
+        const uint32_t c = wcnt[w * 256 + d];
+        wcnt[w * 256 + d] = (uint16_t)run;
+        run += c;
+      }
+      qsum[q * 256 + d] = run;
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    if (tid < 256) {
+      const uint32_t a0 = qsum[tid], a1 = qsum[256 + tid], a2 = qsum[512 + tid], a3 = qsum[768 + tid];
+      qsum[tid] = 0u;
+      qsum[256 + tid] = a0;
+      qsum[512 + tid] = a0 + a1;
+      qsum[768 + tid] = a0 + a1 + a2;
+      tot = a0 + a1 + a2 + a3;
+    }
+    const uint32_t e = block_excl_scan<kCtaSortBlock>(tot, scan, nullptr);
+    if (tid < 256) base[tid] = e;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kCtaSortPer; ++r) {
+      if (dg[r] < 256u) {
+        const uint32_t d = dg[r];
+        const uint32_t p = base[d] + qsum[(warp / (kCtaSortWarps / 4)) * 256 + d] + wcnt[warp * 256 + d] + rank[r];
+        dst[p] = key[r];
+        vd[p] = val[r];
+      }
+    }
+    __syncthreads();
+    K* tk = src;
+    src = dst;
+    dst = tk;
+    uint32_t* tv = vs;
+    vs = vd;
+    vd = tv;
+  }
+  for (uint32_t i = tid; i < n; i += kCtaSortBlock) {
+    kout[i] = src[i];
+    vout[i] = vs[i];
   }
 }
 

@@ -108,7 +108,7 @@ struct cvetl_ctx {
     int journey_ctas = 0;      // persistent journey CTAs per SM (1..3); 0: one CTA per journey
     int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
     int row_block = 256;       // threads per block of the counting pass and the scatter
-    int small_sort_max = 2048;  // pairs up to which one block sorts (0..kCtaSortMax)
+    int small_sort_max = 4096;  // pairs up to which one block sorts (0..kCtaSortMax)
     int small_journey_max = 512;  // journeys of up to this many points take 64-thread CTAs (0: none)
   } tune;
   // CUDA graphs of the batch path after sizing (config.graph), one per shape
@@ -1601,7 +1601,7 @@ cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, doubl
   auto best = c->tune;
   double best_ms = 0.0;
   if ((st = measure(&best_ms)) == CVETL_OK) {
-    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 512, 1024, 2048}, block[] = {128, 256, 512},
+    const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 1024, 2048, 4096}, block[] = {128, 256, 512},
               jmax[] = {0, 128, 256, 512};
     const int* cands[] = {ctas, unroll, smax, block, jmax};
     const int ncand[] = {4, 3, 4, 3, 4};
