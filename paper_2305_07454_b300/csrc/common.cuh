@@ -32,7 +32,8 @@ struct DevState {
   unsigned long long n_dup;
   unsigned long long n_offgrid;
   unsigned long long n_too_late;  // stream mode: records older than the previous watermark
-  uint32_t n_final, n_pending;    // stream mode: finalised / pending (appended by extract)
+  uint32_t n_final, n_pending;    // stream mode: finalised / still pending after a window's split
+  uint32_t n_appended;            // stream mode: rows the window's extract appended
   // largest key and largest complemented key among the collected journey ids: the ids' sort
   // covers only the bits below the highest bit where the smallest and largest key differ
   unsigned long long key_max, key_nmin;

@@ -94,6 +94,7 @@ struct cvetl_ctx {
   // stream mode
   struct {
     bool flushed = false, has_w_prev = false;
+    bool unread_append = false;  // the last extract's counters are still on the device
     int64_t w_prev = 0, window_end = 0;
     uint32_t arrival = 0, n_pending = 0, n_window = 0;
     int side = 0, jgen = 0, cgen = 0;
@@ -136,6 +137,7 @@ struct cvetl_ctx {
   int64_t total_launches = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> event_pool;
+  cudaEvent_t copy_ev = nullptr;  // stream mode: a window's host columns copied
 };
 
 namespace {
@@ -588,6 +590,36 @@ uint32_t* stream_counter(cvetl_ctx* c, const char* name) {
   return p;
 }
 
+// Grows the journey table (rehashing the journeys seen so far) so that it keeps a load <= 1/2
+// with the journeys of up to `pending` more rows. Uses the context's device state.
+cvetl_status ensure_journey_table(cvetl_ctx* c, uint64_t pending) {
+  auto& ss = c->ss;
+  if (ss.jh.cap == 0 || (uint64_t)(ss.n_journeys + pending) * 2 > ss.jh.cap) {
+    uint32_t cap = next_pow2(2ull * ((uint64_t)ss.n_journeys + pending + 1024));
+    Hash nh{};
+    JState nj{};
+    const int gen = ss.jgen ^ 1;
+    cvetl_status s = alloc_journey_table(c, cap, gen, &nh, &nj);
+    if (s != CVETL_OK) return s;
+    uint32_t* nd = stream_counter(c, "sj.distinct");
+    CK(cudaMemsetAsync(nd, 0, 4, c->st));
+    if (ss.jh.cap) {
+      CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+      LAUNCH(ST_STREAM_TABLES, (k_journey_rehash<<<grid_for((size_t)ss.jh.cap + 1, 256), 256, 0, c->st>>>(
+                                   ss.jh, ss.js, nh, nj, nd, c->dstate)));
+      LAUNCH_CHECK();
+      if ((s = read_state(c)) != CVETL_OK) return s;
+      char pre[16];
+      snprintf(pre, sizeof pre, "sj%d.", ss.jgen);
+      free_gen(c, pre);
+    }
+    ss.jh = nh;
+    ss.js = nj;
+    ss.jgen = gen;
+  }
+  return CVETL_OK;
+}
+
 cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
   auto& ss = c->ss;
   if (ss.flushed) return fail(c, CVETL_ESTATE, "the stream was flushed; create a new context for a new stream");
@@ -598,6 +630,10 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
     return fail(c, CVETL_EINVAL, "windows must come in order of window_end_ms");
   const size_t n = (size_t)in->n;
   if ((uint64_t)ss.arrival + n > 0xFFFFFFFFull) return fail(c, CVETL_EINVAL, "the stream exceeds 2^32 rows");
+  {  // the journey table sized for this window's rows before the device state counts them
+    cvetl_status s = ensure_journey_table(c, (uint64_t)ss.n_pending + n);
+    if (s != CVETL_OK) return s;
+  }
   // admission: the pending store must hold what is pending plus this window
   const size_t need = (size_t)ss.n_pending + n;
   int64_t* pj;
@@ -628,6 +664,11 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
     CK(cudaMemcpyAsync(z, in->speed, n * 4, cudaMemcpyHostToDevice, c->st));
     jid = a; ts = b; lat = x; lon = y; spd = z;
   }
+  if (!in->on_device && n) {  // the host columns are copied when the call returns
+    if (!c->copy_ev && cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, CVETL_ECUDA, "cudaEventCreate failed");
+    CK(cudaEventRecord(c->copy_ev, c->st));
+  }
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (n) {
     LAUNCH(ST_STREAM_APPEND, (k_stream_append<<<grid_for(n, 256), 256, 0, c->st>>>(
@@ -635,11 +676,10 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
                                  ss.has_w_prev ? 1 : 0, pj, pr, ss.n_pending, (uint32_t)need, c->dstate)));
     LAUNCH_CHECK();
   }
-  cvetl_status s = read_state(c);
-  if (s != CVETL_OK) return s;
-  ss.n_pending += c->hstate->n_pending;
-  ss.tot_malformed += (int64_t)c->hstate->n_malformed;
-  ss.tot_late += (int64_t)c->hstate->n_too_late;
+  if (!in->on_device && n) CK(cudaEventSynchronize(c->copy_ev));
+  // the appended count and the drop counters stay on the device until the transform reads its
+  // state: no host round trip between the window's extract and its transform
+  ss.unread_append = true;
   ss.arrival += (uint32_t)n;
   ss.n_window = (uint32_t)n;
   ss.window_end = in->window_end_ms;
@@ -653,34 +693,15 @@ cvetl_status stream_extract(cvetl_ctx* c, const cvetl_input* in) {
 cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   auto& ss = c->ss;
   const int64_t wm = ss.window_end - c->cfg.lateness_ms;
-  // the journey table must keep a load <= 1/2 after this window's new journeys
-  if (ss.jh.cap == 0 || (uint64_t)(ss.n_journeys + ss.n_pending) * 2 > ss.jh.cap) {
-    uint32_t cap = next_pow2(2ull * ((uint64_t)ss.n_journeys + ss.n_pending + 1024));
-    Hash nh{};
-    JState nj{};
-    const int gen = ss.jgen ^ 1;
-    cvetl_status s = alloc_journey_table(c, cap, gen, &nh, &nj);
+  if (!ss.unread_append) {  // a flush: no extract before; the table is sized here
+    cvetl_status s = ensure_journey_table(c, ss.n_pending);
     if (s != CVETL_OK) return s;
-    uint32_t* nd = stream_counter(c, "sj.distinct");
-    CK(cudaMemsetAsync(nd, 0, 4, c->st));
-    if (ss.jh.cap) {
-      CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
-      LAUNCH(ST_STREAM_TABLES, (k_journey_rehash<<<grid_for((size_t)ss.jh.cap + 1, 256), 256, 0, c->st>>>(
-                                   ss.jh, ss.js, nh, nj, nd, c->dstate)));
-      LAUNCH_CHECK();
-      if ((s = read_state(c)) != CVETL_OK) return s;
-      char pre[16];
-      snprintf(pre, sizeof pre, "sj%d.", ss.jgen);
-      free_gen(c, pre);
-    }
-    ss.jh = nh;
-    ss.js = nj;
-    ss.jgen = gen;
   }
   Hash& h = ss.jh;
   CK(cudaMemsetAsync(h.cnt, 0, ((size_t)h.cap + 1) * 4, c->st));
-  // split the pending store
-  const uint32_t np = ss.n_pending;
+  // split the pending store: after an extract its size is on the device (np bounds it)
+  const bool app = ss.unread_append;
+  const uint32_t np = ss.n_pending + (app ? ss.n_window : 0u);
   int64_t *pj, *qj;
   Rec *pr, *qr, *fr;
   uint32_t* fs;
@@ -700,10 +721,11 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   uint32_t* uslot;
   ENSURE("j.ukey", (size_t)np + 1, &ukey);
   ENSURE("j.uslot", (size_t)np + 1, &uslot);
-  CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
+  if (!app) CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
   if (np) {
     LAUNCH(ST_STREAM_SPLIT, (k_stream_split<<<grid_for(np, 256), 256, 0, c->st>>>(
-                                pj, pr, np, wm, all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
+                                pj, pr, np, ss.n_pending, app ? &c->dstate->n_appended : nullptr, wm,
+                                all ? 1 : 0, h, qj, qr, fr, fs, c->dstate)));
     LAUNCH_CHECK();
     const uint32_t lim = (uint32_t)std::min(c->tune.small_journey_max, kJSmallMax);
     LAUNCH(ST_COLLECT, (k_stream_touched<<<grid_for((size_t)h.cap + 1, 256), 256, 0, c->st>>>(h, ukey, uslot, c->dstate,
@@ -714,6 +736,11 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   if (s != CVETL_OK) return s;
   if (c->hstate->err & kErrHashOverflow) return fail(c, CVETL_ECUDA, "internal: journey table overflow");
   const uint32_t nf = c->hstate->n_final, nq = c->hstate->n_pending;
+  if (app) {
+    ss.tot_malformed += (int64_t)c->hstate->n_malformed;
+    ss.tot_late += (int64_t)c->hstate->n_too_late;
+    ss.unread_append = false;
+  }
   ss.n_journeys += c->hstate->n_distinct;
   ss.side ^= 1;
   ss.n_pending = nq;
@@ -728,14 +755,19 @@ cvetl_status stream_finalize(cvetl_ctx* c, bool all) {
   ENSURE("j.off32", (size_t)J, &joff);
   ENSURE("j.total", 1, &total);
   ENSURE("j.idtmp", (size_t)J, &jid_tmp);
-  if (J) {
-    LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0, nullptr)));
+  if (J && J <= kOffsetsMax) {  // sizes, offsets and cursors in one block
+    LAUNCH(ST_SIZES, (k_journey_offsets<<<1, kOffsetsBlock, 0, c->st>>>(sslot, J, h, jn, joff, total)));
     LAUNCH_CHECK();
-  }
-  if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
-  if (J) {
-    LAUNCH(ST_CURSORS, (k_journey_cursors<<<(J + 255) / 256, 256, 0, c->st>>>(sslot, J, joff, h)));
-    LAUNCH_CHECK();
+  } else {
+    if (J) {
+      LAUNCH(ST_SIZES, (k_journey_sizes<<<(J + 255) / 256, 256, 0, c->st>>>(skey, sslot, J, h, jn, jid_tmp, 0, nullptr)));
+      LAUNCH_CHECK();
+    }
+    if ((s = scan_u32(c, jn, J, joff, total)) != CVETL_OK) return s;
+    if (J) {
+      LAUNCH(ST_CURSORS, (k_journey_cursors<<<(J + 255) / 256, 256, 0, c->st>>>(sslot, J, joff, h)));
+      LAUNCH_CHECK();
+    }
   }
   Rec* rec;
   ENSURE("rec", nf, &rec);
@@ -817,14 +849,10 @@ cvetl_status stream_fold(cvetl_ctx* c) {
   uint32_t* sidx;
   cvetl_status s = sort_pairs<unsigned long long>(c, "rsort", c->jo.run_sortkey, nullptr, R, 0, 64, &skey, &sidx);
   if (s != CVETL_OK) return s;
-  uint32_t* head;
-  ENSURE("cell.head", (size_t)R, &head);
   CK(cudaMemsetAsync(c->dstate, 0, sizeof(DevState), c->st));
-  if (R) {
-    LAUNCH(ST_CELL_HEADS, (k_cell_heads<<<(R + 255) / 256, 256, 0, c->st>>>(skey, R, head, nullptr)));
-    LAUNCH_CHECK();
+  if (R) {  // each cell's first run found in the fold itself
     LAUNCH(ST_CELL_WRITE, (k_cell_fold<<<(R + 255) / 256, 256, 0, c->st>>>(
-                              skey, sidx, R, head, c->jo.run_cnt, c->jo.run_sum, c->jo.run_min,
+                              skey, sidx, R, nullptr, c->jo.run_cnt, c->jo.run_sum, c->jo.run_min,
                               c->jo.run_max, ss.ch, &c->dstate->n_cells, c->dstate)));
     LAUNCH_CHECK();
   }
@@ -1317,6 +1345,7 @@ cvetl_status cvetl_destroy(cvetl_ctx* c) {
     cudaEventDestroy(p.second.second);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  if (c->copy_ev) cudaEventDestroy(c->copy_ev);
   for (auto& g : c->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

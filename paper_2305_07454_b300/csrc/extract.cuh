@@ -155,6 +155,37 @@ __global__ void k_journey_sizes(const unsigned long long* __restrict__ skey,
   }
 }
 
+// One block for J <= kOffsetsMax journeys (a stream window's): each journey's size, its offset
+// (exclusive prefix of the sizes), its bucket cursor and the total, in one launch instead of the
+// three of the general path. Thread t takes journeys 4t .. 4t + 3.
+constexpr int kOffsetsBlock = 1024;
+constexpr uint32_t kOffsetsMax = 4u * kOffsetsBlock;
+__global__ void __launch_bounds__(kOffsetsBlock) k_journey_offsets(const uint32_t* __restrict__ sslot, uint32_t J,
+                                                                   Hash h, uint32_t* __restrict__ jn,
+                                                                   uint32_t* __restrict__ joff,
+                                                                   uint32_t* __restrict__ total) {
+  __shared__ uint32_t scratch[kOffsetsBlock / 32 + 1];
+  const uint32_t r0 = 4u * threadIdx.x;
+  uint32_t c[4], sum = 0, tot = 0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    c[u] = (r0 + u < J) ? h.cnt[sslot[r0 + u]] : 0u;
+    sum += c[u];
+  }
+  uint32_t base = block_excl_scan<kOffsetsBlock>(sum, scratch, &tot);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const uint32_t r = r0 + u;
+    if (r < J) {
+      jn[r] = c[u];
+      joff[r] = base;
+      h.aux[sslot[r]] = base;
+    }
+    base += c[u];
+  }
+  if (threadIdx.x == 0) *total = tot;
+}
+
 __global__ void k_journey_cursors(const uint32_t* __restrict__ sslot, uint32_t J,
                                   const uint32_t* __restrict__ joff, Hash h) {
   uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;

@@ -15,7 +15,7 @@
 namespace cvetl {
 
 // Appends the window's kept rows to the pending store after its first p_base entries (the
-// record carries its arrival index arrival_base + row; st->n_pending counts the appended rows);
+// record carries its arrival index arrival_base + row; st->n_appended counts the appended rows);
 // rows whose timestamp is below the previous watermark are dropped as too late.
 __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict__ jid,
                                                        const int64_t* __restrict__ ts,
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
       ++late;
       continue;
     }
-    const uint32_t o = p_base + warp_inc(&st->n_pending);
+    const uint32_t o = p_base + warp_inc(&st->n_appended);
     if (o >= p_cap) {
       atomicOr(&st->err, kErrCapacity);
       continue;
@@ -64,13 +64,16 @@ __global__ void __launch_bounds__(256) k_stream_append(const int64_t* __restrict
 
 // Splits the pending store: timestamps <= watermark go to the finalised list (with their hash
 // slot and the count per journey; st->n_final), the rest to the next pending store
-// (st->n_pending).
+// (st->n_pending). The store holds n entries, or, with appended != nullptr, base + *appended of
+// at most n (the count the window's extract left on the device).
 __global__ void __launch_bounds__(256) k_stream_split(const int64_t* __restrict__ p_jid,
                                                       const Rec* __restrict__ p_rec, uint32_t n,
+                                                      uint32_t base, const uint32_t* __restrict__ appended,
                                                       int64_t wm, int finalize_all, Hash h,
                                                       int64_t* __restrict__ q_jid, Rec* __restrict__ q_rec,
                                                       Rec* __restrict__ f_rec,
                                                       uint32_t* __restrict__ f_slot, DevState* st) {
+  if (appended) n = min(n, base + *appended);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Rec r = p_rec[i];
     const int64_t id = p_jid[i];
@@ -186,7 +189,9 @@ __global__ void k_cell_fold(const unsigned long long* __restrict__ skey, const u
                             const float* __restrict__ run_min, const float* __restrict__ run_max,
                             CellHash c, uint32_t* n_cells, DevState* st) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= R || !head[i]) return;
+  if (i >= R) return;
+  // head == nullptr: a cell's first run is found here (its key differs from the previous run's)
+  if (head ? !head[i] : (i > 0 && (skey[i] >> 32) == (skey[i - 1] >> 32))) return;
   const uint32_t key = (uint32_t)(skey[i] >> 32);
   uint32_t cnt = 0;
   double sum = 0.0;
