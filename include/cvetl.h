@@ -359,7 +359,10 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* ctx, const cvetl_lattice_config* lc,
  * finalised so far. cvetl_flush finalises every pending point and closes every open run (end of
  * the stream); afterwards the tables equal those of one batch over the same rows (integers,
  * min and max exactly, sums within rounding) and the stream accepts no more windows.
- * Windows must come in order of window_end_ms. In batch mode cvetl_flush returns CVETL_ESTATE. */
+ * Windows must come in order of window_end_ms. In stream mode cvetl_extract returns without
+ * waiting for the GPU (host columns are copied before it returns); its drop counters and any
+ * device error of the append are read, and reported, by the window's cvetl_transform.
+ * In batch mode cvetl_flush returns CVETL_ESTATE. */
 cvetl_status cvetl_flush(cvetl_ctx* ctx);
 
 /* Per-kernel launch counts and (with profile = 1) CUDA-event times, summed since the
