@@ -14,35 +14,45 @@
 
 namespace cvetl {
 
-constexpr uint32_t kCtaSortMax = 4096;
+// Two block sizes: 1,024 threads for up to kCtaSortMax pairs, 256 threads for up to a quarter of
+// that (a block's fixed per-pass work, zeroing and summing its warps' digit counters, grows with
+// its warps). Each thread ranks kCtaSortPer keys per pass.
+constexpr int kCtaSortPer = 4;
 constexpr int kCtaSortBlock = 1024;
-constexpr int kCtaSortWarps = kCtaSortBlock / 32;
-constexpr int kCtaSortPer = (int)kCtaSortMax / kCtaSortBlock;  // keys per thread per pass
+constexpr int kCtaSortBlockSmall = 256;
+constexpr uint32_t kCtaSortMax = kCtaSortPer * kCtaSortBlock;
+constexpr uint32_t kCtaSortSmallMax = kCtaSortPer * kCtaSortBlockSmall;
+
+static_assert(kCtaSortBlockSmall % 256 == 0 && kCtaSortBlock % 256 == 0, "a thread per digit and group");
 
 // Two key buffers, two value buffers, and the warps' digit counters (uint16, warp-major).
-template <typename K>
+template <typename K, int NT = kCtaSortBlock>
 constexpr size_t cta_sort_smem() {
-  return (size_t)kCtaSortMax * 2 * (sizeof(K) + 4) + (size_t)kCtaSortWarps * 256 * 2;
+  return (size_t)kCtaSortPer * NT * 2 * (sizeof(K) + 4) + (size_t)(NT / 32) * 256 * 2;
 }
 
-// Sorts n <= kCtaSortMax pairs by bits [begin_bit, end_bit) of the key. vin == nullptr means
-// value = input position. Launch with one block of kCtaSortBlock threads and
-// cta_sort_smem<K>() bytes of dynamic shared memory.
-template <typename K>
-__global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict__ kin,
+// Sorts n <= kCtaSortPer * NT pairs by bits [begin_bit, end_bit) of the key. vin == nullptr means
+// value = input position. Launch with one block of NT threads (256 or 1024) and
+// cta_sort_smem<K, NT>() bytes of dynamic shared memory.
+template <typename K, int NT>
+__global__ void __launch_bounds__(NT) k_cta_sort(const K* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin, uint32_t n,
                                                              int begin_bit, int end_bit,
                                                              K* __restrict__ kout,
                                                              uint32_t* __restrict__ vout) {
+  constexpr int kWarps = NT / 32;
+  constexpr uint32_t kCap = (uint32_t)kCtaSortPer * NT;
+  constexpr int kQ = NT / 256;             // groups of warps whose digit counts one thread sums
+  constexpr int kWarpsPerQ = kWarps / kQ;  // 8
   extern __shared__ __align__(16) unsigned char smem[];
   K* ka = reinterpret_cast<K*>(smem);
-  K* kb = ka + kCtaSortMax;
-  uint32_t* va = reinterpret_cast<uint32_t*>(kb + kCtaSortMax);
-  uint32_t* vb = va + kCtaSortMax;
-  uint16_t* wcnt = reinterpret_cast<uint16_t*>(vb + kCtaSortMax);  // [warp][digit]
-  __shared__ uint32_t qsum[4 * 256];  // per quarter of the warps and digit: counts, then offsets
-  __shared__ uint32_t base[256];      // first output position of each digit
-  __shared__ uint32_t scan[kCtaSortBlock / 32 + 1];
+  K* kb = ka + kCap;
+  uint32_t* va = reinterpret_cast<uint32_t*>(kb + kCap);
+  uint32_t* vb = va + kCap;
+  uint16_t* wcnt = reinterpret_cast<uint16_t*>(vb + kCap);  // [warp][digit]
+  __shared__ uint32_t qsum[kQ * 256];  // per group of warps and digit: counts, then offsets
+  __shared__ uint32_t base[256];       // first output position of each digit
+  __shared__ uint32_t scan[NT / 32 + 1];
   __shared__ K s_or, s_and;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int width = end_bit - begin_bit;
@@ -53,7 +63,7 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
   }
   __syncthreads();
   K o = (K)0, a = ~(K)0;
-  for (uint32_t i = tid; i < n; i += kCtaSortBlock) {
+  for (uint32_t i = tid; i < n; i += NT) {
     const K k = kin[i];
     ka[i] = k;
     va[i] = vin ? vin[i] : i;
@@ -76,7 +86,7 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
   uint32_t *vs = va, *vd = vb;
   for (int shift = 0; shift < width; shift += 8) {
     if (((vary >> shift) & (K)255) == (K)0) continue;  // uniform digit: the pass keeps the order
-    for (int i = tid; i < kCtaSortWarps * 256 / 2; i += kCtaSortBlock) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
+    for (int i = tid; i < kWarps * 256 / 2; i += NT) reinterpret_cast<uint32_t*>(wcnt)[i] = 0u;
     __syncthreads();
     // warp w ranks keys [w * 32 * kCtaSortPer, (w + 1) * 32 * kCtaSortPer), 32 at a time in order
     K key[kCtaSortPer];
@@ -97,11 +107,11 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
       rank[r] = before + __popc(peers & lanemask_lt());
     }
     __syncthreads();
-    {  // digit d, quarter q of the warps: exclusive offsets inside the quarter, quarter totals
+    {  // digit d, group q of the warps: exclusive offsets inside the group, group totals
       const int d = tid & 255, q = tid >> 8;
       uint32_t run = 0;
 #pragma unroll
-      for (int w = q * (kCtaSortWarps / 4); w < (q + 1) * (kCtaSortWarps / 4); ++w) {
+      for (int w = q * kWarpsPerQ; w < (q + 1) * kWarpsPerQ; ++w) {
         const uint32_t c = wcnt[w * 256 + d];
         wcnt[w * 256 + d] = (uint16_t)run;
         run += c;
@@ -111,21 +121,21 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
     __syncthreads();
     uint32_t tot = 0;
     if (tid < 256) {
-      const uint32_t a0 = qsum[tid], a1 = qsum[256 + tid], a2 = qsum[512 + tid], a3 = qsum[768 + tid];
-      qsum[tid] = 0u;
-      qsum[256 + tid] = a0;
-      qsum[512 + tid] = a0 + a1;
-      qsum[768 + tid] = a0 + a1 + a2;
-      tot = a0 + a1 + a2 + a3;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const uint32_t a = qsum[q * 256 + tid];
+        qsum[q * 256 + tid] = tot;
+        tot += a;
+      }
     }
-    const uint32_t e = block_excl_scan<kCtaSortBlock>(tot, scan, nullptr);
+    const uint32_t e = block_excl_scan<NT>(tot, scan, nullptr);
     if (tid < 256) base[tid] = e;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kCtaSortPer; ++r) {
       if (dg[r] < 256u) {
         const uint32_t d = dg[r];
-        const uint32_t p = base[d] + qsum[(warp / (kCtaSortWarps / 4)) * 256 + d] + wcnt[warp * 256 + d] + rank[r];
+        const uint32_t p = base[d] + qsum[(warp / kWarpsPerQ) * 256 + d] + wcnt[warp * 256 + d] + rank[r];
         dst[p] = key[r];
         vd[p] = val[r];
       }
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(kCtaSortBlock) k_cta_sort(const K* __restrict_
     vs = vd;
     vd = tv;
   }
-  for (uint32_t i = tid; i < n; i += kCtaSortBlock) {
+  for (uint32_t i = tid; i < n; i += NT) {
     kout[i] = src[i];
     vout[i] = vs[i];
   }

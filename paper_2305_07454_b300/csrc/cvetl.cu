@@ -304,8 +304,13 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   ENSURE((t + ".k2").c_str(), n, &k2);
   ENSURE((t + ".vb").c_str(), n, &vb);
   if (!n_dev && n <= (uint32_t)c->tune.small_sort_max) {  // small: one block, shared memory
-    LAUNCH(ST_CTA_SORT, (k_cta_sort<K><<<1, kCtaSortBlock, cta_sort_smem<K>(), c->st>>>(
-                            keys, vals, n, begin_bit, end_bit, k2, vb)));
+    if (n <= kCtaSortSmallMax)
+      LAUNCH(ST_CTA_SORT, (k_cta_sort<K, kCtaSortBlockSmall><<<1, kCtaSortBlockSmall,
+                                                              cta_sort_smem<K, kCtaSortBlockSmall>(), c->st>>>(
+                              keys, vals, n, begin_bit, end_bit, k2, vb)));
+    else
+      LAUNCH(ST_CTA_SORT, (k_cta_sort<K, kCtaSortBlock><<<1, kCtaSortBlock, cta_sort_smem<K>(), c->st>>>(
+                              keys, vals, n, begin_bit, end_bit, k2, vb)));
     LAUNCH_CHECK();
     *ko = k2;
     *vo = vb;
@@ -1322,9 +1327,10 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            rs::kTile * 8) != cudaSuccess ||
-      cudaFuncSetAttribute(k_cta_sort<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_cta_sort<unsigned long long, kCtaSortBlock>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cta_sort_smem<unsigned long long>()) != cudaSuccess ||
-      cudaFuncSetAttribute(k_cta_sort<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_cta_sort<uint32_t, kCtaSortBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)cta_sort_smem<uint32_t>()) != cudaSuccess) {
     fail(c, CVETL_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
     return bail(CVETL_ECUDA);

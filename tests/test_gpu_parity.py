@@ -105,10 +105,11 @@ def test_journey_sizes_around_tile_edges(orc, sizes):
     compare(run_gpu(cols), orc.run(cols))
 
 
-@pytest.mark.parametrize("n_journeys", [2047, 2048, 2049, 4095, 4096, 4097])
+@pytest.mark.parametrize("n_journeys", [1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097])
 def test_journey_counts_around_the_block_sort_limit(orc, n_journeys):
-    """Up to 4096 pairs take the one-block sort (its default limit), more the device-wide radix
-    sort (journey ids and, with about one run per journey, the runs)."""
+    """Up to 4096 pairs take the one-block sort (its default limit; 256 threads up to 1024 pairs,
+    1024 threads above), more the device-wide radix sort (journey ids and, with about one run per
+    journey, the runs)."""
     rng = np.random.default_rng(n_journeys)
     cols = synth(list(rng.integers(1, 4, n_journeys)), seed=n_journeys)
     compare(run_gpu(cols), orc.run(cols))
