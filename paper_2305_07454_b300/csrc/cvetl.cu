@@ -208,6 +208,15 @@ struct LaunchScope {
   } while (0)
 
 // Grow-only named device buffer. On success *out holds at least `bytes`.
+// Size of a buffer that must hold `bytes`: bytes + bytes / frac at its first allocation and
+// above 256 MB (a batch's buffers, sized once per workload); twice `bytes` when a smaller buffer
+// grows again, so that the buffers of a stream of windows growing through the day move a few
+// times instead of at every larger window (each move frees and allocates, which synchronises
+// the device and stalls every other context on it).
+inline size_t grow_to(size_t bytes, size_t frac, bool again) {
+  return (again && bytes < ((size_t)256 << 20)) ? 2 * bytes : bytes + bytes / frac;
+}
+
 template <typename T>
 cvetl_status ensure(cvetl_ctx* c, const char* name, size_t count, T** out) {
   size_t bytes = count * sizeof(T);
@@ -216,7 +225,7 @@ cvetl_status ensure(cvetl_ctx* c, const char* name, size_t count, T** out) {
   if (b.bytes < bytes) {
     if (c->capturing) return fail(c, CVETL_ECUDA, "internal: buffer %s would move during a graph capture", name);
     c->buf_gen += 1;
-    size_t grow = bytes + bytes / 8;
+    size_t grow = grow_to(bytes, 8, b.bytes > 0);
     size_t after = c->held - b.bytes + grow;
     if (c->cfg.mem_budget_bytes && after > c->cfg.mem_budget_bytes) {
       return fail(c, CVETL_EFULL, "buffer %s needs %zu bytes; the context holds %zu of a %zu budget",
@@ -493,7 +502,7 @@ cvetl_status grow_keep(cvetl_ctx* c, const char* name, size_t count, size_t keep
   }
   if (c->capturing) return fail(c, CVETL_ECUDA, "internal: buffer %s would move during a graph capture", name);
   c->buf_gen += 1;
-  const size_t grow = bytes + bytes / 4;
+  const size_t grow = grow_to(bytes, 4, b.bytes > 0);
   if (c->cfg.mem_budget_bytes && c->held + grow > c->cfg.mem_budget_bytes)
     return fail(c, CVETL_EFULL, "buffer %s needs %zu more bytes; the context holds %zu of a %zu budget",
                 name, grow, c->held, c->cfg.mem_budget_bytes);
