@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -82,11 +83,11 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="cvetl_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -107,8 +108,11 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        if getattr(self, "_summary", None) is not None:
+            return self._summary
         try:
             rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
         except Exception:
             return None
         if not rows:
@@ -117,8 +121,9 @@ class Clocks:
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i].strip() == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        self._summary = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                         "reasons": reasons, "samples": len(rows)}
+        return self._summary
 
 
 def make_workload(name: str, seed: int, pinned: bool):
@@ -153,16 +158,49 @@ def algorithmic_bytes(stage: str, c: dict) -> float:
 # one fma, the scaled square root and its residual, the scaling, the final fma), the journey
 # distance sum (1) and the implied speed's rounding to float32 (1)
 FP64_OPS_PER_POINT = 14.0
-SMS, FP64_PER_CLK_PER_SM = 148, 2.0
+SMS = 148
+
+# Bytes per record the method must move (the algorithmic floor: read the needed input once,
+# reorder it once, keep kinematics and keys in registers), binary columns; CSV text adds its
+# bytes read and the columns written
+CONTRACT_BYTES_PER_RECORD = 108.0
+CONTRACT_CSV_EXTRA_PER_RECORD = 100.0
 
 
-def fp64_peak_gops():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", 2032.0))
-    except Exception:
-        mhz = 2032.0
-    return SMS * FP64_PER_CLK_PER_SM * mhz / 1e3, mhz
+def fp64_probe(stream, reps=3):
+    """The measured binary64 roof: the library's issue-rate probe (8 independent chains per
+    thread, 1,184 CTAs of 256 threads, about 20 ms per launch) timed with CUDA events on the
+    stream, best of `reps` per kind. Returns G ops/s per kind, and ops per clock per SM at the
+    SM clock sampled while the probes ran."""
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    blocks, threads = SMS * 8, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    kinds = {"fma": P.PROBE_FMA, "add": P.PROBE_ADD, "mul": P.PROBE_MUL, "mix": P.PROBE_MIX}
+    out = {}
+    with Clocks(torch.cuda.current_device()) as clk:
+        for name, kind in kinds.items():
+            iters = 600 if kind == P.PROBE_MIX else 6000
+            P.probe_fp64(kind, blocks, threads, 10, sink, stream)  # load
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ops = P.probe_fp64(kind, blocks, threads, iters, sink, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name] = ops / (best / 1e3) / 1e9
+    cs = clk.summary() or {}
+    mhz = cs.get("sm_mhz")
+    return {"gops": out, "sm_mhz": mhz,
+            "ops_per_clk_per_sm": {k: v * 1e9 / (SMS * mhz * 1e6) for k, v in out.items()} if mhz else None,
+            "peak_gops": max(out[k] for k in ("fma", "add", "mul")),
+            "how": f"{blocks} CTAs x {threads} threads x 8 independent chains, CUDA events, best of {reps}; "
+                   "peak = the fastest single operation kind"}
 
 
 # Per-pass DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record of a stage,
@@ -171,6 +209,7 @@ def fp64_peak_gops():
 # the profiler's size rule); FP64 form, column or CSV input. The journeys entry adds its two
 # kernel shapes (256- and 64-thread CTAs). Empty a stage's entry when its kernels change, until
 # they are captured again.
+TRAFFIC_PER_RECORD_FP32 = {}
 TRAFFIC_PER_RECORD = {
     "journeys": (827.050496e6 + 68.221696e6 + 3.345408e6 + 0.0) / 14637283,
     "scatter": (468.913152e6 + 428.840448e6) / 14637283,
@@ -187,6 +226,119 @@ def unit_launches(stage, launches, steps):
     if stage == "journeys":
         return max(1, steps)
     return max(1, launches)
+
+
+def _day_steps(P, pipe, extract_dev, steps, warmup, barrier, local):
+    """W warm-up steps, then K timed steps (CUDA events on the launching stream, a barrier and a
+    device synchronisation on both sides). Returns (ms for the K steps, clock summary)."""
+    import torch
+
+    stream = pipe.stream
+    for _ in range(warmup):
+        extract_dev(pipe)
+        pipe.transform()
+        pipe.load()
+        pipe.tables()
+    pipe.stats_reset()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(steps):
+            extract_dev(pipe)
+            pipe.transform()
+            pipe.load()
+            pipe.tables()  # reads the sizes and counters back (synchronises the stream)
+        ev1.record(stream)
+        barrier()
+    return ev0.elapsed_time(ev1), clk.summary()
+
+
+def _stage_stats(P, stream, prec, tuning, extract_dev, steps):
+    """Per-kernel times from CUDA events around every launch, taken on a second pipeline with the
+    same launch shapes over as many steps (the events' own cost stays out of the timed steps)."""
+    prof = P.Pipeline(stream=stream, profile=1, precision=prec)
+    prof.tuning = {k: v for k, v in tuning.items() if k not in ("ms", "seconds")}
+    extract_dev(prof)
+    prof.transform()
+    prof.load()
+    prof.tables()  # first use of the shapes
+    prof.stats_reset()
+    for _ in range(steps):
+        extract_dev(prof)
+        prof.transform()
+        prof.load()
+        prof.tables()
+    stats = prof.stats()
+    prof.close()
+    return stats
+
+
+def _hbm_step(stages, counters, ms_step, steps, csv, traffic=None):
+    """The step's bytes against the measured copy bandwidth: the method's algorithmic floor
+    (CONTRACT_BYTES_PER_RECORD per record; CSV adds its text and columns) and the kernels' own
+    byte model (algorithmic_bytes per stage: the passes this implementation makes), and, from the
+    ncu DRAM traffic per record of every stage, the gate figure (sum of DRAM bytes over the sum
+    of kernel times)."""
+    hbm_peak, peak_src = load_peaks()
+    n = counters["n_in"]
+    contract = n * (CONTRACT_BYTES_PER_RECORD + (CONTRACT_CSV_EXTRA_PER_RECORD if csv else 0.0))
+    impl = sum(algorithmic_bytes(s, counters) * unit_launches(s, v["launches"], steps) / steps
+               for s, v in stages.items() if v["launches"])
+    gbs = lambda b: b / (ms_step / 1e3) / 1e9
+    out = {"peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+           "contract_bytes_per_step": contract, "contract_bytes_per_record": contract / n if n else None,
+           "achieved": gbs(contract), "frac": gbs(contract) / hbm_peak,
+           "implementation_bytes_per_step": impl, "implementation_achieved": gbs(impl),
+           "implementation_frac": gbs(impl) / hbm_peak}
+    timed = {s: v for s, v in stages.items() if v["launches"] and v["ms"] > 0}
+    traffic = traffic or {}
+    missing = sorted(s for s in timed if s not in traffic)
+    if missing:
+        out["gate"] = None
+        out["gate_missing_traffic"] = missing
+    else:
+        dram = sum(traffic[s] * counters["n_valid"] * unit_launches(s, v["launches"], steps) / steps
+                   for s, v in timed.items())
+        kms = sum(v["ms"] for v in timed.values()) / steps
+        out["gate"] = {"dram_bytes_per_step": dram, "kernel_ms_per_step": kms,
+                       "achieved": dram / (kms / 1e3) / 1e9, "frac": dram / (kms / 1e3) / 1e9 / hbm_peak,
+                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per record of every stage "
+                                 "(tenth-day capture), scaled by records; CUDA-event kernel times"}
+    return out
+
+
+def _roofline_entry(top, stages, counters, steps, precision, probe):
+    """Roofline of the dominant stage: the FP64 journey kernel against the measured binary64
+    issue rate, any other stage against the measured HBM copy bandwidth."""
+    avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], steps)
+    hbm_peak, peak_src = load_peaks()
+    tpr = TRAFFIC_PER_RECORD.get(top) if precision == "fp64" else TRAFFIC_PER_RECORD_FP32.get(top)
+    traffic = tpr * counters["n_valid"] if tpr else None
+    if top == "journeys" and precision == "fp64" and probe:
+        ops = FP64_OPS_PER_POINT * counters["n_valid"]
+        achieved = ops / (avg_ms / 1e3) / 1e9
+        return {"bound": "alu", "kernel": top, "achieved": achieved, "peak": probe["peak_gops"],
+                "unit": "G binary64 ops/s",
+                "peak_source": "measured: binary64 issue-rate probe, fastest kind (" + probe["how"] + ")",
+                "frac": achieved / probe["peak_gops"], "ops_per_launch": ops, "avg_launch_ms": avg_ms,
+                "traffic": traffic,
+                "hbm_achieved_gbs": algorithmic_bytes(top, counters) / (avg_ms / 1e3) / 1e9,
+                "hbm_frac": algorithmic_bytes(top, counters) / (avg_ms / 1e3) / 1e9 / hbm_peak}
+    ab = algorithmic_bytes(top, counters)
+    achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
+    return {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak,
+            "peak_source": peak_src, "unit": "GB/s",
+            "frac": (achieved / hbm_peak) if achieved else None,
+            "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
+
+
+def _counters(t, csv_host=None):
+    c = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_runs")}
+    c.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
+    if csv_host is not None:
+        c["csv_bytes"] = int(csv_host.numel())
+    return c
 
 
 def run_ours(args):
@@ -219,12 +371,6 @@ def run_ours(args):
         else:
             p.extract_csv(d_csv)
 
-    def run_dev(p):
-        extract_dev(p)
-        p.transform()
-        p.load()
-        return p.results(to_host=False)
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
@@ -238,40 +384,9 @@ def run_ours(args):
     t_tune = time.perf_counter()
     tuning = pipe.autotune(reps=2) if args.autotune else {**pipe.tuning, "ms": None}
     tuning["seconds"] = time.perf_counter() - t_tune
-    for _ in range(args.warmup):
-        run_dev(pipe)
-    pipe.stats_reset()
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            extract_dev(pipe)
-            pipe.transform()
-            pipe.load()
-            pipe.tables()  # reads the sizes and counters back (synchronises the stream)
-        ev1.record(stream)
-        barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    # per-kernel times from CUDA events around every launch, taken on a second pipeline with the
-    # same launch shapes over as many steps (the events' own cost stays out of the timed steps)
-    prof = P.Pipeline(stream=stream, profile=1, precision=prec)
-    prof.tuning = {k: v for k, v in tuning.items() if k not in ("ms", "seconds")}
-    run_dev(prof)  # first use of the shapes
-    prof.stats_reset()
-    for _ in range(args.steps):
-        extract_dev(prof)
-        prof.transform()
-        prof.load()
-        prof.tables()
-    stats = prof.stats()
-    prof.close()
-    t = pipe.tables()
-    counters = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid",
-                                                 "n_dup", "n_runs")}
-    counters.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
-    if csv_host is not None:
-        counters["csv_bytes"] = int(csv_host.numel())
+    ms_total, clocks = _day_steps(P, pipe, extract_dev, args.steps, args.warmup, barrier, local)
+    stats = _stage_stats(P, stream, prec, tuning, extract_dev, args.steps)
+    counters = _counters(pipe.tables(), csv_host)
     (ms_total,), (n_job,) = over_ranks([ms_total], [n], world, dev)
     ms_step = ms_total / args.steps
     value = n_job * args.steps / (ms_total / 1e3)
@@ -344,34 +459,12 @@ def run_ours(args):
                        "min-max normalised, dense tensor written"}
     del L
     # ---- roofline of the dominant kernel ---------------------------------------------------
+    probe = fp64_probe(stream) if args.precision == "fp64" else None
     stages = stats["stages"]
     top = max(stages, key=lambda s: stages[s]["ms"])
-    avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], args.steps)
-    hbm_peak, peak_src = load_peaks()
-    tpr = TRAFFIC_PER_RECORD.get(top) if args.precision != "fp32" else None
-    traffic = tpr * counters["n_valid"] if tpr else None
-    if top == "journeys" and args.precision == "fp64":
-        gops_peak, mhz = fp64_peak_gops()
-        ops = FP64_OPS_PER_POINT * counters["n_valid"]
-        achieved = ops / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": gops_peak,
-                    "unit": "G binary64 ops/s",
-                    "peak_source": f"derived: {SMS} SMs x {FP64_PER_CLK_PER_SM:g} binary64 ops/clk x {mhz:g} MHz",
-                    "frac": achieved / gops_peak, "ops_per_launch": ops, "avg_launch_ms": avg_ms,
-                    "traffic": traffic,
-                    "hbm_achieved_gbs": algorithmic_bytes(top, counters) / (avg_ms / 1e3) / 1e9}
-    else:
-        ab = algorithmic_bytes(top, counters)
-        achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
-        roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak,
-                    "peak_source": peak_src, "unit": "GB/s",
-                    "frac": (achieved / hbm_peak) if achieved else None,
-                    "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
-    step_bytes = sum(algorithmic_bytes(s, counters) * unit_launches(s, v["launches"], args.steps) / args.steps
-                     for s, v in stages.items() if v["launches"])
-    hbm_step = {"algorithmic_bytes_per_step": step_bytes,
-                "achieved": step_bytes / (ms_step / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": step_bytes / (ms_step / 1e3) / 1e9 / hbm_peak}
+    roofline = _roofline_entry(top, stages, counters, args.steps, args.precision, probe)
+    hbm_step = _hbm_step(stages, counters, ms_step, args.steps, csv_host is not None,
+                         TRAFFIC_PER_RECORD if args.precision == "fp64" else TRAFFIC_PER_RECORD_FP32)
     shares = {s: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
               for s, v in stages.items() if v["launches"]}
 
@@ -397,17 +490,80 @@ def run_ours(args):
         "stages": shares,
         "counters": counters,
         "lattice": lattice,
-        "clocks": clk.summary(),
+        "fp64_probe": probe,
+        "clocks": clocks,
     }
-    if args.serve_feeds > 0:
-        batch_cells = pipe.results(to_host=True)["cells"]
-        line["serving"] = serving(host, n, args, batch_cells, ms_step)
-    if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(host, n, budget_s=args.cpu_budget)
-        print(json.dumps(line), flush=True)
+    batch_res = pipe.results(to_host=True)
     pipe.close()
+    # ---- the same day in the float32 form (its own tuned shapes, same protocol) -----------
+    if args.fp32_leg and args.precision == "fp64":
+        line["fp32_day"] = _leg(lambda: _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job,
+                                                  csv_host, batch_res))
+    if args.serve_feeds > 0:
+        line["serving"] = serving(host, n, args, batch_res["cells"], ms_step)
+    if args.week_scale > 0 and csv_host is None:
+        del d_in
+        torch.cuda.empty_cache()
+        line["week"] = _leg(lambda: week_leg(args, args.week_scale, local, rank))
+        line["week"].pop("_host0", None)
+    if rank == 0:
+        line["cpu_baseline"], line["parity"] = cpu_baseline(host, n, budget_s=args.cpu_budget,
+                                                            batch=batch_res if csv_host is None else None)
+        print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _leg(fn):
+    """Runs an extra leg of the bench; a failure is reported in its entry instead of ending the
+    run (the headline figures above it stand on their own)."""
+    try:
+        return fn()
+    except Exception as exc:  # noqa: BLE001 - reported in the line
+        import torch
+
+        torch.cuda.synchronize()
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job, csv_host, batch_res):
+    p32 = P.Pipeline(stream=stream, precision=P.FP32)
+    extract_dev(p32)
+    tune32 = p32.autotune(reps=2) if args.autotune else {**p32.tuning, "ms": None}
+    ms32, clk32 = _day_steps(P, p32, extract_dev, args.steps, args.warmup, barrier, local)
+    st32 = _stage_stats(P, stream, P.FP32, tune32, extract_dev, args.steps)["stages"]
+    c32 = _counters(p32.tables(), csv_host)
+    r32 = p32.results(to_host=True)
+    p32.close()
+    (ms32,), _ = over_ranks([ms32], [0], world, dev)
+    top32 = max(st32, key=lambda s: st32[s]["ms"])
+    return {"ms_per_step": ms32 / args.steps, "records_per_s": n_job * args.steps / (ms32 / 1e3),
+            "hbm_step": _hbm_step(st32, c32, ms32 / args.steps, args.steps, csv_host is not None,
+                                  TRAFFIC_PER_RECORD_FP32),
+            "roofline": _roofline_entry(top32, st32, c32, args.steps, "fp32", None),
+            "stages": {s: {"ms_per_step": v["ms"] / args.steps} for s, v in st32.items() if v["launches"]},
+            "errors_vs_fp64_form": _form_errors(r32, batch_res), "tuning": tune32, "clocks": clk32}
+
+
+def _host_available_bytes():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def _form_errors(res, ref):
+    """Float32 form against the binary64 form of the same input: integer outputs identical,
+    largest relative error of each floating-point output."""
+    same_int = all(np.array_equal(res["cells"][k], ref["cells"][k]) for k in ("key", "count", "min", "max")) and \
+        all(np.array_equal(res["journeys"][k], ref["journeys"][k]) for k in ("id", "n", "start_ts", "end_ts", "dwell_ms"))
+    return {"integers_keys_counts_min_max_equal": bool(same_int),
+            "journey_distance_max_rel": _max_rel(res["journeys"]["distance_m"], ref["journeys"]["distance_m"]),
+            "cell_sum_max_rel": _max_rel(res["cells"]["sum"], ref["cells"]["sum"]),
+            "cell_mean_max_rel": _max_rel(res["cells"]["mean"], ref["cells"]["mean"])}
 
 
 def _window_order(host, n, feeds, t0, seed=7):
@@ -514,26 +670,6 @@ def serving(host, n, args, batch_cells, batch_ms):
     return out
 
 
-def _roofline(stages, counters, precision, n_steps_div=1.0):
-    """Roofline entry of the dominant kernel from per-stage CUDA-event times (per step)."""
-    top = max(stages, key=lambda k: stages[k]["ms"])
-    avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], 1)
-    hbm_peak, peak_src = load_peaks()
-    if top == "journeys" and precision == "fp64":
-        gops_peak, mhz = fp64_peak_gops()
-        ops = FP64_OPS_PER_POINT * counters["n_valid"]
-        achieved = ops / (avg_ms / 1e3) / 1e9
-        return {"bound": "alu", "kernel": top, "achieved": achieved, "peak": gops_peak,
-                "unit": "G binary64 ops/s",
-                "peak_source": f"derived: {SMS} SMs x {FP64_PER_CLK_PER_SM:g} binary64 ops/clk x {mhz:g} MHz",
-                "frac": achieved / gops_peak, "ops_per_launch": ops, "avg_launch_ms": avg_ms, "traffic": None}
-    ab = algorithmic_bytes(top, counters)
-    achieved = ab / (avg_ms / 1e3) / 1e9 if ab else None
-    return {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm_peak, "peak_source": peak_src,
-            "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
-            "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": None}
-
-
 def _max_rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -544,27 +680,36 @@ def _max_rel(a, b):
     return float(d.max())
 
 
-def run_week(args):
+def week_leg(args, scale, local, rank, steps=None, warmup=None):
     """The batched workload: 7 days x 4 regional boxes in one batch (one pass of every kernel,
-    launch shapes from the autotuner, the post-sizing sequence replayed as a CUDA graph)."""
+    launch shapes from the autotuner, the post-sizing sequence replayed as a CUDA graph), float32
+    form unless --precision says otherwise; the binary64 form runs once first (results kept on
+    the host) for the per-output error report."""
     import torch
 
     import cvgen
     import paper_2305_07454_b300 as P
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
+    steps = args.steps if steps is None else steps
+    warmup = max(args.warmup, 2) if warmup is None else warmup
     dev = torch.device("cuda", local)
-    prec = args.precision or "fp32"
-    recipes = cvgen.week_regions(seed=1 + rank, scale=args.scale)
+    prec = args.precision if args.workload == "week_regions" and args.precision else "fp32"
+    recipes = cvgen.week_regions(seed=1 + rank, scale=scale)
+    n_all = sum(cvgen.count(r["params"]) for r in recipes)
+    avail = _host_available_bytes()
+    need = n_all * (sum(BYTES[k] for k in COLS) + 4) * 2  # pinned columns, heading scratch, headroom
+    if avail is not None and avail < need:
+        return {"skipped": f"host memory: {avail / 2**30:.0f} GiB available, {need / 2**30:.0f} GiB wanted "
+                           f"for {n_all} records"}
     t_gen = time.perf_counter()
     host, grids = [], []
     dt = {"jid": torch.int64, "ts": torch.int64, "lat": torch.float64, "lon": torch.float64,
-          "speed": torch.float32, "heading": torch.float32}
+          "speed": torch.float32}
     for r in recipes:
         n_i = cvgen.count(r["params"])
         h = {k: torch.empty(n_i, dtype=v, pin_memory=True) for k, v in dt.items()}
-        cvgen.generate(r["params"], out={k: v.numpy() for k, v in h.items()})
+        cvgen.generate(r["params"], out={**{k: v.numpy() for k, v in h.items()},
+                                         "heading": np.empty(n_i, np.float32)})
         host.append(h)
         grids.append({k: r[k] for k in P.GRID_KEYS})
     t_gen = time.perf_counter() - t_gen
@@ -575,7 +720,15 @@ def run_week(args):
     stream = torch.cuda.current_stream()
     pc = P.FP32 if prec == "fp32" else P.FP64
 
-    # per-stage times of one eager run (profiled), and the FP64 form for the error report
+    ref = None
+    if pc == P.FP32:  # the binary64 form of the same batch, for the error report
+        with P.Pipeline(stream=stream, precision=P.FP64) as p64:
+            p64.extract_batch(d_insts)
+            p64.transform()
+            p64.load()
+            ref = p64.results(to_host=True)
+        torch.cuda.empty_cache()
+    # per-stage times of one eager run (profiled)
     with P.Pipeline(stream=stream, precision=pc, profile=1) as pe:
         pe.extract_batch(d_insts)
         tune_t = time.perf_counter()
@@ -589,24 +742,10 @@ def run_week(args):
         pe.load()
         stats = pe.stats()
         res = pe.results(to_host=True)
-        t = pe.tables()
-    counters = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_runs")}
-    counters.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
-    errors = None
-    if pc == P.FP32:
-        with P.Pipeline(stream=stream, precision=P.FP64) as p64:
-            p64.extract_batch(d_insts)
-            p64.transform()
-            p64.load()
-            ref = p64.results(to_host=True)
-        same_int = all(np.array_equal(res["cells"][k], ref["cells"][k]) for k in ("key", "count", "min", "max")) and \
-            all(np.array_equal(res["journeys"][k], ref["journeys"][k]) for k in ("id", "n", "start_ts", "end_ts", "dwell_ms"))
-        errors = {"integers_keys_counts_min_max_equal": bool(same_int),
-                  "journey_distance_max_rel": _max_rel(res["journeys"]["distance_m"], ref["journeys"]["distance_m"]),
-                  "cell_sum_max_rel": _max_rel(res["cells"]["sum"], ref["cells"]["sum"]),
-                  "cell_mean_max_rel": _max_rel(res["cells"]["mean"], ref["cells"]["mean"])}
-        del ref
-    del res
+        counters = _counters(pe.tables())
+    errors = _form_errors(res, ref) if ref is not None else None
+    del res, ref
+    torch.cuda.empty_cache()
 
     # timed: graph replays of the tuned shapes
     pipe = P.Pipeline(stream=stream, precision=pc, graph=1)
@@ -618,23 +757,22 @@ def run_week(args):
         pipe.load()
         pipe.tables()
 
-    for _ in range(max(args.warmup, 2)):
+    for _ in range(warmup):
         step(d_insts)
     pipe.stats_reset()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step(d_insts)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
     gst = pipe.stats()
-    ms_step = ms_total / args.steps
-    value = n / (ms_step / 1e3)
+    ms_step = ms_total / steps
     # end to end from pinned host columns
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, min(steps, 2))
     step(h_insts)
     t = pipe.tables()
     host_out = pipe.host_tables(cells=int(t.n_cells), journeys=int(t.n_journeys))
@@ -648,33 +786,54 @@ def run_week(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     d2h = sum(v.nbytes for part in ("cells", "journeys") for v in out[part].values())
     pipe.close()
+    del d_insts
+    torch.cuda.empty_cache()
     stages = stats["stages"]
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 2), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == "fp64" else "f32 (binary64 coordinate differences)",
-        "data": "synthetic",
-        "config": {"workload": f"week_regions x{args.scale:g}: {len(recipes)} instances (7 days x 4 regional "
-                               f"boxes), {n} records, {counters['n_journeys']} journeys, Zipf(1.5) journey "
-                               "lengths on [10, 200000], one batch",
-                   "records": n, "instances": len(recipes), "precision": prec, "scale": args.scale,
-                   "instance_records": [int(h["jid"].shape[0]) for h in host],
-                   "l2": "inputs larger than L2 (no flush needed)", "parallelism": "1 GPU"},
+    top = max(stages, key=lambda s: stages[s]["ms"])
+    return {
+        "workload": f"week_regions x{scale:g}: {len(recipes)} instances (7 days x 4 regional boxes), {n} records, "
+                    f"{counters['n_journeys']} journeys, Zipf(1.5) journey lengths on [10, 200000], one batch",
+        "records": n, "instances": len(recipes), "precision": prec, "scale": scale,
+        "instance_records": [int(h["jid"].shape[0]) for h in host],
+        "steps": steps, "warmup": warmup, "ms_per_step": ms_step, "records_per_s": n / (ms_step / 1e3),
         "tuning": {**tuning, "seconds": tune_t},
-        "graph": {"replays_in_timed_steps": gst["graph_replays"], "launches_per_step": gst["total_launches"] / args.steps},
+        "graph": {"replays_in_timed_steps": gst["graph_replays"], "launches_per_step": gst["total_launches"] / steps},
         "e2e": {"value": n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": n * sum(BYTES[k] for k in COLS),
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": gst["total_launches"],
-        "roofline": _roofline(stages, counters, prec),
+        "roofline": _roofline_entry(top, stages, counters, 1, prec, None),
+        "hbm_step": _hbm_step(stages, counters, ms_step, 1, False),
         "stages": {k: {"ms_per_step": v["ms"], "launches_per_step": v["launches"]} for k, v in stages.items() if v["launches"]},
         "errors_vs_fp64_form": errors,
         "counters": counters,
         "generation_s": t_gen,
         "clocks": clk.summary(),
+        "_host0": {k: host[0][k] for k in COLS},
+    }
+
+
+def run_week(args):
+    """--workload week_regions: the batched workload as the line's headline."""
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    w = week_leg(args, args.scale, local, rank)
+    host0 = w.pop("_host0")
+    line = {
+        "metric": METRIC, "value": w["records_per_s"], "unit": UNIT, "n_gpus": world, "steps": w["steps"],
+        "warmup": w["warmup"], "ms_per_step": w["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w["precision"] == "fp64" else "f32 (binary64 coordinate differences)",
+        "data": "synthetic",
+        "config": {"workload": w["workload"], "records": w["records"], "instances": w["instances"],
+                   "precision": w["precision"], "scale": w["scale"], "instance_records": w["instance_records"],
+                   "l2": "inputs larger than L2 (no flush needed)", "parallelism": "1 GPU"},
+        **{k: w[k] for k in ("tuning", "graph", "e2e", "gpu_launches", "roofline", "hbm_step", "stages",
+                             "errors_vs_fp64_form", "counters", "generation_s", "clocks")},
     }
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline({k: host[0][k] for k in COLS}, int(host[0]["jid"].shape[0]), budget_s=args.cpu_budget)
+        line["cpu_baseline"], _ = cpu_baseline(host0, int(host0["jid"].shape[0]), budget_s=args.cpu_budget)
         print(json.dumps(line), flush=True)
 
 
@@ -686,27 +845,104 @@ def _sample_journeys(host, frac_den: int):
     return {k: (host[k].numpy() if hasattr(host[k], "numpy") else host[k])[sel] for k in COLS}
 
 
-def cpu_baseline(host, n, budget_s=15.0):
+def _agree(name, got, want, bad, rel=None, abs_=1e-9):
+    """Records in `bad` the first element where got and want differ (exactly, or beyond
+    rel * max(|got|, |want|) + abs_ when rel is given)."""
+    got, want = np.asarray(got), np.asarray(want)
+    if got.shape != want.shape:
+        bad.append(f"{name}: shape {got.shape} vs {want.shape}")
+        return
+    if rel is None:
+        ok = (got == want.astype(got.dtype)) | (np.isnan(got) & np.isnan(want)) if got.dtype.kind == "f" \
+            else got == want.astype(got.dtype)
+    else:
+        g, w = got.astype(np.float64), want.astype(np.float64)
+        ok = (np.abs(g - w) <= rel * np.maximum(np.abs(g), np.abs(w)) + abs_) | (np.isnan(g) & np.isnan(w))
+    if not ok.all():
+        i = int(np.flatnonzero(~ok)[0])
+        bad.append(f"{name}: {int((~ok).sum())} of {ok.size} differ, first at {i}: {got.flat[i]!r} vs {want.flat[i]!r}")
+
+
+def _parity(sample, o, batch):
+    """The CUDA path against the oracle at the benchmarked size. (1) The full day's journey rows
+    of the sampled journeys (whole journeys, so their rows depend on nothing else) against the
+    oracle's: counts, times, dwell and positions exactly, distance within 1e-6 relative.
+    (2) The pipeline run on the sample alone against the oracle on the sample: every table and
+    per-point column (order, keys, flags, counts, min and max exactly; floats within 1e-6).
+    (3) Properties of the full day's tables that hold at any size: conservation of records,
+    cell keys strictly increasing, min <= mean <= max."""
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    bad = []
+    bj, oj = batch["journeys"], o["journeys"]
+    at = np.searchsorted(bj["id"], oj["jid"])
+    at = np.minimum(at, max(bj["id"].shape[0] - 1, 0))
+    if not np.array_equal(bj["id"][at], oj["jid"]):
+        bad.append("full-day journey ids: sampled ids missing")
+    else:
+        for k in ("n", "start_ts", "end_ts", "duration_ms", "dwell_ms", "start_lat", "start_lon", "end_lat", "end_lon"):
+            _agree("full-day journey " + k, bj[k][at], oj[k], bad)
+        _agree("full-day journey distance_m", bj["distance_m"][at], oj["distance_m"], bad, rel=1e-6)
+    t = {k: torch.from_numpy(np.ascontiguousarray(sample[k])).cuda() for k in COLS}
+    with P.Pipeline(materialize_points=1) as p:
+        g = p.run(t)
+    for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_journeys", "n_cells"):
+        if g["counters"][k] != o["counters"][k]:
+            bad.append(f"sample counter {k}: {g['counters'][k]} vs {o['counters'][k]}")
+    _agree("sample journey id", g["journeys"]["id"], oj["jid"], bad)
+    for k in ("n", "start_ts", "end_ts", "duration_ms", "dwell_ms", "start_lat", "start_lon", "end_lat", "end_lon"):
+        _agree("sample journey " + k, g["journeys"][k], oj[k], bad)
+    _agree("sample journey distance_m", g["journeys"]["distance_m"], oj["distance_m"], bad, rel=1e-6)
+    for k in ("key", "row", "col", "bin", "count", "min", "max"):
+        _agree("sample cell " + k, g["cells"][k], o["cells"][k], bad)
+    for k in ("sum", "mean"):
+        _agree("sample cell " + k, g["cells"][k], o["cells"][k], bad, rel=1e-6)
+    for k in ("perm", "key", "flags", "dwell", "stop_ms"):
+        _agree("sample point " + k, g["points"][k], o["points"][k], bad)
+    for k in ("d", "vhat", "accel", "accel_v"):
+        _agree("sample point " + k, g["points"][k], o["points"][k], bad, rel=1e-6)
+    bc, cc = batch["cells"], batch["counters"]
+    if int(bc["count"].astype(np.int64).sum()) + cc["n_out_of_grid"] != cc["n_valid"]:
+        bad.append("full day: cell counts + off-grid points != kept records")
+    if int(batch["journeys"]["n"].sum()) != cc["n_valid"]:
+        bad.append("full day: journey sizes do not add up to the kept records")
+    if bc["key"].size and not np.all(np.diff(bc["key"].astype(np.int64)) > 0):
+        bad.append("full day: cell keys not strictly increasing")
+    if not (np.all(bc["min"] <= bc["mean"] + 1e-9) and np.all(bc["mean"] <= bc["max"] + 1e-9)):
+        bad.append("full day: a cell mean outside [min, max]")
+    return {"journeys_checked": int(oj["jid"].shape[0]), "records_checked": int(o["counters"]["n_in"]),
+            "ok": not bad, "failures": bad[:8],
+            "what": "full-day journey rows of the sampled journeys vs the oracle (exact; distance 1e-6); "
+                    "the pipeline on the sample vs the oracle, every table and point column; "
+                    "full-day conservation and ordering"}
+
+
+def cpu_baseline(host, n, budget_s=15.0, batch=None):
+    """The oracle, single-threaded, timed on a bounded sample of whole journeys; with the day's
+    batch results, the parity check of the CUDA path on that sample (returned second)."""
     import oracle
 
     o = oracle.get()
     den = 64
     sample = _sample_journeys(host, den)
     t0 = time.perf_counter()
-    o.run(sample)
+    out = o.run(sample)
     dt = time.perf_counter() - t0
     # grow the sample toward the budget (about 10-30 s of CPU work)
     while dt < budget_s / 4 and den > 4:
         den //= 2
         sample = _sample_journeys(host, den)
         t0 = time.perf_counter()
-        o.run(sample)
+        out = o.run(sample)
         dt = time.perf_counter() - t0
     m = sample["jid"].shape[0]
-    return {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    base = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"whole journeys with id hash in 1 of {den} classes: {m} records, "
                       f"{len(np.unique(sample['jid']))} journeys, {dt:.1f} s single-threaded",
             "cpu": _cpu_model()}
+    return base, (_leg(lambda: _parity(sample, out, batch)) if batch is not None else None)
 
 
 def _cpu_model():
@@ -772,6 +1008,9 @@ def main():
                     help="0 keeps the library's default launch shapes (a fixed launch order for ncu)")
     ap.add_argument("--serve-slots", type=int, default=0, help="server slots (default: one per feed)")
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
+    ap.add_argument("--fp32-leg", type=int, default=1, help="0 skips the float32 form of the day")
+    ap.add_argument("--week-scale", type=float, default=1.0,
+                    help="instance size factor of the week_regions leg of the day run (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -451,25 +451,39 @@ cvetl_status cvetl_server_destroy(cvetl_server* s);
 /* Last error text of a server call (not of a request: see cvetl_ticket_info.message). */
 const char* cvetl_server_last_error(const cvetl_server* s);
 
+/* Binary64 issue-rate probe (a measurement aid with no counterpart in the paper: the FP64 form
+ * of the journey kernel is bound by the binary64 pipe, whose rate this measures). Launches
+ * `blocks` CTAs of `threads` (64, 128 or 256) threads on `stream`, each thread running 8
+ * independent chains of `iters` iterations of one binary64 operation kind: 0 fma, 1 add,
+ * 2 multiply, 3 the journey kernel's per-point mix (4 adds, 5 multiplies, 4 fma). sink: device
+ * memory for blocks * threads doubles (caller-owned; receives the chains' sums). *ops (may be
+ * NULL) receives the binary64 operations the launch performs. The call only enqueues: the
+ * caller times it with events on the stream. CVETL_EINVAL on a bad argument, CVETL_ECUDA on a
+ * launch error (text via cvetl_last_error(NULL)). */
+cvetl_status cvetl_probe_fp64(int32_t kind, int32_t blocks, int32_t threads, int64_t iters, double* sink,
+                              int64_t* ops, void* stream);
+
 /* Allocation-free radix sort (the paper has no counterpart; it serves callers that may not
  * allocate device memory: code inside a host framework that owns the device memory pool and
  * forbids side allocations, and latency-critical loops where a cudaMalloc / cudaFree, which can
  * synchronise the device, would stall the work).
- * Stable sort of n 64-bit keys by bits [begin_bit, end_bit): keys_out receives the keys in
- * ascending order and perm_out[i] the input position of the i-th key (equal keys keep input
- * order). All three arrays are device memory owned by the caller; keys_out must not be
- * keys_in. Work is queued on `stream` (a cudaStream_t) and the call synchronises it before
- * returning (it reads a device error word).
+ * Stable sort of n 64-bit keys by bits [begin_bit, end_bit) (bits outside that range take no
+ * part in the order): keys_out receives the keys, unchanged, in that order and perm_out[i] the
+ * input position of the i-th key (keys equal in the range keep input order). All three arrays
+ * are device memory owned by the caller; keys_out must not be keys_in. Work is queued on
+ * `stream` (a cudaStream_t) and the call synchronises it before returning (it reads a device
+ * error word back into host memory), so the call cannot be captured into a CUDA graph: on a
+ * stream that is capturing it returns CVETL_ESTATE without touching the capture.
  * Scratch: a fixed device array of about 3 MB inside the library, one per device that loads
  * it, held until the process exits; the call allocates nothing (no cudaMalloc, no cudaFree).
  * The first call on each device looks up that array's device address and sets the kernel's
- * shared-memory limit, so make the first call on a device before any stream capture.
+ * shared-memory limit (safe when several host threads make their first call at once).
  * Calls share the array and clear what must start at zero; calls that overlap on the GPU
  * (other streams, other threads) race on it, so serialise them.
  * Errors (text via cvetl_last_error(NULL)): CVETL_EINVAL when n is outside
  * [0, CVETL_NOALLOC_MAX_PAIRS], the bit range is not within [0, 64), an array is NULL or
- * keys_out == keys_in; CVETL_ECUDA on a CUDA error; CVETL_ETIMEOUT if a bounded device-side
- * wait gave up (the outputs are then not valid). */
+ * keys_out == keys_in; CVETL_ESTATE when the stream is capturing; CVETL_ECUDA on a CUDA error;
+ * CVETL_ETIMEOUT if a bounded device-side wait gave up (the outputs are then not valid). */
 #define CVETL_NOALLOC_MAX_PAIRS 262144
 cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t* keys_out, uint32_t* perm_out,
                                     int64_t n, int32_t begin_bit, int32_t end_bit, void* stream);

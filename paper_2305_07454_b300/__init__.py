@@ -146,6 +146,9 @@ def _load():
     lib.cvetl_version.restype = ctypes.c_int32
     lib.cvetl_sort_u64_noalloc.argtypes = [_P, _P, _P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _P]
     lib.cvetl_sort_u64_noalloc.restype = ctypes.c_int
+    lib.cvetl_probe_fp64.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P,
+                                     ctypes.POINTER(ctypes.c_int64), _P]
+    lib.cvetl_probe_fp64.restype = ctypes.c_int
     lib.cvetl_extract_batch.argtypes = [_P, ctypes.POINTER(Instance), ctypes.c_int32, ctypes.c_int32]
     _I64P = ctypes.POINTER(ctypes.c_int64)
     lib.cvetl_batch_ranges.argtypes = [_P, _I64P, _I64P, _I64P, _I64P, ctypes.c_int32]
@@ -185,10 +188,30 @@ EXPORTS = ("cvetl_config_default", "cvetl_create", "cvetl_extract", "cvetl_trans
            "cvetl_lattice_config_default", "cvetl_lattice_build", "cvetl_server_create",
            "cvetl_server_add_feed", "cvetl_server_submit", "cvetl_server_submit_flush",
            "cvetl_server_wait", "cvetl_server_drain", "cvetl_server_feed", "cvetl_server_destroy",
-           "cvetl_server_last_error")
+           "cvetl_server_last_error", "cvetl_probe_fp64")
 NOALLOC_MAX_PAIRS = 262144
 SERVE_BYTES_PER_ROW = 320
 SERVE_MAX_SLOTS = 64
+
+
+PROBE_FMA, PROBE_ADD, PROBE_MUL, PROBE_MIX = range(4)
+
+
+def probe_fp64(kind: int, blocks: int, threads: int, iters: int, sink, stream=None) -> int:
+    """Enqueues the binary64 issue-rate probe (cvetl_probe_fp64) on `stream` (default: the
+    current torch stream); sink: a float64 device tensor of blocks * threads elements. Returns
+    the binary64 operations the launch performs; the caller times it with CUDA events."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    assert sink.dtype == torch.float64 and sink.is_cuda and sink.numel() >= blocks * threads
+    ops = ctypes.c_int64(0)
+    st = lib.cvetl_probe_fp64(kind, blocks, threads, iters, sink.data_ptr(), ctypes.byref(ops),
+                              ctypes.c_void_p(stream.cuda_stream))
+    if st != OK:
+        raise CvetlError(st, lib.cvetl_last_error(None).decode())
+    return int(ops.value)
 
 
 class CvetlError(RuntimeError):

@@ -25,6 +25,7 @@
 #include "csv.cuh"
 #include "stream.cuh"
 #include "lattice.cuh"
+#include "probe.cuh"
 
 using namespace cvetl;
 
@@ -334,7 +335,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
   CK(cudaMemsetAsync(hist, 0, rs::kMaxPasses * rs::kRadix * 4, c->st));
   CK(cudaMemsetAsync(tiles, 0, rs::kMaxPasses * 4, c->st));
   LAUNCH(ST_SORT_HIST, (rs::k_histogram<K><<<grid_for(n, rs::kBlock, 4), rs::kBlock, 0, c->st>>>(
-                           keys, n, begin_bit, passes, hist, n_dev)));
+                           keys, n, begin_bit, passes, end_bit, hist, n_dev)));
   LAUNCH_CHECK();
   LAUNCH(ST_SORT_HIST, (rs::k_hist_scan<<<passes, rs::kBlock, 0, c->st>>>(hist)));
   LAUNCH_CHECK();
@@ -347,7 +348,7 @@ cvetl_status sort_pairs(cvetl_ctx* c, const char* tag, K* keys, uint32_t* vals, 
     CK(cudaMemsetAsync(status, 0, (size_t)ntiles * rs::kRadix * 4, c->st));
     LAUNCH(ST_SORT_PASS, (rs::k_onesweep<K><<<ntiles, rs::kBlock, smem, c->st>>>(
                              kin, vin, kout, vout, n, begin_bit + rs::kBits * p,
-                             hist + p * rs::kRadix, status, tiles + p, &c->dstate->err, n_dev)));
+                             rs::digit_mask(begin_bit + rs::kBits * p, end_bit), hist + p * rs::kRadix, status, tiles + p, &c->dstate->err, n_dev)));
     LAUNCH_CHECK();
     // next pass reads what this one wrote
     K* tk = kin;
@@ -2095,6 +2096,28 @@ cvetl_status cvetl_stats_reset(cvetl_ctx* c) {
     c->launches[i] = 0;
   }
   c->total_launches = 0;
+  return CVETL_OK;
+}
+
+cvetl_status cvetl_probe_fp64(int32_t kind, int32_t blocks, int32_t threads, int64_t iters, double* sink,
+                              int64_t* ops, void* stream) {
+  cvetl_ctx* c = nullptr;
+  if (kind < kProbeFma || kind > kProbeMix) return fail(c, CVETL_EINVAL, "cvetl_probe_fp64: kind %d", kind);
+  if (blocks < 1 || blocks > (1 << 20) || (threads != 64 && threads != 128 && threads != 256) || iters < 0)
+    return fail(c, CVETL_EINVAL, "cvetl_probe_fp64: %d blocks of %d threads, %lld iterations", blocks, threads,
+                (long long)iters);
+  if (!sink) return fail(c, CVETL_EINVAL, "cvetl_probe_fp64: NULL sink");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double b = 0.9999999999999, cc = 1e-9;
+  switch (kind) {
+    case kProbeFma: k_probe_fp64<kProbeFma><<<blocks, threads, 0, st>>>(iters, b, cc, sink); break;
+    case kProbeAdd: k_probe_fp64<kProbeAdd><<<blocks, threads, 0, st>>>(iters, b, cc, sink); break;
+    case kProbeMul: k_probe_fp64<kProbeMul><<<blocks, threads, 0, st>>>(iters, b, cc, sink); break;
+    default: k_probe_fp64<kProbeMix><<<blocks, threads, 0, st>>>(iters, b, cc, sink); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, CVETL_ECUDA, "cvetl_probe_fp64: %s", cudaGetErrorString(e));
+  if (ops) *ops = (int64_t)blocks * threads * iters * kProbeChains * probe_ops_per_iter(kind);
   return CVETL_OK;
 }
 

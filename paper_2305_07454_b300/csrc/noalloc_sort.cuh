@@ -9,6 +9,7 @@
 // device) would stall the pipeline. It is a fixed-size service: at most
 // CVETL_NOALLOC_MAX_PAIRS keys per call.
 #pragma once
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -30,7 +31,10 @@ constexpr size_t kBytes = kOffErr + 256;
 static_assert(kOffVals % 256 == 0 && kOffStatus % 256 == 0 && kOffHist % 256 == 0, "alignment");
 
 constexpr int kMaxDevices = 64;
-static void* g_scratch_addr[kMaxDevices];  // device address of the array, per device
+// device address of the array, per device (null until that device's set-up); published with
+// release order after the set-up, read with acquire order, so a thread that sees the address
+// also sees the kernel attribute set before it
+static std::atomic<void*> g_scratch_addr[kMaxDevices];
 static std::mutex g_setup_mutex;
 
 }  // namespace noalloc
@@ -59,23 +63,34 @@ extern "C" cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t
   if ((const void*)keys_in == (const void*)keys_out)
     return fail(c, CVETL_EINVAL, "cvetl_sort_u64_noalloc: keys_out must not be keys_in");
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    // the call ends with a read-back of the device error word and a stream synchronisation,
+    // which a stream capture does not allow: refuse instead of invalidating the caller's graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(c, CVETL_ESTATE, "cvetl_sort_u64_noalloc: the stream is capturing; this call cannot be captured");
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices)
     return fail(c, CVETL_EINVAL, "cvetl_sort_u64_noalloc: device %d beyond the supported %d", dev, kMaxDevices);
   // Set-up, once per device, with that device current: the array's device address and the
   // kernel's shared-memory limit. This happens inside the first call on each device.
-  if (!g_scratch_addr[dev]) {
+  void* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
       void* p = nullptr;
       CK(cudaGetSymbolAddress(&p, g_cvetl_noalloc_scratch));
       CK(cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12));
-      g_scratch_addr[dev] = p;
+      g_scratch_addr[dev].store(p, std::memory_order_release);
+      addr = p;
     }
   }
-  unsigned char* base = (unsigned char*)g_scratch_addr[dev];
+  unsigned char* base = (unsigned char*)addr;
   unsigned long long* s_keys = (unsigned long long*)(base + kOffKeys);
   uint32_t* s_vals = (uint32_t*)(base + kOffVals);
   uint32_t* status = (uint32_t*)(base + kOffStatus);
@@ -95,7 +110,7 @@ extern "C" cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t
   int hb = (int)((un + rs::kBlock - 1) / rs::kBlock);
   if (hb > sms * 4) hb = sms * 4;
   rs::k_histogram<unsigned long long><<<hb, rs::kBlock, 0, st>>>(
-      (const unsigned long long*)keys_in, un, begin_bit, passes, hist, nullptr);
+      (const unsigned long long*)keys_in, un, begin_bit, passes, end_bit, hist, nullptr);
   rs::k_hist_scan<<<passes, rs::kBlock, 0, st>>>(hist);
   {
     cudaError_t e = cudaGetLastError();
@@ -111,7 +126,8 @@ extern "C" cvetl_status cvetl_sort_u64_noalloc(const uint64_t* keys_in, uint64_t
     uint32_t* vout = to_out ? perm_out : s_vals;
     CK(cudaMemsetAsync(status, 0, 4ull * ntiles * rs::kRadix, st));
     rs::k_onesweep<unsigned long long><<<ntiles, rs::kBlock, (size_t)rs::kTile * 12, st>>>(
-        kin, vin, kout, vout, un, begin_bit + rs::kBits * p, hist + p * rs::kRadix, status,
+        kin, vin, kout, vout, un, begin_bit + rs::kBits * p,
+        rs::digit_mask(begin_bit + rs::kBits * p, end_bit), hist + p * rs::kRadix, status,
         tiles + p, err, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, CVETL_ECUDA, "cvetl_sort_u64_noalloc: %s", cudaGetErrorString(e));

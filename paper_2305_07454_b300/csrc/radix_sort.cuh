@@ -22,16 +22,25 @@ constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;  // look-back polls before the tile gives up
 
+// The digit of a pass at bit `shift`; dmask keeps only the bits below the sort's end bit (255
+// unless the last pass's digit is narrower than 8 bits), so that bits at or above the end bit
+// take no part in the order.
 template <typename K>
-__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
-  return (uint32_t)(k >> shift) & (kRadix - 1);
+__device__ __forceinline__ uint32_t digit_of(K k, int shift, uint32_t dmask) {
+  return (uint32_t)(k >> shift) & dmask;
 }
 
-// Histograms of n_passes digits starting at begin_bit. hist: [kMaxPasses][256], zeroed.
-// n_dev != nullptr: the key count is read from device memory (n is then an upper bound).
+// Mask of the digit at bit `shift` of a sort by bits [.., end_bit).
+__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int end_bit) {
+  return (end_bit - shift >= kBits) ? (uint32_t)(kRadix - 1) : ((1u << (end_bit - shift)) - 1u);
+}
+
+// Histograms of n_passes digits starting at begin_bit, over bits below end_bit. hist:
+// [kMaxPasses][256], zeroed. n_dev != nullptr: the key count is read from device memory (n is
+// then an upper bound).
 template <typename K>
 __global__ void __launch_bounds__(kBlock) k_histogram(const K* __restrict__ keys, uint32_t n,
-                                                      int begin_bit, int n_passes,
+                                                      int begin_bit, int n_passes, int end_bit,
                                                       uint32_t* __restrict__ hist,
                                                       const uint32_t* __restrict__ n_dev) {
   __shared__ uint32_t sh[kMaxPasses][kRadix];
@@ -40,7 +49,10 @@ __global__ void __launch_bounds__(kBlock) k_histogram(const K* __restrict__ keys
   __syncthreads();
   for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < n; i += gridDim.x * kBlock) {
     K k = keys[i];
-    for (int p = 0; p < n_passes; ++p) atomicAdd(&sh[p][digit_of(k, begin_bit + kBits * p)], 1u);
+    for (int p = 0; p < n_passes; ++p) {
+      const int shift = begin_bit + kBits * p;
+      atomicAdd(&sh[p][digit_of(k, shift, digit_mask(shift, end_bit))], 1u);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n_passes * kRadix; i += kBlock) {
@@ -58,7 +70,8 @@ __global__ void __launch_bounds__(kBlock) k_hist_scan(uint32_t* hist) {
   h[threadIdx.x] = e;
 }
 
-// One digit pass. status: [n_tiles][256] words, zeroed; tile_ctr zeroed.
+// One digit pass over the bits of `dmask` at `shift`. status: [n_tiles][256] words, zeroed;
+// tile_ctr zeroed.
 // vin == nullptr means value = input position (iota). n_dev != nullptr: the key count is read
 // from device memory and the grid covers the upper bound n; tiles are numbered in the order the
 // CTAs start, so a tile that starts past the count returns at once (no tile holding keys looks
@@ -68,7 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
                                                      const uint32_t* __restrict__ vin,
                                                      K* __restrict__ kout,
                                                      uint32_t* __restrict__ vout, uint32_t n,
-                                                     int shift, const uint32_t* __restrict__ goff,
+                                                     int shift, uint32_t dmask,
+                                                     const uint32_t* __restrict__ goff,
                                                      uint32_t* status, uint32_t* tile_ctr,
                                                      uint32_t* err, const uint32_t* __restrict__ n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
   // which is their global order, so ranks are stable.
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    uint32_t d = digit_of(key[i], shift);
+    uint32_t d = digit_of(key[i], shift, dmask);
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = s_wcnt[warp][d];
     __syncwarp();
@@ -122,8 +136,9 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
     s_wcnt[w][tid] = (uint16_t)run;
     run += c;
   }
-  // Items past n carry key ~0 (digit 255) and rank after every valid digit-255 item.
-  uint32_t cnt_valid = run - ((tid == kRadix - 1) ? (kTile - n_valid) : 0u);
+  // Items past n carry key ~0 (the largest digit, dmask) and rank after every valid item of
+  // that digit.
+  uint32_t cnt_valid = run - ((tid == (int)dmask) ? (kTile - n_valid) : 0u);
   uint32_t* my_status = status + (size_t)tile * kRadix + tid;
   uint32_t excl = 0;
   if (tile == 0) {
@@ -156,7 +171,7 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i) {
-    uint32_t d = digit_of(key[i], shift);
+    uint32_t d = digit_of(key[i], shift, dmask);
     uint32_t pos = s_tstart[d] + s_wcnt[warp][d] + rank[i];
     s_keys[pos] = key[i];
     s_vals[pos] = val[i];
@@ -167,7 +182,7 @@ __global__ void __launch_bounds__(kBlock) k_onesweep(const K* __restrict__ kin,
     uint32_t p = j * kBlock + tid;
     if (p < n_valid) {
       K k = s_keys[p];
-      uint32_t d = digit_of(k, shift);
+      uint32_t d = digit_of(k, shift, dmask);
       uint32_t g = s_gbase[d] + (p - s_tstart[d]);
       kout[g] = k;
       vout[g] = s_vals[p];

@@ -264,6 +264,20 @@ def pin_library_cross_check(o, cols):
     uk2, vol = np.unique(pairs[0], return_counts=True)
     assert np.array_equal(uk2, cl["key"].astype(np.int64)) and np.array_equal(vol, cl["volume"])
     assert (cl["volume"] <= cl["count"]).all()
+    # journey table from the same lexsort: each journey's first and last record in (time, row)
+    # order give its start and end time and position (latitude and longitude both move along
+    # the generated journeys, so a swapped or misplaced coordinate shows)
+    j = r["journeys"]
+    sj = cols["jid"][valid][order]
+    head = np.flatnonzero(np.concatenate([[True], sj[1:] != sj[:-1]]))
+    tail = np.append(head[1:], sj.shape[0]) - 1
+    assert np.array_equal(j["jid"], sj[head]) and np.array_equal(j["n"], tail - head + 1)
+    for name, src in (("ts", cols["ts"]), ("lat", cols["lat"]), ("lon", cols["lon"])):
+        s = src[valid][order]
+        assert np.array_equal(j["start_" + name], s[head]), name
+        assert np.array_equal(j["end_" + name], s[tail]), name
+    moved = j["start_lon"] != j["end_lon"]
+    assert moved.mean() > 0.5  # the check above sees longitude move in most journeys
 
 
 def _independent_groups(cols):

@@ -30,12 +30,17 @@ def run32(cols):
 
 
 def report(g, o):
+    """Largest and 99.9th-percentile relative error of every floating-point output."""
     out = {}
-    for part, k, ok in (("points", "d", "d"), ("points", "vhat", "vhat"), ("points", "accel", "accel"),
-                        ("journeys", "distance_m", "distance_m"), ("cells", "sum", "sum"),
-                        ("cells", "mean", "mean")):
-        e = rel_err(g[part][k], o[part][ok])
+    for part, k in (("points", "d"), ("points", "vhat"), ("points", "accel"), ("points", "accel_v"),
+                    ("journeys", "distance_m"), ("cells", "sum"), ("cells", "mean")):
+        e = rel_err(g[part][k], o[part][k])
         out[f"{part}.{k}"] = (float(e.max()) if e.size else 0.0, float(np.quantile(e, 0.999)) if e.size else 0.0)
+    # the acceleration from implied speeds differences two close speeds over a sub-second step,
+    # so its float32 error is bounded in absolute terms (about 1e-4 m/s^2): reported too
+    d = np.abs(np.asarray(g["points"]["accel_v"], np.float64) - o["points"]["accel_v"])
+    out["points.accel_v.abs_m_s2"] = (float(d.max()) if d.size else 0.0,
+                                      float(np.quantile(d, 0.999)) if d.size else 0.0)
     return out
 
 
@@ -44,7 +49,12 @@ def test_fp32_small_day(orc, small_day):
     errs = report(g, o)
     print("float32 form, max / p99.9 relative error per output:", errs)
     for k, (mx, _) in errs.items():
+        if k.startswith("points.accel_v"):
+            continue
         assert mx <= REL32, (k, mx)
+    a_g = np.asarray(g["points"]["accel_v"], np.float64)
+    a_o = o["points"]["accel_v"]
+    assert np.all(np.abs(a_g - a_o) <= REL32 * np.maximum(np.abs(a_g), np.abs(a_o)) + 1e-4)
     # everything that is not floating point is identical to the binary64 form
     import parity
 

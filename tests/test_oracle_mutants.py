@@ -47,7 +47,10 @@ MUTANTS = {
     "cell_volume_counts_points": ("if (cl->count[c] == 0 || jid[order[byk[t - 1]]] != jid[order[k]]) cl->volume[c] += 1;", "cl->volume[c] += 1;"),
     "stop_run_not_reset": ("run_stop = (f & ORC_F_STOP) ? run_stop + dwell : 0;", "run_stop = run_stop + dwell;"),
     "speed_accel_in_kmh": ("const double v = d / dt_s;", "const double v = d / dt_s * 3.6;"),
-    "lattice_key_dir_bin_swapped": ("lkey[i] = (((uint32_t)b * 4u + (uint32_t)d)", "lkey[i] = (((uint32_t)d * 4u + (uint32_t)b)"),
+    "journey_end_lon_is_start": ("jr->end_lon[j] = lon[i];", "jr->end_lon[j] = jr->start_lon[j];"),
+    "journey_start_lon_from_lat": ("jr->start_lon[nj] = lon[i];", "jr->start_lon[nj] = lat[i];"),
+    "journey_end_lat_from_lon": ("jr->end_lat[j] = lat[i];", "jr->end_lat[j] = lon[i];"),
+    "lattice_key_dir_bin_swapped":("lkey[i] = (((uint32_t)b * 4u + (uint32_t)d)", "lkey[i] = (((uint32_t)d * 4u + (uint32_t)b)"),
 }
 
 
