@@ -147,6 +147,8 @@ def algorithmic_bytes(stage: str, c: dict) -> float:
         "hash_count": 28.0 * nin + 4.0 * nin,           # jid, lat, lon, speed read; row slot written
         "scatter": 32.0 * nin + 32.0 * nv,              # ts, lat, lon, speed, slot read; records written
         "journeys": 32.0 * nv + 28.0 * R + 96.0 * J,    # records read; runs and journey rows written
+        "journey_sort": 64.0 * nv,                      # records read, written in (time, row) order
+        "journey_walk": 32.0 * nv + 28.0 * R + 96.0 * J,  # ordered records read; runs and journey rows written
         "cell_write": 28.0 * R + 44.0 * c["n_cells"],
         "csv_count": float(c.get("csv_bytes", 0)),                  # the text read
         "csv_parse": float(c.get("csv_bytes", 0)) + 40.0 * nin,    # the text read; six columns written
@@ -211,7 +213,6 @@ def fp64_probe(stream, reps=3):
 # they are captured again.
 TRAFFIC_PER_RECORD_FP32 = {}
 TRAFFIC_PER_RECORD = {
-    "journeys": (827.050496e6 + 68.221696e6 + 3.345408e6 + 0.0) / 14637283,
     "scatter": (468.913152e6 + 428.840448e6) / 14637283,
     "hash_count": (410.996736e6 + 48.926464e6) / 14637283,
     "csv_parse": (856.018944e6 + 549.557760e6) / 14637283,
@@ -220,10 +221,10 @@ TRAFFIC_PER_RECORD = {
 
 def unit_launches(stage, launches, steps):
     """Number of passes over the stage's algorithmic work in `launches`. Every stage's launch is
-    one pass, except the journeys stage: its two kernel shapes (journeys of up to 512 points in
-    64-thread CTAs, the rest in 256-thread CTAs) share one pass over all points per step, so its
-    time per pass is the sum of both launches."""
-    if stage == "journeys":
+    one pass, except the journey sort (and the fused journey kernel of stream windows): its two
+    kernel shapes (journeys of up to 512 points in 64-thread CTAs, the rest in 256-thread CTAs)
+    share one pass over all points per step, so its time per pass is the sum of both launches."""
+    if stage in ("journeys", "journey_sort"):
         return max(1, steps)
     return max(1, launches)
 
@@ -315,7 +316,7 @@ def _roofline_entry(top, stages, counters, steps, precision, probe):
     hbm_peak, peak_src = load_peaks()
     tpr = TRAFFIC_PER_RECORD.get(top) if precision == "fp64" else TRAFFIC_PER_RECORD_FP32.get(top)
     traffic = tpr * counters["n_valid"] if tpr else None
-    if top == "journeys" and precision == "fp64" and probe:
+    if top in ("journeys", "journey_walk") and precision == "fp64" and probe:
         ops = FP64_OPS_PER_POINT * counters["n_valid"]
         achieved = ops / (avg_ms / 1e3) / 1e9
         return {"bound": "alu", "kernel": top, "achieved": achieved, "peak": probe["peak_gops"],

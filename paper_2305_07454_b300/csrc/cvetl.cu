@@ -35,14 +35,14 @@ enum Stage {
   ST_HASH, ST_COLLECT, ST_SORT_HIST, ST_SORT_PASS, ST_SIZES, ST_SCAN, ST_CURSORS, ST_SCATTER,
   ST_JOURNEYS, ST_CELL_HEADS, ST_CELL_WRITE, ST_CSV_COUNT, ST_CSV_PARSE, ST_STREAM_APPEND,
   ST_STREAM_SPLIT, ST_STREAM_TABLES, ST_CTA_SORT, ST_LATTICE, ST_POINT_EXTRAS, ST_LATTICE_KEYS,
-  ST_LATTICE_FOLD, ST_COUNT
+  ST_LATTICE_FOLD, ST_JOURNEY_SORT, ST_JOURNEY_WALK, ST_COUNT
 };
 const char* kStageNames[ST_COUNT] = {"hash_count", "collect_slots", "radix_histogram",
                                      "radix_onesweep", "journey_sizes", "scan", "journey_cursors",
                                      "scatter", "journeys", "cell_heads", "cell_write",
                                      "csv_count", "csv_parse", "stream_append", "stream_split",
                                      "stream_tables", "cta_sort", "lattice", "point_extras", "lattice_keys",
-                                     "lattice_fold"};
+                                     "lattice_fold", "journey_sort", "journey_walk"};
 
 struct DevBuf {
   void* p = nullptr;
@@ -257,6 +257,19 @@ cvetl_status ensure(cvetl_ctx* c, const char* name, size_t count, T** out) {
     cvetl_status s_ = ensure(c, name, (count), (ptr));    \
     if (s_ != CVETL_OK) return s_;                        \
   } while (0)
+
+// Resident blocks per SM of a kernel (at least 1).
+template <typename F>
+int occupancy(F kernel, int block, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess) per_sm = 1;
+  return per_sm > 0 ? per_sm : 1;
+}
+
+constexpr int kSortSmemA = kJSmem;
+constexpr int kSortSmemB = staged_smem<8192>();
+constexpr int kSortSmemC = cmax(staged_smem<4096>(), kJSmem);
+constexpr int kSortSmemD = cmax(staged_smem<512>(), kJSmallSmem);
 
 int grid_for(size_t n, int block, int max_blocks_per_sm = 8) {
   int dev = 0, sms = 148;
@@ -1017,10 +1030,13 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     LAUNCH_CHECK();
   }
 
-  // 4. per-journey sort, kinematics, keys, journey table, cell runs
+  // 4. per-journey sort into a second record array, then the walk: kinematics, keys, journey
+  // table, cell runs
   Elem *scrA, *scrB;
   ENSURE("scr.a", nv, &scrA);
   ENSURE("scr.b", nv, &scrB);
+  Rec* srec;
+  ENSURE("rec.sorted", nv, &srec);
   JourneyOut& o = c->jo;
   ENSURE("out.j_n", (size_t)J, &o.n);
   ENSURE("out.j_off", (size_t)J, &o.off);
@@ -1059,12 +1075,12 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   ENSURE("run.min", nv, &o.run_min);
   ENSURE("run.max", nv, &o.run_max);
   o.run_cap = (uint32_t)nv;
-  // work list, longest journey first, for the persistent journey kernel
+  // work list, longest journey first, for the sort and the walk
   unsigned long long *szkey, *szsorted;
   uint32_t *order = nullptr, *work;
   ENSURE("j.szkey", (size_t)J, &szkey);
-  ENSURE("j.work", 1, &work);
-  CK(cudaMemsetAsync(work, 0, 4, c->st));
+  ENSURE("j.work", 2, &work);
+  CK(cudaMemsetAsync(work, 0, 8, c->st));
   if (J) {
     LAUNCH(ST_SIZES, (k_size_keys<<<(J + 255) / 256, 256, 0, c->st>>>(jn, J, szkey)));
     LAUNCH_CHECK();
@@ -1073,20 +1089,34 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const bool pers = c->tune.journey_ctas > 0;
-    const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
     const bool f32 = c->cfg.precision == CVETL_FP32;
-    // journeys of up to `split` points (at most 512) to the 64-thread shape, the rest first
-    const uint32_t split = (uint32_t)c->tune.small_journey_max;
-#define JRN(F, P, NT, SM, G) k_journeys<F, P, NT><<<G, NT, SM, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, c->bt, o, \
-                                                                      c->dstate, nullptr, JState{}, order, work, split)
-    if (f32 && pers) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, true, kJBlock, kJSmem, grid)));
-    else if (f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false, kJBlock, kJSmem, grid)));
-    else if (pers) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, true, kJBlock, kJSmem, grid)));
-    else LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false, kJBlock, kJSmem, grid)));
-    if (split && f32) LAUNCH(ST_JOURNEYS, (JRN(Fp32Form, false, kJSmallBlock, kJSmallSmem, J)));
-    else if (split) LAUNCH(ST_JOURNEYS, (JRN(Fp64Form, false, kJSmallBlock, kJSmallSmem, J)));
-#undef JRN
+    // the sort by journey size class (each class a persistent grid over its part of the list)
+    uint32_t *bounds, *cwork;
+    ENSURE("j.bounds", 5, &bounds);
+    ENSURE("j.cwork", 4, &cwork);
+    LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
+    LAUNCH_CHECK();
+    static const int occ[4] = {
+        occupancy(k_journey_sort_class<kJBlock, 0>, kJBlock, kSortSmemA),
+        occupancy(k_journey_sort_class<kJBlock, 8192>, kJBlock, kSortSmemB),
+        occupancy(k_journey_sort_class<kJBlock, 4096>, kJBlock, kSortSmemC),
+        occupancy(k_journey_sort_class<kJSmallBlock, 512>, kJSmallBlock, kSortSmemD)};
+#define JCLS(NT, CAP, SM, K) k_journey_sort_class<NT, CAP><<<(uint32_t)(sms * occ[K]), NT, SM, c->st>>>( \
+    rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 0, kSortSmemA, 0)));
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 8192, kSortSmemB, 1)));
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 4096, kSortSmemC, 2)));
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
+#undef JCLS
+    LAUNCH_CHECK();
+    // the walk: a persistent grid of warps taking journeys longest first
+    static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, 0);
+    static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
+    const uint32_t wgrid = (uint32_t)(sms * (f32 ? occ32 : occ64));
+    if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<wgrid, kWalkBlock, 0, c->st>>>(
+                                        srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
+    else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<wgrid, kWalkBlock, 0, c->st>>>(
+                                     srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
     LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)
       LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(
@@ -1333,6 +1363,10 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
       cudaFuncSetAttribute(k_journeys<Fp32Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp64Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp32Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemA) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemB) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemC) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kJSmallBlock, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemD) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -728,43 +728,29 @@ __device__ RunPart stitch_runs(const StitchSmem<NT>& ss, int nr, const RunPart& 
   return open;
 }
 
-// One journey (rank j) by the whole CTA. Ends with every thread past its last shared-memory use
-// of this journey except the run copy-out (the caller synchronises before the next journey).
-template <class Form, int NT>
-__device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ rec,
-                                            const uint32_t* __restrict__ jn,
-                                            const uint32_t* __restrict__ joff, Elem* scrA, Elem* scrB,
-                                            const GridParams& g, const Batch& bt, const JourneyOut& o,
-                                            DevState* st,
-                                            const uint32_t* __restrict__ jslot, const JState& js) {
+// The journey's bucket R[0..n) in (timestamp, row index) order: either the sorted keys K
+// (((ts - tmin) << pos_bits) | bucket position; position = K[k] & pmask) or, when the keys do not
+// fit 64 bits or a 64-thread CTA meets crowded buckets, the sorted (timestamp, row) pairs E.
+struct JSorted {
+  const unsigned long long* K;
+  const Elem* E;
+  unsigned long long pmask;
+  __device__ __forceinline__ uint32_t pos(int k) const { return K ? (uint32_t)(K[k] & pmask) : E[k].pos; }
+};
+
+// Sorts one journey by the whole CTA (every thread calls it). Uses the dynamic shared memory
+// (keys of up to kCap points and their bucket counters) and, above kCap, the journey's slice of
+// the global scratch scrA / scrB. Ends with a barrier.
+template <int NT>
+__device__ __forceinline__ JSorted journey_sort(const Rec* __restrict__ R, int n, uint32_t off, Elem* scrA,
+                                                Elem* scrB, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kCap = JShape<NT>::kCap, kRunBuf = JShape<NT>::kRunBuf;
+  constexpr int kCap = JShape<NT>::kCap;
   __shared__ typename JSort<NT>::Smem ssort;
-  __shared__ double red_d[NT / 32];
-  __shared__ long long red_i[3][NT / 32];
   __shared__ unsigned long long s_tmin, s_tmax;
   __shared__ int s_flag;
-  __shared__ int64_t s_first_ts, s_last_ts;
-  __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
-  __shared__ float s_last_spd;
-  __shared__ uint32_t s_last_key;
-  __shared__ uint32_t s_nbuf, s_base;
-  __shared__ RunPart s_open;
-  constexpr int kRunBufOff = jrunbuf_off<NT>();
-  RunSlot* rbuf = reinterpret_cast<RunSlot*>(smem_raw + kRunBufOff);
-
   const int tid = threadIdx.x, lane = tid & 31;
-  const int n = (int)jn[j];
-  const uint32_t off = joff[j];
-  const Rec* R = rec + off;
   const bool small = n <= kCap;  // always, with 64 threads
-  // the grid and day the journey's points are keyed on (a journey lies in one batch instance)
-  const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, R[0].idx) : nullptr;
-  // stream mode: the journey continues from its state (last point, open run, running sums)
-  const bool stream = js.n != nullptr;
-  const uint32_t slot = stream ? jslot[j] : 0u;
-  const bool has_prev = stream && js.n[slot] > 0;
-
   // 1. order the bucket by (timestamp, row index)
   // 1a. range of the timestamps (as order-preserving keys)
   unsigned long long lo = ~0ull, hi = 0ull;
@@ -781,7 +767,6 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
   if (tid == 0) {
     s_tmin = ~0ull;
     s_tmax = 0ull;
-    s_nbuf = 0u;
   }
   __syncthreads();
   if (lane == 0) {
@@ -830,7 +815,51 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
     if (tid == 0 && nbits > 64) atomicAdd(&st->n_big, 1u);
     sortedE = sort_big<NT>(reinterpret_cast<Elem*>(smem_raw), R, n, scrA + off, scrB + off);
   }
-  const unsigned long long pmask = (1ull << pos_bits) - 1;
+  __syncthreads();
+  return JSorted{sortedK, sortedE, (1ull << pos_bits) - 1};
+}
+
+
+// One journey (rank j) by the whole CTA. Ends with every thread past its last shared-memory use
+// of this journey except the run copy-out (the caller synchronises before the next journey).
+template <class Form, int NT>
+__device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ rec,
+                                            const uint32_t* __restrict__ jn,
+                                            const uint32_t* __restrict__ joff, Elem* scrA, Elem* scrB,
+                                            const GridParams& g, const Batch& bt, const JourneyOut& o,
+                                            DevState* st,
+                                            const uint32_t* __restrict__ jslot, const JState& js) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kCap = JShape<NT>::kCap, kRunBuf = JShape<NT>::kRunBuf;
+  __shared__ double red_d[NT / 32];
+  __shared__ long long red_i[3][NT / 32];
+  __shared__ int64_t s_first_ts, s_last_ts;
+  __shared__ double s_first_lat, s_first_lon, s_last_lat, s_last_lon;
+  __shared__ float s_last_spd;
+  __shared__ uint32_t s_last_key;
+  __shared__ uint32_t s_nbuf, s_base;
+  __shared__ RunPart s_open;
+  constexpr int kRunBufOff = jrunbuf_off<NT>();
+  RunSlot* rbuf = reinterpret_cast<RunSlot*>(smem_raw + kRunBufOff);
+
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int n = (int)jn[j];
+  const uint32_t off = joff[j];
+  const Rec* R = rec + off;
+  // the grid and day the journey's points are keyed on (a journey lies in one batch instance)
+  const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, R[0].idx) : nullptr;
+  // stream mode: the journey continues from its state (last point, open run, running sums)
+  const bool stream = js.n != nullptr;
+  const uint32_t slot = stream ? jslot[j] : 0u;
+  const bool has_prev = stream && js.n[slot] > 0;
+
+  if (tid == 0) s_nbuf = 0u;
+  // 1. order the bucket by (timestamp, row index)
+  const JSorted srt = journey_sort<NT>(R, n, off, scrA, scrB, st);
+  const bool keyed = srt.K != nullptr;
+  const unsigned long long* sortedK = srt.K;
+  const Elem* sortedE = srt.E;
+  const unsigned long long pmask = srt.pmask;
 
   // 2. walk: thread t owns the sorted positions [k0, k1) and visits them in order; the
   // predecessor stays in registers, runs of equal keys accumulate in the thread
@@ -1094,6 +1123,485 @@ __global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
       journey_one<Form, NT>(j, rec, jn, joff, scrA, scrB, g, bt, o, st, jslot, js);
       __syncthreads();
     }
+  }
+}
+
+// ---------------------------------------------------------------- batch path: sort, then walk
+// The batch path orders each journey's bucket into a second record array in (timestamp, row)
+// order (k_journey_sort), then walks the ordered records with one warp per journey
+// (k_journey_walk). The sort keeps the shared-memory / L2 scheme above; the walk reads each
+// record once, coalesced, with every lane on its own point.
+
+__device__ __forceinline__ void ld_rec(const Rec* p, unsigned long long& a, unsigned long long& b,
+                                       unsigned long long& c, unsigned long long& d) {
+  asm("ld.global.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+__device__ __forceinline__ void st_rec(Rec* p, unsigned long long a, unsigned long long b, unsigned long long c,
+                                       unsigned long long d) {
+  asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+
+// ---- staged sort: the journey's timestamps held in shared memory
+// A journey of n <= CAP points (CAP <= 65536): one pass loads its timestamps (as order-preserving
+// keys) into shared memory T; a counting sort by time bucket (about two points per bucket)
+// places the u16 positions P; an insertion sort by (timestamp, row index) finishes each bucket;
+// the records are then copied to `out` in that order. Shared memory: T (8 B), P (2 B) and the
+// bucket counters (4 B per two points): 12 * CAP bytes. Returns false, having written nothing,
+// when a bucket holds more than kMaxBucket points (the caller then takes the general sort).
+template <int CAP>
+__host__ __device__ constexpr int staged_smem() { return CAP * 12; }
+
+__device__ __forceinline__ bool staged_less(const unsigned long long* T, const Rec* __restrict__ R, uint32_t a,
+                                            uint32_t b) {
+  const unsigned long long ta = T[a], tb = T[b];
+  return ta < tb || (ta == tb && R[a].idx < R[b].idx);
+}
+
+template <int NT, int CAP>
+__device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* T = reinterpret_cast<unsigned long long*>(smem_raw);
+  uint16_t* P = reinterpret_cast<uint16_t*>(smem_raw + 8 * CAP);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem_raw + 10 * CAP);
+  __shared__ unsigned long long s_tmin, s_tmax;
+  __shared__ uint32_t s_scan[NT / 32 + 1];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+    s_tmin = ~0ull;
+    s_tmax = 0ull;
+    s_flag = 0;
+  }
+  // 1. the timestamps, once, into shared memory; their range
+  unsigned long long lo = ~0ull, hi = 0ull;
+#pragma unroll 4
+  for (int i = tid; i < n; i += NT) {
+    const unsigned long long t = (unsigned long long)R[i].ts ^ kSign64;
+    T[i] = t;
+    lo = min(lo, t);
+    hi = max(hi, t);
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o2));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o2));
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(&s_tmin, lo);
+    atomicMax(&s_tmax, hi);
+  }
+  const int nb = max(1, n >> 1);
+  for (int b = tid; b < nb; b += NT) cnt[b] = 0;
+  __syncthreads();
+  const unsigned long long tmin = s_tmin, span = s_tmax - tmin;
+  const bool narrow = span <= 0xFFFFFFFFull;
+  const float scale = (float)nb / ((float)span + 1.0f);
+  // 2. bucket counts
+  for (int i = tid; i < n; i += NT) atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u);
+  __syncthreads();
+  // 3. bucket offsets (each thread a contiguous chunk of buckets), crowded buckets detected
+  const int chunk = (nb + NT - 1) / NT;
+  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
+  uint32_t sum = 0, mx = 0;
+  for (int b = c0; b < c1; ++b) {
+    sum += cnt[b];
+    mx = max(mx, cnt[b]);
+  }
+  uint32_t base = block_excl_scan<NT>(sum, s_scan, nullptr);
+  if (mx > (uint32_t)kMaxBucket) s_flag = 1;
+  for (int b = c0; b < c1; ++b) {
+    const uint32_t v = cnt[b];
+    cnt[b] = base;
+    base += v;
+  }
+  __syncthreads();
+  if (s_flag) return false;
+  // 4. positions by bucket (cnt[b] ends as the end of bucket b)
+  for (int i = tid; i < n; i += NT) P[atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u)] = (uint16_t)i;
+  __syncthreads();
+  // 5. each bucket by (timestamp, row index)
+  for (int b = tid; b < nb; b += NT) {
+    const int b0 = b ? (int)cnt[b - 1] : 0, b1 = (int)cnt[b];
+    for (int i = b0 + 1; i < b1; ++i) {
+      const uint16_t v = P[i];
+      int q = i - 1;
+      while (q >= b0 && staged_less(T, R, v, P[q])) {
+        P[q + 1] = P[q];
+        --q;
+      }
+      P[q + 1] = v;
+    }
+  }
+  __syncthreads();
+  // 6. the records in order
+  for (int k = tid; k < n; k += NT) {
+    unsigned long long a, b, c, d;
+    ld_rec(R + P[k], a, b, c, d);
+    st_rec(out + k, a, b, c, d);
+  }
+  return true;
+}
+
+// Journey size classes over the work list (sizes non-increasing along it): bounds[c] is the
+// first list position of class c, bounds[4] = J; classes: above 8192 points, 4097-8192,
+// 513-4096, up to 512. One thread.
+__device__ __forceinline__ uint32_t sort_class_max(int c) { return c == 0 ? 8192u : (c == 1 ? 4096u : 512u); }
+__global__ void k_size_classes(const uint32_t* __restrict__ jn, const uint32_t* __restrict__ order, uint32_t J,
+                               uint32_t* __restrict__ bounds, uint32_t* __restrict__ work) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  bounds[0] = 0;
+  bounds[4] = J;
+  for (int c = 0; c < 3; ++c) {
+    uint32_t lo = 0, hi = J;  // first w with jn[order[w]] <= sort_class_max(c)
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (jn[order[mid]] <= sort_class_max(c)) hi = mid;
+      else lo = mid + 1;
+    }
+    bounds[c + 1] = lo;
+  }
+  for (int c = 0; c < 4; ++c) work[c] = 0;
+}
+
+// One size class of the journey sort, persistent: CTAs take the class's journeys in list order
+// through its work counter. CAP > 0: the staged sort (the general one when a bucket is crowded);
+// CAP = 0: the general sort (global scratch above 4096 points).
+template <int NT, int CAP>
+__host__ __device__ constexpr int sort_class_min_blocks() { return NT == 64 ? 12 : (CAP > 4096 ? 2 : 3); }
+
+template <int NT, int CAP>
+__global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journey_sort_class(const Rec* __restrict__ rec, const uint32_t* __restrict__ jn,
+                                                           const uint32_t* __restrict__ joff,
+                                                           const uint32_t* __restrict__ order,
+                                                           const uint32_t* __restrict__ bounds, int cls,
+                                                           uint32_t* work, Elem* scrA, Elem* scrB,
+                                                           Rec* __restrict__ srec, DevState* st) {
+  __shared__ uint32_t s_w;
+  const uint32_t w0 = bounds[cls], w1 = bounds[cls + 1];
+  for (;;) {
+    if (threadIdx.x == 0) s_w = w0 + atomicAdd(work, 1u);
+    __syncthreads();
+    const uint32_t w = s_w;
+    __syncthreads();
+    if (w >= w1) break;
+    const uint32_t j = order[w];
+    const int n = (int)jn[j];
+    const uint32_t off = joff[j];
+    const Rec* R = rec + off;
+    bool done = false;
+    if constexpr (CAP > 0) done = journey_sort_staged<NT, CAP>(R, n, srec + off);
+    if (!done) {
+      const JSorted srt = journey_sort<NT>(R, n, off, scrA, scrB, st);
+      for (int k = threadIdx.x; k < n; k += NT) {
+        unsigned long long a, b, c, d;
+        ld_rec(R + srt.pos(k), a, b, c, d);
+        st_rec(srec + off + k, a, b, c, d);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Runs of equal keys inside one warp's iteration: count, compensated speed sum, min, max.
+struct RunAgg {
+  uint32_t cnt;
+  float s, c, mn, mx;
+};
+__device__ __forceinline__ RunAgg agg_then(const RunAgg& a, const RunAgg& b) {  // a before b
+  RunAgg r;
+  r.cnt = a.cnt + b.cnt;
+  r.s = a.s;
+  r.c = a.c;
+  fsum_add(r.s, r.c, b.s);
+  r.c += b.c;
+  r.mn = fminf(a.mn, b.mn);
+  r.mx = fmaxf(a.mx, b.mx);
+  return r;
+}
+// Shuffles of the per-point cosine of the two forms.
+__device__ __forceinline__ Cos64 shfl_cos(const Cos64& c, int src) {
+  Cos64 r;
+  r.t = __shfl_sync(0xffffffffu, c.t, src);
+  r.tf = __shfl_sync(0xffffffffu, c.tf, src);
+  r.eps = __shfl_sync(0xffffffffu, c.eps, src);
+  return r;
+}
+__device__ __forceinline__ float shfl_cos(float c, int src) { return __shfl_sync(0xffffffffu, c, src); }
+__device__ __forceinline__ Cos64 shfl_up_cos(const Cos64& c, int d) {
+  Cos64 r;
+  r.t = __shfl_up_sync(0xffffffffu, c.t, d);
+  r.tf = __shfl_up_sync(0xffffffffu, c.tf, d);
+  r.eps = __shfl_up_sync(0xffffffffu, c.eps, d);
+  return r;
+}
+__device__ __forceinline__ float shfl_up_cos(float c, int d) { return __shfl_up_sync(0xffffffffu, c, d); }
+
+constexpr int kWalkBlock = 128;
+constexpr int kWalkRunCap = 64;  // closed runs staged per warp before they are written out
+
+// A warp's closed runs, staged in shared memory and written out kWalkRunCap at a time with one
+// global allocation (an atomic on the run counter) per batch of runs.
+__device__ __forceinline__ void walk_flush(RunSlot* buf, uint32_t& nbuf, const JourneyOut& o, DevState* st) {
+  const int lane = threadIdx.x & 31;
+  if (nbuf == 0) return;
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(&st->n_runs, nbuf);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  __syncwarp();
+  for (uint32_t i = lane; i < nbuf; i += 32) {
+    const uint32_t gi = base + i;
+    if (gi >= o.run_cap) {
+      atomicOr(&st->err, kErrCapacity);
+      break;
+    }
+    const RunSlot q = buf[i];
+    o.run_sortkey[gi] = ((unsigned long long)q.key << 32) | q.start;
+    o.run_cnt[gi] = q.cnt;
+    o.run_sum[gi] = (double)q.s + (double)q.c;
+    o.run_min[gi] = q.mn;
+    o.run_max[gi] = q.mx;
+  }
+  __syncwarp();
+  nbuf = 0;
+}
+
+// Warp sum of a run aggregate in a fixed shuffle tree (lane 0 holds the result).
+__device__ __forceinline__ RunAgg warp_agg(RunAgg a) {
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    RunAgg q;
+    q.cnt = __shfl_down_sync(0xffffffffu, a.cnt, o2);
+    q.s = __shfl_down_sync(0xffffffffu, a.s, o2);
+    q.c = __shfl_down_sync(0xffffffffu, a.c, o2);
+    q.mn = __shfl_down_sync(0xffffffffu, a.mn, o2);
+    q.mx = __shfl_down_sync(0xffffffffu, a.mx, o2);
+    a = agg_then(a, q);
+  }
+  return a;
+}
+
+__device__ __forceinline__ RunAgg agg_empty() {
+  return RunAgg{0u, 0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
+}
+__device__ __forceinline__ void agg_add(RunAgg& a, float v) {
+  a.cnt += 1;
+  fsum_add(a.s, a.c, v);
+  a.mn = fminf(a.mn, v);
+  a.mx = fmaxf(a.mx, v);
+}
+
+// Stages one closed run (lane 0 of the warp writes it) and flushes the warp's buffer when full.
+__device__ __forceinline__ void walk_put(RunSlot* buf, uint32_t& nbuf, const JourneyOut& o, DevState* st,
+                                         uint32_t key, uint32_t start, const RunAgg& a) {
+  if (nbuf == (uint32_t)kWalkRunCap) walk_flush(buf, nbuf, o, st);
+  if ((threadIdx.x & 31) == 0) {
+    RunSlot& q = buf[nbuf];
+    q.s = a.s;
+    q.c = a.c;
+    q.key = key;
+    q.cnt = a.cnt;
+    q.start = start;
+    q.mn = a.mn;
+    q.mx = a.mx;
+  }
+  nbuf += 1;
+  __syncwarp();
+}
+
+// The walk of journey j (n points at srec[off ..)) by one warp. Iteration t takes points
+// 32t + lane; a point's predecessor is the previous lane's point (a shuffle), lane 0's the last
+// point of the previous iteration (carried). Every per-journey sum and run aggregate is formed in
+// an order fixed by the points' positions alone: each lane sums its own points in order, and the
+// lanes' partial sums are added by a fixed shuffle tree (at the journey's end for the journey
+// sums, when a run closes for the run aggregates: a run's points in one lane accumulate in that
+// lane until the warp reduces the run).
+template <class Form>
+__device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__ S, int n, uint32_t off,
+                                             const GridParams& g, const Batch& bt, const JourneyOut& o,
+                                             DevState* st, RunSlot* rbuf, uint32_t& nbuf,
+                                             unsigned long long& n_dup, unsigned long long& n_off) {
+  const int lane = threadIdx.x & 31;
+  const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, S[0].idx) : nullptr;
+  typename Form::Acc dist;
+  long long dwell = 0;
+  uint32_t dup = 0, offg = 0;
+  // the last point of the previous iteration (valid from the second iteration on)
+  int64_t c_ts = 0;
+  double c_lat = 0.0, c_lon = 0.0;
+  float c_spd = 0.0f;
+  typename Form::Cos c_cos{};
+  uint32_t c_key = kKeyInvalid;
+  int64_t first_ts = 0;
+  // the run open after the previous iteration: key and first position (warp-uniform), and this
+  // lane's share of its points
+  uint32_t o_key = kKeyInvalid, o_start = 0;
+  RunAgg la = agg_empty();
+  // records one iteration ahead
+  unsigned long long na = 0, nb = 0, nc = 0, nd = 0;
+  if (lane < n) ld_rec(S + lane, na, nb, nc, nd);
+  for (int base = 0; base < n; base += 32) {
+    const int k = base + lane;
+    const bool valid = k < n;
+    const unsigned long long ra = na, rb = nb, rc = nc, rd = nd;
+    if (k + 32 < n) ld_rec(S + k + 32, na, nb, nc, nd);
+    const int64_t ts = (int64_t)ra;
+    const double lat = dfrom(rb), lon = dfrom(rc);
+    const float spd = __uint_as_float((uint32_t)rd);
+    const uint32_t idx = (uint32_t)(rd >> 32);
+    typename Form::Cos ccur{};
+    uint32_t key = kKeyInvalid;
+    if (valid) {
+      ccur = Form::cosine(lat, g);
+      key = point_key(lat, lon, ts, g, bi);
+    }
+    // predecessor: the previous lane's point, or the carried one
+    int64_t p_ts = (int64_t)__shfl_up_sync(0xffffffffu, (unsigned long long)ts, 1);
+    double p_lat = __shfl_up_sync(0xffffffffu, lat, 1), p_lon = __shfl_up_sync(0xffffffffu, lon, 1);
+    float p_spd = __shfl_up_sync(0xffffffffu, spd, 1);
+    typename Form::Cos p_cos = shfl_up_cos(ccur, 1);
+    uint32_t p_key = __shfl_up_sync(0xffffffffu, key, 1);
+    if (lane == 0) {
+      p_ts = c_ts;
+      p_lat = c_lat;
+      p_lon = c_lon;
+      p_spd = c_spd;
+      p_cos = c_cos;
+      p_key = c_key;
+    }
+    if (base == 0) first_ts = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)ts, 0);
+    if (valid) {
+      uint8_t fl = 0;
+      typename Form::Dist d = 0;
+      float vh = 0.0f, ac = 0.0f;
+      int64_t dw = 0;
+      if (k == 0) {
+        fl |= kFStart;
+      } else {
+        const int64_t dt = (int64_t)((unsigned long long)ts - (unsigned long long)p_ts);
+        if (dt == 0) fl |= kFDup;
+        d = Form::distance(p_lat, p_lon, p_cos, lat, lon, ccur, g);
+        if (dt > 0) {
+          const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : i64_to_f32_rare(dt);
+          vh = to_f32(d) * (3600.0f / fdt);
+          ac = (spd - p_spd) / (0.0036f * fdt);
+        }
+        if (p_spd < g.v_stop && spd < g.v_stop) {
+          fl |= kFStop;
+          dw = dt;
+        }
+      }
+      if (key == kKeyInvalid) fl |= kFOffgrid;
+      dist.add(d);
+      dwell += dw;
+      dup += (fl & kFDup) ? 1u : 0u;
+      offg += (key == kKeyInvalid) ? 1u : 0u;
+      const uint32_t gp = off + (uint32_t)k;
+      if (o.perm) {
+        o.perm[gp] = idx;
+        o.d[gp] = (double)d;
+        o.vhat[gp] = vh;
+        o.accel[gp] = ac;
+        o.dwell_pt[gp] = dw;
+        o.key[gp] = key;
+        o.flags[gp] = fl;
+      }
+      if (k == 0) {
+        o.start_ts[j] = ts;
+        o.slat[j] = lat;
+        o.slon[j] = lon;
+      }
+      if (k == n - 1) {
+        o.end_ts[j] = ts;
+        o.duration[j] = (int64_t)((unsigned long long)ts - (unsigned long long)first_ts);
+        o.elat[j] = lat;
+        o.elon[j] = lon;
+      }
+    }
+    // runs of equal keys: heads where the key changes (or the journey starts)
+    const bool head = valid && (k == 0 || key != p_key);
+    uint32_t hmask = __ballot_sync(0xffffffffu, head);
+    if (hmask == 0) {
+      if (valid) agg_add(la, spd);  // the open run goes on through the whole iteration
+    } else {
+      // lanes before the first head close the open run
+      int h = __ffs(hmask) - 1;
+      if (valid && lane < h) agg_add(la, spd);
+      const RunAgg r = warp_agg(la);
+      const uint32_t r_cnt = __shfl_sync(0xffffffffu, r.cnt, 0);
+      if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r);
+      // runs that start and end inside this iteration, one warp reduction each
+      hmask &= hmask - 1;
+      while (hmask) {
+        const int h2 = __ffs(hmask) - 1;
+        const uint32_t kh = __shfl_sync(0xffffffffu, key, h);
+        RunAgg a = agg_empty();
+        if (lane >= h && lane < h2) agg_add(a, spd);
+        const RunAgg r2 = warp_agg(a);
+        if (kh != kKeyInvalid) walk_put(rbuf, nbuf, o, st, kh, off + (uint32_t)(base + h), r2);
+        h = h2;
+        hmask &= hmask - 1;
+      }
+      // the last run of the iteration stays open: its lanes start their shares
+      la = agg_empty();
+      if (valid && lane >= h) agg_add(la, spd);
+      o_key = __shfl_sync(0xffffffffu, key, h);
+      o_start = off + (uint32_t)(base + h);
+    }
+    // carry the last point to the next iteration
+    c_ts = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)ts, 31);
+    c_lat = __shfl_sync(0xffffffffu, lat, 31);
+    c_lon = __shfl_sync(0xffffffffu, lon, 31);
+    c_spd = __shfl_sync(0xffffffffu, spd, 31);
+    c_cos = shfl_cos(ccur, 31);
+    c_key = __shfl_sync(0xffffffffu, key, 31);
+  }
+  // the run open at the journey's end
+  {
+    const RunAgg r = warp_agg(la);
+    const uint32_t r_cnt = __shfl_sync(0xffffffffu, r.cnt, 0);
+    if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r);
+  }
+  // journey sums: each lane's own sum, then a fixed shuffle tree
+  const double sd = warp_sum(dist.value());
+  const long long sw = warp_sum(dwell);
+  const uint32_t sdup = warp_sum(dup), soff = warp_sum(offg);
+  if (lane == 0) {
+    o.n[j] = n;
+    o.off[j] = off;
+    o.dist[j] = sd;
+    o.dwell[j] = sw;
+    n_dup += sdup;
+    n_off += soff;
+  }
+}
+
+// One warp per journey, journeys taken longest first from the work list through the work
+// counter; a persistent grid.
+template <class Form>
+__global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __restrict__ srec,
+                                                            const uint32_t* __restrict__ jn,
+                                                            const uint32_t* __restrict__ joff, uint32_t J,
+                                                            GridParams g, Batch bt, JourneyOut o, DevState* st,
+                                                            const uint32_t* __restrict__ order, uint32_t* work) {
+  __shared__ RunSlot s_runs[kWalkBlock / 32][kWalkRunCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RunSlot* rbuf = s_runs[warp];
+  uint32_t nbuf = 0;
+  unsigned long long n_dup = 0, n_off = 0;
+  for (;;) {
+    uint32_t w = 0;
+    if (lane == 0) w = atomicAdd(work, 1u);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= J) break;
+    const uint32_t j = order ? order[w] : w;
+    const uint32_t off = joff[j];
+    walk_journey<Form>(j, srec + off, (int)jn[j], off, g, bt, o, st, rbuf, nbuf, n_dup, n_off);
+  }
+  walk_flush(rbuf, nbuf, o, st);
+  if (lane == 0) {
+    if (n_dup) atomicAdd(&st->n_dup, n_dup);
+    if (n_off) atomicAdd(&st->n_offgrid, n_off);
   }
 }
 

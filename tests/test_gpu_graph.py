@@ -33,7 +33,7 @@ def test_replays_match_the_eager_path(small_day):
         per_run = 2 if p.tuning["small_journey_max"] else 1  # the 256- and 64-thread journey kernels
     for r in runs:
         same(ref, r)
-    assert st["stages"]["journeys"]["launches"] == 3 * per_run
+    assert st["stages"]["journey_sort"]["launches"] == 3 * 5
     assert st["graph_replays"] == 2  # the first run of the shape is eager and captured
 
 

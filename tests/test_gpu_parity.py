@@ -240,9 +240,10 @@ def test_stats_count_launches(small_day):
     with P.Pipeline(profile=1) as p:
         p.run(t, to_host=False)
         s = p.stats()
-        per_run = 2 if p.tuning["small_journey_max"] else 1  # the 256- and 64-thread journey kernels
     assert s["total_launches"] > 10
-    assert s["stages"]["journeys"]["launches"] == per_run and s["stages"]["journeys"]["ms"] > 0
+    # the journey sort: the size-class bounds, then one persistent launch per size class
+    assert s["stages"]["journey_sort"]["launches"] == 5 and s["stages"]["journey_sort"]["ms"] > 0
+    assert s["stages"]["journey_walk"]["launches"] == 1 and s["stages"]["journey_walk"]["ms"] > 0
 
 
 def test_results_into_pinned_buffers(small_day):

@@ -65,8 +65,10 @@ def test_journey_stage_is_one_pass_per_step():
     """The journey stage launches its two CTA shapes once each per step over one pass of the
     points: its time per pass is the stage time per step, and its algorithmic bytes count once
     per step; every other stage's launch is a pass of its own."""
+    assert bench.unit_launches("journey_sort", 20, 10) == 10
+    assert bench.unit_launches("journey_sort", 10, 10) == 10
     assert bench.unit_launches("journeys", 20, 10) == 10
-    assert bench.unit_launches("journeys", 10, 10) == 10
+    assert bench.unit_launches("journey_walk", 10, 10) == 10
     assert bench.unit_launches("radix_onesweep", 160, 10) == 160
     assert bench.unit_launches("scatter", 0, 10) == 1
     c = {"n_in": 100, "n_valid": 90, "n_journeys": 3, "n_runs": 7, "n_cells": 5}
