@@ -1324,7 +1324,8 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   for (int k = -9000; k <= 9000; ++k) {
     const double lat0 = (double)k * 0.01;
     const double rad = M_PI / 180.0;
-    cos_tab[k + 9000] = CosEntry{lat0, std::cos(lat0 * rad), std::sin(lat0 * rad) * rad, 0.0};
+    const double c0 = std::cos(lat0 * rad), s0r = std::sin(lat0 * rad) * rad;
+    cos_tab[k + 9000] = CosEntry{lat0, c0, s0r, (float)c0, (float)s0r};
   }
   CosEntry* d_cos = nullptr;
   if ((s = ensure(c, "grid.cos", cos_tab.size(), &d_cos)) != CVETL_OK) return bail(s);

@@ -514,6 +514,8 @@ __device__ __forceinline__ float haversine_f32(double la1, double lo1, float c1,
 struct Fp64Form {
   typedef Cos64 Cos;
   typedef double Dist;
+  // the per-point rates (implied speed, acceleration) are float32 quotients, correctly rounded
+  static __device__ __forceinline__ float div(float a, float b) { return a / b; }
   static __device__ __forceinline__ Cos64 cosine(double lat, const GridParams& g) {
     return cos64(lat, g.cos_tab);
   }
@@ -531,8 +533,15 @@ struct Fp64Form {
 struct Fp32Form {
   typedef float Cos;
   typedef float Dist;
-  static __device__ __forceinline__ float cosine(double lat, const GridParams&) {
-    return cosf(leading_f32(lat) * kRadF);
+  // the per-point rates by the fast float32 division (within 2 ulp)
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  // cos(lat) from the nearest 0.01-degree table point: c0 - s0 E (E the offset in radians, under
+  // 8.8e-5; the dropped E^2 term is below 4e-9 relative)
+  static __device__ __forceinline__ float cosine(double lat, const GridParams& g) {
+    const float lf = leading_f32(lat);
+    const int k = max(-9000, min(9000, __float2int_rn(lf * 100.0f)));
+    const float2 cs = __ldg(reinterpret_cast<const float2*>(&g.cos_tab[k + 9000].c0f));
+    return fmaf(-cs.y, lf - (float)k * 0.01f, cs.x);
   }
   static __device__ __forceinline__ float distance(double la1, double lo1, float c1, double la2,
                                                    double lo2, float c2, const GridParams& g) {
@@ -930,8 +939,8 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
         if (dt > 0) {
           // stored as float32: computed in float32 from the binary64 distance
           const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : i64_to_f32_rare(dt);
-          vh = to_f32(d) * (3600.0f / fdt);
-          ac = (cur.spd - p_spd) / (0.0036f * fdt);
+          vh = to_f32(d) * Form::div(3600.0f, fdt);
+          ac = Form::div(cur.spd - p_spd, 0.0036f * fdt);
         }
         if (p_spd < g.v_stop && cur.spd < g.v_stop) {
           fl |= kFStop;
@@ -1157,6 +1166,81 @@ __device__ __forceinline__ bool staged_less(const unsigned long long* T, const R
   return ta < tb || (ta == tb && R[a].idx < R[b].idx);
 }
 
+// The points k = 0..m-1 with order-preserving timestamps T[k] in [tmin, tmax], ordered by
+// (timestamp, row index) into the u16 array O: a counting sort by time bucket (max(1, m/2)
+// buckets, about two points each), then an insertion sort inside each bucket; idx_of(k) gives a
+// point's row index (read only for equal timestamps). cnt: max(1, m/2) u32 counters. Returns
+// false, with O unset, when a bucket holds more than kMaxBucket points. Every thread of the CTA
+// calls it; ends with a barrier.
+template <int NT, class IdxOf>
+__device__ bool staged_order(const unsigned long long* T, int m, unsigned long long tmin, unsigned long long tmax,
+                             uint16_t* O, uint32_t* cnt, uint32_t* s_scan, int* s_flag, IdxOf idx_of) {
+  const int tid = threadIdx.x;
+  const int nb = max(1, m >> 1);
+  const unsigned long long span = tmax - tmin;
+  const bool narrow = span <= 0xFFFFFFFFull;
+  const float scale = (float)nb / ((float)span + 1.0f);
+  for (int b = tid; b < nb; b += NT) cnt[b] = 0;
+  if (tid == 0) *s_flag = 0;
+  __syncthreads();
+  for (int i = tid; i < m; i += NT) atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u);
+  __syncthreads();
+  // bucket offsets (each thread a contiguous chunk of buckets); crowded buckets detected
+  const int chunk = (nb + NT - 1) / NT;
+  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
+  uint32_t sum = 0, mx = 0;
+  for (int b = c0; b < c1; ++b) {
+    sum += cnt[b];
+    mx = max(mx, cnt[b]);
+  }
+  uint32_t base = block_excl_scan<NT>(sum, s_scan, nullptr);
+  if (mx > (uint32_t)kMaxBucket) *s_flag = 1;
+  for (int b = c0; b < c1; ++b) {
+    const uint32_t v = cnt[b];
+    cnt[b] = base;
+    base += v;
+  }
+  __syncthreads();
+  if (*s_flag) return false;
+  // positions by bucket (cnt[b] ends as the end of bucket b)
+  for (int i = tid; i < m; i += NT) O[atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u)] = (uint16_t)i;
+  __syncthreads();
+  // each bucket by (timestamp, row index)
+  for (int b = tid; b < nb; b += NT) {
+    const int b0 = b ? (int)cnt[b - 1] : 0, b1 = (int)cnt[b];
+    for (int i = b0 + 1; i < b1; ++i) {
+      const uint16_t v = O[i];
+      const unsigned long long tv = T[v];
+      int q = i - 1;
+      while (q >= b0) {
+        const unsigned long long tq = T[O[q]];
+        if (tq < tv || (tq == tv && idx_of(O[q]) < idx_of(v))) break;
+        O[q + 1] = O[q];
+        --q;
+      }
+      O[q + 1] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Block-wide range of the threads' [lo, hi] into *s_lo, *s_hi (set to ~0 and 0 by the caller
+// before a barrier); ends with a barrier.
+__device__ __forceinline__ void block_range(unsigned long long lo, unsigned long long hi, unsigned long long* s_lo,
+                                            unsigned long long* s_hi) {
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o2));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o2));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(s_lo, lo);
+    atomicMax(s_hi, hi);
+  }
+  __syncthreads();
+}
+
 template <int NT, int CAP>
 __device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1166,13 +1250,12 @@ __device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __res
   __shared__ unsigned long long s_tmin, s_tmax;
   __shared__ uint32_t s_scan[NT / 32 + 1];
   __shared__ int s_flag;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   if (tid == 0) {
     s_tmin = ~0ull;
     s_tmax = 0ull;
-    s_flag = 0;
   }
-  // 1. the timestamps, once, into shared memory; their range
+  // the timestamps, once, into shared memory; their range
   unsigned long long lo = ~0ull, hi = 0ull;
 #pragma unroll 4
   for (int i = tid; i < n; i += NT) {
@@ -1181,60 +1264,11 @@ __device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __res
     lo = min(lo, t);
     hi = max(hi, t);
   }
-#pragma unroll
-  for (int o2 = 16; o2 > 0; o2 >>= 1) {
-    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o2));
-    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o2));
-  }
   __syncthreads();
-  if (lane == 0) {
-    atomicMin(&s_tmin, lo);
-    atomicMax(&s_tmax, hi);
-  }
-  const int nb = max(1, n >> 1);
-  for (int b = tid; b < nb; b += NT) cnt[b] = 0;
-  __syncthreads();
-  const unsigned long long tmin = s_tmin, span = s_tmax - tmin;
-  const bool narrow = span <= 0xFFFFFFFFull;
-  const float scale = (float)nb / ((float)span + 1.0f);
-  // 2. bucket counts
-  for (int i = tid; i < n; i += NT) atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u);
-  __syncthreads();
-  // 3. bucket offsets (each thread a contiguous chunk of buckets), crowded buckets detected
-  const int chunk = (nb + NT - 1) / NT;
-  const int c0 = min(nb, tid * chunk), c1 = min(nb, c0 + chunk);
-  uint32_t sum = 0, mx = 0;
-  for (int b = c0; b < c1; ++b) {
-    sum += cnt[b];
-    mx = max(mx, cnt[b]);
-  }
-  uint32_t base = block_excl_scan<NT>(sum, s_scan, nullptr);
-  if (mx > (uint32_t)kMaxBucket) s_flag = 1;
-  for (int b = c0; b < c1; ++b) {
-    const uint32_t v = cnt[b];
-    cnt[b] = base;
-    base += v;
-  }
-  __syncthreads();
-  if (s_flag) return false;
-  // 4. positions by bucket (cnt[b] ends as the end of bucket b)
-  for (int i = tid; i < n; i += NT) P[atomicAdd(&cnt[time_bucket(T[i] - tmin, narrow, scale, nb)], 1u)] = (uint16_t)i;
-  __syncthreads();
-  // 5. each bucket by (timestamp, row index)
-  for (int b = tid; b < nb; b += NT) {
-    const int b0 = b ? (int)cnt[b - 1] : 0, b1 = (int)cnt[b];
-    for (int i = b0 + 1; i < b1; ++i) {
-      const uint16_t v = P[i];
-      int q = i - 1;
-      while (q >= b0 && staged_less(T, R, v, P[q])) {
-        P[q + 1] = P[q];
-        --q;
-      }
-      P[q + 1] = v;
-    }
-  }
-  __syncthreads();
-  // 6. the records in order
+  block_range(lo, hi, &s_tmin, &s_tmax);
+  if (!staged_order<NT>(T, n, s_tmin, s_tmax, P, cnt, s_scan, &s_flag, [R](int k) { return R[k].idx; }))
+    return false;
+  // the records in order
   for (int k = tid; k < n; k += NT) {
     unsigned long long a, b, c, d;
     ld_rec(R + P[k], a, b, c, d);
@@ -1265,8 +1299,9 @@ __global__ void k_size_classes(const uint32_t* __restrict__ jn, const uint32_t* 
 }
 
 // One size class of the journey sort, persistent: CTAs take the class's journeys in list order
-// through its work counter. CAP > 0: the staged sort (the general one when a bucket is crowded);
-// CAP = 0: the general sort (global scratch above 4096 points).
+// through its work counter. CAP > 0: the staged sort, falling back to the general sort when a
+// time bucket is crowded; CAP = 0 (journeys above 8192 points): the general sort (global scratch
+// above 4096 points).
 template <int NT, int CAP>
 __host__ __device__ constexpr int sort_class_min_blocks() { return NT == 64 ? 12 : (CAP > 4096 ? 2 : 3); }
 
@@ -1483,8 +1518,8 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
         d = Form::distance(p_lat, p_lon, p_cos, lat, lon, ccur, g);
         if (dt > 0) {
           const float fdt = (dt <= 0x7FFFFFFFll) ? (float)(int32_t)dt : i64_to_f32_rare(dt);
-          vh = to_f32(d) * (3600.0f / fdt);
-          ac = (spd - p_spd) / (0.0036f * fdt);
+          vh = to_f32(d) * Form::div(3600.0f, fdt);
+          ac = Form::div(spd - p_spd, 0.0036f * fdt);
         }
         if (p_spd < g.v_stop && spd < g.v_stop) {
           fl |= kFStop;
@@ -1579,7 +1614,16 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
 // One warp per journey, journeys taken longest first from the work list through the work
 // counter; a persistent grid.
 template <class Form>
-__global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __restrict__ srec,
+struct WalkShape {
+  static constexpr int kMinBlocks = 6;  // 80 registers: the binary64 form's working set
+};
+template <>
+struct WalkShape<Fp32Form> {
+  static constexpr int kMinBlocks = 8;  // 64 registers
+};
+
+template <class Form>
+__global__ void __launch_bounds__(kWalkBlock, WalkShape<Form>::kMinBlocks) k_journey_walk(const Rec* __restrict__ srec,
                                                             const uint32_t* __restrict__ jn,
                                                             const uint32_t* __restrict__ joff, uint32_t J,
                                                             GridParams g, Batch bt, JourneyOut o, DevState* st,

@@ -6,9 +6,11 @@
 
 namespace cvetl {
 
-// cosine table entry: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180, unused}
+// cosine table entry: {lat0 = k * 0.01, cos(lat0 deg), sin(lat0 deg) * pi/180} in binary64 and
+// the last two rounded to float32 (for the float32 form)
 struct __align__(32) CosEntry {
-  double lat0, c0, s0r, pad;
+  double lat0, c0, s0r;
+  float c0f, s0rf;
 };
 
 struct GridParams {

@@ -134,6 +134,19 @@ def test_short_journeys_in_64_thread_ctas(orc, split, dup_frac):
     compare(run_gpu(cols, tuning=dict(small_journey_max=split)), orc.run(cols))
 
 
+SORT_EDGES = [512, 513, 2048, 2049, 4096, 4097, 6143, 8192, 8193, 16384, 30001]
+
+
+@pytest.mark.parametrize("dup_frac", [0.01, 0.6])
+def test_journey_sort_size_classes(orc, dup_frac):
+    """The batch sort takes each journey by size class: up to 512, 4096 and 8192 points with the
+    timestamps held in shared memory, larger ones through global scratch; journeys on either side
+    of every class edge, and at dup_frac 0.6 with time buckets crowded past the staged sort's
+    limit (each class then falls back to the general sort)."""
+    cols = synth(SORT_EDGES, seed=31 + int(dup_frac * 10), dup_frac=dup_frac)
+    compare(run_gpu(cols), orc.run(cols))
+
+
 def test_timestamps_spanning_the_int64_range(orc):
     """Timestamps spread over the whole int64 range: the sort keys (time offset and bucket
     position) no longer fit 64 bits and every journey is sorted as (timestamp, row) pairs, in both
