@@ -1090,34 +1090,49 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = c->cfg.precision == CVETL_FP32;
-    // the sort by journey size class (each class a persistent grid over its part of the list)
-    uint32_t *bounds, *cwork;
-    ENSURE("j.bounds", 5, &bounds);
-    ENSURE("j.cwork", 4, &cwork);
-    LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
-    LAUNCH_CHECK();
-    static const int occ[4] = {
-        occupancy(k_journey_sort_class<kJBlock, 0>, kJBlock, kSortSmemA),
-        occupancy(k_journey_sort_class<kJBlock, 8192>, kJBlock, kSortSmemB),
-        occupancy(k_journey_sort_class<kJBlock, 4096>, kJBlock, kSortSmemC),
-        occupancy(k_journey_sort_class<kJSmallBlock, 512>, kJSmallBlock, kSortSmemD)};
+    if (f32) {
+      // the float32 form: the fused journey kernel (sort and walk in one CTA per journey), whose
+      // short walk gains nothing from a separate ordered copy of the records
+      const bool pers = c->tune.journey_ctas > 0;
+      const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
+      // journeys of up to `split` points (at most 512) to the 64-thread shape, the rest first
+      const uint32_t split = (uint32_t)c->tune.small_journey_max;
+      CK(cudaMemsetAsync(work, 0, 4, c->st));
+#define JRN(P, NT, SM, G) k_journeys<Fp32Form, P, NT><<<G, NT, SM, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, \
+                                                                          c->bt, o, c->dstate, nullptr, JState{}, \
+                                                                          order, work, split)
+      if (pers) LAUNCH(ST_JOURNEYS, (JRN(true, kJBlock, kJSmem, grid)));
+      else LAUNCH(ST_JOURNEYS, (JRN(false, kJBlock, kJSmem, grid)));
+      if (split) LAUNCH(ST_JOURNEYS, (JRN(false, kJSmallBlock, kJSmallSmem, J)));
+#undef JRN
+      LAUNCH_CHECK();
+    } else {
+      // the binary64 form: the sort by journey size class (each class a persistent grid over its
+      // part of the list) into a second record array, then the walk of the ordered records
+      uint32_t *bounds, *cwork;
+      ENSURE("j.bounds", 5, &bounds);
+      ENSURE("j.cwork", 4, &cwork);
+      LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
+      LAUNCH_CHECK();
+      static const int occ[4] = {
+          occupancy(k_journey_sort_class<kJBlock, 0>, kJBlock, kSortSmemA),
+          occupancy(k_journey_sort_class<kJBlock, 8192>, kJBlock, kSortSmemB),
+          occupancy(k_journey_sort_class<kJBlock, 4096>, kJBlock, kSortSmemC),
+          occupancy(k_journey_sort_class<kJSmallBlock, 512>, kJSmallBlock, kSortSmemD)};
 #define JCLS(NT, CAP, SM, K) k_journey_sort_class<NT, CAP><<<(uint32_t)(sms * occ[K]), NT, SM, c->st>>>( \
-    rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
-    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 0, kSortSmemA, 0)));
-    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 8192, kSortSmemB, 1)));
-    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 4096, kSortSmemC, 2)));
-    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
+      rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
+      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 0, kSortSmemA, 0)));
+      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 8192, kSortSmemB, 1)));
+      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 4096, kSortSmemC, 2)));
+      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
 #undef JCLS
-    LAUNCH_CHECK();
-    // the walk: a persistent grid of warps taking journeys longest first
-    static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, 0);
-    static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
-    const uint32_t wgrid = (uint32_t)(sms * (f32 ? occ32 : occ64));
-    if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<wgrid, kWalkBlock, 0, c->st>>>(
-                                        srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
-    else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<wgrid, kWalkBlock, 0, c->st>>>(
-                                     srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
-    LAUNCH_CHECK();
+      LAUNCH_CHECK();
+      // the walk: a persistent grid of warps taking journeys longest first
+      static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
+      LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, 0, c->st>>>(
+                                  srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
+      LAUNCH_CHECK();
+    }
     if (o.perm) {  // features over earlier points of a journey (materialised points)
       LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(
                               jn, joff, J, c->ts, o.perm, o.d, o.dwell_pt, o.flags, o.stop_ms, o.accel_v)));

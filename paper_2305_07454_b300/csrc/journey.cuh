@@ -1136,10 +1136,13 @@ __global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
 }
 
 // ---------------------------------------------------------------- batch path: sort, then walk
-// The batch path orders each journey's bucket into a second record array in (timestamp, row)
-// order (k_journey_sort), then walks the ordered records with one warp per journey
-// (k_journey_walk). The sort keeps the shared-memory / L2 scheme above; the walk reads each
-// record once, coalesced, with every lane on its own point.
+// The binary64 form's batch path orders each journey's bucket into a second record array in
+// (timestamp, row) order (k_journey_sort_class, by journey size class), then walks the ordered
+// records with one warp per journey (k_journey_walk): the walk, bound by the binary64 pipe, runs
+// at full occupancy apart from the latency-bound sort. The sort keeps the shared-memory / L2
+// scheme above; the walk reads each record once, coalesced, with every lane on its own point.
+// (The float32 form's walk is short enough that the fused kernel above, without the ordered
+// copy, is faster.)
 
 __device__ __forceinline__ void ld_rec(const Rec* p, unsigned long long& a, unsigned long long& b,
                                        unsigned long long& c, unsigned long long& d) {
@@ -1614,16 +1617,7 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
 // One warp per journey, journeys taken longest first from the work list through the work
 // counter; a persistent grid.
 template <class Form>
-struct WalkShape {
-  static constexpr int kMinBlocks = 6;  // 80 registers: the binary64 form's working set
-};
-template <>
-struct WalkShape<Fp32Form> {
-  static constexpr int kMinBlocks = 8;  // 64 registers
-};
-
-template <class Form>
-__global__ void __launch_bounds__(kWalkBlock, WalkShape<Form>::kMinBlocks) k_journey_walk(const Rec* __restrict__ srec,
+__global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __restrict__ srec,
                                                             const uint32_t* __restrict__ jn,
                                                             const uint32_t* __restrict__ joff, uint32_t J,
                                                             GridParams g, Batch bt, JourneyOut o, DevState* st,
