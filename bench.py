@@ -205,17 +205,22 @@ def fp64_probe(stream, reps=3):
                    "peak = the fastest single operation kind"}
 
 
-# Per-pass DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per record of a stage,
-# from one ncu capture of the tenth-day workload (14,637,283 records) with the kernels as they
-# stand, scaled by records to the workload's pass (the full day is too large to capture under
-# the profiler's size rule); FP64 form, column or CSV input. The journeys entry adds its two
-# kernel shapes (256- and 64-thread CTAs). Empty a stage's entry when its kernels change, until
-# they are captured again.
-TRAFFIC_PER_RECORD_FP32 = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per step and per kept record of
+# every stage, from one ncu capture of the tenth-day workload (14,637,283 records) with the
+# kernels as they stand: one warm step of each path (binary64 form, float32 form, CSV input),
+# scaled by records to the workload (the full day is too large to capture under the profiler's
+# size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "scatter": (468.913152e6 + 428.840448e6) / 14637283,
-    "hash_count": (410.996736e6 + 48.926464e6) / 14637283,
-    "csv_parse": (856.018944e6 + 549.557760e6) / 14637283,
+    "hash_count": 31.157, "collect_slots": 0.144, "radix_histogram": 0.225, "radix_onesweep": 2.535,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.045, "journey_sort": 61.721,
+    "journey_walk": 32.672, "cell_heads": 0.214, "cell_write": 1.075,
+    # CSV input adds (per kept record of the CSV day)
+    "csv_count": 58.656, "csv_parse": 96.275,
+}
+TRAFFIC_PER_RECORD_FP32 = {
+    "hash_count": 31.153, "collect_slots": 0.144, "radix_histogram": 0.225, "radix_onesweep": 2.535,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.045, "journeys": 60.455,
+    "cell_heads": 0.214, "cell_write": 1.075,
 }
 
 
@@ -299,13 +304,12 @@ def _hbm_step(stages, counters, ms_step, steps, csv, traffic=None):
         out["gate"] = None
         out["gate_missing_traffic"] = missing
     else:
-        dram = sum(traffic[s] * counters["n_valid"] * unit_launches(s, v["launches"], steps) / steps
-                   for s, v in timed.items())
+        dram = sum(traffic[s] * counters["n_valid"] for s in timed)
         kms = sum(v["ms"] for v in timed.values()) / steps
         out["gate"] = {"dram_bytes_per_step": dram, "kernel_ms_per_step": kms,
                        "achieved": dram / (kms / 1e3) / 1e9, "frac": dram / (kms / 1e3) / 1e9 / hbm_peak,
-                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per record of every stage "
-                                 "(tenth-day capture), scaled by records; CUDA-event kernel times"}
+                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per step and record of every "
+                                 "stage (tenth-day capture), scaled by records; CUDA-event kernel times"}
     return out
 
 
@@ -315,7 +319,8 @@ def _roofline_entry(top, stages, counters, steps, precision, probe):
     avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], steps)
     hbm_peak, peak_src = load_peaks()
     tpr = TRAFFIC_PER_RECORD.get(top) if precision == "fp64" else TRAFFIC_PER_RECORD_FP32.get(top)
-    traffic = tpr * counters["n_valid"] if tpr else None
+    # per launch (a pass over the stage's work): the step's traffic over the passes per step
+    traffic = tpr * counters["n_valid"] / (unit_launches(top, stages[top]["launches"], steps) / steps) if tpr else None
     if top in ("journeys", "journey_walk") and precision == "fp64" and probe:
         ops = FP64_OPS_PER_POINT * counters["n_valid"]
         achieved = ops / (avg_ms / 1e3) / 1e9
@@ -500,6 +505,9 @@ def run_ours(args):
     if args.fp32_leg and args.precision == "fp64":
         line["fp32_day"] = _leg(lambda: _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job,
                                                   csv_host, batch_res))
+    # ---- the same day extracted from CSV text (binary64 form) ------------------------------
+    if args.csv_leg and csv_host is None:
+        line["csv_day"] = _leg(lambda: _csv_day(P, host, stream, args, barrier, local, world, dev, rank))
     if args.serve_feeds > 0:
         line["serving"] = serving(host, n, args, batch_res["cells"], ms_step)
     if args.week_scale > 0 and csv_host is None:
@@ -544,6 +552,41 @@ def _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job, c
             "roofline": _roofline_entry(top32, st32, c32, args.steps, "fp32", None),
             "stages": {s: {"ms_per_step": v["ms"] / args.steps} for s, v in st32.items() if v["launches"]},
             "errors_vs_fp64_form": _form_errors(r32, batch_res), "tuning": tune32, "clocks": clk32}
+
+
+def _csv_day(P, host, stream, args, barrier, local, world, dev, rank):
+    """The day's records as CSV text (0.5% malformed rows), parsed and processed on the device:
+    device-resident timed steps (extract from the text, transform, load), stage times from a
+    profiled run, the step's bytes against the measured copy bandwidth."""
+    import torch
+
+    import cvgen
+
+    t_gen = time.perf_counter()
+    text, n_bad = cvgen.to_csv({k: host[k].numpy() for k in host}, seed=1 + rank, malformed_frac=0.005)
+    t_gen = time.perf_counter() - t_gen
+    d_csv = torch.from_numpy(text).to(dev)
+    del text
+    torch.cuda.synchronize()
+    extract = lambda p: p.extract_csv(d_csv)
+    pc = P.Pipeline(stream=stream, precision=P.FP64)
+    extract(pc)
+    tune = pc.autotune(reps=2) if args.autotune else {**pc.tuning, "ms": None}
+    ms, clk = _day_steps(P, pc, extract, args.steps, args.warmup, barrier, local)
+    st = _stage_stats(P, stream, P.FP64, tune, extract, args.steps)["stages"]
+    c = _counters(pc.tables())
+    c["csv_bytes"] = int(d_csv.numel())
+    pc.close()
+    del d_csv
+    torch.cuda.empty_cache()
+    (ms,), (nj,) = over_ranks([ms], [c["n_in"]], world, dev)
+    top = max(st, key=lambda k: st[k]["ms"])
+    return {"workload": f"the day as CSV text ({c['csv_bytes']} bytes, {n_bad} malformed rows)",
+            "ms_per_step": ms / args.steps, "records_per_s": nj * args.steps / (ms / 1e3),
+            "hbm_step": _hbm_step(st, c, ms / args.steps, args.steps, True, TRAFFIC_PER_RECORD),
+            "roofline": _roofline_entry(top, st, c, args.steps, "fp64", None),
+            "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in st.items() if v["launches"]},
+            "counters": c, "generation_s": t_gen, "tuning": tune, "clocks": clk}
 
 
 def _host_available_bytes():
@@ -1010,6 +1053,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=0, help="server slots (default: one per feed)")
     ap.add_argument("--serve-budget-gb", type=float, default=8.0)
     ap.add_argument("--fp32-leg", type=int, default=1, help="0 skips the float32 form of the day")
+    ap.add_argument("--csv-leg", type=int, default=1, help="0 skips the day extracted from CSV text")
     ap.add_argument("--week-scale", type=float, default=1.0,
                     help="instance size factor of the week_regions leg of the day run (0 skips it)")
     args = ap.parse_args()

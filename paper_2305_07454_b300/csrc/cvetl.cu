@@ -266,9 +266,10 @@ int occupancy(F kernel, int block, size_t smem) {
   return per_sm > 0 ? per_sm : 1;
 }
 
-constexpr int kSortSmemA = kJSmem;
-constexpr int kSortSmemB = staged_smem<8192>();
-constexpr int kSortSmemC = cmax(staged_smem<4096>(), kJSmem);
+constexpr int kSortBlockB = 512;  // threads of the 4097-8192 class
+constexpr int kSortSmemB = cmax(staged_smem<8192>(), 4096 * 16);  // its fallback's pair sort chunk
+constexpr int kSortBlockC = 512;  // threads of the 513-4096 class
+constexpr int kSortSmemC = cmax(cmax(staged_smem<4096>(), kJSmem), 4096 * 16);
 constexpr int kSortSmemD = cmax(staged_smem<512>(), kJSmallSmem);
 
 int grid_for(size_t n, int block, int max_blocks_per_sm = 8) {
@@ -1090,49 +1091,41 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = c->cfg.precision == CVETL_FP32;
-    if (f32) {
-      // the float32 form: the fused journey kernel (sort and walk in one CTA per journey), whose
-      // short walk gains nothing from a separate ordered copy of the records
-      const bool pers = c->tune.journey_ctas > 0;
-      const uint32_t grid = pers ? (uint32_t)std::min<uint64_t>(J, (uint64_t)sms * (uint64_t)c->tune.journey_ctas) : J;
-      // journeys of up to `split` points (at most 512) to the 64-thread shape, the rest first
-      const uint32_t split = (uint32_t)c->tune.small_journey_max;
-      CK(cudaMemsetAsync(work, 0, 4, c->st));
-#define JRN(P, NT, SM, G) k_journeys<Fp32Form, P, NT><<<G, NT, SM, c->st>>>(rec, jn, joff, J, scrA, scrB, c->gp, \
-                                                                          c->bt, o, c->dstate, nullptr, JState{}, \
-                                                                          order, work, split)
-      if (pers) LAUNCH(ST_JOURNEYS, (JRN(true, kJBlock, kJSmem, grid)));
-      else LAUNCH(ST_JOURNEYS, (JRN(false, kJBlock, kJSmem, grid)));
-      if (split) LAUNCH(ST_JOURNEYS, (JRN(false, kJSmallBlock, kJSmallSmem, J)));
-#undef JRN
-      LAUNCH_CHECK();
-    } else {
-      // the binary64 form: the sort by journey size class (each class a persistent grid over its
-      // part of the list) into a second record array, then the walk of the ordered records
-      uint32_t *bounds, *cwork;
-      ENSURE("j.bounds", 5, &bounds);
-      ENSURE("j.cwork", 4, &cwork);
-      LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
-      LAUNCH_CHECK();
-      static const int occ[4] = {
-          occupancy(k_journey_sort_class<kJBlock, 0>, kJBlock, kSortSmemA),
-          occupancy(k_journey_sort_class<kJBlock, 8192>, kJBlock, kSortSmemB),
-          occupancy(k_journey_sort_class<kJBlock, 4096>, kJBlock, kSortSmemC),
-          occupancy(k_journey_sort_class<kJSmallBlock, 512>, kJSmallBlock, kSortSmemD)};
+    // Journeys above 8192 points (the list's first) take the fused journey kernel (sort and walk
+    // in one CTA; their sort goes through global scratch either way); the others are sorted by
+    // size class (each class a persistent grid over its part of the list) into a second record
+    // array, whose ordered records the walk then reads.
+    uint32_t *bounds, *cwork;
+    ENSURE("j.bounds", 5, &bounds);
+    ENSURE("j.cwork", 4, &cwork);
+    LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
+    LAUNCH_CHECK();
+    static const int occ[4] = {
+        0, occupancy(k_journey_sort_class<kSortBlockB, 8192>, kSortBlockB, kSortSmemB),
+        occupancy(k_journey_sort_class<kSortBlockC, 4096>, kSortBlockC, kSortSmemC),
+        occupancy(k_journey_sort_class<kJSmallBlock, 512>, kJSmallBlock, kSortSmemD)};
+    static const int occ_f32 = occupancy(k_journeys<Fp32Form, true, kJBlock>, kJBlock, kJSmem);
+    static const int occ_f64 = occupancy(k_journeys<Fp64Form, true, kJBlock>, kJBlock, kJSmem);
+#define FUSED(F, OCC) k_journeys<F, true, kJBlock><<<(uint32_t)(sms * OCC), kJBlock, kJSmem, c->st>>>( \
+    rec, jn, joff, J, scrA, scrB, c->gp, c->bt, o, c->dstate, nullptr, JState{}, order, cwork, 0u, bounds + 1)
+    if (f32) LAUNCH(ST_JOURNEYS, (FUSED(Fp32Form, occ_f32)));
+    else LAUNCH(ST_JOURNEYS, (FUSED(Fp64Form, occ_f64)));
+#undef FUSED
 #define JCLS(NT, CAP, SM, K) k_journey_sort_class<NT, CAP><<<(uint32_t)(sms * occ[K]), NT, SM, c->st>>>( \
-      rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
-      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 0, kSortSmemA, 0)));
-      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 8192, kSortSmemB, 1)));
-      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJBlock, 4096, kSortSmemC, 2)));
-      LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
+    rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kSortBlockB, 8192, kSortSmemB, 1)));
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kSortBlockC, 4096, kSortSmemC, 2)));
+    LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
 #undef JCLS
-      LAUNCH_CHECK();
-      // the walk: a persistent grid of warps taking journeys longest first
-      static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
-      LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, 0, c->st>>>(
-                                  srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1)));
-      LAUNCH_CHECK();
-    }
+    LAUNCH_CHECK();
+    // the walk: a persistent grid of warps taking the rest of the list longest first
+    static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, 0);
+    static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
+    if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<(uint32_t)(sms * occ32), kWalkBlock, 0, c->st>>>(
+                                        srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
+    else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, 0, c->st>>>(
+                                     srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
+    LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)
       LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(
                               jn, joff, J, c->ts, o.perm, o.d, o.dwell_pt, o.flags, o.stop_ms, o.accel_v)));
@@ -1379,9 +1372,8 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
       cudaFuncSetAttribute(k_journeys<Fp32Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp64Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp32Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemA) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemB) != cudaSuccess ||
-      cudaFuncSetAttribute(k_journey_sort_class<kJBlock, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemC) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kSortBlockB, 8192>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemB) != cudaSuccess ||
+      cudaFuncSetAttribute(k_journey_sort_class<kSortBlockC, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemC) != cudaSuccess ||
       cudaFuncSetAttribute(k_journey_sort_class<kJSmallBlock, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortSmemD) != cudaSuccess ||
       cudaFuncSetAttribute(rs::k_onesweep<unsigned long long>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, rs::kTile * 12) != cudaSuccess ||

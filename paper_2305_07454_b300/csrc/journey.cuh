@@ -19,6 +19,16 @@ struct JShape<256> {
   static constexpr int kRunBuf = 512;   // closed runs staged in shared memory
   static constexpr int kMinBlocks = 3;
 };
+// 512 threads (the staged sort of journeys of 4097-8192 points): the general sort's shape for its
+// fallback when a time bucket is crowded (keys of up to 4096 points in shared memory, the
+// (timestamp, row) pair sort above that)
+template <>
+struct JShape<512> {
+  static constexpr int kCap = 4096;
+  static constexpr int kEChunk = 4096;
+  static constexpr int kRunBuf = 512;
+  static constexpr int kMinBlocks = 1;
+};
 template <>
 struct JShape<64> {
   static constexpr int kCap = 512;
@@ -1092,7 +1102,8 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
 // The journey kernel. Persistent: each CTA takes the next journey of the work list `order`
 // (journey ranks, longest first, so that the long journeys of an uneven batch start early and
 // the short ones fill the tail) through the work counter until the list is exhausted.
-// Otherwise CTA b takes journey order[b] (rank b without a list): the block scheduler's
+// With wend, the persistent kernel stops at the list's first *wend journeys. Otherwise CTA b takes
+// journey order[b] (rank b without a list): the block scheduler's
 // dispatch order then gives the same longest-first start without the loop.
 // split > 0 shares the journeys between the two shapes: those of up to min(split, 512) points
 // go to the 64-thread kernel (which takes the list from its short end), the rest to the
@@ -1109,7 +1120,7 @@ __global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
     const Rec* __restrict__ rec, const uint32_t* __restrict__ jn, const uint32_t* __restrict__ joff, uint32_t J,
     Elem* scrA, Elem* scrB, GridParams g, Batch bt, JourneyOut o, DevState* st,
     const uint32_t* __restrict__ jslot, JState js, const uint32_t* __restrict__ order, uint32_t* work,
-    uint32_t split) {
+    uint32_t split, const uint32_t* __restrict__ wend = nullptr) {
   if constexpr (!Persistent) {
     if (blockIdx.x >= J) return;
     const uint32_t w = (NT == kJBlock) ? blockIdx.x : J - 1 - blockIdx.x;
@@ -1118,12 +1129,13 @@ __global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
   } else {
     static_assert(!Persistent || NT == kJBlock, "persistent CTAs take the 256-thread shape");
     __shared__ uint32_t s_w;
+    const uint32_t w1 = wend ? *wend : J;  // the list's first w1 journeys (all without wend)
     for (;;) {
       if (threadIdx.x == 0) s_w = atomicAdd(work, 1u);
       __syncthreads();
       const uint32_t w = s_w;
       __syncthreads();
-      if (w >= J) break;
+      if (w >= w1) break;
       const uint32_t j = order ? order[w] : w;
       if (!journey_mine<NT>(jn[j], split)) {
         if (order) break;  // longest first: the rest of the list is the 64-thread kernel's
@@ -1302,9 +1314,8 @@ __global__ void k_size_classes(const uint32_t* __restrict__ jn, const uint32_t* 
 }
 
 // One size class of the journey sort, persistent: CTAs take the class's journeys in list order
-// through its work counter. CAP > 0: the staged sort, falling back to the general sort when a
-// time bucket is crowded; CAP = 0 (journeys above 8192 points): the general sort (global scratch
-// above 4096 points).
+// through its work counter: the staged sort, falling back to the general sort when a time bucket
+// is crowded. (Journeys above 8192 points take the fused journey kernel.)
 template <int NT, int CAP>
 __host__ __device__ constexpr int sort_class_min_blocks() { return NT == 64 ? 12 : (CAP > 4096 ? 2 : 3); }
 
@@ -1327,9 +1338,7 @@ __global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journe
     const int n = (int)jn[j];
     const uint32_t off = joff[j];
     const Rec* R = rec + off;
-    bool done = false;
-    if constexpr (CAP > 0) done = journey_sort_staged<NT, CAP>(R, n, srec + off);
-    if (!done) {
+    if (!journey_sort_staged<NT, CAP>(R, n, srec + off)) {
       const JSorted srt = journey_sort<NT>(R, n, off, scrA, scrB, st);
       for (int k = threadIdx.x; k < n; k += NT) {
         unsigned long long a, b, c, d;
@@ -1614,22 +1623,24 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
   }
 }
 
-// One warp per journey, journeys taken longest first from the work list through the work
-// counter; a persistent grid.
+// One warp per journey, journeys taken longest first from the work list (from position *wbeg
+// on, or all of it) through the work counter; a persistent grid.
 template <class Form>
 __global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __restrict__ srec,
                                                             const uint32_t* __restrict__ jn,
                                                             const uint32_t* __restrict__ joff, uint32_t J,
                                                             GridParams g, Batch bt, JourneyOut o, DevState* st,
-                                                            const uint32_t* __restrict__ order, uint32_t* work) {
+                                                            const uint32_t* __restrict__ order, uint32_t* work,
+                                                            const uint32_t* __restrict__ wbeg) {
   __shared__ RunSlot s_runs[kWalkBlock / 32][kWalkRunCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RunSlot* rbuf = s_runs[warp];
   uint32_t nbuf = 0;
   unsigned long long n_dup = 0, n_off = 0;
+  const uint32_t w0 = wbeg ? *wbeg : 0u;  // the list from position *wbeg on (all without wbeg)
   for (;;) {
     uint32_t w = 0;
-    if (lane == 0) w = atomicAdd(work, 1u);
+    if (lane == 0) w = w0 + atomicAdd(work, 1u);
     w = __shfl_sync(0xffffffffu, w, 0);
     if (w >= J) break;
     const uint32_t j = order ? order[w] : w;

@@ -30,10 +30,9 @@ def test_replays_match_the_eager_path(small_day):
     with P.Pipeline(materialize_points=1, graph=1, profile=1) as p:
         runs = [p.run(t) for _ in range(3)]
         st = p.stats()
-        per_run = 2 if p.tuning["small_journey_max"] else 1  # the 256- and 64-thread journey kernels
     for r in runs:
         same(ref, r)
-    assert st["stages"]["journey_sort"]["launches"] == 3 * 5
+    assert st["stages"]["journey_sort"]["launches"] == 3 * 4 and st["stages"]["journeys"]["launches"] == 3
     assert st["graph_replays"] == 2  # the first run of the shape is eager and captured
 
 

@@ -139,10 +139,11 @@ SORT_EDGES = [512, 513, 2048, 2049, 4096, 4097, 6143, 8192, 8193, 16384, 30001]
 
 @pytest.mark.parametrize("dup_frac", [0.01, 0.6])
 def test_journey_sort_size_classes(orc, dup_frac):
-    """The batch sort takes each journey by size class: up to 512, 4096 and 8192 points with the
-    timestamps held in shared memory, larger ones through global scratch; journeys on either side
-    of every class edge, and at dup_frac 0.6 with time buckets crowded past the staged sort's
-    limit (each class then falls back to the general sort)."""
+    """The batch path takes each journey by size class: up to 512, 4096 and 8192 points sorted
+    with the timestamps held in shared memory and then walked one warp per journey, larger ones by
+    the fused journey kernel; journeys on either side of every class edge, and at dup_frac 0.6 with
+    time buckets crowded past the staged sort's limit (each class then falls back to the general
+    sort)."""
     cols = synth(SORT_EDGES, seed=31 + int(dup_frac * 10), dup_frac=dup_frac)
     compare(run_gpu(cols), orc.run(cols))
 
@@ -254,8 +255,10 @@ def test_stats_count_launches(small_day):
         p.run(t, to_host=False)
         s = p.stats()
     assert s["total_launches"] > 10
-    # the journey sort: the size-class bounds, then one persistent launch per size class
-    assert s["stages"]["journey_sort"]["launches"] == 5 and s["stages"]["journey_sort"]["ms"] > 0
+    # journeys above 8192 points: the fused journey kernel; the rest: the size-class bounds and one
+    # persistent sort launch per size class, then the walk
+    assert s["stages"]["journeys"]["launches"] == 1
+    assert s["stages"]["journey_sort"]["launches"] == 4 and s["stages"]["journey_sort"]["ms"] > 0
     assert s["stages"]["journey_walk"]["launches"] == 1 and s["stages"]["journey_walk"]["ms"] > 0
 
 
