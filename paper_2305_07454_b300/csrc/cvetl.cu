@@ -1119,11 +1119,15 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
 #undef JCLS
     LAUNCH_CHECK();
     // the walk: a persistent grid of warps taking the rest of the list longest first
-    static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, 0);
-    static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, 0);
-    if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<(uint32_t)(sms * occ32), kWalkBlock, 0, c->st>>>(
+    // (the grid's threshold tables in shared memory when they fit)
+    const size_t wsm = walk_thr_shared(c->gp.n_rows, c->gp.n_cols, c->bt.n_inst)
+                           ? (size_t)(c->gp.n_rows + c->gp.n_cols + 2) * sizeof(unsigned long long)
+                           : 0;
+    static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, kWalkThrMax * 8);
+    static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, kWalkThrMax * 8);
+    if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<(uint32_t)(sms * occ32), kWalkBlock, wsm, c->st>>>(
                                         srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
-    else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, 0, c->st>>>(
+    else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, wsm, c->st>>>(
                                      srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
     LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)

@@ -533,10 +533,50 @@ struct Fp64Form {
                                                     double lo2, const Cos64& c2, const GridParams& g) {
     return haversine64(la1, lo1, c1, la2, lo2, c2, g);
   }
+  // A lane's distance sum in 128-bit fixed point (units of 2^-64 m), off the binary64 pipe: each
+  // distance is truncated to a multiple of 2^-64 m (under 5.5e-20 m lost per point) and the sums
+  // are exact, so they do not depend on the order of their terms. Distances are non-negative and
+  // below 2^63 m.
   struct Acc {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double d) { s += d; }
-    __device__ __forceinline__ double value() const { return s; }
+    unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(double d) {
+      const unsigned long long b = dbits(d);
+      const int e = (int)((b >> 52) & 0x7FFull);
+      const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = e - 1011;  // d * 2^64 = m * 2^sh
+      unsigned long long vlo, vhi;
+      if (sh > 0 && sh < 64) {  // 2^-11 m <= d < 2^52 m
+        vhi = m >> (64 - sh);
+        vlo = m << sh;
+      } else if (e == 0 || sh <= -64) {  // zero, or below 2^-64 m
+        vhi = 0;
+        vlo = 0;
+      } else if (sh <= 0) {
+        vhi = 0;
+        vlo = m >> (-sh);
+      } else {
+        vhi = m << min(sh - 64, 10);
+        vlo = 0;
+      }
+      add_fixed(vlo, vhi);
+    }
+    __device__ __forceinline__ void add_fixed(unsigned long long vlo, unsigned long long vhi) {
+      const unsigned long long nlo = lo + vlo;
+      hi += vhi + (nlo < lo ? 1ull : 0ull);
+      lo = nlo;
+    }
+    // hi + lo 2^-64, within one unit in the last place
+    __device__ __forceinline__ double value() const {
+      return (double)hi + __ull2double_rn(lo) * 5.421010862427522e-20;
+    }
+    // the warp's total (valid in lane 0): the lanes' sums added exactly, then rounded
+    __device__ __forceinline__ double warp_total() const {
+      Acc a = *this;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        a.add_fixed(__shfl_down_sync(0xffffffffu, a.lo, o), __shfl_down_sync(0xffffffffu, a.hi, o));
+      return a.value();
+    }
   };
 };
 
@@ -561,6 +601,8 @@ struct Fp32Form {
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float d) { fsum_add(s, c, d); }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    // the warp's total (valid in lane 0), by a fixed shuffle tree
+    __device__ __forceinline__ double warp_total() const { return warp_sum(value()); }
   };
 };
 
@@ -1160,6 +1202,12 @@ __device__ __forceinline__ void ld_rec(const Rec* p, unsigned long long& a, unsi
                                        unsigned long long& c, unsigned long long& d) {
   asm("ld.global.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
+// The same, for records read once (the walk): no L1 allocation, so the stream of records does
+// not evict the grid tables and cosine entries every point looks up.
+__device__ __forceinline__ void ld_rec_once(const Rec* p, unsigned long long& a, unsigned long long& b,
+                                            unsigned long long& c, unsigned long long& d) {
+  asm("ld.global.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
 __device__ __forceinline__ void st_rec(Rec* p, unsigned long long a, unsigned long long b, unsigned long long c,
                                        unsigned long long d) {
   asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
@@ -1467,7 +1515,8 @@ template <class Form>
 __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__ S, int n, uint32_t off,
                                              const GridParams& g, const Batch& bt, const JourneyOut& o,
                                              DevState* st, RunSlot* rbuf, uint32_t& nbuf,
-                                             unsigned long long& n_dup, unsigned long long& n_off) {
+                                             unsigned long long& n_dup, unsigned long long& n_off,
+                                             const unsigned long long* sthr) {
   const int lane = threadIdx.x & 31;
   const BatchInst* bi = bt.n_inst ? bt.inst + inst_of_row(bt, S[0].idx) : nullptr;
   typename Form::Acc dist;
@@ -1486,12 +1535,12 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
   RunAgg la = agg_empty();
   // records one iteration ahead
   unsigned long long na = 0, nb = 0, nc = 0, nd = 0;
-  if (lane < n) ld_rec(S + lane, na, nb, nc, nd);
+  if (lane < n) ld_rec_once(S + lane, na, nb, nc, nd);
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
     const bool valid = k < n;
     const unsigned long long ra = na, rb = nb, rc = nc, rd = nd;
-    if (k + 32 < n) ld_rec(S + k + 32, na, nb, nc, nd);
+    if (k + 32 < n) ld_rec_once(S + k + 32, na, nb, nc, nd);
     const int64_t ts = (int64_t)ra;
     const double lat = dfrom(rb), lon = dfrom(rc);
     const float spd = __uint_as_float((uint32_t)rd);
@@ -1500,7 +1549,7 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
     uint32_t key = kKeyInvalid;
     if (valid) {
       ccur = Form::cosine(lat, g);
-      key = point_key(lat, lon, ts, g, bi);
+      key = sthr ? cell_key<true>(lat, lon, ts, g, sthr, sthr + g.n_rows + 1) : point_key(lat, lon, ts, g, bi);
     }
     // predecessor: the previous lane's point, or the carried one
     int64_t p_ts = (int64_t)__shfl_up_sync(0xffffffffu, (unsigned long long)ts, 1);
@@ -1610,7 +1659,7 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
     if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r);
   }
   // journey sums: each lane's own sum, then a fixed shuffle tree
-  const double sd = warp_sum(dist.value());
+  const double sd = dist.warp_total();
   const long long sw = warp_sum(dwell);
   const uint32_t sdup = warp_sum(dup), soff = warp_sum(offg);
   if (lane == 0) {
@@ -1623,16 +1672,35 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
   }
 }
 
+// Grid threshold tables of up to this many entries (both axes) are copied into the walk's
+// shared memory (16 KB), single-instance runs only.
+constexpr int kWalkThrMax = 2048;
+// resident walk blocks per SM (the register budget per thread follows)
+template <class Form> struct WalkMinBlocks { static constexpr int value = 8; };
+template <> struct WalkMinBlocks<Fp64Form> { static constexpr int value = 7; };
+__host__ __device__ constexpr bool walk_thr_shared(int n_rows, int n_cols, int n_inst) {
+  return n_inst == 0 && n_rows + n_cols + 2 <= kWalkThrMax;
+}
+
 // One warp per journey, journeys taken longest first from the work list (from position *wbeg
-// on, or all of it) through the work counter; a persistent grid.
+// on, or all of it) through the work counter; a persistent grid. The dynamic shared memory
+// holds the grid's threshold tables when walk_thr_shared (8 bytes per entry), else nothing.
 template <class Form>
-__global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __restrict__ srec,
+__global__ void __launch_bounds__(kWalkBlock, WalkMinBlocks<Form>::value) k_journey_walk(const Rec* __restrict__ srec,
                                                             const uint32_t* __restrict__ jn,
                                                             const uint32_t* __restrict__ joff, uint32_t J,
                                                             GridParams g, Batch bt, JourneyOut o, DevState* st,
                                                             const uint32_t* __restrict__ order, uint32_t* work,
                                                             const uint32_t* __restrict__ wbeg) {
   __shared__ RunSlot s_runs[kWalkBlock / 32][kWalkRunCap];
+  extern __shared__ unsigned long long s_thr[];
+  const unsigned long long* sthr = nullptr;
+  if (walk_thr_shared(g.n_rows, g.n_cols, bt.n_inst)) {
+    for (int i = threadIdx.x; i <= g.n_rows; i += kWalkBlock) s_thr[i] = g.row_thr[i];
+    for (int i = threadIdx.x; i <= g.n_cols; i += kWalkBlock) s_thr[g.n_rows + 1 + i] = g.col_thr[i];
+    __syncthreads();
+    sthr = s_thr;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RunSlot* rbuf = s_runs[warp];
   uint32_t nbuf = 0;
@@ -1645,7 +1713,7 @@ __global__ void __launch_bounds__(kWalkBlock, 6) k_journey_walk(const Rec* __res
     if (w >= J) break;
     const uint32_t j = order ? order[w] : w;
     const uint32_t off = joff[j];
-    walk_journey<Form>(j, srec + off, (int)jn[j], off, g, bt, o, st, rbuf, nbuf, n_dup, n_off);
+    walk_journey<Form>(j, srec + off, (int)jn[j], off, g, bt, o, st, rbuf, nbuf, n_dup, n_off, sthr);
   }
   walk_flush(rbuf, nbuf, o, st);
   if (lane == 0) {

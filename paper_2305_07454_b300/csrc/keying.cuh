@@ -45,25 +45,33 @@ __device__ __forceinline__ float leading_f32(double x) {
   return __int_as_float((int)(sign | ((uint32_t)(e - 1023 + 127) << 23) | mant));
 }
 
+// Threshold i of a table in global memory (read-only path) or in shared memory (kShared).
+template <bool kShared>
+__device__ __forceinline__ unsigned long long thr_at(const unsigned long long* __restrict__ thr, int i) {
+  if constexpr (kShared) return thr[i];
+  else return __ldg(thr + i);
+}
+
 // n >= 1. The cell is the r with thr[r] <= u < thr[r + 1]; both bounds of the estimate are
 // loaded together, and a step past either end of the table means off the grid.
+template <bool kShared = false>
 __device__ __forceinline__ int grid_index(double x, const unsigned long long* __restrict__ thr,
                                           int n, float xmin_f, float inv_f) {
   const unsigned long long u = ord_f64(x);
   int r = __float2int_rd((leading_f32(x) - xmin_f) * inv_f);
   r = max(0, min(n - 1, r));
-  unsigned long long lo = __ldg(&thr[r]), hi = __ldg(&thr[r + 1]);
+  unsigned long long lo = thr_at<kShared>(thr, r), hi = thr_at<kShared>(thr, r + 1);
   while (u < lo) {
     if (r == 0) return -1;
     --r;
     hi = lo;
-    lo = __ldg(&thr[r]);
+    lo = thr_at<kShared>(thr, r);
   }
   while (u >= hi) {
     if (r == n - 1) return -1;
     ++r;
     lo = hi;
-    hi = __ldg(&thr[r + 1]);
+    hi = thr_at<kShared>(thr, r + 1);
   }
   return r;
 }
@@ -84,9 +92,14 @@ __device__ __forceinline__ int time_bin(int64_t ts, const GridParams& g) {
   return (int)bin_of(off, g);
 }
 
-__device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts, const GridParams& g) {
-  int r = grid_index(lat, g.row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
-  int c = grid_index(lon, g.col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
+// The key on the grid of g, with its threshold tables at row_thr and col_thr (g's own, or a
+// copy of them in shared memory with kShared).
+template <bool kShared = false>
+__device__ __forceinline__ uint32_t cell_key(double lat, double lon, int64_t ts, const GridParams& g,
+                                             const unsigned long long* __restrict__ row_thr,
+                                             const unsigned long long* __restrict__ col_thr) {
+  int r = grid_index<kShared>(lat, row_thr, g.n_rows, g.lat_min_f, g.inv_cell_f);
+  int c = grid_index<kShared>(lon, col_thr, g.n_cols, g.lon_min_f, g.inv_cell_f);
   int b = time_bin(ts, g);
   if (r < 0 || c < 0 || b < 0) return kKeyInvalid;
   return ((uint32_t)b * (uint32_t)g.n_rows + (uint32_t)r) * (uint32_t)g.n_cols + (uint32_t)c;
@@ -162,7 +175,7 @@ __device__ __forceinline__ uint32_t batch_cell_key(double lat, double lon, int64
 // instance *bi.
 __device__ __forceinline__ uint32_t point_key(double lat, double lon, int64_t ts, const GridParams& g,
                                               const BatchInst* bi) {
-  return bi ? batch_cell_key(lat, lon, ts, g, *bi) : cell_key(lat, lon, ts, g);
+  return bi ? batch_cell_key(lat, lon, ts, g, *bi) : cell_key(lat, lon, ts, g, g.row_thr, g.col_thr);
 }
 
 }  // namespace cvetl
