@@ -1036,8 +1036,8 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   Elem *scrA, *scrB;
   ENSURE("scr.a", nv, &scrA);
   ENSURE("scr.b", nv, &scrB);
-  Rec* srec;
-  ENSURE("rec.sorted", nv, &srec);
+  uint16_t* spos;  // each journey's bucket positions in (timestamp, row) order (journeys up to 8192 points)
+  ENSURE("rec.order", nv, &spos);
   JourneyOut& o = c->jo;
   ENSURE("out.j_n", (size_t)J, &o.n);
   ENSURE("out.j_off", (size_t)J, &o.off);
@@ -1112,7 +1112,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     else LAUNCH(ST_JOURNEYS, (FUSED(Fp64Form, occ_f64)));
 #undef FUSED
 #define JCLS(NT, CAP, SM, K) k_journey_sort_class<NT, CAP><<<(uint32_t)(sms * occ[K]), NT, SM, c->st>>>( \
-    rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, srec, c->dstate)
+    rec, jn, joff, order, bounds, K, cwork + K, scrA, scrB, spos, c->dstate)
     LAUNCH(ST_JOURNEY_SORT, (JCLS(kSortBlockB, 8192, kSortSmemB, 1)));
     LAUNCH(ST_JOURNEY_SORT, (JCLS(kSortBlockC, 4096, kSortSmemC, 2)));
     LAUNCH(ST_JOURNEY_SORT, (JCLS(kJSmallBlock, 512, kSortSmemD, 3)));
@@ -1126,9 +1126,9 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     static const int occ32 = occupancy(k_journey_walk<Fp32Form>, kWalkBlock, kWalkThrMax * 8);
     static const int occ64 = occupancy(k_journey_walk<Fp64Form>, kWalkBlock, kWalkThrMax * 8);
     if (f32) LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp32Form><<<(uint32_t)(sms * occ32), kWalkBlock, wsm, c->st>>>(
-                                        srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
+                                        rec, spos, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
     else LAUNCH(ST_JOURNEY_WALK, (k_journey_walk<Fp64Form><<<(uint32_t)(sms * occ64), kWalkBlock, wsm, c->st>>>(
-                                     srec, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
+                                     rec, spos, jn, joff, J, c->gp, c->bt, o, c->dstate, order, work + 1, bounds + 1)));
     LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)
       LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(

@@ -1304,8 +1304,11 @@ __device__ __forceinline__ void block_range(unsigned long long lo, unsigned long
   __syncthreads();
 }
 
+// The staged order of the journey's bucket R[0..n) into the u16 positions P (at 8 * CAP bytes
+// into the dynamic shared memory, valid until the CTA's next use of it); false when a time
+// bucket is crowded. Every thread of the CTA calls it; ends with a barrier.
 template <int NT, int CAP>
-__device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __restrict__ out) {
+__device__ bool staged_journey_order(const Rec* __restrict__ R, int n) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* T = reinterpret_cast<unsigned long long*>(smem_raw);
   uint16_t* P = reinterpret_cast<uint16_t*>(smem_raw + 8 * CAP);
@@ -1329,15 +1332,12 @@ __device__ bool journey_sort_staged(const Rec* __restrict__ R, int n, Rec* __res
   }
   __syncthreads();
   block_range(lo, hi, &s_tmin, &s_tmax);
-  if (!staged_order<NT>(T, n, s_tmin, s_tmax, P, cnt, s_scan, &s_flag, [R](int k) { return R[k].idx; }))
-    return false;
-  // the records in order
-  for (int k = tid; k < n; k += NT) {
-    unsigned long long a, b, c, d;
-    ld_rec(R + P[k], a, b, c, d);
-    st_rec(out + k, a, b, c, d);
-  }
-  return true;
+  return staged_order<NT>(T, n, s_tmin, s_tmax, P, cnt, s_scan, &s_flag, [R](int k) { return R[k].idx; });
+}
+template <int CAP>
+__device__ __forceinline__ const uint16_t* staged_positions() {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  return reinterpret_cast<const uint16_t*>(smem_raw + 8 * CAP);
 }
 
 // Journey size classes over the work list (sizes non-increasing along it): bounds[c] is the
@@ -1373,7 +1373,7 @@ __global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journe
                                                            const uint32_t* __restrict__ order,
                                                            const uint32_t* __restrict__ bounds, int cls,
                                                            uint32_t* work, Elem* scrA, Elem* scrB,
-                                                           Rec* __restrict__ srec, DevState* st) {
+                                                           uint16_t* __restrict__ spos, DevState* st) {
   __shared__ uint32_t s_w;
   const uint32_t w0 = bounds[cls], w1 = bounds[cls + 1];
   for (;;) {
@@ -1386,13 +1386,12 @@ __global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journe
     const int n = (int)jn[j];
     const uint32_t off = joff[j];
     const Rec* R = rec + off;
-    if (!journey_sort_staged<NT, CAP>(R, n, srec + off)) {
+    if (staged_journey_order<NT, CAP>(R, n)) {
+      const uint16_t* P = staged_positions<CAP>();
+      for (int k = threadIdx.x; k < n; k += NT) spos[off + k] = P[k];
+    } else {
       const JSorted srt = journey_sort<NT>(R, n, off, scrA, scrB, st);
-      for (int k = threadIdx.x; k < n; k += NT) {
-        unsigned long long a, b, c, d;
-        ld_rec(R + srt.pos(k), a, b, c, d);
-        st_rec(srec + off + k, a, b, c, d);
-      }
+      for (int k = threadIdx.x; k < n; k += NT) spos[off + k] = (uint16_t)srt.pos(k);
     }
     __syncthreads();
   }
@@ -1512,7 +1511,8 @@ __device__ __forceinline__ void walk_put(RunSlot* buf, uint32_t& nbuf, const Jou
 // sums, when a run closes for the run aggregates: a run's points in one lane accumulate in that
 // lane until the warp reduces the run).
 template <class Form>
-__device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__ S, int n, uint32_t off,
+__device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__ S, const uint16_t* __restrict__ P,
+                                             int n, uint32_t off,
                                              const GridParams& g, const Batch& bt, const JourneyOut& o,
                                              DevState* st, RunSlot* rbuf, uint32_t& nbuf,
                                              unsigned long long& n_dup, unsigned long long& n_off,
@@ -1533,14 +1533,16 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
   // lane's share of its points
   uint32_t o_key = kKeyInvalid, o_start = 0;
   RunAgg la = agg_empty();
-  // records one iteration ahead
+  // records one iteration ahead, their bucket positions two
   unsigned long long na = 0, nb = 0, nc = 0, nd = 0;
-  if (lane < n) ld_rec_once(S + lane, na, nb, nc, nd);
+  if (lane < n) ld_rec_once(S + P[lane], na, nb, nc, nd);
+  uint32_t pn = (32 + lane < n) ? P[32 + lane] : 0u;
   for (int base = 0; base < n; base += 32) {
     const int k = base + lane;
     const bool valid = k < n;
     const unsigned long long ra = na, rb = nb, rc = nc, rd = nd;
-    if (k + 32 < n) ld_rec_once(S + k + 32, na, nb, nc, nd);
+    if (k + 32 < n) ld_rec_once(S + pn, na, nb, nc, nd);
+    if (k + 64 < n) pn = P[k + 64];
     const int64_t ts = (int64_t)ra;
     const double lat = dfrom(rb), lon = dfrom(rc);
     const float spd = __uint_as_float((uint32_t)rd);
@@ -1686,7 +1688,8 @@ __host__ __device__ constexpr bool walk_thr_shared(int n_rows, int n_cols, int n
 // on, or all of it) through the work counter; a persistent grid. The dynamic shared memory
 // holds the grid's threshold tables when walk_thr_shared (8 bytes per entry), else nothing.
 template <class Form>
-__global__ void __launch_bounds__(kWalkBlock, WalkMinBlocks<Form>::value) k_journey_walk(const Rec* __restrict__ srec,
+__global__ void __launch_bounds__(kWalkBlock, WalkMinBlocks<Form>::value) k_journey_walk(const Rec* __restrict__ rec,
+                                                            const uint16_t* __restrict__ spos,
                                                             const uint32_t* __restrict__ jn,
                                                             const uint32_t* __restrict__ joff, uint32_t J,
                                                             GridParams g, Batch bt, JourneyOut o, DevState* st,
@@ -1713,7 +1716,7 @@ __global__ void __launch_bounds__(kWalkBlock, WalkMinBlocks<Form>::value) k_jour
     if (w >= J) break;
     const uint32_t j = order ? order[w] : w;
     const uint32_t off = joff[j];
-    walk_journey<Form>(j, srec + off, (int)jn[j], off, g, bt, o, st, rbuf, nbuf, n_dup, n_off, sthr);
+    walk_journey<Form>(j, rec + off, spos + off, (int)jn[j], off, g, bt, o, st, rbuf, nbuf, n_dup, n_off, sthr);
   }
   walk_flush(rbuf, nbuf, o, st);
   if (lane == 0) {
