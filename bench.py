@@ -140,26 +140,34 @@ def make_workload(name: str, seed: int, pinned: bool):
     return host, n, int(p.n_journeys)
 
 
+FUSED_MIN_POINTS = 8193  # journeys of this many points and more take the fused journey kernel
+
+
 def algorithmic_bytes(stage: str, c: dict) -> float:
-    """Bytes a stage must move per launch, from the counters."""
+    """Bytes a stage must move per launch, from the counters. The journey stage splits by size:
+    journeys above 8192 points (n_fused points, j_fused journeys) in the fused kernel, the
+    others (n_walk points) ordered by the class sort and walked."""
     nin, nv, J, R = c["n_in"], c["n_valid"], c["n_journeys"], c["n_runs"]
+    nf, jf = c.get("n_fused", 0), c.get("j_fused", 0)
+    nw = nv - nf
     return {
         "hash_count": 28.0 * nin + 4.0 * nin,           # jid, lat, lon, speed read; row slot written
         "scatter": 32.0 * nin + 32.0 * nv,              # ts, lat, lon, speed, slot read; records written
-        "journeys": 32.0 * nv + 28.0 * R + 96.0 * J,    # records read; runs and journey rows written
-        "journey_sort": 64.0 * nv,                      # records read, written in (time, row) order
-        "journey_walk": 32.0 * nv + 28.0 * R + 96.0 * J,  # ordered records read; runs and journey rows written
+        "journeys": 32.0 * nf + 96.0 * jf,              # records read; journey rows written (its runs: below)
+        "journey_sort": 10.0 * nw,                      # timestamps read, u16 ordered positions written
+        "journey_walk": 34.0 * nw + 28.0 * R + 96.0 * (J - jf),  # records and positions read; runs, journeys written
         "cell_write": 28.0 * R + 44.0 * c["n_cells"],
         "csv_count": float(c.get("csv_bytes", 0)),                  # the text read
         "csv_parse": float(c.get("csv_bytes", 0)) + 40.0 * nin,    # the text read; six columns written
     }.get(stage, 0.0)
 
 
-# binary64 operations per point of the journey kernel: the cosine of the latitude (2: offset from
-# the table point, one fma), the distance (10: two differences, two squares, the cosine product,
-# one fma, the scaled square root and its residual, the scaling, the final fma), the journey
-# distance sum (1) and the implied speed's rounding to float32 (1)
-FP64_OPS_PER_POINT = 14.0
+# binary64 operations per point of the journey kernels: the cosine of the latitude (2: offset from
+# the table point, one fma) and the distance (10: two differences, two squares, the cosine
+# product, one fma, the scaled square root and its residual, the scaling, the final fma); the
+# journey distance is summed in integer fixed point and the implied speed rounded to float32 by
+# integer operations, off the binary64 pipe
+FP64_OPS_PER_POINT = 12.0
 SMS = 148
 
 # Bytes per record the method must move (the algorithmic floor: read the needed input once,
@@ -211,24 +219,24 @@ def fp64_probe(stream, reps=3):
 # scaled by records to the workload (the full day is too large to capture under the profiler's
 # size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "hash_count": 31.157, "collect_slots": 0.144, "radix_histogram": 0.225, "radix_onesweep": 2.535,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.045, "journey_sort": 61.721,
-    "journey_walk": 32.672, "cell_heads": 0.214, "cell_write": 1.075,
+    "hash_count": 31.155, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.536,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.049, "journey_sort": 29.76,
+    "journeys": 5.279, "journey_walk": 86.081, "cell_heads": 0.214, "cell_write": 1.074,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.656, "csv_parse": 96.275,
+    "csv_count": 58.657, "csv_parse": 96.28,
 }
 TRAFFIC_PER_RECORD_FP32 = {
-    "hash_count": 31.153, "collect_slots": 0.144, "radix_histogram": 0.225, "radix_onesweep": 2.535,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.045, "journeys": 60.455,
-    "cell_heads": 0.214, "cell_write": 1.075,
+    "hash_count": 31.151, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.535,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 61.033, "journey_sort": 29.766,
+    "journeys": 4.32, "journey_walk": 86.566, "cell_heads": 0.214, "cell_write": 1.073,
 }
 
 
 def unit_launches(stage, launches, steps):
     """Number of passes over the stage's algorithmic work in `launches`. Every stage's launch is
-    one pass, except the journey sort (and the fused journey kernel of stream windows): its two
-    kernel shapes (journeys of up to 512 points in 64-thread CTAs, the rest in 256-thread CTAs)
-    share one pass over all points per step, so its time per pass is the sum of both launches."""
+    one pass, except the journey sort (the class bounds and one launch per size class share one
+    pass over the classes' points per step) and the fused journey kernel of stream windows (its
+    two shapes share one pass), whose time per pass is the sum of their launches."""
     if stage in ("journeys", "journey_sort"):
         return max(1, steps)
     return max(1, launches)
@@ -322,7 +330,8 @@ def _roofline_entry(top, stages, counters, steps, precision, probe):
     # per launch (a pass over the stage's work): the step's traffic over the passes per step
     traffic = tpr * counters["n_valid"] / (unit_launches(top, stages[top]["launches"], steps) / steps) if tpr else None
     if top in ("journeys", "journey_walk") and precision == "fp64" and probe:
-        ops = FP64_OPS_PER_POINT * counters["n_valid"]
+        nf = counters.get("n_fused", 0)  # the points of the kernel's own journeys
+        ops = FP64_OPS_PER_POINT * (nf if top == "journeys" else counters["n_valid"] - nf)
         achieved = ops / (avg_ms / 1e3) / 1e9
         return {"bound": "alu", "kernel": top, "achieved": achieved, "peak": probe["peak_gops"],
                 "unit": "G binary64 ops/s",
@@ -339,11 +348,15 @@ def _roofline_entry(top, stages, counters, steps, precision, probe):
             "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms, "traffic": traffic}
 
 
-def _counters(t, csv_host=None):
+def _counters(t, csv_host=None, pipe=None):
     c = {k: int(getattr(t, k)) for k in ("n_in", "n_malformed", "n_valid", "n_out_of_grid", "n_dup", "n_runs")}
     c.update(n_journeys=int(t.n_journeys), n_cells=int(t.n_cells))
     if csv_host is not None:
         c["csv_bytes"] = int(csv_host.numel())
+    if pipe is not None:  # the journey stage's split by size (from the journey table)
+        jn = pipe.results(to_host=True)["journeys"]["n"]
+        big = jn >= FUSED_MIN_POINTS
+        c.update(n_fused=int(jn[big].sum()), j_fused=int(big.sum()))
     return c
 
 
@@ -392,7 +405,7 @@ def run_ours(args):
     tuning["seconds"] = time.perf_counter() - t_tune
     ms_total, clocks = _day_steps(P, pipe, extract_dev, args.steps, args.warmup, barrier, local)
     stats = _stage_stats(P, stream, prec, tuning, extract_dev, args.steps)
-    counters = _counters(pipe.tables(), csv_host)
+    counters = _counters(pipe.tables(), csv_host, pipe)
     (ms_total,), (n_job,) = over_ranks([ms_total], [n], world, dev)
     ms_step = ms_total / args.steps
     value = n_job * args.steps / (ms_total / 1e3)
@@ -541,7 +554,7 @@ def _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job, c
     tune32 = p32.autotune(reps=2) if args.autotune else {**p32.tuning, "ms": None}
     ms32, clk32 = _day_steps(P, p32, extract_dev, args.steps, args.warmup, barrier, local)
     st32 = _stage_stats(P, stream, P.FP32, tune32, extract_dev, args.steps)["stages"]
-    c32 = _counters(p32.tables(), csv_host)
+    c32 = _counters(p32.tables(), csv_host, p32)
     r32 = p32.results(to_host=True)
     p32.close()
     (ms32,), _ = over_ranks([ms32], [0], world, dev)
@@ -574,7 +587,7 @@ def _csv_day(P, host, stream, args, barrier, local, world, dev, rank):
     tune = pc.autotune(reps=2) if args.autotune else {**pc.tuning, "ms": None}
     ms, clk = _day_steps(P, pc, extract, args.steps, args.warmup, barrier, local)
     st = _stage_stats(P, stream, P.FP64, tune, extract, args.steps)["stages"]
-    c = _counters(pc.tables())
+    c = _counters(pc.tables(), None, pc)
     c["csv_bytes"] = int(d_csv.numel())
     pc.close()
     del d_csv
@@ -786,7 +799,7 @@ def week_leg(args, scale, local, rank, steps=None, warmup=None):
         pe.load()
         stats = pe.stats()
         res = pe.results(to_host=True)
-        counters = _counters(pe.tables())
+        counters = _counters(pe.tables(), None, pe)
     errors = _form_errors(res, ref) if ref is not None else None
     del res, ref
     torch.cuda.empty_cache()

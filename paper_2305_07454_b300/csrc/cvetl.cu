@@ -1031,8 +1031,8 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     LAUNCH_CHECK();
   }
 
-  // 4. per-journey sort into a second record array, then the walk: kinematics, keys, journey
-  // table, cell runs
+  // 4. per-journey order (bucket positions by (timestamp, row)), then the walk: kinematics,
+  // keys, journey table, cell runs
   Elem *scrA, *scrB;
   ENSURE("scr.a", nv, &scrA);
   ENSURE("scr.b", nv, &scrB);
@@ -1092,9 +1092,9 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = c->cfg.precision == CVETL_FP32;
     // Journeys above 8192 points (the list's first) take the fused journey kernel (sort and walk
-    // in one CTA; their sort goes through global scratch either way); the others are sorted by
-    // size class (each class a persistent grid over its part of the list) into a second record
-    // array, whose ordered records the walk then reads.
+    // in one CTA; their sort goes through global scratch either way); the others are ordered by
+    // size class (each class a persistent grid over its part of the list), and the walk reads
+    // their bucketed records through the ordered positions.
     uint32_t *bounds, *cwork;
     ENSURE("j.bounds", 5, &bounds);
     ENSURE("j.cwork", 4, &cwork);

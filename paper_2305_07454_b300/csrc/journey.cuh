@@ -192,10 +192,11 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem*
 //   ds = p/2 + 3p^2/8,  dr = (eC - q)/2 + h/6 + 3h^2/40   (|ds| < 3e-7, |dr| < 2e-8).
 // Every term above 2^-22 relative (differences, squares, the cosine product, m, s0, the
 // residual r, the scaling and the final fma) is binary64; delta, a sum of small corrections, is
-// float32, which puts at most ~1e-14 relative error on d. That is 14 binary64 operations per
-// point (cosine 2, distance 10, journey sum 1, implied speed 1) where the direct evaluation
-// takes about 30 on a part that runs 2 per clock per SM. Larger steps take the general formula
-// through the CUDA math library.
+// float32, which puts at most ~1e-14 relative error on d. That is 12 binary64 operations per
+// point (cosine 2, distance 10; the journey sum is kept in integer fixed point and the implied
+// speed rounded to float32 by integer operations) where the direct evaluation takes about 30 on
+// a part that runs about 1.7 per clock per SM. Larger steps take the general formula through
+// the CUDA math library.
 constexpr double kRad = 0.017453292519943295;  // pi / 180
 constexpr float kRadF = 0.017453292519943295f;
 constexpr float kK2F = 7.615435494667714e-5f;  // (pi/360)^2
@@ -1190,13 +1191,12 @@ __global__ void __launch_bounds__(NT, JShape<NT>::kMinBlocks) k_journeys(
 }
 
 // ---------------------------------------------------------------- batch path: sort, then walk
-// The binary64 form's batch path orders each journey's bucket into a second record array in
-// (timestamp, row) order (k_journey_sort_class, by journey size class), then walks the ordered
-// records with one warp per journey (k_journey_walk): the walk, bound by the binary64 pipe, runs
-// at full occupancy apart from the latency-bound sort. The sort keeps the shared-memory / L2
-// scheme above; the walk reads each record once, coalesced, with every lane on its own point.
-// (The float32 form's walk is short enough that the fused kernel above, without the ordered
-// copy, is faster.)
+// Journeys of up to 8192 points: the batch path orders each journey's bucket by (timestamp,
+// row) (k_journey_sort_class, one persistent grid per size class) and writes only the order,
+// the bucket positions as u16; one warp per journey then walks the bucketed records through
+// those positions (k_journey_walk), at the occupancy that suits the walk rather than the sort.
+// Writing the order instead of a second, ordered record array halves the sort's time; the walk
+// pays with gathered reads (each lane its own 32-byte record) instead of coalesced ones.
 
 __device__ __forceinline__ void ld_rec(const Rec* p, unsigned long long& a, unsigned long long& b,
                                        unsigned long long& c, unsigned long long& d) {

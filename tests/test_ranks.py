@@ -62,14 +62,21 @@ def test_reference_arm_works_on_rank_zero_only(monkeypatch, capsys):
 
 
 def test_journey_stage_is_one_pass_per_step():
-    """The journey stage launches its two CTA shapes once each per step over one pass of the
-    points: its time per pass is the stage time per step, and its algorithmic bytes count once
-    per step; every other stage's launch is a pass of its own."""
+    """The journey sort launches its class bounds and one kernel per size class per step over one
+    pass of the classes' points: its time per pass is the stage time per step, and its
+    algorithmic bytes count once per step; every other stage's launch is a pass of its own. The
+    journey stage's bytes split by size between the fused kernel (journeys above 8192 points)
+    and the sort and walk of the others."""
     assert bench.unit_launches("journey_sort", 20, 10) == 10
     assert bench.unit_launches("journey_sort", 10, 10) == 10
     assert bench.unit_launches("journeys", 20, 10) == 10
     assert bench.unit_launches("journey_walk", 10, 10) == 10
     assert bench.unit_launches("radix_onesweep", 160, 10) == 160
     assert bench.unit_launches("scatter", 0, 10) == 1
-    c = {"n_in": 100, "n_valid": 90, "n_journeys": 3, "n_runs": 7, "n_cells": 5}
-    assert bench.algorithmic_bytes("journeys", c) == 32.0 * 90 + 28.0 * 7 + 96.0 * 3
+    c = {"n_in": 100, "n_valid": 90, "n_journeys": 3, "n_runs": 7, "n_cells": 5, "n_fused": 40, "j_fused": 1}
+    assert bench.algorithmic_bytes("journeys", c) == 32.0 * 40 + 96.0 * 1
+    assert bench.algorithmic_bytes("journey_sort", c) == 10.0 * 50
+    assert bench.algorithmic_bytes("journey_walk", c) == 34.0 * 50 + 28.0 * 7 + 96.0 * 2
+    # without the split every journey is counted as walked
+    c0 = {k: v for k, v in c.items() if k not in ("n_fused", "j_fused")}
+    assert bench.algorithmic_bytes("journey_walk", c0) == 34.0 * 90 + 28.0 * 7 + 96.0 * 3
