@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "CV records/s & % HBM roofline, full-day ETL; p50/p99 window latency"
 UNIT = "records/s"
 COLS = ("jid", "ts", "lat", "lon", "speed")
+L2_BYTES = 126 * 2**20
 BYTES = {"jid": 8, "ts": 8, "lat": 8, "lon": 8, "speed": 4}
 
 
@@ -497,7 +498,8 @@ def run_ours(args):
                                + ("binary columns" if csv_host is None else
                                   f"CSV text ({int(csv_host.numel())} bytes, 0.5% malformed rows)")
                                + ", fully shuffled", "records": n, "journeys": J, "input": args.input, "precision": args.precision,
-                   "l2": "inputs larger than L2 (no flush needed)",
+                   "l2": ("inputs larger than L2 (no flush needed)" if h2d > L2_BYTES else
+                          "inputs smaller than L2, steps back to back without a flush (a parity-size case)"),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    **({"records_all_ranks": n_job} if world > 1 else {})},
         "e2e": {"value": n_job / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
