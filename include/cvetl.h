@@ -250,8 +250,8 @@ typedef struct {
 
 #define CVETL_MAX_INSTANCES 32
 
-/* Extract for a batch (batch-mode context): the instances' rows are concatenated in instance
- * order (all host or all device columns, per on_device), and cvetl_transform / cvetl_load then
+/* Extract for a batch (batch-mode context): the instances' rows are taken in instance order
+ * (all host or all device columns, per on_device), and cvetl_transform / cvetl_load then
  * treat every instance as its own batch in one pass: a journey is (instance, journey id), a
  * point is keyed on its instance's grid and day. The result tables hold the instances one after
  * another: journeys by (instance, id), cells by (instance, key) with each instance's own keys,
@@ -260,7 +260,10 @@ typedef struct {
  * CVETL_EINVAL for n_inst outside [1, CVETL_MAX_INSTANCES], a NULL column, a bad grid, more than
  * CVETL_MAX_RECORDS rows, or keys (sum of n_rows * n_cols * n_bins) reaching 2^32 - 1; the
  * journey ids of a batch must lie within [-2^57, 2^57) (cvetl_transform returns CVETL_EINVAL
- * otherwise). Host columns are copied before the call returns. */
+ * otherwise). Host columns are copied before the call returns; device columns are read in
+ * place through a table of their pointers (not copied), so, as for cvetl_extract, the caller
+ * keeps them alive and unchanged until the work of cvetl_transform (and of cvetl_autotune, which
+ * repeats it) has completed on the stream. */
 cvetl_status cvetl_extract_batch(cvetl_ctx* ctx, const cvetl_instance* inst, int32_t n_inst, int32_t on_device);
 
 /* Slices of a loaded batch, n = n_inst + 1 entries per array (any array may be NULL): the first

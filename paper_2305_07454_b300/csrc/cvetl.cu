@@ -1018,7 +1018,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   if (n) {
     const int U = c->tune.row_unroll, NT = c->tune.row_block;
 #define SCAT(U_, NT_) k_scatter<U_, NT_><<<grid_for((n + U_ - 1) / U_, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
-    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)
+    c->ts, c->lat, c->lon, c->spd, row_slot, n, h, c->bt, rec)
 #define SCAT_NT(U_)                                                    \
     if (NT == 128) LAUNCH(ST_SCATTER, (SCAT(U_, 128)));                \
     else if (NT == 512) LAUNCH(ST_SCATTER, (SCAT(U_, 512)));           \
@@ -1132,7 +1132,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     LAUNCH_CHECK();
     if (o.perm) {  // features over earlier points of a journey (materialised points)
       LAUNCH(ST_POINT_EXTRAS, (k_point_extras<<<grid_for((size_t)J * 32, 256), 256, 0, c->st>>>(
-                              jn, joff, J, c->ts, o.perm, o.d, o.dwell_pt, o.flags, o.stop_ms, o.accel_v)));
+                              jn, joff, J, c->ts, c->bt, o.perm, o.d, o.dwell_pt, o.flags, o.stop_ms, o.accel_v)));
       LAUNCH_CHECK();
     }
   }
@@ -1502,14 +1502,23 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   cudaSetDevice(c->cfg.device);
   c->state = 0;
   const size_t n = (size_t)rows;
-  int64_t *jid, *ts;
-  double *lat, *lon;
-  float* spd;
-  ENSURE("in.jid", n, &jid);
-  ENSURE("in.ts", n, &ts);
-  ENSURE("in.lat", n, &lat);
-  ENSURE("in.lon", n, &lon);
-  ENSURE("in.spd", n, &spd);
+  // Device instances are read in place, through a table of their column pointers (the caller
+  // keeps them unchanged until cvetl_transform returns); host instances are copied into the
+  // context's concatenated columns.
+  const bool in_place = on_device != 0;
+  int64_t *jid = nullptr, *ts = nullptr;
+  double *lat = nullptr, *lon = nullptr;
+  float* spd = nullptr;
+  BatchCols* dcols = nullptr;
+  if (in_place) {
+    ENSURE("batch.cols", (size_t)kMaxInst, &dcols);
+  } else {
+    ENSURE("in.jid", n, &jid);
+    ENSURE("in.ts", n, &ts);
+    ENSURE("in.lat", n, &lat);
+    ENSURE("in.lon", n, &lon);
+    ENSURE("in.spd", n, &spd);
+  }
   // instance table: threshold tables and offsets (kept from the last batch when the instances'
   // grids, days and sizes repeat)
   std::vector<double> key;
@@ -1524,16 +1533,17 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   std::vector<size_t> thr_at(n_inst);
   c->inst_rows.assign(n_inst + 1, 0);
   c->inst_keys.assign(n_inst + 1, 0);
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  std::vector<BatchCols> cols(n_inst);
   for (int i = 0; i < n_inst; ++i) {
     const cvetl_instance& q = inst[i];
     const size_t r0 = (size_t)c->inst_rows[i], m = (size_t)q.n;
-    if (m) {
-      CK(cudaMemcpyAsync(jid + r0, q.jid, m * 8, kind, c->st));
-      CK(cudaMemcpyAsync(ts + r0, q.ts, m * 8, kind, c->st));
-      CK(cudaMemcpyAsync(lat + r0, q.lat, m * 8, kind, c->st));
-      CK(cudaMemcpyAsync(lon + r0, q.lon, m * 8, kind, c->st));
-      CK(cudaMemcpyAsync(spd + r0, q.speed, m * 4, kind, c->st));
+    cols[i] = BatchCols{q.jid, q.ts, q.lat, q.lon, q.speed};
+    if (m && !in_place) {
+      CK(cudaMemcpyAsync(jid + r0, q.jid, m * 8, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(ts + r0, q.ts, m * 8, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(lat + r0, q.lat, m * 8, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(lon + r0, q.lon, m * 8, cudaMemcpyHostToDevice, c->st));
+      CK(cudaMemcpyAsync(spd + r0, q.speed, m * 4, cudaMemcpyHostToDevice, c->st));
     }
     c->inst_rows[i + 1] = (int64_t)(r0 + m);
     c->inst_keys[i + 1] = c->inst_keys[i] + (int64_t)q.n_rows * q.n_cols * c->cfg.n_bins;
@@ -1549,8 +1559,12 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
     bi[i].row_begin = (uint32_t)r0;
     bi[i].key_off = (uint32_t)c->inst_keys[i];
   }
+  // the column table, in stream order before the kernels that read it (pageable source:
+  // staged before the call returns)
+  if (in_place) CK(cudaMemcpyAsync(dcols, cols.data(), cols.size() * sizeof(BatchCols), cudaMemcpyHostToDevice, c->st));
   if (same_tables) {
-    const Batch keep = c->bt;
+    Batch keep = c->bt;
+    keep.cols = dcols;
     c->jid = jid;
     c->ts = ts;
     c->lat = lat;
@@ -1582,6 +1596,7 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   CK(cudaMemcpy(dbi, bi.data(), bi.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
   c->bt.n_inst = n_inst;
   c->bt.inst = dbi;
+  c->bt.cols = dcols;
   c->batch_key = key;
   c->jid = jid;
   c->ts = ts;

@@ -85,10 +85,14 @@ __global__ void __launch_bounds__(NT) k_hash_count(const int64_t* __restrict__ j
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t i = i0 + u * blockDim.x;
-      ok[u] = i < n && row_valid(lat[i], lon[i], spd[i]);
-      id[u] = (i < n) ? (uint64_t)jid[i] : 0;
+      // a batch row's instance; its columns (the concatenated ones, or the instance's own)
+      const int k = (bt.n_inst && i < n) ? inst_of_row(bt, i) : 0;
+      RowCols c;
+      const uint32_t r = row_cols(bt, RowCols{jid, nullptr, lat, lon, spd}, i, k, c);
+      ok[u] = i < n && row_valid(c.lat[r], c.lon[r], c.spd[r]);
+      id[u] = (i < n) ? (uint64_t)c.jid[r] : 0;
       if (i < n && !ok[u]) ++bad;
-      if (ok[u] && bt.n_inst && !composite_id(inst_of_row(bt, i), (int64_t)id[u], &id[u])) {
+      if (ok[u] && bt.n_inst && !composite_id(k, (int64_t)id[u], &id[u])) {
         atomicOr(&st->err, kErrIdRange);
         ok[u] = false;
       }
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const int64_t* __restrict__ ts,
                                                  const double* __restrict__ lon,
                                                  const float* __restrict__ spd,
                                                  const uint32_t* __restrict__ row_slot, uint32_t n,
-                                                 Hash h, Rec* __restrict__ rec) {
+                                                 Hash h, Batch bt, Rec* __restrict__ rec) {
   const uint32_t step = gridDim.x * blockDim.x * U;
   for (uint32_t i0 = blockIdx.x * blockDim.x * U + threadIdx.x; i0 < n; i0 += step) {
     uint32_t slot[U], pos[U];
@@ -220,10 +224,12 @@ __global__ void __launch_bounds__(NT) k_scatter(const int64_t* __restrict__ ts,
     for (int u = 0; u < U; ++u) {
       if (slot[u] == kKeyInvalid) continue;
       const uint32_t i = i0 + u * blockDim.x;
-      const unsigned long long a = (unsigned long long)ts[i];
-      const unsigned long long b = (unsigned long long)__double_as_longlong(lat[i]);
-      const unsigned long long c = (unsigned long long)__double_as_longlong(lon[i]);
-      const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(spd[i])) |
+      RowCols q;
+      const uint32_t r = row_cols(bt, RowCols{nullptr, ts, lat, lon, spd}, i, bt.cols ? inst_of_row(bt, i) : 0, q);
+      const unsigned long long a = (unsigned long long)q.ts[r];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(q.lat[r]);
+      const unsigned long long c = (unsigned long long)__double_as_longlong(q.lon[r]);
+      const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(q.spd[r])) |
                                    ((unsigned long long)i << 32);
       asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + pos[u]), "l"(a), "l"(b),
                    "l"(c), "l"(d)

@@ -1739,7 +1739,7 @@ __global__ void k_size_keys(const uint32_t* __restrict__ jn, uint32_t J, unsigne
 // 32 points at a time, the scan carried from chunk to chunk.
 __global__ void __launch_bounds__(256) k_point_extras(const uint32_t* __restrict__ jn,
                                                       const uint32_t* __restrict__ joff, uint32_t J,
-                                                      const int64_t* __restrict__ ts,
+                                                      const int64_t* __restrict__ ts, Batch bt,
                                                       const uint32_t* __restrict__ perm,
                                                       const double* __restrict__ d,
                                                       const int64_t* __restrict__ dwell,
@@ -1762,7 +1762,7 @@ __global__ void __launch_bounds__(256) k_point_extras(const uint32_t* __restrict
           reset = 0;
         }
         if (k >= 2) {
-          const int64_t t0 = ts[perm[g - 2]], t1 = ts[perm[g - 1]], t2 = ts[perm[g]];
+          const int64_t t0 = row_ts(ts, bt, perm[g - 2]), t1 = row_ts(ts, bt, perm[g - 1]), t2 = row_ts(ts, bt, perm[g]);
           const int64_t dt1 = (int64_t)((unsigned long long)t1 - (unsigned long long)t0);
           const int64_t dt2 = (int64_t)((unsigned long long)t2 - (unsigned long long)t1);
           if (dt1 > 0 && dt2 > 0) {

@@ -125,9 +125,18 @@ struct BatchInst {
   uint32_t key_off;    // first key of the instance in the concatenated key space
 };
 
+// A batch's instance columns read in place (device batches): instance k's own arrays.
+struct BatchCols {
+  const int64_t *jid, *ts;
+  const double *lat, *lon;
+  const float* spd;
+};
+
 struct Batch {
   int n_inst;              // 0: one instance described by GridParams
   const BatchInst* inst;   // n_inst entries, ascending row_begin and key_off
+  const BatchCols* cols;   // n_inst entries when the instances' columns are read in place, else null
+                           // (the batch's rows are then concatenated in the context's columns)
 };
 
 // last instance whose row_begin (or key_off) is <= v
@@ -140,6 +149,35 @@ __device__ __forceinline__ int inst_of_row(const Batch& b, uint32_t row) {
   }
   return lo;
 }
+// The columns batch row i is read from and its index there: the concatenated columns `all`,
+// or its instance's own columns (instance k from inst_of_row).
+struct RowCols {
+  const int64_t *jid, *ts;
+  const double *lat, *lon;
+  const float* spd;
+};
+__device__ __forceinline__ uint32_t row_cols(const Batch& b, const RowCols& all, uint32_t i, int k, RowCols& c) {
+  if (!b.cols) {
+    c = all;
+    return i;
+  }
+  const BatchCols* q = b.cols + k;
+  c.jid = reinterpret_cast<const int64_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q->jid)));
+  c.ts = reinterpret_cast<const int64_t*>(__ldg(reinterpret_cast<const unsigned long long*>(&q->ts)));
+  c.lat = reinterpret_cast<const double*>(__ldg(reinterpret_cast<const unsigned long long*>(&q->lat)));
+  c.lon = reinterpret_cast<const double*>(__ldg(reinterpret_cast<const unsigned long long*>(&q->lon)));
+  c.spd = reinterpret_cast<const float*>(__ldg(reinterpret_cast<const unsigned long long*>(&q->spd)));
+  return i - __ldg(&b.inst[k].row_begin);
+}
+
+// Row i's timestamp (from its instance's own column when the batch is read in place).
+__device__ __forceinline__ int64_t row_ts(const int64_t* __restrict__ ts, const Batch& b, uint32_t i) {
+  if (!b.cols) return ts[i];
+  RowCols c;
+  const uint32_t r = row_cols(b, RowCols{}, i, inst_of_row(b, i), c);
+  return c.ts[r];
+}
+
 __device__ __forceinline__ int inst_of_key(const Batch& b, uint32_t key) {
   int lo = 0, hi = b.n_inst - 1;
   while (lo < hi) {

@@ -148,6 +148,41 @@ def test_journey_sort_size_classes(orc, dup_frac):
     compare(run_gpu(cols), orc.run(cols))
 
 
+def test_long_journeys_with_long_runs(orc):
+    """Journeys above 8192 points (the fused kernel: each of 256 threads walks a contiguous range
+    of the sorted points and the run fragments are stitched across ranges), with stretches that
+    cross many ranges: a parked vehicle (one cell and bin for 5,000 points: a run spanning whole
+    ranges), an off-grid stretch (invalid keys across ranges) and exact duplicates; both forms,
+    with and without the per-point columns."""
+    rng = np.random.default_rng(41)
+    sizes = [8193, 10240, 10241, 12288, 20000, 45000]
+    parts = []
+    for j, m in enumerate(sizes):
+        dt = rng.integers(300, 1000, m)
+        dt[0] = 0
+        dt[1:][rng.random(m - 1) < 0.01] = 0
+        ts = T0 + 3_600_000 + int(rng.integers(0, 3_600_000)) + np.cumsum(dt)
+        lat = 38.0 + np.cumsum(rng.normal(0, 2e-5, m))
+        lon = -92.0 + np.cumsum(rng.normal(0, 2e-5, m))
+        a, b = m // 5, m // 5 + 5000  # parked
+        lat[a:b], lon[a:b] = lat[a], lon[a]
+        c, d = (3 * m) // 5, (3 * m) // 5 + 3000  # off the grid (north of the box)
+        lat[c:d] += 5.0
+        spd = np.abs(rng.normal(40, 30, m)).astype(np.float32)
+        spd[a:b] = 0.0
+        parts.append(dict(jid=np.full(m, 7000 + j, np.int64), ts=ts.astype(np.int64), lat=lat, lon=lon, speed=spd))
+    cols = {k: np.concatenate([q[k] for q in parts]) for k in parts[0]}
+    perm = rng.permutation(cols["jid"].shape[0])
+    cols = {k: np.ascontiguousarray(v[perm]) for k, v in cols.items()}
+    o = orc.run(cols)
+    compare(run_gpu(cols), o)
+    import paper_2305_07454_b300 as P
+
+    compare(run_gpu(cols, precision=P.FP32), o, rel=1e-4)  # the float32 form
+    # without the per-point columns (the bench's configuration)
+    compare(run_gpu(cols, materialize=False), o, points=False)
+
+
 def test_timestamps_spanning_the_int64_range(orc):
     """Timestamps spread over the whole int64 range: the sort keys (time offset and bucket
     position) no longer fit 64 bits and every journey is sorted as (timestamp, row) pairs, in both
