@@ -174,16 +174,20 @@ __device__ __forceinline__ unsigned long long load8(const unsigned char* s, int 
 
 // The value of n (1..8) ASCII decimal digits held in the low n bytes of x (first digit in the
 // lowest byte), or false if one of them is not a digit. The digits are moved to the top bytes
-// and the bottom bytes filled with '0', then pairs, quads and the octet are combined by
-// multiply-and-shift inside the word.
+// and the bottom bytes filled with '0'; each 32-bit half (four digits) is then combined by
+// multiply-and-shift inside the word (pairs, then the quad), and the halves by one multiply-add.
+// 32-bit words keep every step a single integer instruction.
 __device__ __forceinline__ bool digits8(unsigned long long x, int n, unsigned long long& v) {
   const int sh = 8 * (8 - n);
   x = sh ? ((x << sh) | (0x3030303030303030ull >> (64 - sh))) : x;
-  const unsigned long long t = x - 0x3030303030303030ull;  // digit values (a byte below '0' sets its top bit)
-  if (((x + 0x4646464646464646ull) | t) & 0x8080808080808080ull) return false;  // some byte outside '0'..'9'
-  unsigned long long y = (t * 10 + (t >> 8)) & 0x00FF00FF00FF00FFull;      // 2-digit lanes
-  y = (y * 100 + (y >> 16)) & 0x0000FFFF0000FFFFull;                      // 4-digit lanes
-  v = (y * 10000 + (y >> 32)) & 0xFFFFFFFFull;                            // 8 digits
+  const uint32_t a = (uint32_t)x, b = (uint32_t)(x >> 32);  // digits 1-4, digits 5-8
+  uint32_t ta = a - 0x30303030u, tb = b - 0x30303030u;     // a byte below '0' sets its top bit
+  if (((a + 0x46464646u) | ta | (b + 0x46464646u) | tb) & 0x80808080u) return false;  // outside '0'..'9'
+  ta = (ta * 10u + (ta >> 8)) & 0x00FF00FFu;  // 2-digit lanes
+  tb = (tb * 10u + (tb >> 8)) & 0x00FF00FFu;
+  ta = (ta * 100u + (ta >> 16)) & 0xFFFFu;    // 4 digits
+  tb = (tb * 100u + (tb >> 16)) & 0xFFFFu;
+  v = (unsigned long long)(ta * 10000u + tb);
   return true;
 }
 
