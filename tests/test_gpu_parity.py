@@ -183,6 +183,17 @@ def test_long_journeys_with_long_runs(orc):
     compare(run_gpu(cols, materialize=False), o, points=False)
 
 
+def test_very_long_journeys(orc):
+    """Journeys of 120,000, 150,001 (40% exact duplicates) and 400,001 points: above the
+    time-bucket sort's limit of 98,304 points, each is sorted by one CTA's radix sort through
+    global scratch, its keys holding 17-19 position bits."""
+    cols = synth([120000, 400001], seed=43)
+    o = orc.run(cols)
+    compare(run_gpu(cols, materialize=False), o, points=False)
+    dup = synth([150001], seed=44, dup_frac=0.4)
+    compare(run_gpu(dup, materialize=False), orc.run(dup), points=False)
+
+
 def test_timestamps_spanning_the_int64_range(orc):
     """Timestamps spread over the whole int64 range: the sort keys (time offset and bucket
     position) no longer fit 64 bits and every journey is sorted as (timestamp, row) pairs, in both
