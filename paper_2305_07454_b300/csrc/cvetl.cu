@@ -1015,19 +1015,19 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   const size_t nv = c->n_valid;
   Rec* rec;
   ENSURE("rec", nv, &rec);
-  // columns aligned for the vector loads and in one set of columns: 4 rows per thread
+  // columns aligned for the vector loads and in one set of columns: kScatterRows rows per thread
   const auto al = [](const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
-  const bool quads = !c->bt.cols && al(c->ts, 32) && al(c->lat, 32) && al(c->lon, 32) && al(c->spd, 16) &&
-                     al(row_slot, 16);
-  if (n && quads) {
+  const bool groups = !c->bt.cols && al(c->ts, 32) && al(c->lat, 32) && al(c->lon, 32) && al(c->spd, 16) &&
+                      al(row_slot, 16);
+  if (n && groups) {
     const int NT = c->tune.row_block;
-    const uint32_t nq = (uint32_t)((n >> 2) > 0 ? (n >> 2) : 1);
-#define SCAT4(NT_) k_scatter4<NT_><<<grid_for(nq, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
+    const size_t ng = (size_t)n / kScatterRows > 0 ? (size_t)n / kScatterRows : 1;
+#define SCATR(NT_) k_scatter_rows<NT_, kScatterRows><<<grid_for(ng, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
     c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)
-    if (NT == 128) LAUNCH(ST_SCATTER, (SCAT4(128)));
-    else if (NT == 512) LAUNCH(ST_SCATTER, (SCAT4(512)));
-    else LAUNCH(ST_SCATTER, (SCAT4(256)));
-#undef SCAT4
+    if (NT == 128) LAUNCH(ST_SCATTER, (SCATR(128)));
+    else if (NT == 512) LAUNCH(ST_SCATTER, (SCATR(512)));
+    else LAUNCH(ST_SCATTER, (SCATR(256)));
+#undef SCATR
     LAUNCH_CHECK();
   } else if (n) {
     const int U = c->tune.row_unroll, NT = c->tune.row_block;

@@ -238,49 +238,66 @@ __global__ void __launch_bounds__(NT) k_scatter(const int64_t* __restrict__ ts,
   }
 }
 
-// The same scatter with each thread on 4 consecutive rows per iteration, the columns read with
-// 32-byte (timestamp, latitude, longitude) and 16-byte (speed, slot) vector loads: a quarter of
-// the load instructions, for a kernel whose warps wait on the load-store queue. Needs the five
-// columns and the slots 32- / 16-byte aligned and the rows in one set of columns (not a batch
-// read in place); rows past the last full quad go one per thread.
+// The same scatter with each thread on R (a multiple of 4) consecutive rows per iteration, the
+// columns read with 32-byte (timestamp, latitude, longitude) and 16-byte (speed, slot) vector
+// loads: a sixteenth of the load instructions with R = 16, for a kernel whose warps wait on the
+// load-store queue. Needs the five columns and the slots 32- / 16-byte aligned and the rows in
+// one set of columns (not a batch read in place); rows past the last full group go one per
+// thread.
 __device__ __forceinline__ void ld_v4_b64(const void* p, unsigned long long& a, unsigned long long& b,
                                           unsigned long long& c, unsigned long long& d) {
   asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT) k_scatter4(const int64_t* __restrict__ ts, const double* __restrict__ lat,
-                                                 const double* __restrict__ lon, const float* __restrict__ spd,
-                                                 const uint32_t* __restrict__ row_slot, uint32_t n, Hash h,
-                                                 Rec* __restrict__ rec) {
-  const uint32_t nq = n >> 2;
+constexpr int kScatterRows = 16;  // R of the launched kernel
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_scatter_rows(const int64_t* __restrict__ ts, const double* __restrict__ lat,
+                                                     const double* __restrict__ lon, const float* __restrict__ spd,
+                                                     const uint32_t* __restrict__ row_slot, uint32_t n, Hash h,
+                                                     Rec* __restrict__ rec) {
+  static_assert(R % 4 == 0, "rows per thread: a multiple of 4");
+  const uint32_t ng = n / R;
   const uint32_t step = gridDim.x * NT;
-  for (uint32_t q = blockIdx.x * NT + threadIdx.x; q < nq; q += step) {
-    const uint32_t i = q << 2;
-    const uint4 sl = __ldg(reinterpret_cast<const uint4*>(row_slot + i));
-    const uint32_t slot[4] = {sl.x, sl.y, sl.z, sl.w};
-    uint32_t pos[4];
+  for (uint32_t q = blockIdx.x * NT + threadIdx.x; q < ng; q += step) {
+    const uint32_t i = q * R;
+    uint32_t slot[R], pos[R];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) pos[u] = (slot[u] != kKeyInvalid) ? atomicAdd(&h.aux[slot[u]], 1u) : 0u;
-    unsigned long long t[4], la[4], lo[4];
-    ld_v4_b64(ts + i, t[0], t[1], t[2], t[3]);
-    ld_v4_b64(lat + i, la[0], la[1], la[2], la[3]);
-    ld_v4_b64(lon + i, lo[0], lo[1], lo[2], lo[3]);
-    const float4 sp = __ldg(reinterpret_cast<const float4*>(spd + i));
-    const float s4[4] = {sp.x, sp.y, sp.z, sp.w};
+    for (int v = 0; v < R / 4; ++v) {
+      const uint4 sl = __ldg(reinterpret_cast<const uint4*>(row_slot + i) + v);
+      slot[4 * v] = sl.x;
+      slot[4 * v + 1] = sl.y;
+      slot[4 * v + 2] = sl.z;
+      slot[4 * v + 3] = sl.w;
+    }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < R; ++u) pos[u] = (slot[u] != kKeyInvalid) ? atomicAdd(&h.aux[slot[u]], 1u) : 0u;
+    unsigned long long t[R], la[R], lo[R];
+    float sp[R];
+#pragma unroll
+    for (int v = 0; v < R / 4; ++v) {
+      ld_v4_b64(ts + i + 4 * v, t[4 * v], t[4 * v + 1], t[4 * v + 2], t[4 * v + 3]);
+      ld_v4_b64(lat + i + 4 * v, la[4 * v], la[4 * v + 1], la[4 * v + 2], la[4 * v + 3]);
+      ld_v4_b64(lon + i + 4 * v, lo[4 * v], lo[4 * v + 1], lo[4 * v + 2], lo[4 * v + 3]);
+      const float4 s4 = __ldg(reinterpret_cast<const float4*>(spd + i) + v);
+      sp[4 * v] = s4.x;
+      sp[4 * v + 1] = s4.y;
+      sp[4 * v + 2] = s4.z;
+      sp[4 * v + 3] = s4.w;
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
       if (slot[u] == kKeyInvalid) continue;
-      const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(s4[u])) |
+      const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(sp[u])) |
                                    ((unsigned long long)(i + u) << 32);
       asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + pos[u]), "l"(t[u]), "l"(la[u]),
                    "l"(lo[u]), "l"(d)
                    : "memory");
     }
   }
-  // the last n mod 4 rows
-  const uint32_t g = blockIdx.x * NT + threadIdx.x, i = (nq << 2) + g;
-  if (g < (n & 3u) && row_slot[i] != kKeyInvalid) {
+  // the last n mod R rows
+  const uint32_t g = blockIdx.x * NT + threadIdx.x, i = ng * R + g;
+  if (g < n % R && row_slot[i] != kKeyInvalid) {
     const uint32_t p = atomicAdd(&h.aux[row_slot[i]], 1u);
     const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(spd[i])) |
                                  ((unsigned long long)i << 32);
