@@ -92,6 +92,8 @@ struct cvetl_ctx {
   uint32_t* row_slot = nullptr;     // hash slot of each extracted row (last batch)
   int id_bits = 64;                 // bits the journey-id sort covers (from the ids' key span)
   std::vector<double> batch_key;    // the last batch's instance grids and sizes
+  size_t batch_groups = 0;          // row groups of the batch (kScatterRows rows per instance-local group)
+  bool batch_aligned = false;       // a batch read in place whose columns all suit the vector loads
   // stream mode
   struct {
     bool flushed = false, has_w_prev = false;
@@ -118,7 +120,7 @@ struct cvetl_ctx {
     uint64_t n, J, nv, cap, gen;
     const void* cols[5];
     const void* inst;
-    int n_inst, precision, materialize, t0, t1, t2, id_bits;
+    int n_inst, precision, materialize, t0, t1, t2, id_bits, aligned;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof o) == 0; }
   };
   struct GraphEntry {
@@ -1029,6 +1031,16 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     else LAUNCH(ST_SCATTER, (SCATR(256)));
 #undef SCATR
     LAUNCH_CHECK();
+  } else if (n && c->bt.cols && c->batch_aligned && c->batch_groups) {  // a batch read in place, aligned
+    const int NT = c->tune.row_block;
+    const uint32_t G = (uint32_t)c->batch_groups;
+#define SCATG(NT_) k_scatter_groups<NT_, kScatterRows><<<grid_for(G, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
+    row_slot, n, G, c->bt, h, rec)
+    if (NT == 128) LAUNCH(ST_SCATTER, (SCATG(128)));
+    else if (NT == 512) LAUNCH(ST_SCATTER, (SCATG(512)));
+    else LAUNCH(ST_SCATTER, (SCATG(256)));
+#undef SCATG
+    LAUNCH_CHECK();
   } else if (n) {
     const int U = c->tune.row_unroll, NT = c->tune.row_block;
 #define SCAT(U_, NT_) k_scatter<U_, NT_><<<grid_for((n + U_ - 1) / U_, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
@@ -1226,6 +1238,7 @@ cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned
   k.t1 = c->tune.row_unroll * 1024 + c->tune.row_block;
   k.t2 = c->tune.small_sort_max * 1024 + c->tune.small_journey_max;
   k.id_bits = c->id_bits;
+  k.aligned = c->bt.cols && c->batch_aligned ? 1 : 0;
   for (auto& g : c->graphs) {
     if (!(g.key == k)) continue;
     if (!g.exec) return post_sizing(c, h, row_slot, ukey, uslot, J, false);
@@ -1543,11 +1556,19 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   }
   const bool same_tables = key == c->batch_key && c->bt.n_inst == n_inst && c->bt.inst != nullptr;
   std::vector<BatchInst> bi(n_inst);
+  size_t groups = 0;  // instance-local row groups of the scatter
   std::vector<unsigned long long> thr;
   std::vector<size_t> thr_at(n_inst);
   c->inst_rows.assign(n_inst + 1, 0);
   c->inst_keys.assign(n_inst + 1, 0);
   std::vector<BatchCols> cols(n_inst);
+  const auto al = [](const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; };
+  bool aligned = in_place;
+  for (int i = 0; i < n_inst; ++i)
+    if (inst[i].n > 0)
+      aligned = aligned && al(inst[i].jid, 32) && al(inst[i].ts, 32) && al(inst[i].lat, 32) && al(inst[i].lon, 32) &&
+                al(inst[i].speed, 16);
+  c->batch_aligned = aligned;
   for (int i = 0; i < n_inst; ++i) {
     const cvetl_instance& q = inst[i];
     const size_t r0 = (size_t)c->inst_rows[i], m = (size_t)q.n;
@@ -1572,6 +1593,8 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
     bi[i].t0_ms = q.t0_ms;
     bi[i].row_begin = (uint32_t)r0;
     bi[i].key_off = (uint32_t)c->inst_keys[i];
+    bi[i].group_begin = (uint32_t)groups;
+    groups += (m + kScatterRows - 1) / kScatterRows;
   }
   // the column table, in stream order before the kernels that read it (pageable source:
   // staged before the call returns)
@@ -1611,6 +1634,7 @@ cvetl_status cvetl_extract_batch(cvetl_ctx* c, const cvetl_instance* inst, int32
   c->bt.n_inst = n_inst;
   c->bt.inst = dbi;
   c->bt.cols = dcols;
+  c->batch_groups = groups;
   c->batch_key = key;
   c->jid = jid;
   c->ts = ts;

@@ -308,4 +308,78 @@ __global__ void __launch_bounds__(NT) k_scatter_rows(const int64_t* __restrict__
   }
 }
 
+// The 16-row scatter for a batch read in place: row groups numbered per instance (an
+// instance's last group may be partial), each thread's group found by binary search over the
+// instances' first groups, the instance's column pointers read from the batch table (all of
+// them aligned: checked when the batch was extracted). Slots are read one by one unless the
+// group's first row is a multiple of 4.
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_scatter_groups(const uint32_t* __restrict__ row_slot, uint32_t n,
+                                                       uint32_t n_groups, Batch bt, Hash h, Rec* __restrict__ rec) {
+  static_assert(R % 4 == 0, "rows per thread: a multiple of 4");
+  const uint32_t step = gridDim.x * NT;
+  for (uint32_t g = blockIdx.x * NT + threadIdx.x; g < n_groups; g += step) {
+    const int k = inst_of_group(bt, g);
+    const uint32_t row0 = __ldg(&bt.inst[k].row_begin);
+    const uint32_t row1 = (k + 1 < bt.n_inst) ? __ldg(&bt.inst[k + 1].row_begin) : n;
+    const uint32_t r = (g - __ldg(&bt.inst[k].group_begin)) * R;  // the group's first row in the instance
+    const uint32_t i = row0 + r;                                    // and in the batch
+    RowCols c;
+    row_cols(bt, RowCols{}, i, k, c);
+    if (r + R <= row1 - row0) {
+      uint32_t slot[R], pos[R];
+      if ((i & 3u) == 0) {
+#pragma unroll
+        for (int v = 0; v < R / 4; ++v) {
+          const uint4 sl = __ldg(reinterpret_cast<const uint4*>(row_slot + i) + v);
+          slot[4 * v] = sl.x;
+          slot[4 * v + 1] = sl.y;
+          slot[4 * v + 2] = sl.z;
+          slot[4 * v + 3] = sl.w;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < R; ++u) slot[u] = __ldg(row_slot + i + u);
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) pos[u] = (slot[u] != kKeyInvalid) ? atomicAdd(&h.aux[slot[u]], 1u) : 0u;
+      unsigned long long t[R], la[R], lo[R];
+      float sp[R];
+#pragma unroll
+      for (int v = 0; v < R / 4; ++v) {
+        ld_v4_b64(c.ts + r + 4 * v, t[4 * v], t[4 * v + 1], t[4 * v + 2], t[4 * v + 3]);
+        ld_v4_b64(c.lat + r + 4 * v, la[4 * v], la[4 * v + 1], la[4 * v + 2], la[4 * v + 3]);
+        ld_v4_b64(c.lon + r + 4 * v, lo[4 * v], lo[4 * v + 1], lo[4 * v + 2], lo[4 * v + 3]);
+        const float4 s4 = __ldg(reinterpret_cast<const float4*>(c.spd + r) + v);
+        sp[4 * v] = s4.x;
+        sp[4 * v + 1] = s4.y;
+        sp[4 * v + 2] = s4.z;
+        sp[4 * v + 3] = s4.w;
+      }
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        if (slot[u] == kKeyInvalid) continue;
+        const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(sp[u])) |
+                                     ((unsigned long long)(i + u) << 32);
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + pos[u]), "l"(t[u]), "l"(la[u]),
+                     "l"(lo[u]), "l"(d)
+                     : "memory");
+      }
+    } else {  // the instance's partial last group
+      for (uint32_t u = 0; r + u < row1 - row0; ++u) {
+        const uint32_t s = row_slot[i + u];
+        if (s == kKeyInvalid) continue;
+        const uint32_t p = atomicAdd(&h.aux[s], 1u);
+        const unsigned long long d = (unsigned long long)(uint32_t)__float_as_int(canon_speed(c.spd[r + u])) |
+                                     ((unsigned long long)(i + u) << 32);
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(rec + p),
+                     "l"((unsigned long long)c.ts[r + u]),
+                     "l"((unsigned long long)__double_as_longlong(c.lat[r + u])),
+                     "l"((unsigned long long)__double_as_longlong(c.lon[r + u])), "l"(d)
+                     : "memory");
+      }
+    }
+  }
+}
+
 }  // namespace cvetl

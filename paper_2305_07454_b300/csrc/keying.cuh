@@ -123,6 +123,7 @@ struct BatchInst {
   int64_t t0_ms;
   uint32_t row_begin;  // first row of the instance in the concatenated columns
   uint32_t key_off;    // first key of the instance in the concatenated key space
+  uint32_t group_begin;  // first group of the instance's rows (groups of kScatterRows rows, per instance)
 };
 
 // A batch's instance columns read in place (device batches): instance k's own arrays.
@@ -176,6 +177,17 @@ __device__ __forceinline__ int64_t row_ts(const int64_t* __restrict__ ts, const 
   RowCols c;
   const uint32_t r = row_cols(b, RowCols{}, i, inst_of_row(b, i), c);
   return c.ts[r];
+}
+
+// last instance whose first row group is <= g
+__device__ __forceinline__ int inst_of_group(const Batch& b, uint32_t g) {
+  int lo = 0, hi = b.n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&b.inst[mid].group_begin) <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 __device__ __forceinline__ int inst_of_key(const Batch& b, uint32_t key) {

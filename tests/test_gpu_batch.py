@@ -65,6 +65,32 @@ def test_each_instance_matches_the_oracle(orc, precision, rel):
     assert tot["n_in"] == sum(q["jid"].shape[0] for q in insts)
 
 
+def test_device_instances_read_in_place_aligned_or_not(orc):
+    """Device instances are read in place: with every column aligned, the scatter takes 16-row
+    groups per instance (32-byte column loads; an instance's last group may be partial and its
+    first row need not be a multiple of 4); with one column 8 bytes off a 32-byte boundary (a
+    view one element into a larger tensor), the one-row scatter. Both give each instance the
+    oracle's results."""
+    import torch
+
+    import paper_2305_07454_b300 as P
+
+    insts = make(seed=6, days=1)
+    dev = on_device(insts)
+    with P.Pipeline(materialize_points=1) as p:
+        check_instances(orc, insts, p.run_batch(dev))
+    shifted = []
+    for q in dev:
+        r = dict(q)
+        big = torch.empty(q["lat"].shape[0] + 1, dtype=q["lat"].dtype, device=q["lat"].device)
+        big[1:] = q["lat"]
+        r["lat"] = big[1:]  # 8 bytes past the allocation's start
+        assert r["lat"].data_ptr() % 32 != 0
+        shifted.append(r)
+    with P.Pipeline(materialize_points=1) as p:
+        check_instances(orc, insts, p.run_batch(shifted))
+
+
 def test_host_instances_and_one_instance_batch(orc):
     import torch
 
