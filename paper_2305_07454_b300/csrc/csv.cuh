@@ -205,6 +205,19 @@ __device__ __forceinline__ bool digits_at(const unsigned char* s, int pos, int n
   return true;
 }
 
+// The value of the n (1..16) digits at s[pos, pos + n) as two groups, the last min(n, 8)
+// digits and the k = n - 8 before them (none when n <= 8, read as one '0'): the same work for
+// every length, so the lanes of a warp whose fields differ in length do not diverge.
+__device__ __forceinline__ bool digits16_at(const unsigned char* s, int pos, int n, unsigned long long& v) {
+  const int k = n > 8 ? n - 8 : 0;
+  const unsigned long long lead = load8(s, pos), last = load8(s, pos + k);
+  unsigned long long hv, lv;
+  bool ok = digits8(last, n - k, lv);
+  ok &= digits8(k ? lead : 0x30ull, k ? k : 1, hv);
+  v = hv * 100000000ull + lv;
+  return ok;
+}
+
 // Fields of one line of the staged window by the separator masks: an integer field.
 __device__ __forceinline__ bool int_field(const unsigned char* s, int a, int b, long long& out) {
   bool neg = false;
@@ -215,7 +228,7 @@ __device__ __forceinline__ bool int_field(const unsigned char* s, int a, int b, 
   const int n = b - a;
   if (n < 1 || n > 18) return false;
   unsigned long long v;
-  if (!digits_at(s, a, n, v)) return false;
+  if (!(n <= 16 ? digits16_at(s, a, n, v) : digits_at(s, a, n, v))) return false;
   out = neg ? -(long long)v : (long long)v;
   return true;
 }
@@ -250,15 +263,16 @@ __device__ __forceinline__ bool dec_field(const unsigned char* s, int a, int b, 
     }
   }
   if (n > 15) return false;
-  unsigned long long M;  // the n digits, bytes [0, n) of (lo, hi); a second '.' is not a digit
-  if (n <= 8) {
-    if (!digits8(lo, n, M)) return false;
-  } else {
-    const int k = n - 8;  // leading digits, then the last eight
-    unsigned long long v;
-    if (!digits8(lo, k, M) || !digits8((lo >> (8 * k)) | (hi << (64 - 8 * k)), 8, v)) return false;
-    M = M * 100000000ull + v;
-  }
+  // the n digits, bytes [0, n) of (lo, hi) (a second '.' is not a digit), as two groups: the
+  // last min(n, 8) and the k = n - 8 before them (none when n <= 8, read as one '0'), the same
+  // work for every length
+  const int k = n > 8 ? n - 8 : 0;
+  const unsigned long long last = k ? ((lo >> (8 * k)) | (hi << ((64 - 8 * k) & 63))) : lo;
+  unsigned long long M, hv;
+  bool ok = digits8(last, n - k, M);
+  ok &= digits8(k ? lo : 0x30ull, k ? k : 1, hv);
+  if (!ok) return false;
+  M += hv * 100000000ull;
   out = negate_if(dec_to_f64(M, nf), neg);
   return true;
 }
