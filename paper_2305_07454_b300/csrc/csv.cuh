@@ -470,10 +470,18 @@ __global__ void __launch_bounds__(kCsvBlock) k_csv_parse(const unsigned char* __
   const uint32_t row0 = tile_row[tile];
   for (int i = tid; i < nstart; i += kCsvBlock) {
     const int sl = s_start[i];
-    // the line's end: the next newline bit at or after its start
+    // the line's end: the newline before the next line's start, or for the tile's last line
+    // the next newline bit at or after its start
     int w = sl >> 5;
-    uint32_t m = s_nl[w] & (~0u << (sl & 31));
-    while (!m && ++w < nmask) m = s_nl[w];
+    uint32_t m;
+    if (i + 1 < nstart) {
+      const int e = s_start[i + 1] - 1;
+      w = e >> 5;
+      m = 1u << (e & 31);
+    } else {
+      m = s_nl[w] & (~0u << (sl & 31));
+      while (!m && ++w < nmask) m = s_nl[w];
+    }
     int64_t a, b;
     double c, d;
     float e, f;
