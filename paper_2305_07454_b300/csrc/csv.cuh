@@ -163,13 +163,13 @@ __device__ __forceinline__ uint32_t byte_eq_nibble(uint32_t w, uint32_t c4) {
   return (z * 0x00204081u) >> 28;
 }
 
-// 8 bytes at byte offset pos of a 16-byte aligned shared buffer (two aligned loads + shift).
+// 8 bytes at byte offset pos of a 16-byte aligned shared buffer: three aligned 32-bit words and
+// two byte permutes (no shift of a 64-bit value, no branch on the offset).
 __device__ __forceinline__ unsigned long long load8(const unsigned char* s, int pos) {
-  const unsigned long long* w = reinterpret_cast<const unsigned long long*>(s + (pos & ~7));
-  const int sh = (pos & 7) * 8;
-  const unsigned long long lo = w[0];
-  if (sh == 0) return lo;
-  return (lo >> sh) | (w[1] << (64 - sh));
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(s + (pos & ~3));
+  const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(pos & 3);  // bytes off .. off + 3 of the pair
+  const uint32_t w0 = w[0], w1 = w[1], w2 = w[2];
+  return (unsigned long long)__byte_perm(w0, w1, sel) | ((unsigned long long)__byte_perm(w1, w2, sel) << 32);
 }
 
 // The value of n (1..8) ASCII decimal digits held in the low n bytes of x (first digit in the
