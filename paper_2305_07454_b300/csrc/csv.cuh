@@ -30,6 +30,8 @@ __constant__ unsigned long long kPow5[16] = {1ull, 5ull, 25ull, 125ull, 625ull, 
                                              78125ull, 390625ull, 1953125ull, 9765625ull,
                                              48828125ull, 244140625ull, 1220703125ull,
                                              6103515625ull, 30517578125ull};
+// bit length of 5^k
+__constant__ int kLen5[16] = {1, 3, 5, 7, 10, 12, 14, 17, 19, 21, 24, 26, 28, 31, 33, 35};
 // floor(2^(63 + Ld) / 5^k), Ld the bit length of 5^k: a reciprocal in [2^63, 2^64)
 __constant__ unsigned long long kRecip5[16] = {
     0ull,  // k = 0: no division
@@ -56,7 +58,7 @@ __device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
   if (M == 0) return 0.0;
   if (k == 0) return u53_to_f64(M);
   const unsigned long long d = kPow5[k];
-  const int L = 64 - __clzll((long long)M), Ld = 64 - __clzll((long long)d);
+  const int L = 64 - __clzll((long long)M), Ld = kLen5[k];
   const int t = 56 + Ld - L;
   unsigned long long q = __umul64hi(M << (64 - L), kRecip5[k]) >> 7;
   unsigned long long r = (t >= 64 ? 0ull : (M << t)) - q * d;
@@ -64,10 +66,9 @@ __device__ __forceinline__ double dec_to_f64(unsigned long long M, int k) {
     q += 1;
     r -= d;
   }
-  const int b = 64 - __clzll((long long)q);
-  int s = b - 53;  // 2 to 4 bits below the binary64 significand
+  int s = 3 + (int)(q >> 56);  // q has 56 or 57 bits: 3 or 4 below the binary64 significand
   unsigned long long mant = q >> s;
-  const unsigned long long low = q & ((1ull << s) - 1), half = 1ull << (s - 1);
+  const uint32_t low = (uint32_t)q & ((1u << s) - 1u), half = 1u << (s - 1);
   if (low > half || (low == half && (r != 0 || (mant & 1)))) mant += 1;
   if (mant >> 53) {
     mant >>= 1;
