@@ -224,7 +224,7 @@ TRAFFIC_PER_RECORD = {
     "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.941, "journey_sort": 29.767,
     "journeys": 5.24, "journey_walk": 86.221, "cell_heads": 0.214, "cell_write": 1.073,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.664, "csv_parse": 96.271,
+    "csv_count": 58.66, "csv_parse": 97.555,
 }
 TRAFFIC_PER_RECORD_FP32 = {
     "hash_count": 31.162, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.534,
