@@ -220,16 +220,16 @@ def fp64_probe(stream, reps=3):
 # scaled by records to the workload (the full day is too large to capture under the profiler's
 # size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "hash_count": 31.171, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.535,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.941, "journey_sort": 29.767,
-    "journeys": 5.24, "journey_walk": 86.221, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.179, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.535,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.925, "journey_sort": 29.761,
+    "journeys": 5.289, "journey_walk": 86.22, "cell_heads": 0.214, "cell_write": 1.073,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.66, "csv_parse": 97.555,
+    "csv_count": 58.655, "csv_parse": 97.553,
 }
 TRAFFIC_PER_RECORD_FP32 = {
-    "hash_count": 31.162, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.534,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.953, "journey_sort": 29.76,
-    "journeys": 4.621, "journey_walk": 86.552, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.175, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.534,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.923, "journey_sort": 29.787,
+    "journeys": 4.464, "journey_walk": 86.626, "cell_heads": 0.214, "cell_write": 1.073,
 }
 
 
