@@ -233,6 +233,33 @@ TRAFFIC_PER_RECORD_FP32 = {
 }
 
 
+# The kernel sources the traffic figures above were captured with: sha256 over the files of
+# paper_2305_07454_b300/csrc (name and bytes, in name order). When the sources differ, the
+# figures describe other kernels: the line then reports no traffic and no gate figure.
+TRAFFIC_SOURCES_SHA256 = "b1bd1886afbe7260ba51c564931a95927985b1af15256552c7c4c6d7adfd671b"
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2305_07454_b300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_table(precision: str) -> dict:
+    """The ncu DRAM bytes per record of the form's stages, or {} when the kernels have changed
+    since they were captured."""
+    if kernel_sources_sha256() != TRAFFIC_SOURCES_SHA256:
+        return {}
+    return TRAFFIC_PER_RECORD if precision == "fp64" else TRAFFIC_PER_RECORD_FP32
+
+
 def unit_launches(stage, launches, steps):
     """Number of passes over the stage's algorithmic work in `launches`. Every stage's launch is
     one pass, except the journey sort (the class bounds and one launch per size class share one
@@ -309,7 +336,10 @@ def _hbm_step(stages, counters, ms_step, steps, csv, traffic=None):
     timed = {s: v for s, v in stages.items() if v["launches"] and v["ms"] > 0}
     traffic = traffic or {}
     missing = sorted(s for s in timed if s not in traffic)
-    if missing:
+    if not traffic:
+        out["gate"] = None
+        out["gate_missing_traffic"] = "no ncu traffic for these kernels (sources changed since the capture)"
+    elif missing:
         out["gate"] = None
         out["gate_missing_traffic"] = missing
     else:
@@ -327,7 +357,7 @@ def _roofline_entry(top, stages, counters, steps, precision, probe):
     issue rate, any other stage against the measured HBM copy bandwidth."""
     avg_ms = stages[top]["ms"] / unit_launches(top, stages[top]["launches"], steps)
     hbm_peak, peak_src = load_peaks()
-    tpr = TRAFFIC_PER_RECORD.get(top) if precision == "fp64" else TRAFFIC_PER_RECORD_FP32.get(top)
+    tpr = traffic_table(precision).get(top)
     # per launch (a pass over the stage's work): the step's traffic over the passes per step
     traffic = tpr * counters["n_valid"] / (unit_launches(top, stages[top]["launches"], steps) / steps) if tpr else None
     if top in ("journeys", "journey_walk") and precision == "fp64" and probe:
@@ -484,7 +514,7 @@ def run_ours(args):
     top = max(stages, key=lambda s: stages[s]["ms"])
     roofline = _roofline_entry(top, stages, counters, args.steps, args.precision, probe)
     hbm_step = _hbm_step(stages, counters, ms_step, args.steps, csv_host is not None,
-                         TRAFFIC_PER_RECORD if args.precision == "fp64" else TRAFFIC_PER_RECORD_FP32)
+                         traffic_table(args.precision))
     shares = {s: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
               for s, v in stages.items() if v["launches"]}
 
@@ -563,7 +593,7 @@ def _fp32_day(P, stream, extract_dev, args, barrier, local, world, dev, n_job, c
     top32 = max(st32, key=lambda s: st32[s]["ms"])
     return {"ms_per_step": ms32 / args.steps, "records_per_s": n_job * args.steps / (ms32 / 1e3),
             "hbm_step": _hbm_step(st32, c32, ms32 / args.steps, args.steps, csv_host is not None,
-                                  TRAFFIC_PER_RECORD_FP32),
+                                  traffic_table("fp32")),
             "roofline": _roofline_entry(top32, st32, c32, args.steps, "fp32", None),
             "stages": {s: {"ms_per_step": v["ms"] / args.steps} for s, v in st32.items() if v["launches"]},
             "errors_vs_fp64_form": _form_errors(r32, batch_res), "tuning": tune32, "clocks": clk32}
@@ -598,7 +628,7 @@ def _csv_day(P, host, stream, args, barrier, local, world, dev, rank):
     top = max(st, key=lambda k: st[k]["ms"])
     return {"workload": f"the day as CSV text ({c['csv_bytes']} bytes, {n_bad} malformed rows)",
             "ms_per_step": ms / args.steps, "records_per_s": nj * args.steps / (ms / 1e3),
-            "hbm_step": _hbm_step(st, c, ms / args.steps, args.steps, True, TRAFFIC_PER_RECORD),
+            "hbm_step": _hbm_step(st, c, ms / args.steps, args.steps, True, traffic_table("fp64")),
             "roofline": _roofline_entry(top, st, c, args.steps, "fp64", None),
             "stages": {k: {"ms_per_step": v["ms"] / args.steps} for k, v in st.items() if v["launches"]},
             "counters": c, "generation_s": t_gen, "tuning": tune, "clocks": clk}

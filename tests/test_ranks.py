@@ -80,3 +80,17 @@ def test_journey_stage_is_one_pass_per_step():
     # without the split every journey is counted as walked
     c0 = {k: v for k, v in c.items() if k not in ("n_fused", "j_fused")}
     assert bench.algorithmic_bytes("journey_walk", c0) == 34.0 * 90 + 28.0 * 7 + 96.0 * 3
+
+
+def test_traffic_figures_follow_the_kernel_sources(monkeypatch):
+    """The ncu traffic per record is used only while the kernel sources are the ones it was
+    captured with (their hash); with other sources the line has no traffic and no gate figure."""
+    stages = {"scatter": {"launches": 1, "ms": 4.0}}
+    c = {"n_in": 100, "n_valid": 100, "n_journeys": 1, "n_runs": 1, "n_cells": 1}
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA256", bench.kernel_sources_sha256())
+    assert bench.traffic_table("fp64") is bench.TRAFFIC_PER_RECORD
+    assert bench._hbm_step(stages, c, 4.0, 1, False, bench.traffic_table("fp64"))["gate"] is not None
+    monkeypatch.setattr(bench, "TRAFFIC_SOURCES_SHA256", "0" * 64)
+    assert bench.traffic_table("fp64") == {} and bench.traffic_table("fp32") == {}
+    out = bench._hbm_step(stages, c, 4.0, 1, False, bench.traffic_table("fp64"))
+    assert out["gate"] is None and "sources changed" in out["gate_missing_traffic"]
