@@ -160,6 +160,21 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// The lanes of the warp whose label equals this lane's (labels below 2^BITS), by one ballot
+// per label bit: a label's peers agree with it on every bit. A few full-rate vote instructions
+// in place of one match.any, which is far slower per instruction.
+template <int BITS>
+__device__ __forceinline__ uint32_t match_label(uint32_t label) {
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const bool bit = (label >> b) & 1u;
+    const uint32_t v = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? v : ~v;
+  }
+  return m;
+}
+
 // atomicAdd(ctr, 1) for each lane that calls it, as one atomic per warp (the lanes of a warp
 // that reach it together): returns the lane's own slot, in lane order.
 __device__ __forceinline__ uint32_t warp_inc(uint32_t* ctr) {

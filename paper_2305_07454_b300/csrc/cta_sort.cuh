@@ -5,10 +5,10 @@
 // thousand pairs). Here one block loads the pairs into shared memory and runs an LSD radix sort
 // there: it first finds which key bits differ between the pairs (an OR and an AND over the
 // keys) and runs a counting pass only for the 8-bit digits that hold such a bit; a digit that is
-// the same in every key would leave the order unchanged. Each pass ranks a warp's keys by warp
-// match (as the journey kernel's radix sort does), sums the warps' digit counts in order, and
-// scatters; every pass is stable, so the result is the stable order by the key bits
-// [begin_bit, end_bit), equal keys in input order.
+// the same in every key would leave the order unchanged. Each pass ranks a warp's keys by their
+// digits' peer lanes (found by one ballot per digit bit, as in the journey kernel's radix sort),
+// sums the warps' digit counts in order, and scatters; every pass is stable, so the result is
+// the stable order by the key bits [begin_bit, end_bit), equal keys in input order.
 #pragma once
 #include "common.cuh"
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT) k_cta_sort(const K* __restrict__ kin,
       key[r] = in ? src[idx] : (K)0;
       val[r] = in ? vs[idx] : 0u;
       const uint32_t d = in ? (uint32_t)((((key[r] >> begin_bit) & mask) >> shift) & (K)255) : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t peers = match_label<9>(d);  // d <= 256
       const uint32_t before = in ? (uint32_t)wcnt[warp * 256 + d] : 0u;
       __syncwarp();
       if (in && lane == __ffs(peers) - 1) wcnt[warp * 256 + d] = (uint16_t)(before + __popc(peers));

@@ -274,8 +274,8 @@ __device__ __forceinline__ double haversine64(double la1, double lo1, const Cos6
 // ---------------------------------------------------------------- CTA-wide radix sort
 // Stable LSD radix sort of n 64-bit keys (8-bit digits over bits [0, nbits)) by one CTA.
 // A and B are shared memory for n <= kJCap (one tile), else global scratch (a journey's scratch stays in
-// L2 while its CTA works on it). Ranking inside a 4096-key tile uses warp match + popc, as in
-// the device-wide sort; multi-tile passes add a digit histogram and carry running offsets
+// L2 while its CTA works on it). Ranking inside a 4096-key tile takes each digit's peer lanes
+// (one ballot per digit bit) and their count below the lane, as the device-wide sort does; multi-tile passes add a digit histogram and carry running offsets
 // from tile to tile in order, which keeps the sort stable.
 constexpr int kRTile = 16 * kJBlock;  // keys ranked per tile: 16 per thread
 
@@ -327,7 +327,7 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const uint32_t d = (uint32_t)(key[i] >> shift) & 255u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = match_label<8>(d);
         const uint32_t before = sm.wcnt[warp][d];
         __syncwarp();
         if (lane == (__ffs(peers) - 1)) sm.wcnt[warp][d] = (uint16_t)(before + __popc(peers));
