@@ -164,11 +164,11 @@ def algorithmic_bytes(stage: str, c: dict) -> float:
 
 
 # binary64 operations per point of the journey kernels: the cosine of the latitude (2: offset from
-# the table point, one fma) and the distance (10: two differences, two squares, the cosine
-# product, one fma, the scaled square root and its residual, the scaling, the final fma); the
-# journey distance is summed in integer fixed point and the implied speed rounded to float32 by
-# integer operations, off the binary64 pipe
-FP64_OPS_PER_POINT = 12.0
+# the table point, one fma) and the distance (3: two coordinate differences and the final sum of
+# a float32 pair; the squares, products, square root and scaling run on float32 pairs); the
+# journey distance is summed in integer fixed point and the implied speed is the float32
+# rounding of the pair, off the binary64 pipe
+FP64_OPS_PER_POINT = 5.0
 SMS = 148
 
 # Bytes per record the method must move (the algorithmic floor: read the needed input once,

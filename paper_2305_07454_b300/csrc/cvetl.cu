@@ -1399,6 +1399,8 @@ cvetl_status cvetl_create(const cvetl_config* cfg, cvetl_ctx** out) {
   g.asin_c2 = g.asin_c1 / 6.0;
   g.asin_c3 = g.asin_c1 * 0.075;
   g.dist_k = cfg->earth_radius_m * (3.141592653589793 / 180.0);
+  g.dist_kh = (float)g.dist_k;
+  g.dist_kl = (float)(g.dist_k - (double)g.dist_kh);
   if (cudaFuncSetAttribute(k_journeys<Fp64Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp32Form, false, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||
       cudaFuncSetAttribute(k_journeys<Fp64Form, true, kJBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize, kJSmem) != cudaSuccess ||

@@ -186,17 +186,21 @@ __device__ const Elem* sort_big(Elem* E, const Rec* __restrict__ R, int n, Elem*
 //   cos(lat0 + e) = c0 - s0 E - c0 E^2/2 + s0 E^3/6 + O(E^4), E = e pi/180, lat0 the nearest
 //                   0.01 deg (|E| < 8.8e-5, dropped terms < 3e-18); eC collects the E^2, E^3
 //                   terms of both cosines relative to C v / m
-//   sqrt(m) = s0 sqrt(1 + r / s0^2) = s0 (1 + p/2 + 3p^2/8) + O(p^3),  p = r / m,
-//             s0 = m * rsqrt_f32(m),  r = m - s0^2 (|p| ~ 2^-21)
-// so d = 2R asin(sqrt h) = 2R K s0 (1 + ds)(1 + dr) with
-//   ds = p/2 + 3p^2/8,  dr = (eC - q)/2 + h/6 + 3h^2/40   (|ds| < 3e-7, |dr| < 2e-8).
-// Every term above 2^-22 relative (differences, squares, the cosine product, m, s0, the
-// residual r, the scaling and the final fma) is binary64; delta, a sum of small corrections, is
-// float32, which puts at most ~1e-14 relative error on d. That is 12 binary64 operations per
-// point (cosine 2, distance 10; the journey sum is kept in integer fixed point and the implied
-// speed rounded to float32 by integer operations) where the direct evaluation takes about 30 on
-// a part that runs about 1.7 per clock per SM. Larger steps take the general formula through
-// the CUDA math library.
+//   sqrt(m) = s sqrt(1 + r / s^2) = s (1 + p/2 + 3p^2/8) + O(p^3),  p = r / m,
+//             s = sqrt_f32(m) correctly rounded,  r = m - s^2 (|p| <= 2^-23)
+// so d = 2R asin(sqrt h) = 2R K s (1 + ds)(1 + dr) with
+//   ds = p/2 + 3p^2/8,  dr = (eC - q)/2 + h/6 + 3h^2/40   (|ds| < 6e-8, |dr| < 2e-8).
+// The coordinate differences and the cosine c0 - s0 e are binary64 (the differences are exact
+// for nearby points); each is then split into a float32 pair h + l (48 significand bits) and
+// the products, m, the residual r and the scaling by 2R K are evaluated as float32 pairs with
+// error-free products (fmaf) and sums; the pair 2R K s (1 + ds + dr) is added up once in
+// binary64. Each pair step has a relative error of a few 2^-48 and the small corrections ds,
+// dr are float32 (below 5e-15 relative on d): d is within about 1e-14 of the haversine of the
+// same binary64 inputs, as close as the all-binary64 evaluation of the series.
+// That is 5 binary64 operations per point (cosine 2, differences 2, the final sum) on a part
+// that runs about 1.7 of them per clock per SM against 128 float32 operations; the journey sum
+// is kept in integer fixed point and the implied speed rounded to float32 by integer
+// operations. Larger steps take the general formula through the CUDA math library.
 constexpr double kRad = 0.017453292519943295;  // pi / 180
 constexpr float kRadF = 0.017453292519943295f;
 constexpr float kK2F = 7.615435494667714e-5f;  // (pi/360)^2
@@ -212,25 +216,79 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
-// cosine of a latitude: binary64 value c0 - s0 E, its float32 copy, and the float32 relative
-// correction of the E^2 and E^3 terms
+// A value as the unevaluated sum h + l of two float32 (|l| <= ulp(h)).
+struct F2 {
+  float h, l;
+};
+
+// x = h + l by integer operations on the bit pattern: h the leading 24 significand bits of x
+// rounded to nearest (ties up), l the rest rounded to float32 (|l| <= ulp(h) / 2, a relative
+// error below 2^-48; exact when x has at most 48 significand bits), for finite
+// 2^-74 <= |x| < 2^64; smaller x give h = l = 0.
+__device__ __forceinline__ F2 split_f64(double x) {
+  const unsigned long long b = dbits(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo32 = (uint32_t)b, ex = (hi >> 20) & 0x7FFu;
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t low29 = lo32 & 0x1FFFFFFFu;  // the bits below h's, in units of 2^(ex - 1075)
+  const uint32_t up = low29 >> 28;            // the rest is at least half a unit of h
+  const uint32_t hb = (sign | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo32 >> 29)) + up;
+  const float lo = __int2float_rn((int)low29 - (int)(up << 29)) * __uint_as_float((ex - 948u) << 23);
+  const bool ok = ex >= 949u;
+  F2 r;
+  r.h = ok ? __uint_as_float(hb) : 0.0f;
+  r.l = ok ? __uint_as_float(__float_as_uint(lo) ^ sign) : 0.0f;
+  return r;
+}
+
+// Float32-pair steps with error-free products (the rounding error of a.h b.h by fmaf); the
+// intrinsics keep the compiler from fusing a product that a later step takes as rounded.
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  F2 r;
+  r.h = __fmul_rn(a.h, b.h);
+  r.l = fmaf(a.l, b.l, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -r.h))));
+  return r;
+}
+__device__ __forceinline__ F2 f2_sq(F2 a) {
+  F2 r;
+  r.h = __fmul_rn(a.h, a.h);
+  r.l = fmaf(a.l, a.l, fmaf(a.h + a.h, a.l, fmaf(a.h, a.h, -r.h)));
+  return r;
+}
+__device__ __forceinline__ F2 f2_add_pos(F2 a, F2 b) {  // a + b for a, b >= 0 (fast two-sum)
+  const float big = fmaxf(a.h, b.h), small = fminf(a.h, b.h);
+  F2 r;
+  r.h = __fadd_rn(big, small);
+  r.l = __fadd_rn(__fsub_rn(small, __fsub_rn(r.h, big)), __fadd_rn(a.l, b.l));
+  return r;
+}
+__device__ __forceinline__ F2 f2_norm(F2 a) {  // the same value with |l| <= ulp(h) / 2
+  F2 r;
+  r.h = __fadd_rn(a.h, a.l);
+  r.l = __fsub_rn(a.l, __fsub_rn(r.h, a.h));
+  return r;
+}
+
+// cosine of a latitude: the binary64 value c0 - s0 E as a float32 pair, and the float32
+// relative correction of the E^2 and E^3 terms
 struct Cos64 {
-  double t;
-  float tf, eps;
+  float h, l, eps;
 };
 
 __device__ __forceinline__ Cos64 cos64(double lat, const CosEntry* __restrict__ tab) {
   int k = __float2int_rn(leading_f32(lat) * 100.0f);
   k = max(-9000, min(9000, k));
   const double2* p = reinterpret_cast<const double2*>(tab + (k + 9000));
-  const double2 t0 = __ldg(p), t1 = __ldg(p + 1);  // {lat0, cos}, {sin * pi/180, -}
+  const double2 t0 = __ldg(p), t1 = __ldg(p + 1);  // {lat0, cos}, {sin * pi/180, float32 copies}
   const double e = lat - t0.x;                      // degrees
+  const F2 c2 = split_f64(fma(-t1.x, e, t0.y));
   Cos64 c;
-  c.t = fma(-t1.x, e, t0.y);
-  c.tf = leading_f32(c.t);
+  c.h = c2.h;
+  c.l = c2.l;
+  const unsigned long long cs = dbits(t1.y);  // {cos, sin * pi/180} rounded to float32
+  const float c0f = __uint_as_float((uint32_t)cs), s0rf = __uint_as_float((uint32_t)(cs >> 32));
   const float ef = leading_f32(e), E = ef * kRadF;
   // -c0 E^2/2 + s0 E^3/6 = E^2 (s0r e / 6 - c0 / 2), relative to the value
-  c.eps = E * E * fmaf(leading_f32(t1.x) * ef, 1.0f / 6.0f, -0.5f * leading_f32(t0.y)) / c.tf;
+  c.eps = __fdividef(E * E * fmaf(s0rf * ef, 1.0f / 6.0f, -0.5f * c0f), c.h);
   return c;
 }
 
@@ -239,36 +297,51 @@ __device__ __forceinline__ bool tiny_deg(double x) {
   return (dbits(x) & 0x7FFFFFFFFFFFFFFFull) < 0x3F977318FC504817ull;  // 0.0229
 }
 
+// A binary64 distance with its float32 rounding (the implied speed's input).
+struct D64 {
+  double d;
+  float f;
+  __device__ D64(int = 0) : d(0.0), f(0.0f) {}
+  __device__ D64(double x, float xf) : d(x), f(xf) {}
+  __device__ explicit operator double() const { return d; }
+};
+
 __device__ __forceinline__ float to_f32(double x) { return f64_to_f32_rn(x); }
 __device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(const D64& x) { return x.f; }
 
-__device__ __forceinline__ double haversine64(double la1, double lo1, const Cos64& c1, double la2,
+__device__ __forceinline__ D64 haversine64(double la1, double lo1, const Cos64& c1, double la2,
                                               double lo2, const Cos64& c2, const GridParams& g) {
   const double dp = la2 - la1, dl = lo2 - lo1;  // exact for nearby points
   if (tiny_deg(dp) && tiny_deg(dl)) {
-    const double u = dp * dp, v = dl * dl;
-    const double C = c1.t * c2.t;
-    const double m = fma(C, v, u);
-    if (__double_as_longlong(m) == 0) return 0.0;
-    const float mf = leading_f32(m);
-    if (mf > 0.0f) {
-      const double s0 = m * f32_to_f64(rsqrtf(mf));
-      const double r = fma(-s0, s0, m);
-      const float dpf = leading_f32(dp), dlf = leading_f32(dl);
-      const float uf = dpf * dpf, vf = dlf * dlf, Cvf = c1.tf * c2.tf * vf;
-      const float inv_m = 1.0f / mf;
+    const F2 dpp = split_f64(dp), dlp = split_f64(dl);
+    const F2 u = f2_sq(dpp), v = f2_sq(dlp);
+    const F2 C = f2_mul(F2{c1.h, c1.l}, F2{c2.h, c2.l});
+    const F2 m = f2_norm(f2_add_pos(u, f2_mul(C, v)));
+    const float mf = m.h;
+    if (mf >= 1e-30f) {
+      const float s = __fsqrt_rn(mf);
+      const float t = __fmul_rn(s, s), te = fmaf(s, s, -t);  // s^2 = t + te
+      const float r = __fadd_rn(__fsub_rn(mf, t), __fsub_rn(m.l, te));  // m - s^2 (mf - t exact)
+      const float uf = u.h, vf = v.h, Cvf = c1.h * c2.h * vf;
+      const float inv_m = __frcp_rn(mf);
       const float q = (kK2F / 3.0f) * fmaf(Cvf, vf, uf * uf) * inv_m;
       const float eC = Cvf * (c1.eps + c2.eps) * inv_m;
       const float hf = kK2F * mf;
-      const float p = leading_f32(r) * inv_m;
+      const float p = r * inv_m;
       const float ds = p * fmaf(0.375f, p, 0.5f);
       const float dr = fmaf(0.5f, eC - q, hf * fmaf(hf, 0.075f, 1.0f / 6.0f));
       const float delta = fmaf(ds, dr, ds + dr);
-      const double Ks = g.dist_k * s0;
-      return fma(Ks, f32_to_f64(delta), Ks);
+      const float dh = __fmul_rn(g.dist_kh, s);
+      float dlo = fmaf(g.dist_kl, s, fmaf(g.dist_kh, s, -dh));
+      dlo = fmaf(dh, delta, dlo);
+      // exact: the pair spans under 53 bits; its float32 rounding is that of the sum
+      return D64((double)dh + (double)dlo, __fadd_rn(dh, dlo));
     }
+    if (((dbits(dp) | dbits(dl)) << 1) == 0) return D64();
   }
-  return haversine_m(la1, lo1, la2, lo2, g.radius_m);
+  const double x = haversine_m(la1, lo1, la2, lo2, g.radius_m);
+  return D64(x, f64_to_f32_rn(x));
 }
 
 // ---------------------------------------------------------------- CTA-wide radix sort
@@ -524,14 +597,14 @@ __device__ __forceinline__ float haversine_f32(double la1, double lo1, float c1,
 
 struct Fp64Form {
   typedef Cos64 Cos;
-  typedef double Dist;
+  typedef D64 Dist;
   // the per-point rates (implied speed, acceleration) are float32 quotients, correctly rounded
   static __device__ __forceinline__ float div(float a, float b) { return a / b; }
   static __device__ __forceinline__ Cos64 cosine(double lat, const GridParams& g) {
     return cos64(lat, g.cos_tab);
   }
-  static __device__ __forceinline__ double distance(double la1, double lo1, const Cos64& c1, double la2,
-                                                    double lo2, const Cos64& c2, const GridParams& g) {
+  static __device__ __forceinline__ D64 distance(double la1, double lo1, const Cos64& c1, double la2,
+                                                 double lo2, const Cos64& c2, const GridParams& g) {
     return haversine64(la1, lo1, c1, la2, lo2, c2, g);
   }
   // A lane's distance sum in 128-bit fixed point (units of 2^-64 m), off the binary64 pipe: each
@@ -540,6 +613,7 @@ struct Fp64Form {
   // below 2^63 m.
   struct Acc {
     unsigned long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(const D64& x) { add(x.d); }
     __device__ __forceinline__ void add(double d) {
       const unsigned long long b = dbits(d);
       const int e = (int)((b >> 52) & 0x7FFull);
@@ -1416,16 +1490,16 @@ __device__ __forceinline__ RunAgg agg_then(const RunAgg& a, const RunAgg& b) {  
 // Shuffles of the per-point cosine of the two forms.
 __device__ __forceinline__ Cos64 shfl_cos(const Cos64& c, int src) {
   Cos64 r;
-  r.t = __shfl_sync(0xffffffffu, c.t, src);
-  r.tf = __shfl_sync(0xffffffffu, c.tf, src);
+  r.h = __shfl_sync(0xffffffffu, c.h, src);
+  r.l = __shfl_sync(0xffffffffu, c.l, src);
   r.eps = __shfl_sync(0xffffffffu, c.eps, src);
   return r;
 }
 __device__ __forceinline__ float shfl_cos(float c, int src) { return __shfl_sync(0xffffffffu, c, src); }
 __device__ __forceinline__ Cos64 shfl_up_cos(const Cos64& c, int d) {
   Cos64 r;
-  r.t = __shfl_up_sync(0xffffffffu, c.t, d);
-  r.tf = __shfl_up_sync(0xffffffffu, c.tf, d);
+  r.h = __shfl_up_sync(0xffffffffu, c.h, d);
+  r.l = __shfl_up_sync(0xffffffffu, c.l, d);
   r.eps = __shfl_up_sync(0xffffffffu, c.eps, d);
   return r;
 }

@@ -26,6 +26,7 @@ struct GridParams {
   const CosEntry* cos_tab;  // k = -9000..9000
   double asin_c1, asin_c2, asin_c3;  // 2R, 2R/6, 2R*3/40: d = sqrt(h) (c1 + h (c2 + h c3))
   double dist_k;                     // 2R pi/360: distance per degree of sqrt(m) (binary64 series)
+  float dist_kh, dist_kl;            // dist_k as a float32 pair (the leading float, the rest)
 };
 
 // ---------------------------------------------------------------- keying (Algorithm 2)
