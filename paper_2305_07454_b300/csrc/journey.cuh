@@ -351,6 +351,7 @@ __device__ __forceinline__ D64 haversine64(double la1, double lo1, const Cos64& 
 // (one ballot per digit bit) and their count below the lane, as the device-wide sort does; multi-tile passes add a digit histogram and carry running offsets
 // from tile to tile in order, which keeps the sort stable.
 constexpr int kRTile = 16 * kJBlock;  // keys ranked per tile: 16 per thread
+constexpr int kBucketLoads = 8;        // keys or timestamps a thread reads at once in a counting pass
 
 struct SortSmem {
   uint16_t wcnt[kJBlock / 32][256];
@@ -379,7 +380,14 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
     if (!one_tile) {
       sm.run[tid] = 0;
       __syncthreads();
-      for (int i = tid; i < n; i += kJBlock) atomicAdd(&sm.run[(uint32_t)(A[i] >> shift) & 255u], 1u);
+      for (int i0 = tid; i0 < n; i0 += kJBlock * kBucketLoads) {  // keys read kBucketLoads at a time
+        unsigned long long a[kBucketLoads];
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u) a[u] = i0 + u * kJBlock < n ? A[i0 + u * kJBlock] : 0ull;
+#pragma unroll
+        for (int u = 0; u < kBucketLoads; ++u)
+          if (i0 + u * kJBlock < n) atomicAdd(&sm.run[(uint32_t)(a[u] >> shift) & 255u], 1u);
+      }
       __syncthreads();
       uint32_t v = sm.run[tid];
       uint32_t e = block_excl_scan<kJBlock>(v, sm.scan, nullptr);
@@ -444,7 +452,7 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
 }
 
 // Counting sort of a journey's keys by a monotone time bucket, then insertion sort inside each
-// bucket. Timestamps of a journey are spread almost evenly over its span (regular sampling),
+// bucket (up to four keys: loaded together and put in order by a five-step network). Timestamps of a journey are spread almost evenly over its span (regular sampling),
 // so with about one bucket per point the buckets hold a few keys each and the sort is O(n).
 // bucket(t) = min(nb - 1, floor(float(t) * nb / (span + 1))) is non-decreasing in t, so the
 // buckets' concatenation is in key order once each bucket is sorted. Returns false when some
@@ -466,6 +474,12 @@ __device__ __forceinline__ unsigned long long rec_key(const Rec* __restrict__ R,
   return ((((unsigned long long)R[i].ts ^ kSign64) - tmin) << pos_bits) | (unsigned long long)i;
 }
 
+__device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b) {
+  const unsigned long long x = min(a, b), y = max(a, b);
+  a = x;
+  b = y;
+}
+
 template <int NT>
 __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long long tmin, int pos_bits,
                                     unsigned long long* B, int n, unsigned long long span,
@@ -475,9 +489,17 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
   const bool narrow = span <= 0xFFFFFFFFull;
   for (int i = tid; i < nb; i += NT) cnt[i] = 0;
   __syncthreads();
-  for (int i = tid; i < n; i += NT) {
-    const int b = time_bucket(rec_key(R, i, tmin, pos_bits) >> pos_bits, narrow, scale, nb);
-    atomicAdd(&cnt[b], 1u);
+  // the records' timestamps are read kBucketLoads at a time (independent loads in flight)
+  for (int i0 = tid; i0 < n; i0 += NT * kBucketLoads) {
+    unsigned long long t[kBucketLoads];
+#pragma unroll
+    for (int u = 0; u < kBucketLoads; ++u) {
+      const int i = i0 + u * NT;
+      t[u] = i < n ? (unsigned long long)R[i].ts : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBucketLoads; ++u)
+      if (i0 + u * NT < n) atomicAdd(&cnt[time_bucket((t[u] ^ kSign64) - tmin, narrow, scale, nb)], 1u);
   }
   __syncthreads();
   const int chunk = (nb + NT - 1) / NT;
@@ -497,14 +519,40 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
   }
   __syncthreads();
   if (*flag) return false;
-  for (int i = tid; i < n; i += NT) {
-    const unsigned long long k = rec_key(R, i, tmin, pos_bits);
-    const int b = time_bucket(k >> pos_bits, narrow, scale, nb);
-    B[atomicAdd(&cnt[b], 1u)] = k;
+  for (int i0 = tid; i0 < n; i0 += NT * kBucketLoads) {
+    unsigned long long t[kBucketLoads];
+#pragma unroll
+    for (int u = 0; u < kBucketLoads; ++u) {
+      const int i = i0 + u * NT;
+      t[u] = i < n ? (unsigned long long)R[i].ts : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kBucketLoads; ++u) {
+      const int i = i0 + u * NT;
+      if (i < n) {
+        const unsigned long long d = (t[u] ^ kSign64) - tmin;
+        B[atomicAdd(&cnt[time_bucket(d, narrow, scale, nb)], 1u)] = (d << pos_bits) | (unsigned long long)i;
+      }
+    }
   }
   __syncthreads();
   for (int b = tid; b < nb; b += NT) {
     const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
+    if (hi - lo <= 1) continue;
+    if (hi - lo <= 4) {  // up to four keys: loaded together, sorted in registers
+      unsigned long long v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = lo + q < hi ? B[lo + q] : ~0ull;
+      cswap(v[0], v[1]);
+      cswap(v[2], v[3]);
+      cswap(v[0], v[2]);
+      cswap(v[1], v[3]);
+      cswap(v[1], v[2]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (lo + q < hi) B[lo + q] = v[q];
+      continue;
+    }
     for (int i = lo + 1; i < hi; ++i) {
       const unsigned long long v = B[i];
       int q = i - 1;
@@ -526,7 +574,7 @@ __device__ void fix_ties(unsigned long long* K, int n, int pos_bits, const Rec* 
   const unsigned long long mask = (1ull << pos_bits) - 1;
   for (int k = threadIdx.x; k < n; k += NT) {
     const unsigned long long t = K[k] >> pos_bits;
-    const bool lead = (k == 0 || (K[k - 1] >> pos_bits) != t) && (k + 1 < n && (K[k + 1] >> pos_bits) == t);
+    const bool lead = (k + 1 < n && (K[k + 1] >> pos_bits) == t) && (k == 0 || (K[k - 1] >> pos_bits) != t);
     if (lead) {
       int e = k + 1;
       while (e < n && (K[e] >> pos_bits) == t) ++e;
@@ -1038,15 +1086,15 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
       run.mx = __int_as_float((int)0xFF800000u);
       in_pre = true;
     }
-    // the next record is loaded one point ahead, so its latency overlaps this point's work
+    // the next record is loaded one point ahead and the position of the one after it two, so
+    // that neither load waits on the other within an iteration
     uint32_t nxt_p = keyed ? (uint32_t)(sortedK[k0] & pmask) : sortedE[k0].pos;
     Rec nxt = R[nxt_p];
+    if (k0 + 1 < k1) nxt_p = keyed ? (uint32_t)(sortedK[k0 + 1] & pmask) : sortedE[k0 + 1].pos;
     for (int k = k0; k < k1; ++k) {
       const Rec cur = nxt;
-      if (k + 1 < k1) {
-        nxt_p = keyed ? (uint32_t)(sortedK[k + 1] & pmask) : sortedE[k + 1].pos;
-        nxt = R[nxt_p];
-      }
+      if (k + 1 < k1) nxt = R[nxt_p];
+      if (k + 2 < k1) nxt_p = keyed ? (uint32_t)(sortedK[k + 2] & pmask) : sortedE[k + 2].pos;
       const typename Form::Cos ccur = Form::cosine(cur.lat, g);
       const uint32_t key = point_key(cur.lat, cur.lon, cur.ts, g, bi);
       uint8_t fl = 0;
