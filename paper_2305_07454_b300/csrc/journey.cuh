@@ -452,7 +452,8 @@ __device__ unsigned long long* cta_radix_sort(unsigned long long* A, unsigned lo
 }
 
 // Counting sort of a journey's keys by a monotone time bucket, then insertion sort inside each
-// bucket (up to four keys: loaded together and put in order by a five-step network). Timestamps of a journey are spread almost evenly over its span (regular sampling),
+// bucket (up to four or eight keys: loaded together and put in order by a 5- or 19-step
+// network), equal timestamps (always in one bucket) ordered by extracted-row index. Timestamps of a journey are spread almost evenly over its span (regular sampling),
 // so with about one bucket per point the buckets hold a few keys each and the sort is O(n).
 // bucket(t) = min(nb - 1, floor(float(t) * nb / (span + 1))) is non-decreasing in t, so the
 // buckets' concatenation is in key order once each bucket is sorted. Returns false when some
@@ -536,6 +537,9 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
     }
   }
   __syncthreads();
+  // Each bucket in key order, then equal timestamps (which share a bucket) by extracted-row
+  // index, as fix_ties does for the other sorts.
+  const unsigned long long pmask = (1ull << pos_bits) - 1;
   for (int b = tid; b < nb; b += NT) {
     const int lo = b ? (int)cnt[b - 1] : 0, hi = (int)cnt[b];
     if (hi - lo <= 1) continue;
@@ -548,11 +552,67 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
       cswap(v[0], v[2]);
       cswap(v[1], v[3]);
       cswap(v[1], v[2]);
+      bool tie = false;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) tie |= lo + q + 1 < hi && (v[q] >> pos_bits) == (v[q + 1] >> pos_bits);
+      if (tie) {  // odd-even transposition by (timestamp, row index)
+        uint32_t x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = lo + q < hi ? R[v[q] & pmask].idx : 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = r & 1; q < 3; q += 2)
+            if ((v[q] >> pos_bits) == (v[q + 1] >> pos_bits) && x[q] > x[q + 1]) {
+              const unsigned long long tv = v[q];
+              v[q] = v[q + 1];
+              v[q + 1] = tv;
+              const uint32_t tx = x[q];
+              x[q] = x[q + 1];
+              x[q + 1] = tx;
+            }
+      }
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (lo + q < hi) B[lo + q] = v[q];
       continue;
     }
+    if (hi - lo <= 8) {  // up to eight keys: Batcher's 19-step network in registers
+      unsigned long long v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = lo + q < hi ? B[lo + q] : ~0ull;
+      cswap(v[0], v[1]); cswap(v[2], v[3]); cswap(v[4], v[5]); cswap(v[6], v[7]);
+      cswap(v[0], v[2]); cswap(v[1], v[3]); cswap(v[4], v[6]); cswap(v[5], v[7]);
+      cswap(v[1], v[2]); cswap(v[5], v[6]);
+      cswap(v[0], v[4]); cswap(v[1], v[5]); cswap(v[2], v[6]); cswap(v[3], v[7]);
+      cswap(v[2], v[4]); cswap(v[3], v[5]);
+      cswap(v[1], v[2]); cswap(v[3], v[4]); cswap(v[5], v[6]);
+      bool tie = false;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) tie |= lo + q + 1 < hi && (v[q] >> pos_bits) == (v[q + 1] >> pos_bits);
+      if (tie) {  // odd-even transposition by (timestamp, row index)
+        uint32_t x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = lo + q < hi ? R[v[q] & pmask].idx : 0xFFFFFFFFu;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int q = r & 1; q < 7; q += 2)
+            if ((v[q] >> pos_bits) == (v[q + 1] >> pos_bits) && x[q] > x[q + 1]) {
+              const unsigned long long tv = v[q];
+              v[q] = v[q + 1];
+              v[q + 1] = tv;
+              const uint32_t tx = x[q];
+              x[q] = x[q + 1];
+              x[q + 1] = tx;
+            }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (lo + q < hi) B[lo + q] = v[q];
+      continue;
+    }
+    bool tie = false;
     for (int i = lo + 1; i < hi; ++i) {
       const unsigned long long v = B[i];
       int q = i - 1;
@@ -561,6 +621,19 @@ __device__ bool cta_bucket_sort_rec(const Rec* __restrict__ R, unsigned long lon
         --q;
       }
       B[q + 1] = v;
+    }
+    for (int i = lo + 1; i < hi; ++i) tie |= (B[i - 1] >> pos_bits) == (B[i] >> pos_bits);
+    if (tie) {  // insertion by (timestamp, row index)
+      for (int i = lo + 1; i < hi; ++i) {
+        const unsigned long long v = B[i];
+        const uint32_t vi = R[v & pmask].idx;
+        int q = i - 1;
+        while (q >= lo && (B[q] >> pos_bits) == (v >> pos_bits) && R[B[q] & pmask].idx > vi) {
+          B[q + 1] = B[q];
+          --q;
+        }
+        B[q + 1] = v;
+      }
     }
   }
   __syncthreads();
@@ -977,9 +1050,11 @@ __device__ __forceinline__ JSorted journey_sort(const Rec* __restrict__ R, int n
                           : reinterpret_cast<uint32_t*>(smem_raw);
     const int nb = small ? max(1, n) : min(n, kBucketsBig);
     unsigned long long* K = nullptr;
+    bool ties_done = false;  // the time-bucket sort orders equal timestamps by row index itself
     if (n <= kBucketsBig * 8 &&
         cta_bucket_sort_rec<NT>(R, tmin, pos_bits, KB, n, s_tmax - tmin, cnt, nb, ssort.scan, &s_flag)) {
       K = KB;
+      ties_done = true;
     } else if constexpr (NT == kJBlock) {
       unsigned long long* GA = reinterpret_cast<unsigned long long*>(scrA + off);
       unsigned long long* GB = reinterpret_cast<unsigned long long*>(scrB + off);
@@ -990,7 +1065,7 @@ __device__ __forceinline__ JSorted journey_sort(const Rec* __restrict__ R, int n
       keyed = false;
     }
     if (keyed) {
-      fix_ties<NT>(K, n, pos_bits, R);
+      if (!ties_done) fix_ties<NT>(K, n, pos_bits, R);
       sortedK = K;
     }
   }
