@@ -181,12 +181,25 @@ __global__ void k_lattice_fold(const unsigned long long* __restrict__ skey, cons
     uint32_t vol = 0;
     double sum = 0.0;
     unsigned long long prev_rank = ~0ull;
-    for (uint32_t e = e0; e < e1; ++e) {
-      const float sp = __uint_as_float(sspd[e]);
-      sum += f32_to_f64_exact(((__float_as_uint(sp) & 0x7FFFFFFFu) == 0) ? 0.0f : sp);
-      const unsigned long long rk = skey[e] & rmask;
-      vol += (rk != prev_rank) ? 1u : 0u;
-      prev_rank = rk;
+    // the cell's entries four at a time: the loads first (independent), then the sum in order
+    for (uint32_t e4 = e0; e4 < e1; e4 += 4) {
+      uint32_t sv[4];
+      unsigned long long kv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = e4 + u < e1;
+        sv[u] = in ? sspd[e4 + u] : 0u;
+        kv[u] = in ? skey[e4 + u] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (e4 + u >= e1) break;
+        const float sp = __uint_as_float(sv[u]);
+        sum += f32_to_f64_exact(((sv[u] & 0x7FFFFFFFu) == 0) ? 0.0f : sp);
+        const unsigned long long rk = kv[u] & rmask;
+        vol += (rk != prev_rank) ? 1u : 0u;
+        prev_rank = rk;
+      }
     }
     const uint32_t cnt = e1 - e0;
     const uint32_t key = (uint32_t)lk, cells = (uint32_t)n_rows * (uint32_t)n_cols;
