@@ -455,10 +455,11 @@ cvetl_status cvetl_server_destroy(cvetl_server* s);
 const char* cvetl_server_last_error(const cvetl_server* s);
 
 /* Binary64 issue-rate probe (a measurement aid with no counterpart in the paper: the FP64 form
- * of the journey kernel is bound by the binary64 pipe, whose rate this measures). Launches
+ * of the journey kernels runs part of its per-point arithmetic on the binary64 pipe, whose rate
+ * this measures). Launches
  * `blocks` CTAs of `threads` (64, 128 or 256) threads on `stream`, each thread running 8
  * independent chains of `iters` iterations of one binary64 operation kind: 0 fma, 1 add,
- * 2 multiply, 3 the journey kernel's per-point mix (4 adds, 5 multiplies, 4 fma). sink: device
+ * 2 multiply, 3 a mix of 4 adds, 5 multiplies and 4 fma. sink: device
  * memory for blocks * threads doubles (caller-owned; receives the chains' sums). *ops (may be
  * NULL) receives the binary64 operations the launch performs. The call only enqueues: the
  * caller times it with events on the stream. CVETL_EINVAL on a bad argument, CVETL_ECUDA on a

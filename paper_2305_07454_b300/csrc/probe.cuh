@@ -1,6 +1,7 @@
-// probe.cuh — binary64 issue-rate probe: the measured roof of the FP64 form's journey kernel,
-// whose per-point work is bound by the binary64 pipe (a part with about 2 binary64 operations
-// per clock per SM). Every thread runs kChains independent dependency chains of one operation
+// probe.cuh — binary64 issue-rate probe: the measured rate of the binary64 pipe (a part with
+// about 2 binary64 operations per clock per SM), the roof of the FP64 form's journey kernels
+// for the binary64 operations they keep (the coordinate differences, the cosines and the
+// distance's final sum). Every thread runs kChains independent dependency chains of one operation
 // kind, enough to keep the pipe's latency covered at a few warps per scheduler; the caller times
 // the launch with CUDA events on its stream. Intrinsics with explicit rounding keep the compiler
 // from fusing the mix's multiplies and adds into fma.
