@@ -1838,22 +1838,25 @@ cvetl_status cvetl_lattice_build(cvetl_ctx* c, const cvetl_lattice_config* lc, c
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(&dropped, ctr, 8, cudaMemcpyDeviceToHost));
   const uint32_t m = (uint32_t)((uint64_t)c->n_valid - dropped);
-  uint32_t *head, *cidx, *total, *chan;
-  ENSURE("lat.head", (size_t)m, &head);
-  ENSURE("lat.idx", (size_t)m, &cidx);
+  // cell starts: the segment heads counted per tile, the tile counts scanned, the heads' positions
+  // written in order (the keys read twice, no per-key flag or index arrays)
+  const uint32_t ntl = (m + kLatTile - 1) / kLatTile;
+  uint32_t *tcnt, *toff, *total, *chan;
+  ENSURE("lat.tcnt", (size_t)ntl + 1, &tcnt);
+  ENSURE("lat.toff", (size_t)ntl + 1, &toff);
   ENSURE("lat.total", 1, &total);
   ENSURE("lat.chan", 16, &chan);
   CK(cudaMemsetAsync(chan, 0xFF, 32, c->st));
   CK(cudaMemsetAsync(chan + 8, 0, 32, c->st));
   if (m) {
-    LAUNCH(ST_LATTICE, (k_lattice_heads<<<grid_for(m, 256), 256, 0, c->st>>>(skey, m, lp.rank_bits, head)));
+    LAUNCH(ST_LATTICE, (k_lattice_tile_heads<<<ntl, 256, 0, c->st>>>(skey, m, lp.rank_bits, tcnt)));
     LAUNCH_CHECK();
   }
-  if ((s = scan_u32(c, head, m, cidx, total)) != CVETL_OK) return s;
+  if ((s = scan_u32(c, tcnt, ntl, toff, total)) != CVETL_OK) return s;
   uint32_t* start;
   ENSURE("lat.start", (size_t)m + 1, &start);
   if (m) {
-    LAUNCH(ST_LATTICE, (k_lattice_starts<<<grid_for(m, 256), 256, 0, c->st>>>(head, cidx, m, total, start)));
+    LAUNCH(ST_LATTICE, (k_lattice_tile_starts<<<ntl, 256, 0, c->st>>>(skey, m, lp.rank_bits, toff, total, start)));
     LAUNCH_CHECK();
   }
   LatticeOut& lo = c->lattice;

@@ -118,10 +118,61 @@ __global__ void __launch_bounds__(256) k_lattice_keys(const uint32_t* __restrict
   if (threadIdx.x == 0 && s) atomicAdd(n_dropped, s);
 }
 
-__global__ void k_lattice_heads(const unsigned long long* __restrict__ skey, uint32_t m, int rank_bits,
-                                uint32_t* __restrict__ head) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    head[i] = (i == 0 || (skey[i] >> rank_bits) != (skey[i - 1] >> rank_bits)) ? 1u : 0u;
+// Segment heads of the sorted keys (a key whose cell differs from its predecessor's) counted
+// per tile of kLatTile keys: thread t of the block takes keys [16t, 16t + 16) of its tile.
+constexpr int kLatPer = 16;
+constexpr int kLatTile = 256 * kLatPer;
+
+__device__ __forceinline__ uint32_t lat_heads(const unsigned long long* __restrict__ skey, uint32_t m,
+                                              int rank_bits, uint32_t i0, uint32_t& mask) {
+  unsigned long long prev = i0 ? (skey[i0 - 1] >> rank_bits) : ~0ull;
+  mask = 0;
+  if (i0 + kLatPer <= m) {  // 16 keys in four 32-byte loads
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(skey + i0);
+#pragma unroll
+    for (int v = 0; v < kLatPer / 2; ++v) {
+      const ulonglong2 kk = __ldg(p + v);
+      const unsigned long long a = kk.x >> rank_bits, b = kk.y >> rank_bits;
+      mask |= (i0 + 2 * v == 0 || a != prev ? 1u : 0u) << (2 * v);
+      mask |= (b != a ? 1u : 0u) << (2 * v + 1);
+      prev = b;
+    }
+  } else {
+    for (int u = 0; u < kLatPer && i0 + u < m; ++u) {
+      const unsigned long long a = skey[i0 + u] >> rank_bits;
+      mask |= (i0 + u == 0 || a != prev ? 1u : 0u) << u;
+      prev = a;
+    }
+  }
+  return (uint32_t)__popc(mask);
+}
+
+__global__ void __launch_bounds__(256) k_lattice_tile_heads(const unsigned long long* __restrict__ skey, uint32_t m,
+                                                            int rank_bits, uint32_t* __restrict__ tile_cnt) {
+  __shared__ uint32_t scratch[8];
+  const uint32_t i0 = blockIdx.x * kLatTile + threadIdx.x * kLatPer;
+  uint32_t mask, c = 0;
+  if (i0 < m) c = lat_heads(skey, m, rank_bits, i0, mask);
+  const uint32_t tot = block_sum<256, uint32_t>(c, scratch);
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+// Cell starts: the q-th segment head's position at start[q], and start[K] = m. The tile's heads
+// are numbered from its offset (the exclusive scan of the tile counts) in key order.
+__global__ void __launch_bounds__(256) k_lattice_tile_starts(const unsigned long long* __restrict__ skey, uint32_t m,
+                                                             int rank_bits, const uint32_t* __restrict__ tile_off,
+                                                             const uint32_t* __restrict__ K,
+                                                             uint32_t* __restrict__ start) {
+  __shared__ uint32_t scratch[256 / 32 + 1];
+  const uint32_t i0 = blockIdx.x * kLatTile + threadIdx.x * kLatPer;
+  uint32_t mask = 0, c = 0;
+  if (i0 < m) c = lat_heads(skey, m, rank_bits, i0, mask);
+  uint32_t o = tile_off[blockIdx.x] + block_excl_scan<256>(c, scratch, nullptr);
+  while (mask) {
+    start[o++] = i0 + (uint32_t)(__ffs(mask) - 1);
+    mask &= mask - 1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[*K] = m;
 }
 
 struct LatticeOut {
@@ -140,14 +191,6 @@ __device__ __forceinline__ uint32_t ord_f32(float x) {
 }
 __device__ __forceinline__ float from_ord_f32(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u ^ 0x80000000u) : ~u);
-}
-
-// Cell starts: start[cidx[i]] = i for every segment head i, and start[K] = m.
-__global__ void k_lattice_starts(const uint32_t* __restrict__ head, const uint32_t* __restrict__ cidx, uint32_t m,
-                                 const uint32_t* __restrict__ K, uint32_t* __restrict__ start) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-    if (head[i]) start[cidx[i]] = i;
-  if (blockIdx.x == 0 && threadIdx.x == 0) start[*K] = m;
 }
 
 // Sort keys of the cells by length, longest first (ties by cell).
