@@ -1595,14 +1595,13 @@ __global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journe
   }
 }
 
-// Runs of equal keys inside one warp's iteration: count, compensated speed sum, min, max.
+// Runs of equal keys inside one warp's iteration: compensated speed sum, min, max (a run's
+// count follows from its first and last positions).
 struct RunAgg {
-  uint32_t cnt;
   float s, c, mn, mx;
 };
 __device__ __forceinline__ RunAgg agg_then(const RunAgg& a, const RunAgg& b) {  // a before b
   RunAgg r;
-  r.cnt = a.cnt + b.cnt;
   r.s = a.s;
   r.c = a.c;
   fsum_add(r.s, r.c, b.s);
@@ -1663,7 +1662,6 @@ __device__ __forceinline__ RunAgg warp_agg(RunAgg a) {
 #pragma unroll
   for (int o2 = 16; o2 > 0; o2 >>= 1) {
     RunAgg q;
-    q.cnt = __shfl_down_sync(0xffffffffu, a.cnt, o2);
     q.s = __shfl_down_sync(0xffffffffu, a.s, o2);
     q.c = __shfl_down_sync(0xffffffffu, a.c, o2);
     q.mn = __shfl_down_sync(0xffffffffu, a.mn, o2);
@@ -1674,10 +1672,9 @@ __device__ __forceinline__ RunAgg warp_agg(RunAgg a) {
 }
 
 __device__ __forceinline__ RunAgg agg_empty() {
-  return RunAgg{0u, 0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
+  return RunAgg{0.f, 0.f, __int_as_float(0x7F800000), __int_as_float((int)0xFF800000u)};
 }
 __device__ __forceinline__ void agg_add(RunAgg& a, float v) {
-  a.cnt += 1;
   fsum_add(a.s, a.c, v);
   a.mn = fminf(a.mn, v);
   a.mx = fmaxf(a.mx, v);
@@ -1685,14 +1682,14 @@ __device__ __forceinline__ void agg_add(RunAgg& a, float v) {
 
 // Stages one closed run (lane 0 of the warp writes it) and flushes the warp's buffer when full.
 __device__ __forceinline__ void walk_put(RunSlot* buf, uint32_t& nbuf, const JourneyOut& o, DevState* st,
-                                         uint32_t key, uint32_t start, const RunAgg& a) {
+                                         uint32_t key, uint32_t start, uint32_t cnt, const RunAgg& a) {
   if (nbuf == (uint32_t)kWalkRunCap) walk_flush(buf, nbuf, o, st);
   if ((threadIdx.x & 31) == 0) {
     RunSlot& q = buf[nbuf];
     q.s = a.s;
     q.c = a.c;
     q.key = key;
-    q.cnt = a.cnt;
+    q.cnt = cnt;
     q.start = start;
     q.mn = a.mn;
     q.mx = a.mx;
@@ -1824,8 +1821,8 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
       int h = __ffs(hmask) - 1;
       if (valid && lane < h) agg_add(la, spd);
       const RunAgg r = warp_agg(la);
-      const uint32_t r_cnt = __shfl_sync(0xffffffffu, r.cnt, 0);
-      if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r);
+      const uint32_t r_cnt = off + (uint32_t)(base + h) - o_start;
+      if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r_cnt, r);
       // runs that start and end inside this iteration, one warp reduction each
       hmask &= hmask - 1;
       while (hmask) {
@@ -1834,7 +1831,7 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
         RunAgg a = agg_empty();
         if (lane >= h && lane < h2) agg_add(a, spd);
         const RunAgg r2 = warp_agg(a);
-        if (kh != kKeyInvalid) walk_put(rbuf, nbuf, o, st, kh, off + (uint32_t)(base + h), r2);
+        if (kh != kKeyInvalid) walk_put(rbuf, nbuf, o, st, kh, off + (uint32_t)(base + h), (uint32_t)(h2 - h), r2);
         h = h2;
         hmask &= hmask - 1;
       }
@@ -1855,8 +1852,8 @@ __device__ __forceinline__ void walk_journey(uint32_t j, const Rec* __restrict__
   // the run open at the journey's end
   {
     const RunAgg r = warp_agg(la);
-    const uint32_t r_cnt = __shfl_sync(0xffffffffu, r.cnt, 0);
-    if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r);
+    const uint32_t r_cnt = off + (uint32_t)n - o_start;
+    if (o_key != kKeyInvalid && r_cnt > 0) walk_put(rbuf, nbuf, o, st, o_key, o_start, r_cnt, r);
   }
   // journey sums: each lane's own sum, then a fixed shuffle tree
   const double sd = dist.warp_total();
