@@ -220,23 +220,23 @@ def fp64_probe(stream, reps=3):
 # scaled by records to the workload (the full day is too large to capture under the profiler's
 # size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "hash_count": 31.193, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.569,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.926, "journey_sort": 29.541,
-    "journeys": 5.082, "journey_walk": 86.197, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.185, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.569,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.934, "journey_sort": 29.533,
+    "journeys": 4.645, "journey_walk": 86.186, "cell_heads": 0.214, "cell_write": 1.073,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.656, "csv_parse": 97.55,
+    "csv_count": 58.666, "csv_parse": 97.545,
 }
 TRAFFIC_PER_RECORD_FP32 = {
-    "hash_count": 31.184, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.568,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.94, "journey_sort": 29.536,
-    "journeys": 5.058, "journey_walk": 86.621, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.182, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.568,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.93, "journey_sort": 29.565,
+    "journeys": 4.97, "journey_walk": 86.709, "cell_heads": 0.214, "cell_write": 1.073,
 }
 
 
 # The kernel sources the traffic figures above were captured with: sha256 over the files of
 # paper_2305_07454_b300/csrc (name and bytes, in name order). When the sources differ, the
 # figures describe other kernels: the line then reports no traffic and no gate figure.
-TRAFFIC_SOURCES_SHA256 = "af767f820944cb4a576934e8c349cf2bafdf4528f106b9748c9d2432fde77aed"
+TRAFFIC_SOURCES_SHA256 = "dd93630f75a8c3fe607c863067f9c7f804aa2adc97696f19ea3a88863ccc1af0"
 
 
 def kernel_sources_sha256() -> str:
