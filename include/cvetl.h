@@ -282,11 +282,13 @@ typedef struct {
                               2, 4 (default) or 8 */
   int32_t small_sort_max;  /* sorts of up to this many pairs run in one thread block (0..4096,
                               default 4096), larger ones device-wide */
-  int32_t row_block;       /* threads per block of the counting pass and the scatter: 128, 256
-                              (default) or 512 */
+  int32_t row_block;       /* threads per block of the counting pass (and of the scatter of
+                              unaligned columns): 128, 256 (default) or 512 */
   int32_t small_journey_max; /* journeys of up to this many points (0..512, default 512) take
                                 64-thread CTAs of a second journey kernel, the rest the 256-thread
                                 one; 0: every journey takes a 256-thread CTA */
+  int32_t scatter_block;   /* threads per block of the scatter of aligned columns (16 consecutive
+                              rows per thread): 128 (default), 256 or 512 */
 } cvetl_tuning;
 
 cvetl_status cvetl_tuning_get(cvetl_ctx* ctx, cvetl_tuning* out);
@@ -296,7 +298,7 @@ cvetl_status cvetl_tuning_set(cvetl_ctx* ctx, const cvetl_tuning* t);
 /* Autotuner (batch-mode contexts). Times cvetl_transform + cvetl_load on the extracted rows
  * with CUDA events for candidate shapes: each field in turn over its candidates (journey_ctas
  * 0..3, row_unroll 2/4/8, small_sort_max 0/1024/2048/4096, row_block 128/256/512,
- * small_journey_max 0/128/256/512) with the others fixed, the median of
+ * small_journey_max 0/128/256/512, scatter_block 128/256/512) with the others fixed, the median of
  * `reps` timed runs (1..10) after one untimed run per candidate, a candidate kept only when at
  * least 2% faster. The context keeps the fastest shapes; *out (may be NULL) receives them and
  * *ms_best (may be NULL) their median time. Needs a preceding cvetl_extract or

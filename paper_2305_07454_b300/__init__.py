@@ -92,7 +92,7 @@ GRID_KEYS = ("lat_min", "lon_min", "n_rows", "n_cols", "t0_ms")
 class Tuning(ctypes.Structure):
     _fields_ = [("journey_ctas", ctypes.c_int32), ("row_unroll", ctypes.c_int32),
                 ("small_sort_max", ctypes.c_int32), ("row_block", ctypes.c_int32),
-                ("small_journey_max", ctypes.c_int32)]
+                ("small_journey_max", ctypes.c_int32), ("scatter_block", ctypes.c_int32)]
 
 
 DXN_CARDINAL, DXN_QUADRANT = 0, 1

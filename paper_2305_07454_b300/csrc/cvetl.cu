@@ -111,9 +111,10 @@ struct cvetl_ctx {
   struct {
     int journey_ctas = 0;      // persistent journey CTAs per SM (1..3); 0: one CTA per journey
     int row_unroll = 4;        // rows per thread per iteration of the counting pass and the scatter
-    int row_block = 256;       // threads per block of the counting pass and the scatter
+    int row_block = 256;       // threads per block of the counting pass (and the unaligned scatter)
     int small_sort_max = 4096;  // pairs up to which one block sorts (0..kCtaSortMax)
     int small_journey_max = 512;  // journeys of up to this many points take 64-thread CTAs (0: none)
+    int scatter_block = 128;   // threads per block of the 16-row scatter (aligned columns)
   } tune;
   // CUDA graphs of the batch path after sizing (config.graph), one per shape
   struct GraphKey {
@@ -1022,7 +1023,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
   const bool groups = !c->bt.cols && al(c->ts, 32) && al(c->lat, 32) && al(c->lon, 32) && al(c->spd, 16) &&
                       al(row_slot, 16);
   if (n && groups) {
-    const int NT = c->tune.row_block;
+    const int NT = c->tune.scatter_block;
     const size_t ng = (size_t)n / kScatterRows > 0 ? (size_t)n / kScatterRows : 1;
 #define SCATR(NT_) k_scatter_rows<NT_, kScatterRows><<<grid_for(ng, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
     c->ts, c->lat, c->lon, c->spd, row_slot, n, h, rec)
@@ -1032,7 +1033,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
 #undef SCATR
     LAUNCH_CHECK();
   } else if (n && c->bt.cols && c->batch_aligned && c->batch_groups) {  // a batch read in place, aligned
-    const int NT = c->tune.row_block;
+    const int NT = c->tune.scatter_block;
     const uint32_t G = (uint32_t)c->batch_groups;
 #define SCATG(NT_) k_scatter_groups<NT_, kScatterRows><<<grid_for(G, NT_, 2048 / NT_), NT_, 0, c->st>>>( \
     row_slot, n, G, c->bt, h, rec)
@@ -1235,7 +1236,7 @@ cvetl_status run_graph(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsigned
   k.precision = c->cfg.precision;
   k.materialize = c->cfg.materialize_points;
   k.t0 = c->tune.journey_ctas;
-  k.t1 = c->tune.row_unroll * 1024 + c->tune.row_block;
+  k.t1 = (c->tune.row_unroll * 1024 + c->tune.row_block) * 1024 + c->tune.scatter_block;
   k.t2 = c->tune.small_sort_max * 1024 + c->tune.small_journey_max;
   k.id_bits = c->id_bits;
   k.aligned = c->bt.cols && c->batch_aligned ? 1 : 0;
@@ -1677,6 +1678,7 @@ cvetl_status cvetl_tuning_get(cvetl_ctx* c, cvetl_tuning* out) {
   out->row_block = c->tune.row_block;
   out->small_sort_max = c->tune.small_sort_max;
   out->small_journey_max = c->tune.small_journey_max;
+  out->scatter_block = c->tune.scatter_block;
   return CVETL_OK;
 }
 
@@ -1692,11 +1694,14 @@ cvetl_status cvetl_tuning_set(cvetl_ctx* c, const cvetl_tuning* t) {
     return fail(c, CVETL_EINVAL, "small_sort_max must be in [0, %u]", kCtaSortMax);
   if (t->small_journey_max < 0 || t->small_journey_max > kJSmallMax)
     return fail(c, CVETL_EINVAL, "small_journey_max must be in [0, %d]", kJSmallMax);
+  if (t->scatter_block != 128 && t->scatter_block != 256 && t->scatter_block != 512)
+    return fail(c, CVETL_EINVAL, "scatter_block must be 128, 256 or 512");
   c->tune.journey_ctas = t->journey_ctas;
   c->tune.row_unroll = t->row_unroll;
   c->tune.row_block = t->row_block;
   c->tune.small_sort_max = t->small_sort_max;
   c->tune.small_journey_max = t->small_journey_max;
+  c->tune.scatter_block = t->scatter_block;
   return CVETL_OK;
 }
 
@@ -1749,15 +1754,15 @@ cvetl_status cvetl_autotune(cvetl_ctx* c, int32_t reps, cvetl_tuning* out, doubl
   if ((st = measure(&best_ms)) == CVETL_OK) {
     const int ctas[] = {0, 1, 2, 3}, unroll[] = {2, 4, 8}, smax[] = {0, 1024, 2048, 4096}, block[] = {128, 256, 512},
               jmax[] = {0, 128, 256, 512};
-    const int* cands[] = {ctas, unroll, smax, block, jmax};
-    const int ncand[] = {4, 3, 4, 3, 4};
-    for (int field = 0; field < 5 && st == CVETL_OK; ++field) {
+    const int* cands[] = {ctas, unroll, smax, block, jmax, block};
+    const int ncand[] = {4, 3, 4, 3, 4, 3};
+    for (int field = 0; field < 6 && st == CVETL_OK; ++field) {
       const int* cand = cands[field];
       const int nc = ncand[field];
       for (int k = 0; k < nc && st == CVETL_OK; ++k) {
         auto t = best;
         int& f = field == 0 ? t.journey_ctas : field == 1 ? t.row_unroll : field == 2 ? t.small_sort_max
-                 : field == 3 ? t.row_block : t.small_journey_max;
+                 : field == 3 ? t.row_block : field == 4 ? t.small_journey_max : t.scatter_block;
         if (f == cand[k]) continue;
         f = cand[k];
         c->tune = t;

@@ -1,4 +1,4 @@
-"""Launch shapes (persistent or per-journey CTAs, rows per thread, one-block sort limit) change
+"""Launch shapes (persistent or per-journey CTAs, rows per thread, block sizes, one-block sort limit) change
 where the work runs, never a result bit; the autotuner picks valid shapes and leaves the context
 ready for transform and load."""
 import pytest
@@ -8,12 +8,12 @@ from test_gpu_batch import make, on_device
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [dict(journey_ctas=0, row_unroll=4, small_sort_max=2048, row_block=256, small_journey_max=0),
-          dict(journey_ctas=1, row_unroll=2, small_sort_max=0, row_block=128, small_journey_max=512),
-          dict(journey_ctas=3, row_unroll=8, small_sort_max=512, row_block=512, small_journey_max=128),
-          dict(journey_ctas=2, row_unroll=4, small_sort_max=1024, row_block=128, small_journey_max=0),
-          dict(journey_ctas=0, row_unroll=4, small_sort_max=2048, row_block=256, small_journey_max=256),
-          dict(journey_ctas=0, row_unroll=4, small_sort_max=4096, row_block=256, small_journey_max=512)]
+SHAPES = [dict(journey_ctas=0, row_unroll=4, small_sort_max=2048, row_block=256, small_journey_max=0, scatter_block=128),
+          dict(journey_ctas=1, row_unroll=2, small_sort_max=0, row_block=128, small_journey_max=512, scatter_block=256),
+          dict(journey_ctas=3, row_unroll=8, small_sort_max=512, row_block=512, small_journey_max=128, scatter_block=512),
+          dict(journey_ctas=2, row_unroll=4, small_sort_max=1024, row_block=128, small_journey_max=0, scatter_block=128),
+          dict(journey_ctas=0, row_unroll=4, small_sort_max=2048, row_block=256, small_journey_max=256, scatter_block=512),
+          dict(journey_ctas=0, row_unroll=4, small_sort_max=4096, row_block=256, small_journey_max=512, scatter_block=256)]
 
 
 def tables(p, insts):
@@ -56,7 +56,7 @@ def test_autotune_picks_valid_shapes_and_leaves_the_context_extracted():
         t = p.autotune(reps=1)
         assert t["journey_ctas"] in (0, 1, 2, 3) and t["row_unroll"] in (2, 4, 8)
         assert t["small_sort_max"] in (0, 512, 1024, 2048, 4096) and t["row_block"] in (128, 256, 512) and t["ms"] > 0
-        assert t["small_journey_max"] in (0, 128, 256, 512)
+        assert t["small_journey_max"] in (0, 128, 256, 512) and t["scatter_block"] in (128, 256, 512)
         assert {k: v for k, v in t.items() if k != "ms"} == p.tuning
         p.transform()
         p.load()
@@ -74,7 +74,8 @@ def test_bad_shapes_are_rejected():
     with P.Pipeline() as p:
         before = p.tuning
         for bad in (dict(journey_ctas=4), dict(row_unroll=3), dict(small_sort_max=4097), dict(journey_ctas=-1),
-                    dict(row_block=64), dict(small_journey_max=513), dict(small_journey_max=-1)):
+                    dict(row_block=64), dict(small_journey_max=513), dict(small_journey_max=-1),
+                    dict(scatter_block=1024)):
             with pytest.raises(P.CvetlError) as e:
                 p.tuning = bad
             assert e.value.status == P.EINVAL
