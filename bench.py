@@ -220,23 +220,23 @@ def fp64_probe(stream, reps=3):
 # scaled by records to the workload (the full day is too large to capture under the profiler's
 # size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "hash_count": 31.185, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.569,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.934, "journey_sort": 29.533,
-    "journeys": 4.645, "journey_walk": 86.186, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.179, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.569,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.98, "journey_sort": 29.561,
+    "journeys": 4.901, "journey_walk": 86.116, "cell_heads": 0.214, "cell_write": 1.073,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.666, "csv_parse": 97.545,
+    "csv_count": 58.663, "csv_parse": 97.551,
 }
 TRAFFIC_PER_RECORD_FP32 = {
-    "hash_count": 31.182, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.568,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.93, "journey_sort": 29.565,
-    "journeys": 4.97, "journey_walk": 86.709, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.183, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.568,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.981, "journey_sort": 29.532,
+    "journeys": 4.981, "journey_walk": 86.677, "cell_heads": 0.214, "cell_write": 1.074,
 }
 
 
 # The kernel sources the traffic figures above were captured with: sha256 over the files of
 # paper_2305_07454_b300/csrc (name and bytes, in name order). When the sources differ, the
 # figures describe other kernels: the line then reports no traffic and no gate figure.
-TRAFFIC_SOURCES_SHA256 = "dd93630f75a8c3fe607c863067f9c7f804aa2adc97696f19ea3a88863ccc1af0"
+TRAFFIC_SOURCES_SHA256 = "9fb9a8bad793142e7b928277408dac5d68a8e3b2336e28b165b086e2c21cc16d"
 
 
 def kernel_sources_sha256() -> str:
