@@ -1504,9 +1504,11 @@ __device__ __forceinline__ void block_range(unsigned long long lo, unsigned long
 
 // The staged order of the journey's bucket R[0..n) into the u16 positions P (at 8 * CAP bytes
 // into the dynamic shared memory, valid until the CTA's next use of it); false when a time
-// bucket is crowded. Every thread of the CTA calls it; ends with a barrier.
+// bucket is crowded. Once its timestamps are read, the nn records at Rn (the CTA's next
+// journey, or none) are prefetched into L2, so that its own load finds them there. Every thread
+// of the CTA calls it; ends with a barrier.
 template <int NT, int CAP>
-__device__ bool staged_journey_order(const Rec* __restrict__ R, int n) {
+__device__ bool staged_journey_order(const Rec* __restrict__ R, int n, const Rec* Rn = nullptr, int nn = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* T = reinterpret_cast<unsigned long long*>(smem_raw);
   uint16_t* P = reinterpret_cast<uint16_t*>(smem_raw + 8 * CAP);
@@ -1528,6 +1530,9 @@ __device__ bool staged_journey_order(const Rec* __restrict__ R, int n) {
     lo = min(lo, t);
     hi = max(hi, t);
   }
+  // the next journey's records into L2 (one prefetch per 128-byte line) while this one sorts
+  for (int i = tid; i < (nn + 3) / 4; i += NT)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(Rn + 4 * i));
   __syncthreads();
   block_range(lo, hi, &s_tmin, &s_tmax);
   return staged_order<NT>(T, n, s_tmin, s_tmax, P, cnt, s_scan, &s_flag, [R](int k) { return R[k].idx; });
@@ -1560,8 +1565,9 @@ __global__ void k_size_classes(const uint32_t* __restrict__ jn, const uint32_t* 
 }
 
 // One size class of the journey sort, persistent: CTAs take the class's journeys in list order
-// through its work counter: the staged sort, falling back to the general sort when a time bucket
-// is crowded. (Journeys above 8192 points take the fused journey kernel.)
+// through its work counter, each claim one journey ahead of the one sorted (whose records are
+// prefetched into L2 meanwhile): the staged sort, falling back to the general sort when a time
+// bucket is crowded. (Journeys above 8192 points take the fused journey kernel.)
 template <int NT, int CAP>
 __host__ __device__ constexpr int sort_class_min_blocks() { return NT == 64 ? 12 : (CAP > 4096 ? 2 : 3); }
 
@@ -1572,19 +1578,33 @@ __global__ void __launch_bounds__(NT, sort_class_min_blocks<NT, CAP>()) k_journe
                                                            const uint32_t* __restrict__ bounds, int cls,
                                                            uint32_t* work, Elem* scrA, Elem* scrB,
                                                            uint16_t* __restrict__ spos, DevState* st) {
-  __shared__ uint32_t s_w;
+  __shared__ uint32_t s_w, s_wn;
   const uint32_t w0 = bounds[cls], w1 = bounds[cls + 1];
+  uint32_t wc = 0;
+  if (threadIdx.x == 0) wc = w0 + atomicAdd(work, 1u);
   for (;;) {
-    if (threadIdx.x == 0) s_w = w0 + atomicAdd(work, 1u);
+    // the next journey is claimed one ahead, so that its records can be fetched during this one
+    if (threadIdx.x == 0) {
+      s_w = wc;
+      s_wn = wc < w1 ? w0 + atomicAdd(work, 1u) : w1;
+      wc = s_wn;
+    }
     __syncthreads();
-    const uint32_t w = s_w;
+    const uint32_t w = s_w, wn = s_wn;
     __syncthreads();
     if (w >= w1) break;
     const uint32_t j = order[w];
     const int n = (int)jn[j];
     const uint32_t off = joff[j];
     const Rec* R = rec + off;
-    if (staged_journey_order<NT, CAP>(R, n)) {
+    const Rec* Rn = nullptr;
+    int nn = 0;
+    if (wn < w1) {
+      const uint32_t jn2 = order[wn];
+      Rn = rec + joff[jn2];
+      nn = (int)jn[jn2];
+    }
+    if (staged_journey_order<NT, CAP>(R, n, Rn, nn)) {
       const uint16_t* P = staged_positions<CAP>();
       for (int k = threadIdx.x; k < n; k += NT) spos[off + k] = P[k];
     } else {

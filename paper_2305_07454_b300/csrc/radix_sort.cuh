@@ -113,7 +113,9 @@ __device__ __forceinline__ uint32_t look_back(const uint32_t* status, uint32_t t
 // from device memory and the grid covers the upper bound n; tiles are numbered in the order the
 // CTAs start, so a tile that starts past the count returns at once (no tile holding keys looks
 // back at it).
-// A tile first counts its warps' digits (the digit's lanes found by ballots, the lowest of them
+// A tile loads its keys, prefetches into L2 those of the tile one wave of resident CTAs later
+// (numbered 3 per SM past its own: the tile that starts about when this one finishes), then
+// counts its warps' digits (the digit's lanes found by ballots, the lowest of them
 // adding their number), publishes its counts, looks back for the earlier tiles' totals, then
 // ranks its keys in input order, warp by warp (i-major, lane-minor, their global order, so the
 // pass is stable), writes them to their tile positions in shared memory and copies the tile
@@ -155,6 +157,20 @@ __global__ void __launch_bounds__(kBlock, 3) k_onesweep(const K* __restrict__ ki
     bool ok = idx < n;
     key[i] = ok ? kin[idx] : ~K(0);
     val[i] = ok ? (vin ? vin[idx] : idx) : 0u;
+  }
+  {
+    // the tile one wave of resident CTAs ahead (3 per SM) into L2 while this one ranks: one
+    // prefetch per 128-byte line, inside the arrays
+    uint32_t nsm;
+    asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+    const unsigned long long b2 = (unsigned long long)(tile + 3u * nsm) * kTile;
+    if (b2 < n) {
+      const uint32_t m2 = min((unsigned long long)kTile, n - b2);
+      const uint32_t kl = (m2 * (uint32_t)sizeof(K) + 127u) / 128u;
+      if ((uint32_t)tid < kl) asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)(kin + b2) + 128u * tid));
+      const uint32_t vl = vin ? (m2 * 4u + 127u) / 128u : 0u;
+      if ((uint32_t)tid < vl) asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)(vin + b2) + 128u * tid));
+    }
   }
   // the warps' digit counts
 #pragma unroll
