@@ -220,23 +220,23 @@ def fp64_probe(stream, reps=3):
 # scaled by records to the workload (the full day is too large to capture under the profiler's
 # size rule). A stage's entry is only valid while its kernels are the ones captured.
 TRAFFIC_PER_RECORD = {
-    "hash_count": 31.181, "collect_slots": 0.144, "radix_histogram": 0.225, "radix_onesweep": 2.563,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.985, "journey_sort": 30.097,
-    "journeys": 5.11, "journey_walk": 86.295, "cell_heads": 0.214, "cell_write": 1.073,
+    "hash_count": 31.183, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.563,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.987, "journey_sort": 30.096,
+    "journeys": 5.048, "journey_walk": 86.278, "cell_heads": 0.214, "cell_write": 1.073,
     # CSV input adds (per kept record of the CSV day)
-    "csv_count": 58.675, "csv_parse": 97.541,
+    "csv_count": 58.654, "csv_parse": 97.572,
 }
 TRAFFIC_PER_RECORD_FP32 = {
-    "hash_count": 31.18, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.566,
-    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.981, "journey_sort": 30.085,
-    "journeys": 5.041, "journey_walk": 86.926, "cell_heads": 0.214, "cell_write": 1.074,
+    "hash_count": 31.181, "collect_slots": 0.144, "radix_histogram": 0.224, "radix_onesweep": 2.565,
+    "journey_sizes": 0.044, "scan": 0.22, "journey_cursors": 0.003, "scatter": 60.985, "journey_sort": 30.119,
+    "journeys": 5.043, "journey_walk": 86.737, "cell_heads": 0.214, "cell_write": 1.073,
 }
 
 
 # The kernel sources the traffic figures above were captured with: sha256 over the files of
 # paper_2305_07454_b300/csrc (name and bytes, in name order). When the sources differ, the
 # figures describe other kernels: the line then reports no traffic and no gate figure.
-TRAFFIC_SOURCES_SHA256 = "656bad4639da4bc92913031307ff14dd80ebb1668291885cc5f648ab979273a3"
+TRAFFIC_SOURCES_SHA256 = "6131ae99dabbc1197068a5aac2eb1df811f4306e6b125ea26ea9e21fd3f996a2"
 
 
 def kernel_sources_sha256() -> str:

@@ -1125,7 +1125,7 @@ cvetl_status post_sizing(cvetl_ctx* c, const Hash& h, uint32_t* row_slot, unsign
     uint32_t *bounds, *cwork;
     ENSURE("j.bounds", 5, &bounds);
     ENSURE("j.cwork", 4, &cwork);
-    LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 32, 0, c->st>>>(jn, order, J, bounds, cwork)));
+    LAUNCH(ST_JOURNEY_SORT, (k_size_classes<<<1, 96, 0, c->st>>>(jn, order, J, bounds, cwork)));
     LAUNCH_CHECK();
     static const int occ[4] = {
         0, occupancy(k_journey_sort_class<kSortBlockB, 8192>, kSortBlockB, kSortSmemB),

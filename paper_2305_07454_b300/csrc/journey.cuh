@@ -1090,7 +1090,7 @@ __device__ __forceinline__ void journey_one(uint32_t j, const Rec* __restrict__ 
                                             DevState* st,
                                             const uint32_t* __restrict__ jslot, const JState& js) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kCap = JShape<NT>::kCap, kRunBuf = JShape<NT>::kRunBuf;
+  constexpr int kRunBuf = JShape<NT>::kRunBuf;
   __shared__ double red_d[NT / 32];
   __shared__ long long red_i[3][NT / 32];
   __shared__ int64_t s_first_ts, s_last_ts;
@@ -1545,23 +1545,41 @@ __device__ __forceinline__ const uint16_t* staged_positions() {
 
 // Journey size classes over the work list (sizes non-increasing along it): bounds[c] is the
 // first list position of class c, bounds[4] = J; classes: above 8192 points, 4097-8192,
-// 513-4096, up to 512. One thread.
+// 513-4096, up to 512. One warp per class boundary (96 threads): a 32-way search, each round
+// probing 32 evenly spaced positions of the range that holds the boundary and keeping the part
+// between the last probe below the class limit's side and the first at or under it (about
+// four rounds of two dependent loads for 60,000 journeys, against 16 for a binary search).
 __device__ __forceinline__ uint32_t sort_class_max(int c) { return c == 0 ? 8192u : (c == 1 ? 4096u : 512u); }
 __global__ void k_size_classes(const uint32_t* __restrict__ jn, const uint32_t* __restrict__ order, uint32_t J,
                                uint32_t* __restrict__ bounds, uint32_t* __restrict__ work) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  bounds[0] = 0;
-  bounds[4] = J;
-  for (int c = 0; c < 3; ++c) {
-    uint32_t lo = 0, hi = J;  // first w with jn[order[w]] <= sort_class_max(c)
-    while (lo < hi) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (jn[order[mid]] <= sort_class_max(c)) hi = mid;
-      else lo = mid + 1;
-    }
-    bounds[c + 1] = lo;
+  if (blockIdx.x != 0) return;
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    bounds[0] = 0;
+    bounds[4] = J;
   }
-  for (int c = 0; c < 4; ++c) work[c] = 0;
+  if (threadIdx.x < 4) work[threadIdx.x] = 0;
+  if (c >= 3) return;
+  const uint32_t lim = sort_class_max(c);
+  // the first w with jn[order[w]] <= lim lies in [lo, hi] (hi = J: none)
+  uint32_t lo = 0, hi = J;
+  while (lo < hi) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    // the last lane probes hi - 1
+    const uint32_t q = (uint32_t)min((unsigned long long)lo + (unsigned long long)(lane + 1) * step - 1,
+                                     (unsigned long long)hi - 1);
+    const uint32_t under = __ballot_sync(0xffffffffu, jn[order[q]] <= lim);
+    if (under == 0) {
+      lo = hi;  // every position below hi is above the limit
+    } else {
+      const int f = __ffs(under) - 1;
+      const uint32_t qf = __shfl_sync(0xffffffffu, q, f);
+      const uint32_t qp = __shfl_sync(0xffffffffu, q, f > 0 ? f - 1 : 0);
+      hi = qf;
+      if (f > 0) lo = qp + 1;
+    }
+  }
+  if (lane == 0) bounds[c + 1] = lo;
 }
 
 // One size class of the journey sort, persistent: CTAs take the class's journeys in list order
